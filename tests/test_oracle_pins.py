@@ -1,0 +1,541 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+closed forms, textbook values, library routines, symmetries and invariants
+of the method (arXiv:2211.12243 §2.3).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+from scipy.spatial import cKDTree
+
+from paper_2211_12243_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# kernel (§2.3.2): unit normalisation and compact support
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", ["wendland", "cubic"])
+@pytest.mark.parametrize("H", [1.0, 0.37, 2.5])
+def test_kernel_unit_integral(orc, kernel, H):
+    f = lambda r: 4.0 * math.pi * r * r * float(orc.kernel_W(r, H, kernel))
+    val, err = integrate.quad(f, 0.0, H, epsabs=1e-14, epsrel=1e-13, points=[0.5 * H])
+    assert abs(val - 1.0) < 1e-12
+
+
+def test_kernel_central_values_and_support(orc):
+    # Wendland C2: W(0,H) = 21/(2 pi H^3); cubic M4: 8/(pi H^3)
+    assert float(orc.kernel_W(0.0, 1.0, "wendland")) == pytest.approx(21 / (2 * math.pi), rel=1e-15)
+    assert float(orc.kernel_W(0.0, 2.0, "cubic")) == pytest.approx(8 / (math.pi * 8), rel=1e-15)
+    for k in ("wendland", "cubic"):
+        assert float(orc.kernel_W(1.0, 1.0, k)) == 0.0
+        assert float(orc.kernel_W(1.3, 1.0, k)) == 0.0
+        # continuity of the cubic spline at q = 1/2
+    a = float(orc.kernel_W(0.5 - 1e-12, 1.0, "cubic"))
+    b = float(orc.kernel_W(0.5 + 1e-12, 1.0, "cubic"))
+    assert abs(a - b) < 1e-10
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "cubic"])
+def test_kernel_dWdH_matches_difference_quotient(orc, kernel):
+    for r in (0.05, 0.3, 0.49, 0.51, 0.8, 0.97):
+        H, e = 1.0, 1e-6
+        fd = (float(orc.kernel_W(r, H + e, kernel)) - float(orc.kernel_W(r, H - e, kernel))) / (2 * e)
+        assert float(orc.kernel_dWdH(r, H, kernel)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# neighbour search (§2.2.3): brute force, the cell grid and scipy agree
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [(1.0, 1.0, 1.0), (4.0, 1.0, 1.0), (1.0, 2.0, 0.5)])
+def test_neighbours_match_kdtree_and_brute_force(orc, L):
+    rng = np.random.default_rng(7)
+    n = 1500
+    L = np.array(L)
+    pos = rng.random((n, 3)) * L
+    hs = rng.uniform(0.05, 0.2, n) * L.min()
+    off_b, idx_b = orc.neighbours(pos[:, 0], pos[:, 1], pos[:, 2], L, hs, use_grid=False)
+    off_g, idx_g = orc.neighbours(pos[:, 0], pos[:, 1], pos[:, 2], L, hs, use_grid=True)
+    assert np.array_equal(off_b, off_g) and np.array_equal(idx_b, idx_g)
+    tree = cKDTree(pos, boxsize=L)
+    for i in range(n):
+        ref = sorted(tree.query_ball_point(pos[i], hs[i]))
+        got = idx_b[off_b[i]:off_b[i + 1]].tolist()
+        assert got == ref
+        assert i in got  # self included
+
+
+# --------------------------------------------------------------------------
+# density and smoothing length (§2.3.2, §2.3.5 Eq. 18)
+# --------------------------------------------------------------------------
+def _lattice_shells(rmax):
+    """(distance/a, multiplicity) of simple-cubic lattice shells below rmax*a."""
+    k = int(math.ceil(rmax)) + 1
+    g = np.arange(-k, k + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    r2 = (X * X + Y * Y + Z * Z).ravel()
+    vals, counts = np.unique(r2, return_counts=True)
+    keep = np.sqrt(vals) < rmax
+    return np.sqrt(vals[keep]), counts[keep]
+
+
+def test_density_on_perfect_lattice_matches_shell_sum(orc):
+    # perfect lattice: h solves (4 pi/3) h^3 sum_shells c_s W(r_s, h) = N_NGB,
+    # computed here by counting lattice shells, independently of the search
+    n = 10
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    h, om, it, st = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])
+    assert st == 0
+    a = 1.0 / n
+    r, c = _lattice_shells(4.0)
+
+    def g(hh):
+        q = r * a / hh
+        t = np.clip(1 - q, 0, None)
+        Wsum = np.sum(c * 21 / (2 * math.pi * hh ** 3) * t ** 4 * (1 + 4 * q))
+        return 4 * math.pi / 3 * hh ** 3 * Wsum - 32.0
+
+    href = optimize.brentq(g, 1.2 * a, 3.0 * a, xtol=1e-16, rtol=1e-15)
+    assert np.allclose(h, href, rtol=1e-12, atol=0)
+    assert np.ptp(h) / href < 1e-12 and np.ptp(om) / om.mean() < 1e-12
+
+
+def test_density_partition_of_unity_volume(orc):
+    # Eq. 7 with f = 1: sum_i V_i approximates the box volume to O(h^2)
+    w = W.lattice_wave(12)
+    cfg = orc.config()
+    h, om, it, st = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])
+    assert st == 0
+    assert abs(om.sum() - 1.0) < 0.05
+
+
+def test_density_residual_and_monotone_bracket(orc):
+    # the returned h is a root: moving h by +-1e-9 relative flips the sign of
+    # (4 pi/3) h^3 n(h) - N, evaluated on an independent KD-tree neighbour set
+    w = W.lognormal(3000, seed=1, grid=16, contrast=100.0)
+    cfg = orc.config()
+    h, om, it, st = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])
+    assert st == 0 and it.max() < 40
+    pos = np.stack([w["x"], w["y"], w["z"]], 1)
+    tree = cKDTree(pos, boxsize=w["L"])
+    for i in range(0, 3000, 97):
+        for s, sign in ((1 - 1e-9, -1), (1 + 1e-9, 1)):
+            hh = h[i] * s
+            js = tree.query_ball_point(pos[i], hh)
+            d = pos[js] - pos[i]
+            d -= np.round(d / w["L"]) * w["L"]
+            q = np.linalg.norm(d, axis=1) / hh
+            t = np.clip(1 - q, 0, None)
+            val = 4 * math.pi / 3 * hh ** 3 * np.sum(21 / (2 * math.pi * hh ** 3) * t ** 4 * (1 + 4 * q)) - 32
+            assert np.sign(val) == sign
+        # omega is 1/sum_j W at the converged h (independent neighbour set)
+        js = tree.query_ball_point(pos[i], h[i])
+        d = pos[js] - pos[i]
+        d -= np.round(d / w["L"]) * w["L"]
+        q = np.linalg.norm(d, axis=1) / h[i]
+        t = np.clip(1 - q, 0, None)
+        Wsum = np.sum(21 / (2 * math.pi * h[i] ** 3) * t ** 4 * (1 + 4 * q))
+        assert om[i] == pytest.approx(1 / Wsum, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# E matrix, B = E^-1, N_cond (Eqs. 11, 19)
+# --------------------------------------------------------------------------
+def _b9(B6):
+    xx, xy, xz, yy, yz, zz = B6.T
+    return np.stack([np.stack([xx, xy, xz], -1), np.stack([xy, yy, yz], -1),
+                     np.stack([xz, yz, zz], -1)], -2)
+
+
+def test_matrices_inverse_and_isotropic_lattice(orc):
+    n = 10
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    h, om, _, _ = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    B, E = _b9(B6), _b9(E6)
+    I = np.einsum("nij,njk->nik", B, E)
+    assert np.abs(I - np.eye(3)).max() < 1e-12
+    # cubic symmetry: E proportional to I, so N_cond = 1 (§2.3.5)
+    assert np.abs(nc - 1.0).max() < 1e-12
+    # value of E_xx from lattice shells: sum_s omega W(r_s,h) * sum_{d in shell} d_x^2
+    a = 1.0 / n
+    r, c = _lattice_shells(h[0] / a)
+    # sum over a shell of d_x^2 = c_s r_s^2 a^2 / 3 by cubic symmetry
+    q = r * a / h[0]
+    t = np.clip(1 - q, 0, None)
+    Wr = 21 / (2 * math.pi * h[0] ** 3) * t ** 4 * (1 + 4 * q)
+    Exx = np.sum(om[0] * Wr * c * (r * a) ** 2 / 3.0)
+    assert E6[:, 0] == pytest.approx(Exx, rel=1e-12)
+    assert np.abs(E6[:, 1]).max() < 1e-12 * Exx
+
+
+def test_ncond_detects_planar_neighbourhood(orc):
+    # all particles in one plane z = const: E is singular -> N_cond = inf
+    n = 12
+    a = 1.0 / n
+    g = (np.arange(n) + 0.5) * a
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x, y = X.ravel(), Y.ravel()
+    z = np.full(x.size, 0.5)
+    L = np.array([1.0, 1.0, 1.0])
+    h = np.full(x.size, 3.1 * a)
+    om = np.full(x.size, a * a)
+    cfg = orc.config()
+    B6, E6, nc = orc.matrices(cfg, x, y, z, L, h, om)
+    assert np.all(~np.isfinite(nc) | (nc > 1e8))
+
+
+# --------------------------------------------------------------------------
+# gradient estimator (Eq. 10): linear exactness, quadratic on a lattice
+# --------------------------------------------------------------------------
+def _state_with_primitives(orc, cfg, w, rho, v, p):
+    h, om, _, st = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])
+    assert st == 0
+    m = rho * om
+    U = p * om / (cfg.gamma - 1.0)
+    P = v * m[:, None]
+    E = U + 0.5 * m * np.sum(v * v, 1)
+    return h, om, m, P, E, U
+
+
+def test_gradients_exact_for_linear_fields(orc):
+    w = W.lattice_wave(12, jitter=0.05)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1)
+    g = np.array([[0.3, -0.2, 0.1], [0.05, 0.02, -0.04], [-0.01, 0.03, 0.02],
+                  [0.02, 0.0, 0.01], [0.2, 0.1, -0.3]])
+    c0 = np.array([2.0, 0.1, -0.2, 0.05, 3.0])
+    f = c0 + (x - 0.5) @ g.T   # linear inside the box
+    rho, v, p = f[:, 0], f[:, 1:4], f[:, 4]
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, rho, v, p)
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    assert np.allclose(prims[0], rho, rtol=1e-13) and np.allclose(prims[4], p, rtol=1e-12)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    inner = np.all((x > h.max() + 1e-3) & (x < 1 - h.max() - 1e-3), axis=1)
+    assert inner.sum() > 50
+    assert np.abs(grad[inner] - g[None]).max() < 1e-10
+    # linear fields create no new extrema: the limiter leaves them alone
+    assert np.all(alpha[inner] == 1.0)
+
+
+def test_gradients_exact_for_quadratic_on_perfect_lattice(orc):
+    # odd moments of a cubic lattice neighbourhood vanish, so the LV estimator
+    # is exact for quadratics at lattice points (second order, §2.3.3)
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config(limiter=False)
+    x = np.stack([w["x"], w["y"], w["z"]], 1) - 0.5
+    Hq = np.array([[0.4, 0.1, -0.2], [0.1, -0.3, 0.05], [-0.2, 0.05, 0.2]])
+    f = 5.0 + 0.5 * np.einsum("ni,ij,nj->n", x, Hq, x) + x @ np.array([0.1, 0.2, 0.3])
+    v = np.zeros((x.shape[0], 3))
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, f, v, np.full(x.shape[0], 1.0))
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    inner = np.all(np.abs(x) < 0.5 - h.max() - 1e-3, axis=1)
+    exact = x @ Hq.T + np.array([0.1, 0.2, 0.3])
+    assert np.abs(grad[inner, 0] - exact[inner]).max() < 1e-10
+
+
+def test_limiter_bounds(orc):
+    # conditioned BJ: after limiting, every midpoint extrapolation stays within
+    # beta * (f_max - f_i) and beta * (f_min - f_i), beta in [1, 2]; a step
+    # function is limited (alpha < 1) next to the jump
+    w = W.lattice_wave(10, jitter=0.1)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1)
+    rho = np.where(x[:, 0] < 0.5, 1.0, 4.0)
+    p = np.where(x[:, 0] < 0.5, 1.0, 0.5)
+    v = np.zeros_like(x)
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, rho, v, p)
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    assert np.all(alpha <= 1.0) and np.all(alpha >= 0.0)
+    near = np.abs(x[:, 0] - 0.5) < 0.5 / 10
+    assert np.all(alpha[near, 0] < 1.0)
+    off, idx = orc.neighbours(w["x"], w["y"], w["z"], w["L"], h)
+    for i in range(0, x.shape[0], 37):
+        js = idx[off[i]:off[i + 1]]
+        d = x[js] - x[i]
+        d -= np.round(d) * 1.0
+        for f in range(5):
+            vals = prims[f][js]
+            fmax, fmin = vals.max(), vals.min()
+            ext = 0.5 * d @ (alpha[i, f] * grad[i, f])
+            assert ext.max() <= 2.0 * (fmax - prims[f][i]) + 1e-12
+            assert ext.min() >= 2.0 * (fmin - prims[f][i]) - 1e-12
+
+
+# --------------------------------------------------------------------------
+# Riemann solvers (§2.3.3): Toro's tables, jump conditions, invariants
+# --------------------------------------------------------------------------
+def _toro_rows():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "toro_2009_table_4_2.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        a, b, c = line.split("|")
+        rows.append((list(map(float, a.split())), list(map(float, b.split())), float(c)))
+    return rows
+
+
+def _star_densities(orc, d, g, ps, us):
+    rl, ul, pl, rr, ur, pr = d
+    out = []
+    for eps in (-1e-9, 1e-9):
+        V = us + eps
+        out.append(orc.riemann_sample(rl, ul - V, pl, rr, ur - V, pr, g, ps, us - V)[0])
+    return out
+
+
+@pytest.mark.parametrize("row", range(5))
+def test_exact_riemann_matches_toro_table(orc, row):
+    d, star, tol = _toro_rows()[row]
+    r = orc.riemann_star(*d, 1.4)
+    assert r["vacuum"] == 0 and r["bisect"] == 0
+    assert r["p"] == pytest.approx(star[0], rel=tol)
+    assert r["u"] == pytest.approx(star[1], rel=tol, abs=1e-9)
+    rl_s, rr_s = _star_densities(orc, d, 1.4, r["p"], r["u"])
+    assert rl_s == pytest.approx(star[2], rel=tol)
+    assert rr_s == pytest.approx(star[3], rel=tol)
+
+
+@pytest.mark.parametrize("d", [(1.0, 0.0, 1.0, 0.125, 0.0, 0.1), (1.0, 0.3, 5.0, 0.2, -0.4, 0.1),
+                               (0.5, -1.0, 0.1, 2.0, 1.0, 3.0), (1.0, 0.0, 1e-6, 1.0, 0.0, 1e4)])
+@pytest.mark.parametrize("g", [1.4, 5.0 / 3.0])
+def test_exact_riemann_jump_conditions(orc, d, g):
+    """Shock side: Rankine-Hugoniot (mass, momentum, energy) with the shock
+    speed from mass conservation.  Rarefaction side: isentrope and the
+    Riemann invariant u +- 2c/(g-1)."""
+    rl, ul, pl, rr, ur, pr = d
+    r = orc.riemann_star(*d, g)
+    ps, us = r["p"], r["u"]
+    rls, rrs = _star_densities(orc, d, g, ps, us)
+    for (rk, uk, pk, rs, sgn) in ((rl, ul, pl, rls, -1), (rr, ur, pr, rrs, 1)):
+        if ps > pk:
+            S = (rs * us - rk * uk) / (rs - rk)
+            ek = pk / ((g - 1) * rk) + 0.5 * uk * uk
+            es = ps / ((g - 1) * rs) + 0.5 * us * us
+            mom_k = rk * uk * (uk - S) + pk
+            mom_s = rs * us * (us - S) + ps
+            assert mom_s == pytest.approx(mom_k, rel=1e-9, abs=1e-12 * max(pk, ps))
+            en_k = rk * ek * (uk - S) + pk * uk
+            en_s = rs * es * (us - S) + ps * us
+            assert en_s == pytest.approx(en_k, rel=1e-8, abs=1e-10 * max(pk, ps) * (abs(us) + 1))
+        else:
+            assert ps / rs ** g == pytest.approx(pk / rk ** g, rel=1e-10)
+            ck, cs = math.sqrt(g * pk / rk), math.sqrt(g * ps / rs)
+            assert us - sgn * 2 * cs / (g - 1) == pytest.approx(uk - sgn * 2 * ck / (g - 1), rel=1e-10, abs=1e-10)
+
+
+def test_exact_riemann_special_cases(orc):
+    g = 5.0 / 3.0
+    # pure contact: equal p and u, any density jump -> p* = p, u* = u
+    r = orc.riemann_star(1.0, 0.3, 2.0, 0.1, 0.3, 2.0, g)
+    assert r["p"] == pytest.approx(2.0, rel=1e-15) and r["u"] == pytest.approx(0.3, rel=1e-15)
+    # mirror-symmetric data -> u* = 0
+    r = orc.riemann_star(1.0, 0.7, 1.0, 1.0, -0.7, 1.0, g)
+    assert abs(r["u"]) < 1e-15
+    # Galilean shift of both velocities shifts u*, leaves p*
+    a = orc.riemann_star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g)
+    b = orc.riemann_star(1.0, 2.5, 1.0, 0.125, 2.5, 0.1, g)
+    assert b["p"] == pytest.approx(a["p"], rel=1e-13) and b["u"] == pytest.approx(a["u"] + 2.5, rel=1e-13)
+    # vacuum generation is flagged
+    r = orc.riemann_star(1.0, -20.0, 0.1, 1.0, 20.0, 0.1, g)
+    assert r["vacuum"] == 1
+    # the root does not depend on the starting guess
+    for p0 in (1e-8, 0.01, 0.5, 3.0, 100.0):
+        c = orc.riemann_star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g, p0=p0)
+        assert c["p"] == pytest.approx(a["p"], rel=1e-14)
+
+
+def test_hllc_consistency(orc):
+    g = 1.4
+    n = np.array([0.6, 0.8, 0.0])
+    w = np.array([0.8, -0.6, 0.5]) * 0.3
+    # identical states: HLLC returns the physical flux
+    rho, u, p = 1.3, 0.4, 2.0
+    F, ps, ss = orc.hllc(rho, u, p, w, rho, u, p, w, n, g)
+    E = p / (g - 1) + 0.5 * rho * (u * u + w @ w)
+    assert F[0] == pytest.approx(rho * u, rel=1e-14)
+    assert np.allclose(F[1:4], rho * u * (u * n + w) + p * n, rtol=1e-14)
+    assert F[4] == pytest.approx(u * (E + p), rel=1e-14)
+    # isolated contact is resolved exactly: S* = u, p* = p, upwind mass flux
+    F, ps, ss = orc.hllc(1.0, 0.2, 1.0, w, 0.1, 0.2, 1.0, -w, n, g)
+    assert ss == pytest.approx(0.2, rel=1e-14) and ps == pytest.approx(1.0, rel=1e-14)
+    assert F[0] == pytest.approx(1.0 * 0.2, rel=1e-14)
+
+
+def test_pair_limiter_bounds(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        a, b = rng.uniform(-2, 2, 2)
+        e = rng.uniform(-4, 4)
+        out = orc.pair_limit(e, a, b)
+        d = abs(a - b)
+        lo, hi = min(a, b), max(a, b)
+        # never beyond the neighbour bracket widened by psi1 d
+        assert lo - 0.5 * d - 1e-15 <= out <= hi + 0.5 * d + 1e-15
+        # never past the mean by more than psi2 d towards the far side
+        if a < b:
+            assert out <= 0.5 * (a + b) + 0.25 * d + 1e-15
+        elif a > b:
+            assert out >= 0.5 * (a + b) - 0.25 * d - 1e-15
+        # values inside [own, mean] are untouched
+        if min(a, 0.5 * (a + b)) <= e <= max(a, 0.5 * (a + b)):
+            assert out == e
+    # positive quantities stay positive
+    assert orc.pair_limit(-1.0, 0.1, 5.0, positive=True) > 0.0
+    for _ in range(500):
+        a, b = rng.uniform(1e-3, 2, 2)
+        assert orc.pair_limit(rng.uniform(-4, 4), a, b, positive=True) > 0.0
+
+
+# --------------------------------------------------------------------------
+# full step: conservation (Eq. 15), MFM masses, Galilean invariance, mirror
+# --------------------------------------------------------------------------
+def _moving(w, seed=5, amp=0.3):
+    rng = np.random.default_rng(seed)
+    n = w["x"].size
+    v = rng.normal(0, amp, (n, 3))
+    w = dict(w)
+    w["px"], w["py"], w["pz"] = w["m"] * v[:, 0], w["m"] * v[:, 1], w["m"] * v[:, 2]
+    w["E"] = w["U"] + 0.5 * w["m"] * np.sum(v * v, 1)
+    return w
+
+
+def _cons_drift(orc, cfg, w, dt):
+    s, out, info = orc.step(cfg, w, dt)
+    assert info["status"] == 0
+    v = np.stack([w["px"], w["py"], w["pz"]], 1) / w["m"][:, None]
+    cs = np.sqrt(cfg.gamma * (cfg.gamma - 1) * w["U"] / w["m"])
+    res = {}
+    res["M"] = abs(math.fsum(s["m"]) - math.fsum(w["m"])) / math.fsum(np.abs(w["m"]))
+    res["E"] = abs(math.fsum(s["E"]) - math.fsum(w["E"])) / math.fsum(np.abs(w["E"]))
+    pscale = math.fsum(w["m"] * (np.linalg.norm(v, axis=1) + cs))
+    for k in ("px", "py", "pz"):
+        res[k] = abs(math.fsum(s[k]) - math.fsum(w[k])) / pscale
+    return s, out, info, res
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+@pytest.mark.parametrize("riemann", ["exact", "hllc"])
+def test_step_conserves_mass_momentum_energy(orc, scheme, riemann):
+    w = _moving(W.lattice_wave(10, jitter=0.05))
+    cfg = orc.config(scheme=scheme, riemann=riemann)
+    s, out, info, res = _cons_drift(orc, cfg, w, dt=-1.0)
+    assert info["dt"] > 0 and info["flux"]["pairs"] > 0
+    for k, v in res.items():
+        assert v < 1e-13, (k, v)
+    if scheme == "mfm":
+        assert np.array_equal(s["m"], w["m"])   # zero mass flux, bitwise
+        assert np.all(out["dQ"][:, 0] == 0.0)
+    # the flux really moved something
+    assert np.abs(out["dQ"][:, 1:5]).max() > 0
+
+
+def test_step_sod_conserves(orc):
+    w = W.sod(8)
+    cfg = orc.config()
+    s, out, info, res = _cons_drift(orc, cfg, w, dt=-1.0)
+    for k, v in res.items():
+        assert v < 1e-13, (k, v)
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_flux_galilean_invariance(orc, scheme):
+    """Boosting every velocity by V leaves dm unchanged and transforms
+    dP -> dP + dm V, dE -> dE + dP.V + dm V^2/2 (the boost/de-boost of §2.3.3)."""
+    w = _moving(W.lattice_wave(8, jitter=0.05), amp=0.2)
+    V = np.array([0.7, -0.4, 0.25])
+    wb = dict(w)
+    wb["px"], wb["py"], wb["pz"] = w["px"] + w["m"] * V[0], w["py"] + w["m"] * V[1], w["pz"] + w["m"] * V[2]
+    wb["E"] = w["E"] + (w["px"] * V[0] + w["py"] * V[1] + w["pz"] * V[2]) + 0.5 * w["m"] * (V @ V)
+    cfg = orc.config(scheme=scheme, alpha1=0.0)
+    dt = 2e-3
+    _, o1, _ = orc.step(cfg, w, dt)
+    _, o2, _ = orc.step(cfg, wb, dt)
+    d1, d2 = o1["dQ"], o2["dQ"]
+    scale = np.abs(d1).max(0) + 1e-300
+    assert np.allclose(d2[:, 0], d1[:, 0], atol=1e-11 * scale[0] + 1e-300)
+    dP = d1[:, 1:4] + d1[:, :1] * V
+    assert np.abs(d2[:, 1:4] - dP).max() < 1e-10 * scale[1:4].max()
+    dE = d1[:, 4] + d1[:, 1:4] @ V + 0.5 * d1[:, 0] * (V @ V)
+    assert np.abs(d2[:, 4] - dE).max() < 1e-10 * scale[4]
+    # the internal-energy change (Eq. 24) is frame independent
+    assert np.abs(d2[:, 5] - d1[:, 5]).max() < 1e-10 * scale[5]
+
+
+def test_flux_mirror_symmetry(orc):
+    """Reflecting x -> L - x and v_x -> -v_x mirrors the update."""
+    w = _moving(W.lattice_wave(8, jitter=0.05), amp=0.2)
+    wm = dict(w)
+    xm = 1.0 - w["x"]
+    xm[xm >= 1.0] -= 1.0
+    wm["x"] = xm
+    wm["px"] = -w["px"]
+    cfg = orc.config()
+    dt = 2e-3
+    _, o1, _ = orc.step(cfg, w, dt)
+    _, o2, _ = orc.step(cfg, wm, dt)
+    sgn = np.array([1, -1, 1, 1, 1, 1])
+    scale = np.abs(o1["dQ"]).max(0)
+    assert np.all(np.abs(o2["dQ"] - o1["dQ"] * sgn) <= 1e-10 * scale + 1e-300)
+
+
+def test_uniform_state_is_stationary(orc):
+    # perfect lattice, uniform rho, p, v: every particle is in equilibrium;
+    # sum_j A_ij = 0 by symmetry, so the update vanishes to round-off
+    w = W.lattice_wave(8, jitter=0.0)
+    w = dict(w)
+    w["m"] = np.full(w["x"].size, 1.0 / 512)
+    w["U"] = w["m"] * 1.0 / (w["gamma"] - 1)
+    w["E"] = w["U"].copy()
+    cfg = orc.config()
+    s, out, info = orc.step(cfg, w, 1e-3)
+    assert np.abs(out["dQ"][:, 1:5]).max() < 1e-15 * 1e-3 * 10
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_sod_tube_follows_exact_solution(orc, scheme):
+    """Multi-step 3D Sod tube (§3.1.2 setup family; gamma = 5/3, rho_R = 1/8):
+    the density near the x = 2 interface approaches the exact Riemann
+    solution (pinned above by Toro's tables) far better than the frozen
+    initial state does."""
+    g = 5.0 / 3.0
+    s = W.sod(16)
+    cfg = orc.config(scheme=scheme)
+    t = 0.0
+    while t < 0.4:
+        s, out, info = orc.step(cfg, s, -1.0)
+        assert info["status"] == 0
+        t += info["dt"]
+    r = orc.riemann_star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g)
+    x = s["x"]
+    sel = (x > 1.3) & (x < 3.0)
+
+    def exact(xx):
+        out = []
+        for xi in xx:
+            c = (xi - 2.0) / t
+            rr, uu, pp, _ = orc.riemann_sample(1.0, -c, 1.0, 0.125, -c, 0.1, g, r["p"], r["u"] - c)
+            out.append((rr, uu + c, pp))
+        return np.array(out)
+
+    ex = exact(x[sel])
+    prims = orc.primitives(cfg, s["m"], s["px"], s["py"], s["pz"], s["E"], s["U"], s["omega"])
+    rho, vx, p = prims[0][sel], prims[1][sel], prims[4][sel]
+    frozen = np.stack([np.where(x[sel] < 2.0, 1.0, 0.125), np.zeros(sel.sum()),
+                       np.where(x[sel] < 2.0, 1.0, 0.1)], 1)
+    for k, f in enumerate((rho, vx, p)):
+        l1 = np.mean(np.abs(f - ex[:, k]))
+        l1_frozen = np.mean(np.abs(frozen[:, k] - ex[:, k]))
+        assert l1 < (0.6, 0.3, 0.5)[k] * l1_frozen, (k, l1, l1_frozen)
+    # transverse motion stays negligible (§3.1.2)
+    assert np.abs(prims[2][sel]).max() < 1e-2 and np.abs(prims[3][sel]).max() < 1e-2
