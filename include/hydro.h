@@ -1,0 +1,226 @@
+/*
+ * hydro.h -- C ABI of the GB300 (sm_103a) MFV/MFM hydro step.
+ *
+ * The method is the mesh-less finite-volume / finite-mass scheme of
+ * arXiv:2211.12243 ("Mesh-free hydrodynamics in pkdgrav3 for galaxy
+ * formation simulations"), §2.2.3 and §2.3: a bucketed neighbour search,
+ * kernel density and smoothing-length sums (Eqs. 5-7, 18), the
+ * Lanson-Vila gradient with its E matrix and condition-number guard
+ * (Eqs. 10-11, 19), slope limiters (§2.3.6), and per-pair Riemann fluxes
+ * through the effective face A_ij (Eq. 13 and the definition after it),
+ * scattered antisymmetrically (Eqs. 15-16) so that mass, momentum and energy
+ * are conserved by construction.
+ *
+ * Conventions that hold for every entry point:
+ *   - Every pointer argument documented as "device" is caller-owned device
+ *     memory of the context's GPU; the library never frees it.  Host pointers
+ *     are read before the call returns.
+ *   - Particle arrays are structure-of-arrays in the CALLER's order; outputs
+ *     are written in the caller's order too (the library sorts internally
+ *     and un-permutes).
+ *   - Calls are asynchronous on the given stream unless stated otherwise.
+ *     They return a hydro_status; errors detected on the device are
+ *     collected in a status word read by hydro_sync_status() (and by
+ *     hydro_step when it is given a stats pointer).  No call aborts or
+ *     throws across the ABI.
+ *   - All particles must lie in [0, L) of their periodic box.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_ctx hydro_ctx;       /* opaque: scratch, box plan, MLP */
+typedef struct CUstream_st *hydro_stream; /* a cudaStream_t (NULL = legacy default) */
+
+typedef enum {
+    HYDRO_OK = 0,
+    HYDRO_EINVAL = -1,      /* bad argument (NULL pointer, size mismatch, ...) */
+    HYDRO_ENOMEM = -2,      /* device allocation failed */
+    HYDRO_ECAPACITY = -3,   /* caller's neighbour-list buffer too small; needed set */
+    HYDRO_ENOCONV_H = -4,   /* smoothing-length iteration did not converge */
+    HYDRO_ENCOND = -5,      /* N_cond above threshold after all N_NGB growths */
+    HYDRO_ERIEMANN = -6,    /* Riemann iteration failed (after bisection) */
+    HYDRO_ENONFINITE = -7,  /* non-finite value produced or given */
+    HYDRO_ECUDA = -8,       /* CUDA runtime error */
+    HYDRO_ESTATE = -9,      /* call order violated (e.g. density before lists) */
+    HYDRO_ESEARCH = -10     /* a solved h exceeded the search radius of the lists */
+} hydro_status;
+
+enum { HYDRO_KERNEL_WENDLAND_C2 = 0, HYDRO_KERNEL_CUBIC = 1 };
+enum { HYDRO_MFV = 0, HYDRO_MFM = 1 };
+enum { HYDRO_RIEMANN_EXACT = 0, HYDRO_RIEMANN_HLLC = 1 };
+enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1 };
+
+/* Method parameters.  hydro_config_default() fills the values used by the
+ * paper where it states them (N_cond threshold 100 and growth 1.2, §2.3.5;
+ * pairwise limiter psi1 = 0.5, psi2 = 0.25, §2.3.6; alpha1 = 1/100, §2.3.7)
+ * and this library's readings elsewhere. */
+typedef struct {
+    double gamma;        /* adiabatic index */
+    int kernel;          /* HYDRO_KERNEL_*; compact support radius H = h */
+    double n_ngb;        /* N_NGB of Eq. 18 */
+    int scheme;          /* HYDRO_MFV or HYDRO_MFM (§2.3.3) */
+    int riemann;         /* HYDRO_RIEMANN_EXACT (Toro 2009) or _HLLC */
+    int precision;       /* HYDRO_FP64: every step in double.
+                            HYDRO_MIXED: pair geometry, kernel sums and fluxes in
+                            float; E^-1, h refinement and flux accumulation in
+                            double-class precision. */
+    int learned_guess;   /* 1: MLP star-pressure guess for the exact solver */
+    int limiter;         /* 1: conditioned BJ + pairwise limiters (§2.3.6) */
+    int time_extrap;     /* 1: half-step predictor of the face states (Eq. 16) */
+    double ncond_crit;   /* N_cond threshold (100) */
+    double ngb_grow;     /* N_NGB growth factor on failure (1.2) */
+    int max_ngb_grow;    /* growth rounds before HYDRO_ENCOND (5) */
+    double psi1, psi2;   /* pairwise limiter (0.5, 0.25) */
+    double beta_min, beta_max; /* conditioned BJ (1, 2) */
+    double c_cfl;        /* CFL factor of Eq. 31 (0.2) */
+    double alpha1;       /* total-energy pressure switch (1/100) */
+    double h_tol;        /* relative Newton tolerance on h (1e-10) */
+    double p_tol;        /* relative Newton tolerance on p* (1e-12 FP64) */
+    int max_h_iter;      /* cap on the h iteration (60) */
+    int max_newton;      /* cap on Riemann Newton iterations (100) */
+    double search_margin;/* hydro_step: search radius = margin * h_in (1.15) */
+} hydro_config;
+
+/* Caller-owned particle state, caller order, all device pointers, n each.
+ * Conserved variables of Eq. 2 integrated over the particle volume:
+ * mass, momentum (px, py, pz), total energy etot, internal energy eint
+ * (Eq. 24).  h: compact-support radius (in: guess, out: solved);
+ * omega: particle volume V_i = omega_i (out). */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z;
+    double *mass, *px, *py, *pz, *etot, *eint;
+    double *h, *omega;
+} hydro_particles;
+
+/* Neighbour lists in CSR form (device memory, caller order):
+ * row i = { j : r_ij < h_search_i } including j = i, ascending j.
+ * off has n+1 entries; idx has `capacity` entries.  `needed` receives the
+ * total entry count (also when it exceeds capacity, in which case nothing
+ * is written to idx and HYDRO_ECAPACITY is returned). */
+typedef struct {
+    int64_t *off;
+    int32_t *idx;
+    int64_t capacity;
+    int64_t needed;
+} hydro_nbrlist;
+
+/* Per-step diagnostics (host struct filled by hydro_step / hydro_get_stats). */
+typedef struct {
+    int status;               /* device status word of the last step */
+    double dt;                /* timestep used */
+    double dt_next;           /* CFL estimate from the start-of-step state */
+    int64_t grad_pairs;       /* directed pairs j != i, r_ij < h_i (gradient stage) */
+    int64_t flux_pairs;       /* unordered pairs r_ij < max(h_i, h_j) (flux stage) */
+    int64_t newton_iters;     /* Riemann Newton iterations summed over faces */
+    int64_t guess_fallbacks;  /* learned guesses rejected for the plain guess */
+    int64_t vacuum_faces;
+    int64_t first_order_faces;
+    int ngb_rounds;           /* N_cond growth rounds taken */
+    int64_t ncond_fail;       /* particles above the threshold at the end */
+    int list_rebuilds;        /* neighbour-list rebuilds for h beyond the radius */
+    double mass[2], mom[2][3], energy[2];   /* totals before / after the step */
+    float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
+} hydro_stats;
+
+/* Defaults described above.  Always succeeds. */
+void hydro_config_default(hydro_config *cfg);
+
+/* Create a context on the current CUDA device.  HYDRO_EINVAL on bad config. */
+int hydro_create(hydro_ctx **ctx, const hydro_config *cfg);
+void hydro_destroy(hydro_ctx *ctx);
+
+/* Replace the method parameters (the box plan and scratch are kept). */
+int hydro_set_config(hydro_ctx *ctx, const hydro_config *cfg);
+
+/* Define the independent periodic boxes the particles live in.
+ * box_off: host, nbox+1 ascending offsets with box_off[0] = 0 -- particles
+ * box_off[k] .. box_off[k+1]-1 (caller order) belong to box k (each box
+ * holds at least one particle).  box_len: host, 3*nbox lengths Lx, Ly, Lz.
+ * One box is the common case: nbox = 1, box_off = {0, n}.
+ * Plans the bucket tree topology and allocates its storage (synchronous). */
+int hydro_set_boxes(hydro_ctx *ctx, int64_t nbox, const int64_t *box_off,
+                    const double *box_len);
+
+/* Pre-allocate every per-particle scratch buffer for up to max_n particles
+ * and `nbr_per_particle` candidate entries per particle, so that later calls
+ * allocate nothing (synchronous).  Optional: calls grow scratch on demand. */
+int hydro_reserve(hydro_ctx *ctx, int64_t max_n, int nbr_per_particle);
+
+/* §2.2.3 bucketed neighbour search.  Sorts the particles along a Morton
+ * curve, cuts buckets of 32, and lists for every particle all j with
+ * r_ij < h_search_i (device, n doubles, caller order; minimum-image distance
+ * r_ij^2 = (dx^2 + dy^2) + dz^2 in double, dx folded once into
+ * [-L/2, L/2]).  The lists stay in the context for the next calls.
+ * out (optional, may be NULL): the same lists exported in caller order,
+ * rows ascending. */
+int hydro_build_neighbours(hydro_ctx *ctx, const hydro_particles *p,
+                           const double *h_search, hydro_nbrlist *out,
+                           hydro_stream stream);
+
+/* §2.3.2 / §2.3.5: solve (4 pi / 3) h_i^3 omega_i^-1 = N_NGB (Eq. 18) with
+ * omega_i^-1 = sum_j W(r_ij, h_i) (Eq. 6, self term included), starting
+ * from p->h, over the lists of the last hydro_build_neighbours.  Writes
+ * p->h and p->omega.  A root beyond the list radius is HYDRO_ESEARCH
+ * (reported through the status word). */
+int hydro_density(hydro_ctx *ctx, hydro_particles *p, hydro_stream stream);
+
+/* §2.3.3 / §2.3.6: primitives (rho = m/omega, v = P/m, p from Eq. 23 or the
+ * internal energy), E_i (Eq. 11, weight omega_j, W(r, h_i)), B_i = E_i^-1,
+ * N_cond,i (Eq. 19), the gradients of (rho, vx, vy, vz, p) (Eq. 10) and the
+ * conditioned Barth-Jespersen factors.  Outputs, device, caller order:
+ * B[6n] (xx, xy, xz, yy, yz, zz), grad[15n] (per particle: d rho/dx..dz,
+ * d vx/dx..dz, d vy, d vz, d p), alpha[5n], ncond[n]; any may be NULL.
+ * Requires p->h, p->omega (e.g. from hydro_density) and lists covering h. */
+int hydro_gradients(hydro_ctx *ctx, const hydro_particles *p, double *B, double *grad,
+                    double *alpha, double *ncond, hydro_stream stream);
+
+/* §2.3.3 / §2.3.4 / §2.3.6: for every unordered pair with
+ * r_ij < max(h_i, h_j): the face vector A_ij, extrapolated and limited face
+ * states, the Riemann problem in the frame moving with (v_i + v_j)/2, the
+ * MFV or MFM flux, and c = dt |A_ij| F scattered as dQ_i -= c, dQ_j += c.
+ * Inputs B, grad, alpha as produced by hydro_gradients (device, caller
+ * order).  dt > 0.  Output dQ[6n] (device, caller order): dm, dpx, dpy,
+ * dpz, dE, dU (dU from Eq. 24 with the start-of-step velocity). */
+int hydro_fluxes(hydro_ctx *ctx, const hydro_particles *p, const double *B,
+                 const double *grad, const double *alpha, double dt, double *dQ,
+                 hydro_stream stream);
+
+/* One full step: neighbour search with radius search_margin * h, density
+ * (re-searching when a root leaves the radius), the N_cond guard
+ * (N_NGB,i *= ngb_grow, density redone, §2.3.5), gradients, fluxes with the
+ * given dt (dt <= 0: CFL dt = min_i c_cfl h_i / v_sig,i, Eqs. 31-32),
+ * conserved update (Eq. 16), internal energy (Eq. 24) and drift
+ * x += dt (v^n + v^{n+1}) / 2 wrapped into the box.  Updates p in place.
+ * stats (host, optional): filled after a stream synchronisation. */
+int hydro_step(hydro_ctx *ctx, hydro_particles *p, double dt, hydro_stats *stats,
+               hydro_stream stream);
+
+/* Read (synchronising the stream) and clear the device status word:
+ * returns the first error recorded by any kernel since the last read. */
+int hydro_sync_status(hydro_ctx *ctx, hydro_stream stream);
+
+/* Statistics of the last hydro_step (host copy, synchronising). */
+int hydro_get_stats(hydro_ctx *ctx, hydro_stats *stats, hydro_stream stream);
+
+/* Install the weights of the star-pressure MLP (12 -> 64 -> 64 -> 1) used
+ * when cfg.learned_guess = 1.  `weights`: host, `bytes` = 4 * (12*64 + 64 +
+ * 64*64 + 64 + 64 + 1 + 24) float32 values in the order W1, b1, W2, b2, w3,
+ * b3, feature mean[12], feature scale[12] (row-major, W[out][in]). */
+int hydro_mlp_load(hydro_ctx *ctx, const void *weights, size_t bytes);
+
+/* Human-readable message for a hydro_status. */
+const char *hydro_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

@@ -95,7 +95,7 @@ def lib():
         L.orc_flux_pairs.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp]
         L.orc_fluxes.restype = None
         L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 15 + [d, i64, vp, vp, vp,
-                                 P(FluxStats), vp])
+                                 P(FluxStats), vp, vp])
         L.orc_riemann_guess.restype = d
         L.orc_riemann_guess.argtypes = [d] * 7
         L.orc_riemann_star.restype = i32
@@ -215,8 +215,9 @@ def flux_pairs(x, y, z, L, h):
 
 
 def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
-           pair_guess=None, want_faces=False):
-    """dQ[n,6] = (dm, dpx, dpy, dpz, dE, dU) of Eqs. 16 and 24; (dQ, stats, faces)."""
+           pair_guess=None, want_faces=False, want_abs=False):
+    """dQ[n,6] = (dm, dpx, dpy, dpz, dE, dU) of Eqs. 16 and 24; (dQ, stats, faces)
+    or, with want_abs, (dQ, stats, faces, dQabs[n,5] = sum over faces of |c|)."""
     x, y, z, L, h, omega, B6 = map(_f64, (x, y, z, L, h, omega, B6))
     grad, alpha = _f64(grad), _f64(alpha)
     rho, vx, vy, vz, p = map(_f64, prims)
@@ -229,9 +230,12 @@ def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
     st = FluxStats()
     faces = np.zeros((npairs, 9)) if want_faces else None
     pg = None if pair_guess is None else _f64(pair_guess)
+    dQabs = np.zeros((n, 5)) if want_abs else None
     lib().orc_fluxes(C.byref(cfg), n, _p(x), _p(y), _p(z), _p(L), _p(h), _p(omega), _p(B6),
                      _p(rho), _p(vx), _p(vy), _p(vz), _p(p), _p(grad), _p(alpha), float(dt),
-                     npairs, _p(pairs), _p(pg), _p(dQ), C.byref(st), _p(faces))
+                     npairs, _p(pairs), _p(pg), _p(dQ), C.byref(st), _p(faces), _p(dQabs))
+    if want_abs:
+        return dQ, st.as_dict(), faces, dQabs
     return dQ, st.as_dict(), faces
 
 

@@ -1106,7 +1106,7 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
                 const double *B6, const double *rho, const double *vx, const double *vy,
                 const double *vz, const double *p, const double *grad, const double *alpha,
                 double dt, int64_t npairs, const int64_t *pairs, const double *pair_guess,
-                double *dQ, orc_flux_stats *st, double *face_out)
+                double *dQ, orc_flux_stats *st, double *face_out, double *dQabs)
 {
     const double *Wp[5] = {rho, vx, vy, vz, p};
     double *cf = (double *)malloc((size_t)(npairs > 0 ? npairs : 1) * 5 * sizeof(double));
@@ -1161,6 +1161,19 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
         dQ[6 * i + 5] = dU;
     }
     free(acc);
+    /* scale of the per-particle flux error (sum over the particle's faces of
+     * |c| per component), used to normalise comparisons of dQ whose net
+     * value may cancel */
+    if (dQabs) {
+        memset(dQabs, 0, (size_t)n * 5 * sizeof(double));
+        for (int64_t k = 0; k < npairs; k++) {
+            int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+            for (int q = 0; q < 5; q++) {
+                dQabs[5 * i + q] += fabs(cf[5 * k + q]);
+                dQabs[5 * j + q] += fabs(cf[5 * k + q]);
+            }
+        }
+    }
     free(cf);
 }
 
@@ -1241,7 +1254,7 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     }
     orc_flux_stats fst;
     orc_fluxes(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, dt, np, pairs,
-               NULL, dQ, &fst, NULL);
+               NULL, dQ, &fst, NULL, NULL);
     free(pairs);
     /* directed gradient pairs */
     if (info) {

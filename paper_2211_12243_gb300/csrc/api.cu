@@ -1,0 +1,532 @@
+// C ABI of the hydro library (declared in include/hydro.h).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "hydro_internal.cuh"
+
+using namespace hyd;
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HYDRO_OK : (e == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA); }
+
+#define API_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e__ = (call);                        \
+        if (e__ != cudaSuccess) return cuda_status(e__); \
+    } while (0)
+
+int flags_to_status(int f) {
+    if (f & ST_NONFINITE) return HYDRO_ENONFINITE;
+    if (f & ST_LIST_CAPACITY) return HYDRO_ECAPACITY;
+    if (f & ST_LIST_OVERFLOW) return HYDRO_ECAPACITY;
+    if (f & ST_STACK) return HYDRO_ECAPACITY;
+    if (f & ST_SEARCH) return HYDRO_ESEARCH;
+    if (f & ST_NOCONV_H) return HYDRO_ENOCONV_H;
+    if (f & ST_RIEMANN) return HYDRO_ERIEMANN;
+    if (f & ST_NCOND) return HYDRO_ENCOND;
+    return HYDRO_OK;
+}
+
+bool valid_config(const hydro_config *c) {
+    if (!c) return false;
+    if (!(c->gamma > 1.0)) return false;
+    if (c->kernel != HYDRO_KERNEL_WENDLAND_C2 && c->kernel != HYDRO_KERNEL_CUBIC) return false;
+    double kn = c->kernel == HYDRO_KERNEL_WENDLAND_C2 ? 14.0 : 32.0 / 3.0;
+    if (!(c->n_ngb > kn)) return false;   // the self term alone must not reach N_NGB
+    if (c->scheme != HYDRO_MFV && c->scheme != HYDRO_MFM) return false;
+    if (c->riemann != HYDRO_RIEMANN_EXACT && c->riemann != HYDRO_RIEMANN_HLLC) return false;
+    if (c->precision != HYDRO_FP64 && c->precision != HYDRO_MIXED) return false;
+    if (!(c->search_margin >= 1.0)) return false;
+    if (c->max_h_iter < 1 || c->max_newton < 1 || c->max_ngb_grow < 0) return false;
+    return true;
+}
+
+bool valid_particles(const hydro_ctx *c, const hydro_particles *p, bool need_state) {
+    if (!p || p->n != c->plan.n || p->n <= 0) return false;
+    if (!p->x || !p->y || !p->z || !p->h) return false;
+    if (need_state && (!p->mass || !p->px || !p->py || !p->pz || !p->etot || !p->eint || !p->omega))
+        return false;
+    return true;
+}
+
+// rows of the plan: buckets per box, then groups of 32 children per level
+void make_plan(Plan &P) {
+    P.nbucket = 0;
+    for (int64_t k = 0; k < P.nbox; k++) P.nbucket += (P.box_off[k + 1] - P.box_off[k] + 31) / 32;
+    P.node_first.clear(); P.node_cnt.clear(); P.node_box.clear(); P.level_off.clear();
+    std::vector<int64_t> lvl_first(P.nbox), lvl_count(P.nbox);
+    P.level_off.push_back(0);
+    for (int64_t k = 0; k < P.nbox; k++) {
+        int64_t o = P.box_off[k], e = P.box_off[k + 1];
+        lvl_first[k] = (int64_t)P.node_first.size();
+        for (int64_t s = o; s < e; s += 32) {
+            P.node_first.push_back((int32_t)s);
+            P.node_cnt.push_back((int32_t)std::min<int64_t>(32, e - s));
+            P.node_box.push_back((int32_t)k);
+        }
+        lvl_count[k] = (int64_t)P.node_first.size() - lvl_first[k];
+    }
+    P.level_off.push_back((int64_t)P.node_first.size());
+    P.nlevels = 1;
+    for (;;) {
+        bool all_one = true;
+        for (int64_t k = 0; k < P.nbox; k++) all_one &= (lvl_count[k] == 1);
+        if (all_one) break;
+        for (int64_t k = 0; k < P.nbox; k++) {
+            int64_t f = lvl_first[k], c = lvl_count[k];
+            lvl_first[k] = (int64_t)P.node_first.size();
+            for (int64_t t = 0; t < c; t += 32) {
+                P.node_first.push_back((int32_t)(f + t));
+                P.node_cnt.push_back((int32_t)std::min<int64_t>(32, c - t));
+                P.node_box.push_back((int32_t)k);
+            }
+            lvl_count[k] = (int64_t)P.node_first.size() - lvl_first[k];
+        }
+        P.level_off.push_back((int64_t)P.node_first.size());
+        P.nlevels++;
+    }
+    P.nnode = (int64_t)P.node_first.size();
+    P.box_root.assign(P.nbox, 0);
+    for (int64_t k = 0; k < P.nbox; k++) P.box_root[k] = (int32_t)lvl_first[k];
+}
+
+template <typename T>
+cudaError_t upload(DevBuf<T> &b, const std::vector<T> &v) {
+    HYD_CUDA(b.ensure(v.size()));
+    return cudaMemcpy(b.get(), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t ensure_state(hydro_ctx *c, int64_t n) {
+    HYD_CUDA(c->d_nngb.ensure(n));
+    HYD_CUDA(c->d_active.ensure(n));
+    return cudaSuccess;
+}
+
+// sort, gather, tree, lists (with capacity retries)
+int build_all(hydro_ctx *c, const hydro_particles *p, const double *h_in, const double *h_search,
+              double margin, bool want_Q, cudaStream_t st) {
+    API_CUDA(sort_particles(c, p, st));
+    API_CUDA(gather_state(c, p, h_in, h_search, margin, want_Q, st));
+    int cap = 128;
+    for (int attempt = 0; attempt < 4; attempt++) {
+        API_CUDA(build_tree(c, st));
+        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+        API_CUDA(build_lists(c, cap, st));
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        int f = c->h_cnt->flags;
+        if (f & ST_STACK) return HYDRO_ECAPACITY;
+        bool again = false;
+        if (f & ST_LIST_OVERFLOW) {
+            cap *= 2;
+            if (cap > 256) return HYDRO_ECAPACITY;
+            again = true;
+        }
+        if (f & ST_LIST_CAPACITY) {
+            unsigned long long need = c->h_cnt->list_cursor;
+            int per = (int)((need * 5 / 4) / (unsigned long long)c->plan.n + 1);
+            c->nbr_per_particle = std::max(c->nbr_per_particle, per);
+            again = true;
+        }
+        if (!again) {
+            c->have_lists = true;
+            return HYDRO_OK;
+        }
+    }
+    return HYDRO_ECAPACITY;
+}
+
+// density with re-searches when a root leaves the list radius
+int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &rebuilds,
+                cudaStream_t st) {
+    API_CUDA(run_density(c, only_active, st));
+    for (;;) {
+        int sf = 0;
+        API_CUDA(cudaMemcpyAsync(&sf, &c->d_cnt->search_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        if (sf == 0) return HYDRO_OK;
+        if (rebuilds >= 4) return HYDRO_ESEARCH;
+        rebuilds++;
+        // widen the radius of the failed particles and search again
+        API_CUDA(grow_search_radius(c, st));
+        int cap = 128;
+        for (int attempt = 0; attempt < 4; attempt++) {
+            API_CUDA(build_tree(c, st));
+            API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+            API_CUDA(build_lists(c, cap, st));
+            API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+            API_CUDA(cudaStreamSynchronize(st));
+            int f = c->h_cnt->flags;
+            if (!(f & (ST_LIST_OVERFLOW | ST_LIST_CAPACITY))) break;
+            if (f & ST_LIST_OVERFLOW) cap *= 2;
+            if (f & ST_LIST_CAPACITY) {
+                unsigned long long need = c->h_cnt->list_cursor;
+                int per = (int)((need * 5 / 4) / (unsigned long long)c->plan.n + 1);
+                c->nbr_per_particle = std::max(c->nbr_per_particle, per);
+            }
+            if (cap > 256) return HYDRO_ECAPACITY;
+        }
+        API_CUDA(run_density(c, true, st));
+    }
+}
+
+__global__ void k_fill(int64_t n, double *a, double v, uint8_t *act) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n) { a[s] = v; act[s] = 1; }
+}
+
+cudaError_t reset_guard(hydro_ctx *c, cudaStream_t st) {
+    int64_t n = c->plan.n;
+    k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c->d_nngb.get(), c->cfg.n_ngb,
+                                                         c->d_active.get());
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+void hydro_config_default(hydro_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->gamma = 5.0 / 3.0;
+    c->kernel = HYDRO_KERNEL_WENDLAND_C2;
+    c->n_ngb = 32.0;
+    c->scheme = HYDRO_MFV;
+    c->riemann = HYDRO_RIEMANN_EXACT;
+    c->precision = HYDRO_FP64;
+    c->learned_guess = 0;
+    c->limiter = 1;
+    c->time_extrap = 1;
+    c->ncond_crit = 100.0;
+    c->ngb_grow = 1.2;
+    c->max_ngb_grow = 5;
+    c->psi1 = 0.5;
+    c->psi2 = 0.25;
+    c->beta_min = 1.0;
+    c->beta_max = 2.0;
+    c->c_cfl = 0.2;
+    c->alpha1 = 0.01;
+    c->h_tol = 1e-10;
+    c->p_tol = 1e-12;
+    c->max_h_iter = 60;
+    c->max_newton = 100;
+    c->search_margin = 1.15;
+}
+
+int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
+    if (!out) return HYDRO_EINVAL;
+    *out = nullptr;
+    if (!valid_config(cfg)) return HYDRO_EINVAL;
+    hydro_ctx *c = new (std::nothrow) hydro_ctx();
+    if (!c) return HYDRO_ENOMEM;
+    c->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_cnt, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_cnt, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters));
+    if (e == cudaSuccess) {
+        for (int k = 0; k < 8 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
+        c->have_events = e == cudaSuccess;
+    }
+    if (e != cudaSuccess) {
+        hydro_destroy(c);
+        return cuda_status(e);
+    }
+    memset(&c->last_stats, 0, sizeof(c->last_stats));
+    *out = c;
+    return HYDRO_OK;
+}
+
+void hydro_destroy(hydro_ctx *c) {
+    if (!c) return;
+    if (c->d_cnt) cudaFree(c->d_cnt);
+    if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    if (c->have_events)
+        for (int k = 0; k < 8; k++) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+int hydro_set_config(hydro_ctx *c, const hydro_config *cfg) {
+    if (!c || !valid_config(cfg)) return HYDRO_EINVAL;
+    bool prec_changed = cfg->precision != c->cfg.precision;
+    c->cfg = *cfg;
+    if (prec_changed) c->have_lists = false;
+    return HYDRO_OK;
+}
+
+int hydro_set_boxes(hydro_ctx *c, int64_t nbox, const int64_t *box_off, const double *box_len) {
+    if (!c || nbox < 1 || !box_off || !box_len) return HYDRO_EINVAL;
+    if (box_off[0] != 0) return HYDRO_EINVAL;
+    for (int64_t k = 0; k < nbox; k++) {
+        if (box_off[k + 1] <= box_off[k]) return HYDRO_EINVAL;
+        for (int a = 0; a < 3; a++)
+            if (!(box_len[3 * k + a] > 0.0) || !isfinite(box_len[3 * k + a])) return HYDRO_EINVAL;
+    }
+    if (box_off[nbox] > INT32_MAX) return HYDRO_EINVAL;
+    Plan &P = c->plan;
+    P.nbox = nbox;
+    P.n = box_off[nbox];
+    P.box_off.assign(box_off, box_off + nbox + 1);
+    P.box_len.assign(box_len, box_len + 3 * nbox);
+    make_plan(P);
+    std::vector<Box> boxes(nbox);
+    for (int64_t k = 0; k < nbox; k++) {
+        for (int a = 0; a < 3; a++) {
+            boxes[k].L[a] = box_len[3 * k + a];
+            boxes[k].s[a] = (float)(box_len[3 * k + a] / 4294967296.0);
+        }
+        boxes[k].pad = 0.f;
+    }
+    API_CUDA(upload(c->d_boxes, boxes));
+    API_CUDA(upload(c->d_box_off, P.box_off));
+    API_CUDA(upload(c->d_node_first, P.node_first));
+    API_CUDA(upload(c->d_node_cnt, P.node_cnt));
+    API_CUDA(upload(c->d_node_box, P.node_box));
+    API_CUDA(upload(c->d_box_root, P.box_root));
+    API_CUDA(c->d_node_aabb.ensure(P.nnode));
+    API_CUDA(c->d_node_aabb_hi.ensure(P.nnode));
+    c->have_plan = true;
+    c->have_lists = false;
+    return HYDRO_OK;
+}
+
+int hydro_reserve(hydro_ctx *c, int64_t max_n, int nbr_per_particle) {
+    if (!c || max_n <= 0 || nbr_per_particle < 0) return HYDRO_EINVAL;
+    if (nbr_per_particle > 0) c->nbr_per_particle = nbr_per_particle;
+    int64_t n = max_n;
+    API_CUDA(c->d_keys.ensure(n)); API_CUDA(c->d_keys_alt.ensure(n));
+    API_CUDA(c->d_perm.ensure(n)); API_CUDA(c->d_perm_alt.ensure(n));
+    API_CUDA(c->d_xs.ensure(n)); API_CUDA(c->d_ys.ensure(n)); API_CUDA(c->d_zs.ensure(n));
+    API_CUDA(c->d_qx.ensure(n)); API_CUDA(c->d_qy.ensure(n)); API_CUDA(c->d_qz.ensure(n));
+    API_CUDA(c->d_hs.ensure(n)); API_CUDA(c->d_hsorted.ensure(n)); API_CUDA(c->d_omsorted.ensure(n));
+    API_CUDA(c->d_pbox.ensure(n));
+    API_CUDA(c->d_Q.ensure((size_t)6 * n));
+    API_CUDA(c->d_dQ.ensure((size_t)5 * n));
+    if (c->cfg.precision == HYDRO_MIXED) {
+        API_CUDA(c->d_recf.ensure((size_t)REC * n));
+        API_CUDA(c->d_q64.ensure((size_t)3 * n));
+    } else {
+        API_CUDA(c->d_recd.ensure((size_t)REC * n));
+    }
+    API_CUDA(c->d_nngb.ensure(n));
+    API_CUDA(c->d_active.ensure(n));
+    API_CUDA(c->d_nbr_off.ensure(n + 1));
+    API_CUDA(c->d_nbr_cnt.ensure(n));
+    API_CUDA(c->d_nbr_idx.ensure((size_t)n * c->nbr_per_particle));
+    return HYDRO_OK;
+}
+
+int hydro_build_neighbours(hydro_ctx *c, const hydro_particles *p, const double *h_search,
+                           hydro_nbrlist *out, hydro_stream stream) {
+    if (!c || !c->have_plan || !h_search) return HYDRO_EINVAL;
+    if (!valid_particles(c, p, false)) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(ensure_state(c, p->n));
+    int rc = build_all(c, p, p->h, h_search, 1.0, false, st);
+    if (rc != HYDRO_OK) return rc;
+    if (out) {
+        if (!out->off) return HYDRO_EINVAL;
+        API_CUDA(export_lists(c, out, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        if (out->needed > out->capacity) return HYDRO_ECAPACITY;
+    }
+    return HYDRO_OK;
+}
+
+int hydro_density(hydro_ctx *c, hydro_particles *p, hydro_stream stream) {
+    if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
+    if (!valid_particles(c, p, false) || !p->omega) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the guess h from the caller, in sorted order
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->h, p->n, 1, c->d_hsorted.get(), p->n, st));
+    API_CUDA(reset_guard(c, st));
+    API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+    API_CUDA(run_density(c, false, st));
+    int sf = 0, fl = 0;
+    API_CUDA(cudaMemcpyAsync(&sf, &c->d_cnt->search_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaMemcpyAsync(&fl, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), c->d_hsorted.get(), p->n, 1, p->n, p->h, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), c->d_omsorted.get(), p->n, 1, p->n, p->omega, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    if (sf) return HYDRO_ESEARCH;
+    return flags_to_status(fl);
+}
+
+// gather the caller's state (h, omega, conserved) into the sorted buffers
+static int stage_state(hydro_ctx *c, const hydro_particles *p, cudaStream_t st) {
+    const int64_t n = p->n;
+    API_CUDA(c->d_Q.ensure((size_t)6 * n));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->mass, n, 1, c->d_Q.get(), n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->px, n, 1, c->d_Q.get() + n, n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->py, n, 1, c->d_Q.get() + 2 * n, n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->pz, n, 1, c->d_Q.get() + 3 * n, n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->etot, n, 1, c->d_Q.get() + 4 * n, n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->eint, n, 1, c->d_Q.get() + 5 * n, n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->h, n, 1, c->d_hsorted.get(), n, st));
+    API_CUDA(gather_from_caller(c->d_perm.get(), p->omega, n, 1, c->d_omsorted.get(), n, st));
+    return HYDRO_OK;
+}
+
+int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *grad,
+                    double *alpha, double *ncond, hydro_stream stream) {
+    if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
+    if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = p->n;
+    int rc = stage_state(c, p, st);
+    if (rc) return rc;
+    API_CUDA(reset_guard(c, st));
+    API_CUDA(run_primitives(c, st));
+    API_CUDA(c->d_out.ensure((size_t)27 * n));
+    double *stg = c->d_out.get();
+    API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+    API_CUDA(run_gradients(c, stg, stg + 6 * n, stg + 21 * n, stg + 26 * n, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), stg, n, 6, n, B, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), stg + 6 * n, n, 15, n, grad, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), stg + 21 * n, n, 5, n, alpha, st));
+    API_CUDA(scatter_to_caller(c->d_perm.get(), stg + 26 * n, n, 1, n, ncond, st));
+    return HYDRO_OK;
+}
+
+int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const double *grad,
+                 const double *alpha, double dt, double *dQ, hydro_stream stream) {
+    if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
+    if (!valid_particles(c, p, true) || !B || !grad || !alpha || !dQ || !(dt > 0.0))
+        return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = stage_state(c, p, st);
+    if (rc) return rc;
+    API_CUDA(run_primitives(c, st));
+    API_CUDA(load_gradients(c, B, grad, alpha, st));
+    API_CUDA(run_fluxes(c, dt, nullptr, st));
+    API_CUDA(export_dQ(c, dQ, st));
+    return HYDRO_OK;
+}
+
+int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
+               hydro_stream stream) {
+    if (!c || !c->have_plan) return HYDRO_EINVAL;
+    if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = p->n;
+    const bool timing = stats != nullptr && c->have_events;
+    API_CUDA(ensure_state(c, n));
+    API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
+    if (timing) API_CUDA(cudaEventRecord(c->ev[0], st));
+    int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
+    if (rc) return rc;
+    if (timing) API_CUDA(cudaEventRecord(c->ev[1], st));
+    API_CUDA(reset_guard(c, st));
+    int rebuilds = 0, rounds = 0, ncond_fail = 0;
+    bool first = true;
+    for (;;) {
+        rc = density_all(c, p, !first, rebuilds, st);
+        if (rc) return rc;
+        if (first && timing) API_CUDA(cudaEventRecord(c->ev[2], st));
+        API_CUDA(run_primitives(c, st));
+        API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, st));
+        API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        first = false;
+        if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
+        API_CUDA(guard_grow(c, st));
+        rounds++;
+    }
+    if (timing) API_CUDA(cudaEventRecord(c->ev[3], st));
+    const double *dt_dev = dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
+    API_CUDA(run_sums(c, 0, st));
+    API_CUDA(run_fluxes(c, dt, dt_dev, st));
+    if (timing) API_CUDA(cudaEventRecord(c->ev[4], st));
+    API_CUDA(run_update(c, p, dt, dt_dev, st));
+    API_CUDA(run_sums(c, 1, st));
+    if (timing) API_CUDA(cudaEventRecord(c->ev[5], st));
+    c->last_stats.ngb_rounds = rounds;
+    c->last_stats.list_rebuilds = rebuilds;
+    c->last_stats.ncond_fail = ncond_fail;
+    if (stats) {
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        hydro_stats &S = c->last_stats;
+        const DevCounters &H = *c->h_cnt;
+        S.status = flags_to_status(H.flags);
+        if (ncond_fail && S.status == HYDRO_OK) S.status = HYDRO_ENCOND;
+        double dtmin;
+        memcpy(&dtmin, &H.dt_min_bits, sizeof(double));
+        S.dt_next = dtmin;
+        S.dt = dt > 0.0 ? dt : dtmin;
+        S.grad_pairs = (int64_t)H.grad_pairs;
+        S.flux_pairs = (int64_t)H.flux_pairs;
+        S.newton_iters = (int64_t)H.newton_iters;
+        S.guess_fallbacks = (int64_t)H.guess_fallbacks;
+        S.vacuum_faces = (int64_t)H.vacuum;
+        S.first_order_faces = (int64_t)H.first_order;
+        for (int w = 0; w < 2; w++) {
+            S.mass[w] = H.sums[w][0];
+            for (int a = 0; a < 3; a++) S.mom[w][a] = H.sums[w][1 + a];
+            S.energy[w] = H.sums[w][4];
+        }
+        if (timing) {
+            cudaEventElapsedTime(&S.ms_neighbours, c->ev[0], c->ev[1]);
+            cudaEventElapsedTime(&S.ms_density, c->ev[1], c->ev[2]);
+            cudaEventElapsedTime(&S.ms_gradients, c->ev[2], c->ev[3]);
+            cudaEventElapsedTime(&S.ms_fluxes, c->ev[3], c->ev[4]);
+            cudaEventElapsedTime(&S.ms_update, c->ev[4], c->ev[5]);
+            S.ms_sort = 0.f;
+        }
+        *stats = S;
+        return S.status;
+    }
+    return HYDRO_OK;
+}
+
+int hydro_sync_status(hydro_ctx *c, hydro_stream stream) {
+    if (!c) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int f = 0;
+    API_CUDA(cudaMemcpyAsync(&f, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+    return flags_to_status(f);
+}
+
+int hydro_get_stats(hydro_ctx *c, hydro_stats *stats, hydro_stream stream) {
+    if (!c || !stats) return HYDRO_EINVAL;
+    API_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *stats = c->last_stats;
+    return HYDRO_OK;
+}
+
+int hydro_mlp_load(hydro_ctx *c, const void *weights, size_t bytes) {
+    if (!c || !weights) return HYDRO_EINVAL;
+    const size_t nf = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 24;
+    if (bytes != nf * sizeof(float)) return HYDRO_EINVAL;
+    API_CUDA(c->d_mlp.ensure(nf));
+    API_CUDA(cudaMemcpy(c->d_mlp.get(), weights, bytes, cudaMemcpyHostToDevice));
+    c->have_mlp = true;
+    return HYDRO_OK;
+}
+
+const char *hydro_strerror(int s) {
+    switch (s) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_EINVAL: return "invalid argument";
+    case HYDRO_ENOMEM: return "device allocation failed";
+    case HYDRO_ECAPACITY: return "neighbour-list capacity exceeded";
+    case HYDRO_ENOCONV_H: return "smoothing-length iteration did not converge";
+    case HYDRO_ENCOND: return "condition number above threshold after all N_NGB growths";
+    case HYDRO_ERIEMANN: return "Riemann solver failed";
+    case HYDRO_ENONFINITE: return "non-finite value";
+    case HYDRO_ECUDA: return "CUDA runtime error";
+    case HYDRO_ESTATE: return "call order violated";
+    case HYDRO_ESEARCH: return "smoothing length beyond the neighbour search radius";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,380 @@
+// Smoothing length and particle volume (§2.3.2 Eqs. 5-6, §2.3.5 Eq. 18):
+// per particle, solve g(h) = (4 pi/3) h^3 sum_j W(r_ij, h) - N_NGB = 0 by
+// safeguarded Newton over the particle's neighbour list, then
+// omega = 1 / sum_j W(r_ij, h) (self term included).
+//
+// g is non-decreasing in h (h^3 W(r, h) is a function of r/h that grows as
+// r/h falls), so [lo, hi] brackets the root; a Newton proposal outside the
+// bracket (or beyond the list's search radius) is replaced by bisection or
+// clamped.  The list covers every j with r < h_search, so g is exact for
+// any h <= h_search; a root beyond h_search is reported for a re-search.
+//
+// FP64 path: everything in double.  Mixed path: the Newton iteration runs in
+// float on the fixed-point separations, then one Newton step evaluated in
+// double-float (pairs of floats, Dekker/Knuth error-free transformations)
+// on the exact 64-bit separations refines h to double-class accuracy
+// without the GPU's scarce FP64 pipe; omega is taken from that evaluation.
+#include "hydro_internal.cuh"
+
+namespace hyd {
+
+namespace {
+
+struct DensArgs {
+    int64_t n;
+    const int64_t *nbr_off;
+    const int32_t *nbr_cnt;
+    const int32_t *nbr_idx;
+    const double *hs;
+    const double *xs, *ys, *zs;
+    const int32_t *pbox;
+    const Box *boxes;
+    uint8_t *active;          // bit0: solve this particle; bit1: search failed
+    const double *nngb;       // per particle N_NGB (NULL: n_ngb)
+    double n_ngb;
+    int kernel;
+    double tol;
+    int max_iter;
+    bool only_active;
+    double *h;                // sorted, in: guess, out: solution
+    double *om;               // sorted out
+    DevCounters *cnt;
+};
+
+// ---------------------------------------------------------------- FP64 path
+__global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    if (a.only_active && !(a.active[s] & 1)) return;
+    const Box bx = a.boxes[a.pbox[s]];
+    const double xi = a.xs[s], yi = a.ys[s], zi = a.zs[s];
+    const double hsi = a.hs[s];
+    const double N = a.nngb ? a.nngb[s] : a.n_ngb;
+    const int64_t o = a.nbr_off[s];
+    const int c = a.nbr_cnt[s];
+    const double Kn = kernel_Kn<double>(a.kernel);
+    double h = a.h[s];
+    if (!(h > 0.0) || h > hsi) h = hsi;
+    double lo = 0.0, hi = -1.0;
+    bool conv = false, fail = false;
+    for (int it = 1; it <= a.max_iter; it++) {
+        double f = 0.0, mq = 0.0, ih = 1.0 / h;
+        for (int k = 0; k < c; k++) {
+            int j = a.nbr_idx[o + k];
+            double dx = fold64(a.xs[j] - xi, bx.L[0]);
+            double dy = fold64(a.ys[j] - yi, bx.L[1]);
+            double dz = fold64(a.zs[j] - zi, bx.L[2]);
+            double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+            double fv, mv;
+            kernel_f<double>(a.kernel, q, fv, mv);
+            f += fv;
+            mq += mv;
+        }
+        double g = Kn * f - N;
+        double dg = Kn * mq * ih;
+        if (g == 0.0) { conv = true; break; }
+        if (g < 0.0) {
+            if (h >= hsi) { fail = true; break; }
+            lo = fmax(lo, h);
+        } else {
+            hi = (hi < 0.0 || h < hi) ? h : hi;
+        }
+        double hn = dg > 0.0 ? h - g / dg : -1.0;
+        if (hn > 0.0 && fabs(hn - h) <= a.tol * h && hn <= hsi) { h = hn; conv = true; break; }
+        if (hi < 0.0) {
+            if (!(hn > lo) || hn > 2.0 * h) hn = 2.0 * h;
+            if (hn > hsi) hn = hsi;
+        } else if (!(hn > lo && hn < hi)) {
+            hn = 0.5 * (lo + hi);
+        }
+        h = hn;
+    }
+    if (fail) {
+        a.active[s] = 3;
+        atomicAdd(&a.cnt->search_fail, 1);
+        set_flag(a.cnt, ST_SEARCH);
+        return;
+    }
+    if (!conv) set_flag(a.cnt, ST_NOCONV_H);
+    double sw = 0.0, ih = 1.0 / h;
+    for (int k = 0; k < c; k++) {
+        int j = a.nbr_idx[o + k];
+        double dx = fold64(a.xs[j] - xi, bx.L[0]);
+        double dy = fold64(a.ys[j] - yi, bx.L[1]);
+        double dz = fold64(a.zs[j] - zi, bx.L[2]);
+        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+        sw += kernel_shape<double>(a.kernel, q);
+    }
+    sw *= kernel_norm<double>(a.kernel, h);
+    double om = 1.0 / sw;
+    a.h[s] = h;
+    a.om[s] = om;
+    rec[s * REC + R_H] = h;
+    rec[s * REC + R_OM] = om;
+}
+
+// ------------------------------------------------------- double-float tools
+// value = hi + lo, |lo| <= ulp(hi)/2
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = a * b;
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    df p = two_prod(a.hi, b);
+    p.lo += a.lo * b;
+    return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+// square root by one Newton correction of the float root
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (a.hi <= 0.f) return {0.f, 0.f};
+    float x = sqrtf(a.hi);
+    df xx = two_prod(x, x);
+    df r = df_sub(a, xx);
+    float corr = r.hi / (2.f * x);
+    return quick_two_sum(x, corr);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    float q1 = a.hi / b.hi;
+    df r = df_sub(a, df_mulf(b, q1));
+    float q2 = r.hi / b.hi;
+    return quick_two_sum(q1, q2);
+}
+__device__ __forceinline__ df from_i64(long long v) {
+    float h = (float)v;
+    long long r = v - (long long)h;
+    return {h, (float)r};
+}
+
+// ---------------------------------------------------------------- mixed path
+__global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
+                                const uint64_t *__restrict__ q64y,
+                                const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    if (a.only_active && !(a.active[s] & 1)) return;
+    const Box bx = a.boxes[a.pbox[s]];
+    const float *ri = rec + s * REC;
+    const uint32_t qxi = __float_as_uint(ri[R_X]), qyi = __float_as_uint(ri[R_Y]),
+                   qzi = __float_as_uint(ri[R_Z]);
+    const double hsi_d = a.hs[s];
+    const float hsi = (float)hsi_d;
+    const float N = (float)(a.nngb ? a.nngb[s] : a.n_ngb);
+    const int64_t o = a.nbr_off[s];
+    const int c = a.nbr_cnt[s];
+    const float Kn = kernel_Kn<float>(a.kernel);
+    float h = (float)a.h[s];
+    if (!(h > 0.f) || h > hsi) h = hsi;
+    float lo = 0.f, hi = -1.f;
+    bool conv = false, fail = false;
+    const float ftol = 2e-6f;
+    for (int it = 1; it <= a.max_iter; it++) {
+        float f = 0.f, mq = 0.f, ih = 1.f / h;
+        for (int k = 0; k < c; k++) {
+            int j = a.nbr_idx[o + k];
+            const float *rj = rec + (int64_t)j * REC;
+            float4 pj = *reinterpret_cast<const float4 *>(rj);
+            float dx = qdiff(qxi, __float_as_uint(pj.x), bx.s[0]);
+            float dy = qdiff(qyi, __float_as_uint(pj.y), bx.s[1]);
+            float dz = qdiff(qzi, __float_as_uint(pj.z), bx.s[2]);
+            float q = sqrtf(dx * dx + dy * dy + dz * dz) * ih;
+            float fv, mv;
+            kernel_f<float>(a.kernel, q, fv, mv);
+            f += fv;
+            mq += mv;
+        }
+        float g = Kn * f - N;
+        float dg = Kn * mq * ih;
+        if (g == 0.f) { conv = true; break; }
+        if (g < 0.f) {
+            if (h >= hsi) { fail = true; break; }
+            lo = fmaxf(lo, h);
+        } else {
+            hi = (hi < 0.f || h < hi) ? h : hi;
+        }
+        float hn = dg > 0.f ? h - g / dg : -1.f;
+        if (hn > 0.f && fabsf(hn - h) <= ftol * h && hn <= hsi) { h = hn; conv = true; break; }
+        if (hi < 0.f) {
+            if (!(hn > lo) || hn > 2.f * h) hn = 2.f * h;
+            if (hn > hsi) hn = hsi;
+        } else if (!(hn > lo && hn < hi)) {
+            hn = 0.5f * (lo + hi);
+        }
+        h = hn;
+    }
+    if (fail) {
+        a.active[s] = 3;
+        atomicAdd(&a.cnt->search_fail, 1);
+        set_flag(a.cnt, ST_SEARCH);
+        return;
+    }
+    if (!conv) set_flag(a.cnt, ST_NOCONV_H);
+    // one Newton step in double-float on exact 64-bit fixed-point separations
+    const uint64_t xi64 = q64x[s], yi64 = q64y[s], zi64 = q64z[s];
+    const float sx = (float)(bx.L[0] * 5.421010862427522e-20);  // L / 2^64
+    const float sy = (float)(bx.L[1] * 5.421010862427522e-20);
+    const float sz = (float)(bx.L[2] * 5.421010862427522e-20);
+    df hd = {h, 0.f};
+    df ih = df_div({1.f, 0.f}, hd);
+    df F = {0.f, 0.f}, MQ = {0.f, 0.f};
+    for (int k = 0; k < c; k++) {
+        int j = a.nbr_idx[o + k];
+        long long ix = (long long)(q64x[j] - xi64);
+        long long iy = (long long)(q64y[j] - yi64);
+        long long iz = (long long)(q64z[j] - zi64);
+        df dx = df_mulf(from_i64(ix), sx);
+        df dy = df_mulf(from_i64(iy), sy);
+        df dz = df_mulf(from_i64(iz), sz);
+        df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+        df q = df_mul(df_sqrt(r2), ih);
+        if (q.hi >= 1.f) continue;
+        df one = {1.f, 0.f};
+        df t = df_sub(one, q);
+        df t2 = df_mul(t, t);
+        if (a.kernel == 0) {
+            df t3 = df_mul(t2, t);
+            df fv = df_mul(df_mul(t3, t), df_add(one, df_mulf(q, 4.f)));
+            df mv = df_mulf(df_mul(df_mul(q, q), t3), 20.f);
+            F = df_add(F, fv);
+            MQ = df_add(MQ, mv);
+        } else {
+            df q2 = df_mul(q, q);
+            df fv, mv;
+            if (q.hi <= 0.5f) {
+                fv = df_add(df_sub(one, df_mulf(q2, 6.f)), df_mulf(df_mul(q2, q), 6.f));
+                mv = df_sub(df_mulf(q2, 12.f), df_mulf(df_mul(q2, q), 18.f));
+            } else {
+                fv = df_mulf(df_mul(t2, t), 2.f);
+                mv = df_mulf(df_mul(q, t2), 6.f);
+            }
+            F = df_add(F, fv);
+            MQ = df_add(MQ, mv);
+        }
+    }
+    // g = Kn F - N, dg = Kn MQ / h  ->  h_new = h - g / dg = h - (F - N/Kn) h / MQ
+    double Fd = (double)F.hi + (double)F.lo;
+    double MQd = (double)MQ.hi + (double)MQ.lo;
+    double hN = (double)h;
+    double Kd = a.kernel == 0 ? 14.0 : 32.0 / 3.0;
+    double hnew = MQd > 0.0 ? hN - (Fd - (double)N / Kd) * hN / MQd : hN;
+    // omega from the sum at h (first order in the small correction)
+    // sum_j W(r, hnew) = norm(hnew) sum f(q_new); d/dh [h^3 sum W] = Kn MQ / h * 3/(4 pi)
+    double normh = kernel_norm<double>(a.kernel, hnew);
+    double fsum = Fd + (hnew - hN) * MQd / hN;   // first-order update of sum f(q)
+    double om = 1.0 / (normh * fsum);
+    a.h[s] = hnew;
+    a.om[s] = om;
+    float *rr = rec + s * REC;
+    rr[R_H] = (float)hnew;
+    rr[R_OM] = (float)om;
+}
+
+// widen the search radius of particles whose root lay beyond it; the
+// radius never exceeds half the shortest box side (one periodic image)
+__global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *__restrict__ hs,
+                              const double *__restrict__ h, double margin,
+                              const int32_t *__restrict__ pbox, const Box *__restrict__ boxes) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint8_t a = active[s];
+    if (a & 2) {
+        const Box bx = boxes[pbox[s]];
+        double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+        hs[s] = fmin(fmax(hs[s] * 1.5, h[s] * margin), half);
+        active[s] = 1;
+    } else {
+        active[s] = 0;
+    }
+}
+
+__global__ void k_fixed64(int64_t n, const double *__restrict__ xs, const double *__restrict__ ys,
+                          const double *__restrict__ zs, const int32_t *__restrict__ pbox,
+                          const Box *__restrict__ boxes, uint64_t *__restrict__ qx,
+                          uint64_t *__restrict__ qy, uint64_t *__restrict__ qz) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const Box bx = boxes[pbox[s]];
+    const double two64 = 18446744073709551616.0;
+    double t;
+    t = xs[s] / bx.L[0] * two64; qx[s] = t >= two64 ? 0ull : (uint64_t)t;
+    t = ys[s] / bx.L[1] * two64; qy[s] = t >= two64 ? 0ull : (uint64_t)t;
+    t = zs[s] / bx.L[2] * two64; qz[s] = t >= two64 ? 0ull : (uint64_t)t;
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st) {
+    const int64_t n = c->plan.n;
+    DensArgs a;
+    a.n = n;
+    a.nbr_off = c->d_nbr_off.get();
+    a.nbr_cnt = c->d_nbr_cnt.get();
+    a.nbr_idx = c->d_nbr_idx.get();
+    a.hs = c->d_hs.get();
+    a.xs = c->d_xs.get(); a.ys = c->d_ys.get(); a.zs = c->d_zs.get();
+    a.pbox = c->d_pbox.get();
+    a.boxes = c->d_boxes.get();
+    a.active = c->d_active.get();
+    a.nngb = c->d_nngb.get();
+    a.n_ngb = c->cfg.n_ngb;
+    a.kernel = c->cfg.kernel;
+    a.tol = c->cfg.h_tol;
+    a.max_iter = c->cfg.max_h_iter;
+    a.only_active = only_active;
+    a.h = c->d_hsorted.get();
+    a.om = c->d_omsorted.get();
+    a.cnt = c->d_cnt;
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_fail, 0, sizeof(int), st));
+    if (c->cfg.precision == HYDRO_MIXED) {
+        // 64-bit fixed-point copies for the refinement step (xs.. are sorted)
+        HYD_CUDA(c->d_q64.ensure((size_t)3 * n));
+        uint64_t *q64 = c->d_q64.get();
+        k_fixed64<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
+                                                     c->d_pbox.get(), c->d_boxes.get(), q64,
+                                                     q64 + n, q64 + 2 * n);
+        HYD_CUDA(cudaGetLastError());
+        k_density_mixed<<<grid_for(n, 128), 128, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
+                                                          c->d_recf.get());
+    } else {
+        k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t grow_search_radius(hydro_ctx *c, stream_t st) {
+    const int64_t n = c->plan.n;
+    k_grow_search<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_hs.get(),
+                                                     c->d_hsorted.get(), c->cfg.search_margin,
+                                                     c->d_pbox.get(), c->d_boxes.get());
+    return cudaGetLastError();
+}
+
+}  // namespace hyd

@@ -1,0 +1,336 @@
+// Pair fluxes (§2.3.3 and §2.3.4): for every unordered pair with
+// r_ij < max(h_i, h_j), the effective face
+//   A_ij = V_i omega_j B_i mu(x_i, x_j) - V_j omega_i B_j mu(x_j, x_i)
+//        = omega_i omega_j [B_i dx W(r, h_i) + B_j dx W(r, h_j)],  dx = x_j - x_i,
+// face states extrapolated to the midpoint (Eqs. 20-21) with the limited
+// gradients, the pairwise limiter, the half-step predictor, a Riemann
+// problem along A_ij in the frame moving with (v_i + v_j)/2, and the flux
+// c = dt |A_ij| F applied antisymmetrically: Q_i -= c, Q_j += c (Eq. 16).
+//
+// Ownership: particle i computes the pair {i, j} found in its own list
+// (r < h_i) when i < j or when r >= h_j (then j's list does not see i), so
+// each unordered pair is computed exactly once.  The owner accumulates its
+// own -c in double registers; the partner's +c goes through double atomics.
+#include "hydro_internal.cuh"
+#include "pairgeom.cuh"
+#include "riemann.cuh"
+
+namespace hyd {
+
+struct FluxArgs {
+    int64_t n;
+    const int64_t *nbr_off;
+    const int32_t *nbr_cnt;
+    const int32_t *nbr_idx;
+    const double *xs, *ys, *zs, *h;
+    const int32_t *pbox;
+    const Box *boxes;
+    int kernel, scheme, riemann, limiter, time_extrap;
+    double gamma, psi1, psi2, p_tol;
+    int max_newton;
+    double dt;
+    const double *dt_dev;
+    double *dQ;              // 5 n, sorted SoA
+    DevCounters *cnt;
+    const float *mlp;        // learned star-pressure guess (NULL: off)
+};
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ int sgn_(R v) { return (v > R(0)) - (v < R(0)); }
+
+// pairwise limiter of the face value e seen from the side with cell value a
+template <typename R>
+__device__ __forceinline__ R pair_limit(R e, R a, R b, R psi1, R psi2, bool positive) {
+    if (a == b) return a;
+    R d = fabs(a - b);
+    R mean = R(0.5) * (a + b);
+    R d1 = psi1 * d, d2 = psi2 * d;
+    R lo = a < b ? a : b, hi = a > b ? a : b;
+    R lox = lo - d1, hix = hi + d1;
+    if (positive) {
+        if (sgn_(lox) != sgn_(lo)) lox = lo == R(0) ? R(0) : lo / (R(1) + d1 / fabs(lo));
+        if (sgn_(hix) != sgn_(hi)) hix = hi == R(0) ? R(0) : hi / (R(1) + d1 / fabs(hi));
+    }
+    if (a < b) {
+        R t = e < mean + d2 ? e : mean + d2;
+        return t > lox ? t : lox;
+    }
+    R t = e > mean - d2 ? e : mean - d2;
+    return t < hix ? t : hix;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_full(const R *p, R v[REC]) {
+    if (sizeof(R) == 4) {
+#pragma unroll
+        for (int k = 0; k < REC / 4; k++) {
+            float4 t = reinterpret_cast<const float4 *>(p)[k];
+            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < REC / 2; k++) {
+            double2 t = reinterpret_cast<const double2 *>(p)[k];
+            v[2 * k] = t.x; v[2 * k + 1] = t.y;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load4(const R *p, R v[4]) {
+    if (sizeof(R) == 4) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        double2 t0 = reinterpret_cast<const double2 *>(p)[0];
+        double2 t1 = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    }
+}
+
+// r < h_j decided exactly (float path: band + double fallback)
+__device__ __forceinline__ bool member_j(float r2, float hjf, const FluxArgs &a, int64_t i,
+                                         int64_t j, const Box &bx) {
+    float lo = hjf * hjf * (1.0f - 1e-4f), hi = hjf * hjf * (1.0f + 1e-4f);
+    double Lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+    bool tiny = (double)hjf < Lmin * (1.0 / 4096.0);
+    if (!tiny) {
+        if (r2 < lo) return true;
+        if (r2 > hi) return false;
+    }
+    double hj = a.h[j];
+    double ex = fold64(__dsub_rn(a.xs[j], a.xs[i]), bx.L[0]);
+    double ey = fold64(__dsub_rn(a.ys[j], a.ys[i]), bx.L[1]);
+    double ez = fold64(__dsub_rn(a.zs[j], a.zs[i]), bx.L[2]);
+    return r2_exact(ex, ey, ez) < __dmul_rn(hj, hj);
+}
+__device__ __forceinline__ bool member_j(double r2, double hj, const FluxArgs &, int64_t,
+                                         int64_t, const Box &) {
+    return r2 < __dmul_rn(hj, hj);
+}
+
+struct FaceStats {
+    unsigned long long pairs, iters, vacuum, first_order;
+};
+
+// the flux c (mass, momentum, energy) that particle i gives to particle j
+template <typename R>
+__device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, const R *ri,
+                                          const R *rj, const R d[3], R r, R norm_i, R ih_i,
+                                          R dt, R c[5], FaceStats &fs) {
+    c[0] = c[1] = c[2] = c[3] = c[4] = R(0);
+    const R wi = norm_i * kernel_shape<R>(a.kernel, r * ih_i);
+    const R hj = rj[R_H];
+    const R wj = kernel_norm<R>(a.kernel, hj) * kernel_shape<R>(a.kernel, r / hj);
+    const R *Bi = ri + R_B, *Bj = rj + R_B;
+    R A[3];
+    {
+        R ti0 = Bi[0] * d[0] + Bi[1] * d[1] + Bi[2] * d[2];
+        R ti1 = Bi[1] * d[0] + Bi[3] * d[1] + Bi[4] * d[2];
+        R ti2 = Bi[2] * d[0] + Bi[4] * d[1] + Bi[5] * d[2];
+        R tj0 = Bj[0] * d[0] + Bj[1] * d[1] + Bj[2] * d[2];
+        R tj1 = Bj[1] * d[0] + Bj[3] * d[1] + Bj[4] * d[2];
+        R tj2 = Bj[2] * d[0] + Bj[4] * d[1] + Bj[5] * d[2];
+        R oo = ri[R_OM] * rj[R_OM];
+        A[0] = oo * (ti0 * wi + tj0 * wj);
+        A[1] = oo * (ti1 * wi + tj1 * wj);
+        A[2] = oo * (ti2 * wi + tj2 * wj);
+    }
+    R Amag = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+    if (!(Amag > R(0))) return;
+    const R inA = R(1) / Amag;
+    const R nh[3] = {A[0] * inA, A[1] * inA, A[2] * inA};
+
+    R Lf[5], Rf[5];
+    const R *Gi = ri + R_G, *Gj = rj + R_G;
+#pragma unroll
+    for (int f = 0; f < 5; f++) {
+        Lf[f] = ri[R_RHO + f] + R(0.5) * (d[0] * Gi[3 * f] + d[1] * Gi[3 * f + 1] + d[2] * Gi[3 * f + 2]);
+        Rf[f] = rj[R_RHO + f] - R(0.5) * (d[0] * Gj[3 * f] + d[1] * Gj[3 * f + 1] + d[2] * Gj[3 * f + 2]);
+    }
+    if (a.limiter) {
+        const R p1 = (R)a.psi1, p2 = (R)a.psi2;
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            bool pos = (f == 0 || f == 4);
+            Lf[f] = pair_limit<R>(Lf[f], ri[R_RHO + f], rj[R_RHO + f], p1, p2, pos);
+            Rf[f] = pair_limit<R>(Rf[f], rj[R_RHO + f], ri[R_RHO + f], p1, p2, pos);
+        }
+    }
+    const R g = K.g;
+    if (a.time_extrap) {
+        const R hdt = R(0.5) * dt;
+        R divi = Gi[3] + Gi[7] + Gi[11];
+        R divj = Gj[3] + Gj[7] + Gj[11];
+        Lf[0] -= hdt * ri[R_RHO] * divi;
+        Rf[0] -= hdt * rj[R_RHO] * divj;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            Lf[1 + q] -= hdt * Gi[12 + q] / ri[R_RHO];
+            Rf[1 + q] -= hdt * Gj[12 + q] / rj[R_RHO];
+        }
+        Lf[4] -= hdt * g * ri[R_P] * divi;
+        Rf[4] -= hdt * g * rj[R_P] * divj;
+    }
+    if (!(Lf[0] > R(0) && Lf[4] > R(0) && Rf[0] > R(0) && Rf[4] > R(0))) {
+#pragma unroll
+        for (int f = 0; f < 5; f++) { Lf[f] = ri[R_RHO + f]; Rf[f] = rj[R_RHO + f]; }
+        fs.first_order++;
+    }
+    const R vf[3] = {R(0.5) * (ri[R_VX] + rj[R_VX]), R(0.5) * (ri[R_VY] + rj[R_VY]),
+                     R(0.5) * (ri[R_VZ] + rj[R_VZ])};
+    R vl[3], vr[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) { vl[q] = Lf[1 + q] - vf[q]; vr[q] = Rf[1 + q] - vf[q]; }
+    const R ul = vl[0] * nh[0] + vl[1] * nh[1] + vl[2] * nh[2];
+    const R ur = vr[0] * nh[0] + vr[1] * nh[1] + vr[2] * nh[2];
+    R wl[3], wr[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) { wl[q] = vl[q] - ul * nh[q]; wr[q] = vr[q] - ur * nh[q]; }
+    const R rl = Lf[0], pl = Lf[4], rr = Rf[0], pr = Rf[4];
+
+    R F[5];
+    if (a.riemann == HYDRO_RIEMANN_HLLC) {
+        R ps, ss;
+        hllc_flux<R>(K, rl, ul, pl, wl, rr, ur, pr, wr, nh, F, ps, ss);
+        if (a.scheme == HYDRO_MFM) {
+            F[0] = R(0);
+            F[1] = ps * nh[0]; F[2] = ps * nh[1]; F[3] = ps * nh[2];
+            F[4] = ps * ss;
+        }
+    } else {
+        R ps, us;
+        R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)fmax(a.p_tol, 2e-6);
+        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, R(-1), tol, a.max_newton, ps, us);
+        fs.iters += so.iters;
+        if (so.vacuum) { fs.vacuum++; return; }
+        if (a.scheme == HYDRO_MFM) {
+            F[0] = R(0);
+            F[1] = ps * nh[0]; F[2] = ps * nh[1]; F[3] = ps * nh[2];
+            F[4] = ps * us;
+        } else {
+            R rs, uu, pp;
+            int side;
+            star_sample<R>(K, rl, ul, pl, rr, ur, pr, ps, us, rs, uu, pp, side);
+            const R *wt = side < 0 ? wl : wr;
+            R v2 = uu * uu + wt[0] * wt[0] + wt[1] * wt[1] + wt[2] * wt[2];
+            R et = R(0.5) * rs * v2 + pp / K.gm1;
+            R m = rs * uu;
+            F[0] = m;
+            F[1] = m * (uu * nh[0] + wt[0]) + pp * nh[0];
+            F[2] = m * (uu * nh[1] + wt[1]) + pp * nh[1];
+            F[3] = m * (uu * nh[2] + wt[2]) + pp * nh[2];
+            F[4] = uu * (et + pp);
+        }
+    }
+    // back to the lab frame
+    const R vf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+    const R Fe = F[4] + (F[1] * vf[0] + F[2] * vf[1] + F[3] * vf[2]) + R(0.5) * F[0] * vf2;
+    const R sA = dt * Amag;
+    c[0] = sA * F[0];
+    c[1] = sA * (F[1] + F[0] * vf[0]);
+    c[2] = sA * (F[2] + F[0] * vf[1]);
+    c[3] = sA * (F[3] + F[0] * vf[2]);
+    c[4] = sA * Fe;
+}
+
+__device__ __forceinline__ unsigned long long wsum(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_fluxes(FluxArgs a, const R *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    FaceStats fs{0, 0, 0, 0};
+    if (s < a.n) {
+        const Box bx = a.boxes[a.pbox[s]];
+        R ri[REC];
+        load_full<R>(rec + s * REC, ri);
+        const double hd = a.h[s];
+        Member mem;
+        mem.init(a.xs, a.ys, a.zs, s, hd, bx);
+        const R h = ri[R_H];
+        const R ih = R(1) / h;
+        const R norm = kernel_norm<R>(a.kernel, h);
+        const GasK<R> K(a.gamma);
+        const R dt = (R)(a.dt_dev ? *a.dt_dev : a.dt);
+        double acc[5] = {0, 0, 0, 0, 0};
+        const int64_t o = a.nbr_off[s];
+        const int cnt = a.nbr_cnt[s];
+        for (int k = 0; k < cnt; k++) {
+            const int j = a.nbr_idx[o + k];
+            if (j == s) continue;
+            R rj[REC];
+            load4<R>(rec + (int64_t)j * REC, rj);
+            R d[3], r2;
+            rec_sep(ri, rj, bx, d, r2);
+            if (!mem(r2, j)) continue;
+            if (j < s && member_j(r2, rj[R_H], a, s, j, bx)) continue;   // j owns the pair
+            load_full<R>(rec + (int64_t)j * REC, rj);
+            R c[5];
+            face_flux<R>(a, K, ri, rj, d, sqrt(r2), norm, ih, dt, c, fs);
+            fs.pairs++;
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                acc[q] -= (double)c[q];
+                atomicAdd(&a.dQ[q * a.n + j], (double)c[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + s], acc[q]);
+    }
+    unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
+                       fo = wsum(fs.first_order);
+    if ((threadIdx.x & 31) == 0) {
+        if (p) atomicAdd(&a.cnt->flux_pairs, p);
+        if (it) atomicAdd(&a.cnt->newton_iters, it);
+        if (va) atomicAdd(&a.cnt->vacuum, va);
+        if (fo) atomicAdd(&a.cnt->first_order, fo);
+    }
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
+    HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
+    // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 5 * sizeof(unsigned long long), st));
+    FluxArgs a;
+    a.n = n;
+    a.nbr_off = c->d_nbr_off.get();
+    a.nbr_cnt = c->d_nbr_cnt.get();
+    a.nbr_idx = c->d_nbr_idx.get();
+    a.xs = c->d_xs.get(); a.ys = c->d_ys.get(); a.zs = c->d_zs.get();
+    a.h = c->d_hsorted.get();
+    a.pbox = c->d_pbox.get();
+    a.boxes = c->d_boxes.get();
+    a.kernel = c->cfg.kernel;
+    a.scheme = c->cfg.scheme;
+    a.riemann = c->cfg.riemann;
+    a.limiter = c->cfg.limiter;
+    a.time_extrap = c->cfg.time_extrap;
+    a.gamma = c->cfg.gamma;
+    a.psi1 = c->cfg.psi1;
+    a.psi2 = c->cfg.psi2;
+    a.p_tol = c->cfg.p_tol;
+    a.max_newton = c->cfg.max_newton;
+    a.dt = dt;
+    a.dt_dev = dt_dev;
+    a.dQ = c->d_dQ.get();
+    a.cnt = c->d_cnt;
+    a.mlp = nullptr;
+    if (c->cfg.precision == HYDRO_MIXED)
+        k_fluxes<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
+    else
+        k_fluxes<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
+    return cudaGetLastError();
+}
+
+}  // namespace hyd

@@ -1,0 +1,353 @@
+// Primitive variables, the E matrix and its inverse, the condition number,
+// the Lanson-Vila gradients and the conditioned Barth-Jespersen limiter
+// (§2.3.3 Eqs. 10-11, §2.3.5 Eq. 19, §2.3.6, §2.3.7 Eq. 23).
+//
+// One thread per particle walks its neighbour list twice: pass 1
+// accumulates E_i = sum_j omega_j W(r_ij, h_i) dx dx^T (6 unique entries),
+// S_f = sum_j omega_j W (f_j - f_i) dx for f = (rho, vx, vy, vz, p), the
+// neighbour extremes of f and the signal velocity of Eq. 32; B_i = E_i^-1 is
+// formed in double by cofactors (the one place the mixed path pays for
+// FP64 per particle), grad f = B S_f; pass 2 collects the largest midpoint
+// extrapolations (1/2) dx . grad f that the limiter compares with the
+// extremes.  Neighbour records are read as whole vectors from the sorted
+// record array (the first 40 B of the line in float).
+#include "hydro_internal.cuh"
+#include "pairgeom.cuh"
+
+namespace hyd {
+
+namespace {
+
+struct GradArgs {
+    int64_t n;
+    const int64_t *nbr_off;
+    const int32_t *nbr_cnt;
+    const int32_t *nbr_idx;
+    const double *xs, *ys, *zs, *h;
+    const int32_t *pbox;
+    const Box *boxes;
+    int kernel;
+    double gamma;
+    double ncond_crit, beta_min, beta_max, c_cfl;
+    int limiter;
+    double *outB, *outG, *outA, *outN;   // sorted staging (may be NULL)
+    uint8_t *active;                     // bit 2 set when N_cond fails
+    DevCounters *cnt;
+};
+
+template <typename R>
+__device__ __forceinline__ void load10(const R *p, R v[10]);
+
+template <>
+__device__ __forceinline__ void load10<float>(const float *p, float v[10]) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    float4 b = *reinterpret_cast<const float4 *>(p + 4);
+    float2 c = *reinterpret_cast<const float2 *>(p + 8);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    v[8] = c.x; v[9] = c.y;
+}
+
+template <>
+__device__ __forceinline__ void load10<double>(const double *p, double v[10]) {
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        double2 a = *reinterpret_cast<const double2 *>(p + 2 * k);
+        v[2 * k] = a.x;
+        v[2 * k + 1] = a.y;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long mypairs = 0;
+    if (s < a.n) {
+        const Box bx = a.boxes[a.pbox[s]];
+        R ri[10];
+        load10<R>(rec + s * REC, ri);
+        const double hd = a.h[s];
+        const R h = (R)hd;
+        Member mem;
+        mem.init(a.xs, a.ys, a.zs, s, hd, bx);
+        const R ih = R(1) / h;
+        const R norm = kernel_norm<R>(a.kernel, h);
+        const R fi[5] = {ri[R_RHO], ri[R_VX], ri[R_VY], ri[R_VZ], ri[R_P]};
+        const R g = (R)a.gamma;
+        const R ci = sqrt(g * ri[R_P] / ri[R_RHO]);
+        R E[6] = {0, 0, 0, 0, 0, 0};
+        R S[5][3];
+        R fmx[5], fmn[5];
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            S[f][0] = S[f][1] = S[f][2] = R(0);
+            fmx[f] = fmn[f] = fi[f];
+        }
+        R vs = R(0);
+        const int64_t o = a.nbr_off[s];
+        const int c = a.nbr_cnt[s];
+        for (int k = 0; k < c; k++) {
+            int j = a.nbr_idx[o + k];
+            if (j == s) continue;
+            R rj[10];
+            load10<R>(rec + (int64_t)j * REC, rj);
+            R d[3], r2;
+            rec_sep(ri, rj, bx, d, r2);
+            if (!mem(r2, j)) continue;
+            mypairs++;
+            R r = sqrt(r2);
+            R w = rj[R_OM] * norm * kernel_shape<R>(a.kernel, r * ih);
+            E[0] += w * d[0] * d[0];
+            E[1] += w * d[0] * d[1];
+            E[2] += w * d[0] * d[2];
+            E[3] += w * d[1] * d[1];
+            E[4] += w * d[1] * d[2];
+            E[5] += w * d[2] * d[2];
+            const R fj[5] = {rj[R_RHO], rj[R_VX], rj[R_VY], rj[R_VZ], rj[R_P]};
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                R wd = w * (fj[f] - fi[f]);
+                S[f][0] += wd * d[0];
+                S[f][1] += wd * d[1];
+                S[f][2] += wd * d[2];
+                fmx[f] = fj[f] > fmx[f] ? fj[f] : fmx[f];
+                fmn[f] = fj[f] < fmn[f] ? fj[f] : fmn[f];
+            }
+            R cj = sqrt(g * rj[R_P] / rj[R_RHO]);
+            R wdot = (d[0] * (rj[R_VX] - ri[R_VX]) + d[1] * (rj[R_VY] - ri[R_VY]) +
+                      d[2] * (rj[R_VZ] - ri[R_VZ])) / r;
+            R sig = ci + cj - (wdot < R(0) ? wdot : R(0));
+            vs = sig > vs ? sig : vs;
+        }
+        // B = E^-1 in double, N_cond (Eq. 19)
+        double e00 = E[0], e01 = E[1], e02 = E[2], e11 = E[3], e12 = E[4], e22 = E[5];
+        double c00 = e11 * e22 - e12 * e12;
+        double c01 = e12 * e02 - e01 * e22;
+        double c02 = e01 * e12 - e11 * e02;
+        double det = e00 * c00 + e01 * c01 + e02 * c02;
+        double Bd[6];
+        double ncond;
+        if (det != 0.0 && isfinite(det)) {
+            double id = 1.0 / det;
+            Bd[0] = c00 * id;
+            Bd[1] = c01 * id;
+            Bd[2] = c02 * id;
+            Bd[3] = (e00 * e22 - e02 * e02) * id;
+            Bd[4] = (e02 * e01 - e00 * e12) * id;
+            Bd[5] = (e00 * e11 - e01 * e01) * id;
+            double nE = e00 * e00 + e11 * e11 + e22 * e22 + 2.0 * (e01 * e01 + e02 * e02 + e12 * e12);
+            double nB = Bd[0] * Bd[0] + Bd[3] * Bd[3] + Bd[5] * Bd[5] +
+                        2.0 * (Bd[1] * Bd[1] + Bd[2] * Bd[2] + Bd[4] * Bd[4]);
+            ncond = sqrt(nB * nE) / 3.0;
+        } else {
+            for (int k = 0; k < 6; k++) Bd[k] = 0.0;
+            ncond = INFINITY;
+        }
+        const R B[6] = {(R)Bd[0], (R)Bd[1], (R)Bd[2], (R)Bd[3], (R)Bd[4], (R)Bd[5]};
+        R G[5][3];
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            G[f][0] = B[0] * S[f][0] + B[1] * S[f][1] + B[2] * S[f][2];
+            G[f][1] = B[1] * S[f][0] + B[3] * S[f][1] + B[4] * S[f][2];
+            G[f][2] = B[2] * S[f][0] + B[4] * S[f][1] + B[5] * S[f][2];
+        }
+        R alpha[5] = {R(1), R(1), R(1), R(1), R(1)};
+        if (a.limiter) {
+            R dp[5] = {0, 0, 0, 0, 0}, dm[5] = {0, 0, 0, 0, 0};
+            for (int k = 0; k < c; k++) {
+                int j = a.nbr_idx[o + k];
+                if (j == s) continue;
+                const R *pj = rec + (int64_t)j * REC;
+                R rj[4];
+                if (sizeof(R) == 4) {
+                    float4 t = *reinterpret_cast<const float4 *>(pj);
+                    rj[0] = t.x; rj[1] = t.y; rj[2] = t.z; rj[3] = t.w;
+                } else {
+                    rj[0] = pj[0]; rj[1] = pj[1]; rj[2] = pj[2]; rj[3] = pj[3];
+                }
+                R d[3], r2;
+                rec_sep(ri, rj, bx, d, r2);
+                if (!mem(r2, j)) continue;
+#pragma unroll
+                for (int f = 0; f < 5; f++) {
+                    R e = R(0.5) * (d[0] * G[f][0] + d[1] * G[f][1] + d[2] * G[f][2]);
+                    dp[f] = e > dp[f] ? e : dp[f];
+                    dm[f] = e < dm[f] ? e : dm[f];
+                }
+            }
+            double ratio = a.ncond_crit / ncond;
+            double beta = a.beta_max * fmin(ratio * ratio, 1.0);
+            beta = fmax(beta, a.beta_min);
+#pragma unroll
+            for (int f = 0; f < 5; f++) {
+                R rp = dp[f] > R(0) ? (fmx[f] - fi[f]) / dp[f] : R(INFINITY);
+                R rm = dm[f] < R(0) ? (fmn[f] - fi[f]) / dm[f] : R(INFINITY);
+                R al = (R)beta * (rp < rm ? rp : rm);
+                alpha[f] = al < R(1) ? al : R(1);
+            }
+        }
+        R *rs = rec + s * REC;
+#pragma unroll
+        for (int k = 0; k < 6; k++) rs[R_B + k] = B[k];
+#pragma unroll
+        for (int f = 0; f < 5; f++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) rs[R_G + 3 * f + q] = alpha[f] * G[f][q];
+        if (a.outB) {
+            for (int k = 0; k < 6; k++) a.outB[k * a.n + s] = Bd[k];
+        }
+        if (a.outG) {
+            for (int f = 0; f < 5; f++)
+                for (int q = 0; q < 3; q++) a.outG[(3 * f + q) * a.n + s] = (double)G[f][q];
+        }
+        if (a.outA) {
+            for (int f = 0; f < 5; f++) a.outA[f * a.n + s] = (double)alpha[f];
+        }
+        if (a.outN) a.outN[s] = ncond;
+        // CFL timestep of Eq. 31 with the signal velocity of Eq. 32
+        if (vs > R(0)) {
+            double dti = a.c_cfl * hd / (double)vs;
+            atomicMin(&a.cnt->dt_min_bits, (unsigned long long)__double_as_longlong(dti));
+        }
+        // N_cond guard (§2.3.5)
+        if (!(ncond <= a.ncond_crit)) {
+            a.active[s] |= 4;
+            atomicAdd(&a.cnt->ncond_fail, 1);
+        }
+    }
+    unsigned long long tot = warp_sum_ull(mypairs);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.cnt->grad_pairs, tot);
+}
+
+// primitives from the sorted conserved state and omega (§2.3.2, Eq. 23)
+template <typename R>
+__global__ void k_primitives(int64_t n, const double *__restrict__ Q,
+                             const double *__restrict__ om, const double *__restrict__ h,
+                             double gm1, double alpha1, R *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
+    double E = Q[4 * n + s], U = Q[5 * n + s];
+    double w = om[s];
+    double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
+    double therm = U;
+    if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
+    R *r = rec + s * REC;
+    r[R_H] = (R)h[s];
+    r[R_RHO] = (R)(m / w);
+    r[R_VX] = (R)(px / m);
+    r[R_VY] = (R)(py / m);
+    r[R_VZ] = (R)(pz / m);
+    r[R_P] = (R)(therm * gm1 / w);
+    r[R_OM] = (R)w;
+}
+
+// N_NGB *= grow for particles that failed the N_cond check; they (only)
+// get their density solved again
+__global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__restrict__ nngb,
+                             double grow) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint8_t a = active[s];
+    if (a & 4) {
+        nngb[s] *= grow;
+        active[s] = 1;
+    } else {
+        active[s] = 0;
+    }
+}
+
+// caller's B, grad, alpha (already gathered to sorted SoA staging) into
+// the records: B and the limited gradients alpha * grad
+template <typename R>
+__global__ void k_load_grads(int64_t n, const double *__restrict__ st, R *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    R *r = rec + s * REC;
+    for (int k = 0; k < 6; k++) r[R_B + k] = (R)st[k * n + s];
+    for (int f = 0; f < 5; f++) {
+        double al = st[(21 + f) * n + s];
+        for (int q = 0; q < 3; q++) r[R_G + 3 * f + q] = (R)(al * st[(6 + 3 * f + q) * n + s]);
+    }
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t run_primitives(hydro_ctx *c, stream_t st) {
+    const int64_t n = c->plan.n;
+    double gm1 = c->cfg.gamma - 1.0;
+    if (c->cfg.precision == HYDRO_MIXED)
+        k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
+                                                              c->d_hsorted.get(), gm1,
+                                                              c->cfg.alpha1, c->d_recf.get());
+    else
+        k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
+                                                               c->d_hsorted.get(), gm1,
+                                                               c->cfg.alpha1, c->d_recd.get());
+    return cudaGetLastError();
+}
+
+cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
+                          double *ncond_out, stream_t st) {
+    const int64_t n = c->plan.n;
+    GradArgs a;
+    a.n = n;
+    a.nbr_off = c->d_nbr_off.get();
+    a.nbr_cnt = c->d_nbr_cnt.get();
+    a.nbr_idx = c->d_nbr_idx.get();
+    a.xs = c->d_xs.get(); a.ys = c->d_ys.get(); a.zs = c->d_zs.get();
+    a.h = c->d_hsorted.get();
+    a.pbox = c->d_pbox.get();
+    a.boxes = c->d_boxes.get();
+    a.kernel = c->cfg.kernel;
+    a.gamma = c->cfg.gamma;
+    a.ncond_crit = c->cfg.ncond_crit;
+    a.beta_min = c->cfg.beta_min;
+    a.beta_max = c->cfg.beta_max;
+    a.c_cfl = c->cfg.c_cfl;
+    a.limiter = c->cfg.limiter;
+    a.outB = B_out; a.outG = grad_out; a.outA = alpha_out; a.outN = ncond_out;
+    a.active = c->d_active.get();
+    a.cnt = c->d_cnt;
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
+    const unsigned long long inf_bits = 0x7FF0000000000000ull;
+    HYD_CUDA(cudaMemcpyAsync(&c->d_cnt->dt_min_bits, &inf_bits, sizeof(inf_bits),
+                             cudaMemcpyHostToDevice, st));
+    if (c->cfg.precision == HYDRO_MIXED)
+        k_gradients<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
+    else
+        k_gradients<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
+    return cudaGetLastError();
+}
+
+cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
+    const int64_t n = c->plan.n;
+    k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_nngb.get(),
+                                                   c->cfg.ngb_grow);
+    return cudaGetLastError();
+}
+
+cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
+                           const double *alpha, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_out.ensure((size_t)27 * n));
+    double *stg = c->d_out.get();
+    HYD_CUDA(gather_from_caller(c->d_perm.get(), B, n, 6, stg, n, st));
+    HYD_CUDA(gather_from_caller(c->d_perm.get(), grad, n, 15, stg + 6 * n, n, st));
+    HYD_CUDA(gather_from_caller(c->d_perm.get(), alpha, n, 5, stg + 21 * n, n, st));
+    if (c->cfg.precision == HYDRO_MIXED)
+        k_load_grads<float><<<grid_for(n, 256), 256, 0, st>>>(n, stg, c->d_recf.get());
+    else
+        k_load_grads<double><<<grid_for(n, 256), 256, 0, st>>>(n, stg, c->d_recd.get());
+    return cudaGetLastError();
+}
+
+}  // namespace hyd

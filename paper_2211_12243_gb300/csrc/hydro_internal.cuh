@@ -1,0 +1,307 @@
+// Internal declarations of the GB300 hydro library (not part of the ABI).
+//
+// Data layout in HBM (all arrays in Morton-sorted order, index s):
+//   xs, ys, zs        double   positions (master copy, exact geometry)
+//   qx, qy, qz        uint32   fixed-point positions q = x/L * 2^32; an
+//                              int32 difference is the minimum-image dx
+//   hs                double   search radius of the neighbour lists
+//   rec[s][32]        R        per-particle record, one 128 B (float) or
+//                              256 B (double) line, read whole by the pair
+//                              kernels when particle s is a neighbour:
+//                              x y z h | rho vx vy vz | p omega B(6) |
+//                              limited grad rho(3) v(9) p(3) | pad
+//                              (in float records x y z hold the q bits)
+//   Qs[6][n]          double   conserved m, px, py, pz, E, U (sorted copy)
+//   nbr_off/nbr_cnt   int64/int32  per-particle slice of nbr_idx (sorted ids)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "hydro.h"
+
+namespace hyd {
+
+constexpr int BUCKET = 32;   // particles per bucket (one warp)
+constexpr int REC = 32;      // scalars per particle record
+constexpr int MAX_LEVELS = 8;
+
+// record slots
+enum : int {
+    R_X = 0, R_Y = 1, R_Z = 2, R_H = 3,
+    R_RHO = 4, R_VX = 5, R_VY = 6, R_VZ = 7,
+    R_P = 8, R_OM = 9, R_B = 10,           // B: 10..15 (xx xy xz yy yz zz)
+    R_G = 16,                              // 16..30: grad rho, vx, vy, vz, p (limited)
+    R_PAD = 31
+};
+
+// device status bits (first error wins in the word; bits accumulate in flags)
+enum : int {
+    ST_LIST_OVERFLOW = 1,     // per-particle staging capacity exceeded
+    ST_LIST_CAPACITY = 2,     // global list storage exceeded
+    ST_SEARCH = 4,            // h root beyond the search radius
+    ST_NOCONV_H = 8,
+    ST_NCOND = 16,
+    ST_RIEMANN = 32,
+    ST_NONFINITE = 64,
+    ST_STACK = 128,
+};
+
+struct Box {
+    double L[3];      // lengths
+    float s[3];       // L / 2^32 (metres per fixed-point unit)
+    float pad;
+};
+
+// scalars the device reads every step
+struct DevCounters {
+    unsigned long long list_cursor;   // entries used in nbr_idx
+    unsigned long long list_needed;   // entries the build wanted
+    unsigned long long dt_min_bits;   // CFL dt, as ordered bits of a positive double
+    int flags;                        // ST_* bits
+    int search_fail;                  // particles whose h left the radius
+    int ncond_fail;                   // particles above the N_cond threshold
+    int pad0;
+    unsigned long long grad_pairs;
+    unsigned long long flux_pairs;
+    unsigned long long newton_iters;
+    unsigned long long guess_fallbacks;
+    unsigned long long vacuum;
+    unsigned long long first_order;
+    double sums[2][5];                // totals before / after (m, px, py, pz, E)
+};
+
+// bucket tree topology (host plan, mirrored on the device)
+struct Plan {
+    int64_t n = 0, nbox = 0;
+    int64_t nbucket = 0, nnode = 0;
+    int nlevels = 0;
+    std::vector<int64_t> box_off;          // nbox+1
+    std::vector<double> box_len;           // 3 nbox
+    std::vector<int64_t> level_off;        // nlevels+1 (node ids, level-major)
+    std::vector<int32_t> node_first, node_cnt, node_box;
+    std::vector<int32_t> box_root;
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    // grow (contents not preserved); returns cudaSuccess or the error
+    cudaError_t ensure(size_t n) {
+        if (n <= cap && p) return cudaSuccess;
+        release();
+        size_t want = n > 0 ? n : 1;
+        cudaError_t e = cudaMalloc((void **)&p, want * sizeof(T));
+        if (e != cudaSuccess) { p = nullptr; cap = 0; return e; }
+        cap = want;
+        return cudaSuccess;
+    }
+    T *get() const { return p; }
+};
+
+}  // namespace hyd
+
+struct hydro_ctx {
+    hydro_config cfg;
+    int device = 0;
+    hyd::Plan plan;
+    bool have_plan = false;
+    bool have_lists = false;
+    int64_t list_n = 0;
+    int nbr_per_particle = 64;
+
+    // plan on device
+    hyd::DevBuf<int32_t> d_node_first, d_node_cnt, d_node_box, d_box_root;
+    hyd::DevBuf<int64_t> d_box_off;
+    hyd::DevBuf<hyd::Box> d_boxes;
+    hyd::DevBuf<uint4> d_node_aabb;          // lo.xyz, hmax bits | hi.xyz, pad
+    hyd::DevBuf<uint4> d_node_aabb_hi;
+
+    // sort scratch
+    hyd::DevBuf<unsigned long long> d_keys, d_keys_alt;
+    hyd::DevBuf<int32_t> d_perm, d_perm_alt;
+    hyd::DevBuf<int64_t> d_scan_tmp;
+    hyd::DevBuf<int32_t> d_hist;
+
+    // sorted state
+    hyd::DevBuf<double> d_xs, d_ys, d_zs, d_hs, d_hsorted, d_omsorted;
+    hyd::DevBuf<uint32_t> d_qx, d_qy, d_qz;
+    hyd::DevBuf<uint64_t> d_q64;      // 3 n, mixed-path refinement
+    hyd::DevBuf<int32_t> d_pbox;
+    hyd::DevBuf<double> d_Q;          // 6 n
+    hyd::DevBuf<double> d_dQ;         // 5 n
+    hyd::DevBuf<float> d_recf;        // 32 n (MIXED)
+    hyd::DevBuf<double> d_recd;       // 32 n (FP64)
+    hyd::DevBuf<double> d_out;        // staging of outputs (up to 27 n)
+    hyd::DevBuf<double> d_nngb;       // per-particle N_NGB
+    hyd::DevBuf<uint8_t> d_active;    // density / guard flags
+    hyd::DevBuf<double> d_vsig_dt;    // per-particle CFL dt
+
+    // neighbour lists
+    hyd::DevBuf<int32_t> d_nbr_idx;
+    hyd::DevBuf<int64_t> d_nbr_off;
+    hyd::DevBuf<int32_t> d_nbr_cnt;
+
+    // reductions
+    hyd::DevBuf<double> d_partials;
+
+    // MLP
+    hyd::DevBuf<float> d_mlp;
+    bool have_mlp = false;
+
+    // device counters + pinned host mirror
+    hyd::DevCounters *d_cnt = nullptr;
+    hyd::DevCounters *h_cnt = nullptr;
+    int pending_status = 0;
+
+    hydro_stats last_stats;
+    cudaEvent_t ev[8];
+    bool have_events = false;
+};
+
+namespace hyd {
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+using stream_t = cudaStream_t;
+
+// sort.cu
+cudaError_t sort_particles(hydro_ctx *c, const hydro_particles *p, stream_t st);
+cudaError_t gather_state(hydro_ctx *c, const hydro_particles *p, const double *h_in,
+                         const double *h_search, double search_margin, bool want_Q,
+                         stream_t st);
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                               stream_t st);
+cudaError_t scatter_to_caller(const int32_t *perm, const double *src, int64_t n, int ncomp,
+                              int64_t src_stride, double *dst, stream_t st);
+cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n, int ncomp,
+                               double *dst, int64_t dst_stride, stream_t st);
+
+// neighbours.cu
+cudaError_t build_tree(hydro_ctx *c, stream_t st);
+cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
+cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
+
+// density.cu
+cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st);
+cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
+
+// gradients.cu
+cudaError_t run_primitives(hydro_ctx *c, stream_t st);
+cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
+                          double *ncond_out, stream_t st);
+cudaError_t guard_grow(hydro_ctx *c, stream_t st);
+cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
+                           const double *alpha, stream_t st);
+
+// fluxes.cu
+cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st);
+
+// update.cu
+cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
+                       stream_t st);
+cudaError_t run_sums(hydro_ctx *c, int which, stream_t st);
+cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st);
+
+}  // namespace hyd
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace hyd {
+
+__device__ __forceinline__ void set_flag(DevCounters *c, int bit) { atomicOr(&c->flags, bit); }
+
+// one fold of a separation into [-L/2, L/2]; exact IEEE operations only
+__device__ __forceinline__ double fold64(double d, double L) {
+    double half = __dmul_rn(0.5, L);
+    if (d > half) return __dsub_rn(d, L);
+    if (d < -half) return __dadd_rn(d, L);
+    return d;
+}
+
+// r^2 = (dx^2 + dy^2) + dz^2 rounded step by step (no contraction)
+__device__ __forceinline__ double r2_exact(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ float qdiff(uint32_t a, uint32_t b, float s) {
+    return (float)(int32_t)(b - a) * s;
+}
+
+// Kernel normalised sums used by the density iteration:
+//   (4 pi / 3) h^3 W(r, h) = Kn * f(q),  h dW/dh-term: d/dh [Kn f(q)] = Kn f'(q) (-q/h)
+// Wendland C2: W = 21/(2 pi H^3) (1-q)^4 (1+4q)  -> Kn = 14
+// cubic M4:    W = 8/(pi H^3) {1-6q^2+6q^3 ; 2(1-q)^3} -> Kn = 32/3
+template <typename R>
+__device__ __forceinline__ void kernel_f(int kernel, R q, R &f, R &mqfp) {
+    // f(q) and -q f'(q)
+    if (q >= R(1)) { f = R(0); mqfp = R(0); return; }
+    if (kernel == 0) {
+        R t = R(1) - q;
+        R t3 = t * t * t;
+        f = t3 * t * (R(1) + R(4) * q);
+        mqfp = R(20) * q * q * t3;
+    } else {
+        if (q <= R(0.5)) {
+            f = R(1) - R(6) * q * q + R(6) * q * q * q;
+            mqfp = R(12) * q * q - R(18) * q * q * q;
+        } else {
+            R t = R(1) - q;
+            f = R(2) * t * t * t;
+            mqfp = R(6) * q * t * t;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R kernel_Kn(int kernel) {
+    return kernel == 0 ? R(14) : R(32.0 / 3.0);
+}
+
+// W(r, H) / norm where norm = 21/(2 pi H^3) (Wendland) or 8/(pi H^3) (cubic)
+template <typename R>
+__device__ __forceinline__ R kernel_shape(int kernel, R q) {
+    if (q >= R(1)) return R(0);
+    if (kernel == 0) {
+        R t = R(1) - q;
+        R t2 = t * t;
+        return t2 * t2 * (R(1) + R(4) * q);
+    }
+    if (q <= R(0.5)) return R(1) - R(6) * q * q + R(6) * q * q * q;
+    R t = R(1) - q;
+    return R(2) * t * t * t;
+}
+
+template <typename R>
+__device__ __forceinline__ R kernel_norm(int kernel, R H) {
+    const R pi = R(3.14159265358979323846);
+    R H3 = H * H * H;
+    return kernel == 0 ? R(21) / (R(2) * pi * H3) : R(8) / (pi * H3);
+}
+
+__device__ __forceinline__ double ordered_min_bits(double v) { return v; }
+
+}  // namespace hyd
+#endif
+
+#define HYD_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e__ = (call);                                   \
+        if (e__ != cudaSuccess) return e__;                         \
+    } while (0)

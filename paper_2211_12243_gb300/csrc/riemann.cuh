@@ -1,0 +1,244 @@
+// Device Riemann solvers for the per-face problem of §2.3.3: the exact
+// iterative solver (Toro 2009, ch. 4; the paper's choice) and HLLC
+// (Toro 2009, ch. 10).  Templated on the arithmetic type: double for the
+// FP64 path, float for the mixed path.
+#pragma once
+
+#include "hydro_internal.cuh"
+
+namespace hyd {
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return rsqrt(v); }
+
+template <typename R> __device__ __forceinline__ R pow_(R a, R b);
+template <> __device__ __forceinline__ float pow_<float>(float a, float b) { return __powf(a, b); }
+template <> __device__ __forceinline__ double pow_<double>(double a, double b) { return pow(a, b); }
+
+// gamma-dependent constants of Toro's formulae
+template <typename R>
+struct GasK {
+    R g, gm1, gp1;
+    R z;      // (g-1)/(2g)
+    R zi;     // 2g/(g-1)
+    R g4;     // 2/(g-1)
+    R g5;     // 2/(g+1)
+    R g6;     // (g-1)/(g+1)
+    R g2;     // (g+1)/(2g)
+    R inv_g;  // 1/g
+    R mzr;    // -(g+1)/(2g)
+    __device__ explicit GasK(double gamma) {
+        g = (R)gamma;
+        gm1 = (R)(gamma - 1.0);
+        gp1 = (R)(gamma + 1.0);
+        z = (R)((gamma - 1.0) / (2.0 * gamma));
+        zi = (R)(2.0 * gamma / (gamma - 1.0));
+        g4 = (R)(2.0 / (gamma - 1.0));
+        g5 = (R)(2.0 / (gamma + 1.0));
+        g6 = (R)((gamma - 1.0) / (gamma + 1.0));
+        g2 = (R)((gamma + 1.0) / (2.0 * gamma));
+        inv_g = (R)(1.0 / gamma);
+        mzr = (R)(-(gamma + 1.0) / (2.0 * gamma));
+    }
+};
+
+// one side's pressure function and derivative
+template <typename R>
+__device__ __forceinline__ void side_f(const GasK<R> &k, R p, R rk, R pk, R ck, R &f, R &df) {
+    if (p > pk) {
+        R A = k.g5 / rk;
+        R Bk = k.g6 * pk;
+        R q = sqrt(A / (p + Bk));
+        f = (p - pk) * q;
+        df = q * (R(1) - R(0.5) * (p - pk) / (Bk + p));
+    } else {
+        R pr = p / pk;
+        R t = pow_(pr, k.z);
+        f = k.g4 * ck * (t - R(1));
+        df = t / (pr * k.g * pk) * ck;   // = (1/(rk ck)) (p/pk)^(-(g+1)/(2g))
+    }
+}
+
+// Toro's adaptive initial guess
+template <typename R>
+__device__ __forceinline__ R star_guess(const GasK<R> &k, R rl, R ul, R pl, R cl, R rr, R ur,
+                                        R pr, R cr) {
+    R ppv = R(0.5) * (pl + pr) - R(0.125) * (ur - ul) * (rl + rr) * (cl + cr);
+    ppv = ppv > R(0) ? ppv : R(0);
+    R pmin = pl < pr ? pl : pr, pmax = pl > pr ? pl : pr;
+    if (pmax <= R(2) * pmin && ppv >= pmin && ppv <= pmax) return ppv;
+    if (ppv < pmin) {
+        R pq = pow_(pl / pr, k.z);
+        R um = (pq * ul / cl + ur / cr + k.g4 * (pq - R(1))) / (pq / cl + R(1) / cr);
+        R tl = R(1) + R(0.5) * k.gm1 * (ul - um) / cl;
+        R tr = R(1) + R(0.5) * k.gm1 * (um - ur) / cr;
+        return R(0.5) * (pl * pow_(tl, k.zi) + pr * pow_(tr, k.zi));
+    }
+    R gl = sqrt((k.g5 / rl) / (k.g6 * pl + ppv));
+    R gr = sqrt((k.g5 / rr) / (k.g6 * pr + ppv));
+    return (gl * pl + gr * pr - (ur - ul)) / (gl + gr);
+}
+
+struct StarOut {
+    int iters;
+    int bisect;
+    int vacuum;
+};
+
+// Newton iteration for p* from p0 (> 0, else the adaptive guess); stop when
+// the relative change falls below tol, then one more Newton step; bisection
+// on the bracket after max_newton iterations.
+template <typename R>
+__device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
+                                              R p0, R tol, int max_newton, R &ps, R &us) {
+    StarOut o{0, 0, 0};
+    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    R du = ur - ul;
+    if (k.g4 * (cl + cr) <= du) {
+        o.vacuum = 1;
+        ps = R(0);
+        us = R(0);
+        return o;
+    }
+    R p = p0 > R(0) ? p0 : star_guess(k, rl, ul, pl, cl, rr, ur, pr, cr);
+    const R pfloor = sizeof(R) == 8 ? R(1e-300) : R(1e-37);
+    if (!(p > pfloor)) p = pfloor;
+    bool conv = false;
+    R fl, dfl, fr, dfr;
+    for (int it = 1; it <= max_newton; it++) {
+        side_f(k, p, rl, pl, cl, fl, dfl);
+        side_f(k, p, rr, pr, cr, fr, dfr);
+        R pn = p - (fl + fr + du) / (dfl + dfr);
+        if (!(pn > pfloor)) pn = pfloor;
+        R ch = R(2) * fabs(pn - p) / (pn + p);
+        p = pn;
+        o.iters = it;
+        if (ch < tol) { conv = true; break; }
+    }
+    if (conv) {
+        side_f(k, p, rl, pl, cl, fl, dfl);
+        side_f(k, p, rr, pr, cr, fr, dfr);
+        R pn = p - (fl + fr + du) / (dfl + dfr);
+        if (pn > pfloor) p = pn;
+    } else {
+        R lo = R(0), hi = pl > pr ? pl : pr;
+        for (int guard = 0; guard < 2100; guard++) {
+            side_f(k, hi, rl, pl, cl, fl, dfl);
+            side_f(k, hi, rr, pr, cr, fr, dfr);
+            if (fl + fr + du > R(0)) break;
+            lo = hi;
+            hi = hi * R(2);
+        }
+        for (int it = 0; it < 200; it++) {
+            R mid = R(0.5) * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            side_f(k, mid, rl, pl, cl, fl, dfl);
+            side_f(k, mid, rr, pr, cr, fr, dfr);
+            if (fl + fr + du > R(0)) hi = mid; else lo = mid;
+        }
+        p = R(0.5) * (lo + hi);
+        o.bisect = 1;
+    }
+    side_f(k, p, rl, pl, cl, fl, dfl);
+    side_f(k, p, rr, pr, cr, fr, dfr);
+    ps = p;
+    us = R(0.5) * (ul + ur) + R(0.5) * (fr - fl);
+    return o;
+}
+
+// state at x/t = 0 of the exact solution; side = -1 left of the contact
+template <typename R>
+__device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
+                                            R ps, R us, R &rho, R &u, R &p, int &side) {
+    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    if (R(0) <= us) {
+        side = -1;
+        if (ps > pl) {
+            R sl = ul - cl * sqrt(k.g2 * ps / pl + k.z);
+            if (R(0) <= sl) { rho = rl; u = ul; p = pl; }
+            else { R t = ps / pl; rho = rl * (t + k.g6) / (k.g6 * t + R(1)); u = us; p = ps; }
+        } else {
+            if (R(0) <= ul - cl) { rho = rl; u = ul; p = pl; }
+            else {
+                R t = ps / pl;
+                R cml = cl * pow_(t, k.z);
+                if (R(0) > us - cml) { rho = rl * pow_(t, k.inv_g); u = us; p = ps; }
+                else {
+                    R cc = k.g5 + k.g6 / cl * ul;
+                    rho = rl * pow_(cc, k.g4);
+                    u = k.g5 * (cl + R(0.5) * k.gm1 * ul);
+                    p = pl * pow_(cc, k.zi);
+                }
+            }
+        }
+    } else {
+        side = 1;
+        if (ps > pr) {
+            R sr = ur + cr * sqrt(k.g2 * ps / pr + k.z);
+            if (R(0) >= sr) { rho = rr; u = ur; p = pr; }
+            else { R t = ps / pr; rho = rr * (t + k.g6) / (k.g6 * t + R(1)); u = us; p = ps; }
+        } else {
+            if (R(0) >= ur + cr) { rho = rr; u = ur; p = pr; }
+            else {
+                R t = ps / pr;
+                R cmr = cr * pow_(t, k.z);
+                if (R(0) <= us + cmr) { rho = rr * pow_(t, k.inv_g); u = us; p = ps; }
+                else {
+                    R cc = k.g5 - k.g6 / cr * ur;
+                    rho = rr * pow_(cc, k.g4);
+                    u = k.g5 * (-cr + R(0.5) * k.gm1 * ur);
+                    p = pr * pow_(cc, k.zi);
+                }
+            }
+        }
+    }
+}
+
+// HLLC flux along n (face frame) with the pressure-based wave speeds.
+// F[0] mass, F[1..3] momentum, F[4] energy; ps/ss: star pressure, contact.
+template <typename R>
+__device__ __forceinline__ void hllc_flux(const GasK<R> &k, R rl, R ul, R pl, const R *wl, R rr,
+                                          R ur, R pr, const R *wr, const R *n, R *F, R &ps,
+                                          R &ss) {
+    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    R ppv = R(0.5) * (pl + pr) - R(0.125) * (ur - ul) * (rl + rr) * (cl + cr);
+    ppv = ppv > R(0) ? ppv : R(0);
+    R ql = ppv <= pl ? R(1) : sqrt(R(1) + k.g2 * (ppv / pl - R(1)));
+    R qr = ppv <= pr ? R(1) : sqrt(R(1) + k.g2 * (ppv / pr - R(1)));
+    R sl = ul - cl * ql, sr = ur + cr * qr;
+    ss = (pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur)) / (rl * (sl - ul) - rr * (sr - ur));
+    ps = pl + rl * (sl - ul) * (ss - ul);
+    R w2l = wl[0] * wl[0] + wl[1] * wl[1] + wl[2] * wl[2];
+    R w2r = wr[0] * wr[0] + wr[1] * wr[1] + wr[2] * wr[2];
+    R El = pl / k.gm1 + R(0.5) * rl * (ul * ul + w2l);
+    R Er = pr / k.gm1 + R(0.5) * rr * (ur * ur + w2r);
+    R fm, fn, fe;
+    const R *wt;
+    if (R(0) <= sl) {
+        fm = rl * ul; fn = rl * ul * ul + pl; fe = ul * (El + pl); wt = wl;
+    } else if (R(0) <= ss) {
+        R kk = rl * (sl - ul) / (sl - ss);
+        R e2 = kk * (El / rl + (ss - ul) * (ss + pl / (rl * (sl - ul))));
+        fm = rl * ul + sl * (kk - rl);
+        fn = rl * ul * ul + pl + sl * (kk * ss - rl * ul);
+        fe = ul * (El + pl) + sl * (e2 - El);
+        wt = wl;
+    } else if (R(0) <= sr) {
+        R kk = rr * (sr - ur) / (sr - ss);
+        R e2 = kk * (Er / rr + (ss - ur) * (ss + pr / (rr * (sr - ur))));
+        fm = rr * ur + sr * (kk - rr);
+        fn = rr * ur * ur + pr + sr * (kk * ss - rr * ur);
+        fe = ur * (Er + pr) + sr * (e2 - Er);
+        wt = wr;
+    } else {
+        fm = rr * ur; fn = rr * ur * ur + pr; fe = ur * (Er + pr); wt = wr;
+    }
+    F[0] = fm;
+    F[1] = fn * n[0] + fm * wt[0];
+    F[2] = fn * n[1] + fm * wt[1];
+    F[3] = fn * n[2] + fm * wt[2];
+    F[4] = fe;
+}
+
+}  // namespace hyd

@@ -1,0 +1,157 @@
+// End of the step (§2.3.4 Eq. 16, §2.3.7 Eq. 24): conserved update, the
+// separately integrated internal energy, the drift, and compensated
+// totals of mass, momentum and energy for the conservation diagnostics.
+#include "hydro_internal.cuh"
+
+namespace hyd {
+
+namespace {
+
+constexpr int SUM_THREADS = 256;
+constexpr int SUM_BLOCKS = 608;   // 4 per SM on 152 SMs
+
+struct UpdArgs {
+    int64_t n;
+    const int32_t *perm;
+    const int32_t *pbox;
+    const Box *boxes;
+    double *Q;             // 6 n sorted (updated in place)
+    const double *dQ;      // 5 n sorted
+    const double *xs, *ys, *zs, *h, *om;
+    double dt;
+    const double *dt_dev;
+    hydro_particles p;
+    DevCounters *cnt;
+};
+
+__global__ void k_update(UpdArgs a) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    const int64_t n = a.n;
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+    double m0 = a.Q[s], px0 = a.Q[n + s], py0 = a.Q[2 * n + s], pz0 = a.Q[3 * n + s];
+    double E0 = a.Q[4 * n + s], U0 = a.Q[5 * n + s];
+    double dm = a.dQ[s], dpx = a.dQ[n + s], dpy = a.dQ[2 * n + s], dpz = a.dQ[3 * n + s];
+    double dE = a.dQ[4 * n + s];
+    double vx0 = px0 / m0, vy0 = py0 / m0, vz0 = pz0 / m0;
+    double dU = dE - (vx0 * dpx + vy0 * dpy + vz0 * dpz) + 0.5 * (vx0 * vx0 + vy0 * vy0 + vz0 * vz0) * dm;
+    double m1 = m0 + dm, px1 = px0 + dpx, py1 = py0 + dpy, pz1 = pz0 + dpz;
+    double E1 = E0 + dE, U1 = U0 + dU;
+    double vx1 = px1 / m1, vy1 = py1 / m1, vz1 = pz1 / m1;
+    const Box bx = a.boxes[a.pbox[s]];
+    double x = a.xs[s] + dt * 0.5 * (vx0 + vx1);
+    double y = a.ys[s] + dt * 0.5 * (vy0 + vy1);
+    double z = a.zs[s] + dt * 0.5 * (vz0 + vz1);
+    if (x >= bx.L[0]) x -= bx.L[0];
+    if (x < 0.0) x += bx.L[0];
+    if (y >= bx.L[1]) y -= bx.L[1];
+    if (y < 0.0) y += bx.L[1];
+    if (z >= bx.L[2]) z -= bx.L[2];
+    if (z < 0.0) z += bx.L[2];
+    if (!(isfinite(m1) && isfinite(px1) && isfinite(py1) && isfinite(pz1) && isfinite(E1) &&
+          isfinite(U1) && isfinite(x) && isfinite(y) && isfinite(z)))
+        atomicOr(&a.cnt->flags, ST_NONFINITE);
+    a.Q[s] = m1; a.Q[n + s] = px1; a.Q[2 * n + s] = py1; a.Q[3 * n + s] = pz1;
+    a.Q[4 * n + s] = E1; a.Q[5 * n + s] = U1;
+    const int64_t o = a.perm[s];
+    a.p.x[o] = x; a.p.y[o] = y; a.p.z[o] = z;
+    a.p.mass[o] = m1; a.p.px[o] = px1; a.p.py[o] = py1; a.p.pz[o] = pz1;
+    a.p.etot[o] = E1; a.p.eint[o] = U1;
+    a.p.h[o] = a.h[s];
+    a.p.omega[o] = a.om[s];
+}
+
+struct KS {
+    double s, c;
+};
+__device__ __forceinline__ void ks_add(KS &k, double v) {
+    double t = k.s + v;
+    if (fabs(k.s) >= fabs(v)) k.c += (k.s - t) + v;
+    else k.c += (v - t) + k.s;
+    k.s = t;
+}
+
+__global__ void k_sums(int64_t n, const double *__restrict__ Q, double *__restrict__ partials) {
+    KS acc[5];
+    for (int q = 0; q < 5; q++) acc[q] = {0.0, 0.0};
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        for (int q = 0; q < 5; q++) ks_add(acc[q], Q[q * n + s]);
+    __shared__ double sh[SUM_THREADS][5];
+    for (int q = 0; q < 5; q++) sh[threadIdx.x][q] = acc[q].s + acc[q].c;
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        KS k = {0.0, 0.0};
+        for (int t = 0; t < SUM_THREADS; t++) ks_add(k, sh[t][threadIdx.x]);
+        partials[blockIdx.x * 5 + threadIdx.x] = k.s + k.c;
+    }
+}
+
+__global__ void k_sums_final(const double *__restrict__ partials, int nb, double *__restrict__ out) {
+    int q = threadIdx.x;
+    if (q >= 5) return;
+    KS k = {0.0, 0.0};
+    for (int b = 0; b < nb; b++) ks_add(k, partials[b * 5 + q]);
+    out[q] = k.s + k.c;
+}
+
+__global__ void k_export_dQ(int64_t n, const int32_t *__restrict__ perm,
+                            const double *__restrict__ Q, const double *__restrict__ dQ,
+                            double *__restrict__ out) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double m0 = Q[s];
+    double vx = Q[n + s] / m0, vy = Q[2 * n + s] / m0, vz = Q[3 * n + s] / m0;
+    double dm = dQ[s], dpx = dQ[n + s], dpy = dQ[2 * n + s], dpz = dQ[3 * n + s];
+    double dE = dQ[4 * n + s];
+    double dU = dE - (vx * dpx + vy * dpy + vz * dpz) + 0.5 * (vx * vx + vy * vy + vz * vz) * dm;
+    int64_t o = perm[s];
+    out[6 * o + 0] = dm;
+    out[6 * o + 1] = dpx;
+    out[6 * o + 2] = dpy;
+    out[6 * o + 3] = dpz;
+    out[6 * o + 4] = dE;
+    out[6 * o + 5] = dU;
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
+                       stream_t st) {
+    UpdArgs a;
+    a.n = c->plan.n;
+    a.perm = c->d_perm.get();
+    a.pbox = c->d_pbox.get();
+    a.boxes = c->d_boxes.get();
+    a.Q = c->d_Q.get();
+    a.dQ = c->d_dQ.get();
+    a.xs = c->d_xs.get(); a.ys = c->d_ys.get(); a.zs = c->d_zs.get();
+    a.h = c->d_hsorted.get();
+    a.om = c->d_omsorted.get();
+    a.dt = dt;
+    a.dt_dev = dt_dev;
+    a.p = *p;
+    a.cnt = c->d_cnt;
+    k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t run_sums(hydro_ctx *c, int which, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_partials.ensure((size_t)SUM_BLOCKS * 5));
+    k_sums<<<SUM_BLOCKS, SUM_THREADS, 0, st>>>(n, c->d_Q.get(), c->d_partials.get());
+    HYD_CUDA(cudaGetLastError());
+    k_sums_final<<<1, 32, 0, st>>>(c->d_partials.get(), SUM_BLOCKS, c->d_cnt->sums[which]);
+    return cudaGetLastError();
+}
+
+cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st) {
+    const int64_t n = c->plan.n;
+    k_export_dQ<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_perm.get(), c->d_Q.get(), c->d_dQ.get(),
+                                                   dQ);
+    return cudaGetLastError();
+}
+
+}  // namespace hyd
