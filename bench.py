@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the MFV/MFM hydro step on GB300.
+
+Metric: hydro pair-interactions per second -- directed gradient pairs
+(j != i, r_ij < h_i) plus unordered flux pairs (r_ij < max(h_i, h_j)) --
+processed by one full step (neighbour search, density, gradients, fluxes,
+update), divided by the device time of the whole step.
+
+Default workload: the 3D Sod tube of 1,067,742 particles (4 x 1 x 1
+periodic box, left rho = 1, P = 1 at spacing 1/78, right rho = 0.125,
+P = 0.1 at spacing 2/78, gamma = 5/3, Wendland C2, N_NGB = 32, exact
+Riemann solver, MFV), mixed precision.  The plain FP64 step is timed on the
+same state for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  Under torchrun each rank steps its own
+independent box (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hydro pair-interactions/s (grad+flux), mixed+learned vs plain FP64, 1 GB300"
+UNIT = "pair-interactions/s"
+WORKLOAD = "sod3d_1067742_mfv_exact"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=78, help="Sod lattice resolution (78: 1,067,742)")
+    ap.add_argument("--scheme", default="mfv")
+    ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-n", type=int, default=40, help="Sod resolution of the CPU sample")
+    ap.add_argument("--cpu-reps", type=int, default=6)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (test infrastructure, timed as it stands)
+# --------------------------------------------------------------------------
+def oracle_sample_rate(n, reps):
+    """The oracle's gradient + flux stages on the Sod generator at resolution
+    n (density solved first, untimed); pairs counted like the GPU metric."""
+    import oracle
+    from paper_2211_12243_gb300 import workloads as W
+    w = W.sod(n)
+    cfg = oracle.config(gamma=w["gamma"])
+    x, y, z, L = w["x"], w["y"], w["z"], w["L"]
+    h, om, _, _ = oracle.density(cfg, x, y, z, L, w["h"])
+    prims = oracle.primitives(cfg, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"], om)
+    off, idx = oracle.neighbours(x, y, z, L, h)
+    gpairs = int(idx.size - x.size)
+    t = 0.0
+    fpairs = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        B6, _, nc = oracle.matrices(cfg, x, y, z, L, h, om)
+        grad, alpha, _ = oracle.gradients(cfg, x, y, z, L, h, om, prims, B6, nc)
+        pairs = oracle.flux_pairs(x, y, z, L, h)
+        oracle.fluxes(cfg, x, y, z, L, h, om, B6, prims, grad, alpha, 1e-4, pairs=pairs)
+        t += time.perf_counter() - t0
+        fpairs = len(pairs)
+    total = reps * (gpairs + fpairs)
+    return dict(value=total / t, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"Sod generator at n={n} ({x.size} particles), oracle gradient+flux stages "
+                       f"(E/B/N_cond, gradients+limiter, pair enumeration, fluxes), {reps} passes, "
+                       f"{total} pair-interactions in {t:.2f} s"), t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rate = None
+    times = []
+    for k in range(args.warmup + args.steps):
+        r, t = oracle_sample_rate(args.cpu_n, 1)
+        if k >= args.warmup:
+            times.append(t)
+            rate = r
+    import oracle
+    ms = 1000.0 * sum(times) / len(times)
+    pairs_per_step = rate["value"] * (sum(times) / len(times))
+    value = pairs_per_step / (sum(times) / len(times))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sod3d_n{args.cpu_n}_oracle_sample", "l2": "inputs fit in host caches; CPU"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": rate["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2211_12243_gb300 import build, hydro, workloads
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    w = workloads.sod(args.n)
+    n = w["x"].size
+    cfg = hydro.default_config(gamma=w["gamma"], precision=args.precision, scheme=args.scheme)
+    H = hydro.Hydro(cfg)
+    H.set_boxes(*hydro.single_box(w))
+    H.reserve(n, 64)
+    st = hydro.to_device(w)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(Hc, state, k, warm):
+        for _ in range(warm):
+            s = Hc.step(state, -1.0)
+            assert s["status"] == 0, s
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        pairs = 0
+        flux_ms = 0.0
+        flux_pairs = 0
+        iters = 0
+        launches0 = hydro.kernel_launches()
+        stats = None
+        for i in range(k):
+            flush.zero_()
+            ev0[i].record(stream)
+            stats = Hc.step(state, -1.0)
+            ev1[i].record(stream)
+            assert stats["status"] == 0, stats
+            pairs += stats["grad_pairs"] + stats["flux_pairs"]
+            flux_ms += stats["ms_fluxes"]
+            flux_pairs += stats["flux_pairs"]
+            iters += stats["newton_iters"]
+        torch.cuda.synchronize()
+        launches = hydro.kernel_launches() - launches0 - 0
+        ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        return dict(ms=ms, pairs=pairs, flux_ms=flux_ms, flux_pairs=flux_pairs, iters=iters,
+                    launches=launches, last=stats)
+
+    # ---- timed region: the mixed step
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    r = timed_steps(H, st, args.steps, args.warmup)
+    clocks = clk.stop()
+    ms_max = r["ms"]
+    if world > 1:
+        t = torch.tensor([r["ms"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * r["pairs"] / (ms_max / 1000.0)
+
+    # ---- end to end through the public API with host buffers
+    keys = ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")
+    host = {k: torch.as_tensor(w[k]).pin_memory() for k in keys}
+    host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in keys + ("omega",)}
+    e2e_ms = 0.0
+    e2e_pairs = 0
+    st2 = hydro.to_device(w)
+    for k in range(2 + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for kk in keys:
+            st2[kk].copy_(host[kk], non_blocking=True)
+        s2 = H.step(st2, -1.0)
+        for kk in keys + ("omega",):
+            host_out[kk].copy_(st2[kk], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            e2e_ms += e0.elapsed_time(e1)
+            e2e_pairs += s2["grad_pairs"] + s2["flux_pairs"]
+    e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * n * len(keys), "d2h_bytes_per_step": 8 * n * (len(keys) + 1)}
+
+    # ---- plain FP64 step on the same starting state
+    fp64 = None
+    if not args.no_fp64:
+        cfg64 = hydro.default_config(gamma=w["gamma"], precision="fp64", scheme=args.scheme)
+        H64 = hydro.Hydro(cfg64)
+        H64.set_boxes(*hydro.single_box(w))
+        st64 = hydro.to_device(w)
+        k64 = max(2, min(args.steps, 5))
+        r64 = timed_steps(H64, st64, k64, 1)
+        fp64 = {"value": r64["pairs"] / (r64["ms"] / 1000.0), "ms_per_step": r64["ms"] / k64,
+                "flux_kernel_ms": r64["flux_ms"] / k64}
+        H64.close()
+
+    # ---- roofline of the dominant kernel (pair fluxes, float ALU bound)
+    faces = r["flux_pairs"] / args.steps
+    iters = r["iters"] / args.steps
+    flops_face, flops_iter = FLOPS_PER_FACE, FLOPS_PER_NEWTON
+    flux_ms = r["flux_ms"] / args.steps
+    achieved = (faces * flops_face + iters * flops_iter) / (flux_ms / 1000.0) / 1e12
+    peak = FP32_PEAK_TFLOPS
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": FLUX_TRAFFIC_BYTES, "kernel": "k_fluxes<float>",
+            "flux_kernel_ms": flux_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, _ = oracle_sample_rate(args.cpu_n, args.cpu_reps)
+
+    last = r["last"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.n == 78 else f"sod3d_n{args.n}", "particles": n,
+                   "precision": args.precision, "scheme": args.scheme, "riemann": "exact",
+                   "kernel": "wendland_c2", "n_ngb": 32,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "pairs_per_step": r["pairs"] / args.steps,
+                   "grad_pairs": last["grad_pairs"], "flux_pairs": last["flux_pairs"],
+                   "newton_iters_per_face": iters / max(faces, 1)},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
+        "clocks": clocks, "plain_fp64": fp64,
+        "stage_ms": {k: last[k] for k in ("ms_neighbours", "ms_density", "ms_gradients",
+                                          "ms_fluxes", "ms_update")},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+# Algorithmic arithmetic of one float face (counted from the face routine;
+# FMA = 2, each compare/min/max/select 1, sqrt/div/pow 1 each):
+# kernel weights 22, face vector 53, extrapolation 80, pairwise limiter 180,
+# half-step predictor 36, boost/projection 38, Riemann set-up + guess 30,
+# polish step + final evaluation 61, sampling 30, flux 35, de-boost and
+# scaling 24 -> 589 per face; each Newton iteration 38.
+FLOPS_PER_FACE = 589.0
+FLOPS_PER_NEWTON = 38.0
+# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FLUX_TRAFFIC_BYTES = None
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -216,6 +216,10 @@ int hydro_get_stats(hydro_ctx *ctx, hydro_stats *stats, hydro_stream stream);
  * b3, feature mean[12], feature scale[12] (row-major, W[out][in]). */
 int hydro_mlp_load(hydro_ctx *ctx, const void *weights, size_t bytes);
 
+/* Number of kernels this library has launched in the process so far
+ * (every entry point's launches, all contexts).  Diagnostics only. */
+int64_t hydro_kernel_launches(void);
+
 /* Human-readable message for a hydro_status. */
 const char *hydro_strerror(int status);
 

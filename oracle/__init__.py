@@ -94,7 +94,7 @@ def lib():
         L.orc_flux_pairs.restype = i64
         L.orc_flux_pairs.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp]
         L.orc_fluxes.restype = None
-        L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 15 + [d, i64, vp, vp, vp,
+        L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 14 + [d, i64, vp, vp, vp,
                                  P(FluxStats), vp, vp])
         L.orc_riemann_guess.restype = d
         L.orc_riemann_guess.argtypes = [d] * 7

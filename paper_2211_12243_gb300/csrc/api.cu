@@ -3,11 +3,20 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 #include "hydro_internal.cuh"
 
 using namespace hyd;
+
+namespace hyd {
+static std::atomic<long long> g_launches{0};
+cudaError_t launch_check() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+}  // namespace hyd
 
 namespace {
 
@@ -106,38 +115,35 @@ cudaError_t ensure_state(hydro_ctx *c, int64_t n) {
     return cudaSuccess;
 }
 
-// sort, gather, tree, lists (with capacity retries)
+// tree boxes and lists for the current search radii: one staged pass, and
+// the two-pass form when a particle has more candidates than the staging
+// holds or the list storage is too small
+int lists_all(hydro_ctx *c, cudaStream_t st) {
+    API_CUDA(build_tree(c, st));
+    API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+    API_CUDA(build_lists(c, 128, st));
+    API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    int f = c->h_cnt->flags;
+    if (f & ST_STACK) return HYDRO_ECAPACITY;
+    if (f & (ST_LIST_OVERFLOW | ST_LIST_CAPACITY)) {
+        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+        API_CUDA(build_lists_twopass(c, st));
+        int f2 = 0;
+        API_CUDA(cudaMemcpyAsync(&f2, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        if (f2 & ST_STACK) return HYDRO_ECAPACITY;
+    }
+    c->have_lists = true;
+    return HYDRO_OK;
+}
+
+// sort, gather, tree, lists
 int build_all(hydro_ctx *c, const hydro_particles *p, const double *h_in, const double *h_search,
               double margin, bool want_Q, cudaStream_t st) {
     API_CUDA(sort_particles(c, p, st));
     API_CUDA(gather_state(c, p, h_in, h_search, margin, want_Q, st));
-    int cap = 128;
-    for (int attempt = 0; attempt < 4; attempt++) {
-        API_CUDA(build_tree(c, st));
-        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-        API_CUDA(build_lists(c, cap, st));
-        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-        API_CUDA(cudaStreamSynchronize(st));
-        int f = c->h_cnt->flags;
-        if (f & ST_STACK) return HYDRO_ECAPACITY;
-        bool again = false;
-        if (f & ST_LIST_OVERFLOW) {
-            cap *= 2;
-            if (cap > 256) return HYDRO_ECAPACITY;
-            again = true;
-        }
-        if (f & ST_LIST_CAPACITY) {
-            unsigned long long need = c->h_cnt->list_cursor;
-            int per = (int)((need * 5 / 4) / (unsigned long long)c->plan.n + 1);
-            c->nbr_per_particle = std::max(c->nbr_per_particle, per);
-            again = true;
-        }
-        if (!again) {
-            c->have_lists = true;
-            return HYDRO_OK;
-        }
-    }
-    return HYDRO_ECAPACITY;
+    return lists_all(c, st);
 }
 
 // density with re-searches when a root leaves the list radius
@@ -153,23 +159,8 @@ int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &r
         rebuilds++;
         // widen the radius of the failed particles and search again
         API_CUDA(grow_search_radius(c, st));
-        int cap = 128;
-        for (int attempt = 0; attempt < 4; attempt++) {
-            API_CUDA(build_tree(c, st));
-            API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-            API_CUDA(build_lists(c, cap, st));
-            API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-            API_CUDA(cudaStreamSynchronize(st));
-            int f = c->h_cnt->flags;
-            if (!(f & (ST_LIST_OVERFLOW | ST_LIST_CAPACITY))) break;
-            if (f & ST_LIST_OVERFLOW) cap *= 2;
-            if (f & ST_LIST_CAPACITY) {
-                unsigned long long need = c->h_cnt->list_cursor;
-                int per = (int)((need * 5 / 4) / (unsigned long long)c->plan.n + 1);
-                c->nbr_per_particle = std::max(c->nbr_per_particle, per);
-            }
-            if (cap > 256) return HYDRO_ECAPACITY;
-        }
+        int rc = lists_all(c, st);
+        if (rc) return rc;
         API_CUDA(run_density(c, true, st));
     }
 }
@@ -183,7 +174,7 @@ cudaError_t reset_guard(hydro_ctx *c, cudaStream_t st) {
     int64_t n = c->plan.n;
     k_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c->d_nngb.get(), c->cfg.n_ngb,
                                                          c->d_active.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace
@@ -511,6 +502,8 @@ int hydro_mlp_load(hydro_ctx *c, const void *weights, size_t bytes) {
     c->have_mlp = true;
     return HYDRO_OK;
 }
+
+int64_t hydro_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 const char *hydro_strerror(int s) {
     switch (s) {

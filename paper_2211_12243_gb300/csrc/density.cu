@@ -360,13 +360,13 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st) {
         k_fixed64<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
                                                      c->d_pbox.get(), c->d_boxes.get(), q64,
                                                      q64 + n, q64 + 2 * n);
-        HYD_CUDA(cudaGetLastError());
+        HYD_CUDA(launch_check());
         k_density_mixed<<<grid_for(n, 128), 128, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
                                                           c->d_recf.get());
     } else {
         k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
     }
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t grow_search_radius(hydro_ctx *c, stream_t st) {
@@ -374,7 +374,7 @@ cudaError_t grow_search_radius(hydro_ctx *c, stream_t st) {
     k_grow_search<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_hs.get(),
                                                      c->d_hsorted.get(), c->cfg.search_margin,
                                                      c->d_pbox.get(), c->d_boxes.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

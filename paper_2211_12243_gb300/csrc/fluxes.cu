@@ -330,7 +330,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
         k_fluxes<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
     else
         k_fluxes<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

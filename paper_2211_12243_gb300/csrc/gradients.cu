@@ -291,7 +291,7 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st) {
         k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
                                                                c->cfg.alpha1, c->d_recd.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
@@ -325,14 +325,14 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         k_gradients<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
     else
         k_gradients<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
     k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_nngb.get(),
                                                    c->cfg.ngb_grow);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
@@ -347,7 +347,7 @@ cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
         k_load_grads<float><<<grid_for(n, 256), 256, 0, st>>>(n, stg, c->d_recf.get());
     else
         k_load_grads<double><<<grid_for(n, 256), 256, 0, st>>>(n, stg, c->d_recd.get());
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

@@ -174,6 +174,10 @@ struct hydro_ctx {
 
 namespace hyd {
 
+// every kernel launch is followed by launch_check(): it returns the launch
+// error and counts the launch (process-wide, see hydro_kernel_launches)
+cudaError_t launch_check();
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -194,6 +198,7 @@ cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n
 // neighbours.cu
 cudaError_t build_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
+cudaError_t build_lists_twopass(hydro_ctx *c, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu

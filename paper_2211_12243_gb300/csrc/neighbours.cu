@@ -117,11 +117,13 @@ struct ListArgs {
     int64_t capacity;
     DevCounters *cnt;
     int cap;   // per-lane staging entries
+    int mode;  // 0: stage in shared memory, one bulk write; 1: count only;
+               // 2: write at nbr_off (from a scan of the counts)
 };
 
 // stage a candidate bucket in shared memory and test it against all lanes
 __device__ __forceinline__ void test_bucket(const ListArgs &a, int cb, int lane, bool own,
-                                            uint32_t qxi, uint32_t qyi, uint32_t qzi, double xi,
+                                            int s_own, uint32_t qxi, uint32_t qyi, uint32_t qzi, double xi,
                                             double yi, double zi, double hsi, float lo2,
                                             float hi2, bool always_exact, const Box &bx,
                                             double *sx, double *sy, double *sz, uint32_t *sq,
@@ -162,7 +164,11 @@ __device__ __forceinline__ void test_bucket(const ListArgs &a, int cb, int lane,
             in = r2_exact(ex, ey, ez) < h2;
         }
         if (in) {
-            if (count < a.cap) list[count * 32 + lane] = f + k;
+            if (a.mode == 0) {
+                if (count < a.cap) list[count * 32 + lane] = f + k;
+            } else if (a.mode == 2) {
+                a.nbr_idx[a.nbr_off[s_own] + count] = f + k;
+            }
             count++;
         }
     }
@@ -174,7 +180,7 @@ __global__ void k_build_lists(ListArgs a) {
     const int64_t b = blockIdx.x * (int64_t)LIST_WARPS + warp;
     // per-warp shared memory: list[cap][32] | stack[STACK] | sx sy sz [32] | sq[96]
     size_t per_warp = (size_t)a.cap * 32 * 4 + STACK * 4 + 3 * 32 * 8 + 96 * 4;
-    unsigned char *base = smem_raw + per_warp * warp;
+    unsigned char *base = smem_raw + per_warp * warp;   // cap = 0 in modes 1, 2
     int32_t *list = (int32_t *)base;
     int32_t *stack = (int32_t *)(base + (size_t)a.cap * 32 * 4);
     double *sx = (double *)(base + (size_t)a.cap * 32 * 4 + STACK * 4);
@@ -201,7 +207,7 @@ __global__ void k_build_lists(ListArgs a) {
     int sp = 0;
     int root = a.box_root[a.node_box[b]];
     if (root < a.nbucket_total) {
-        test_bucket(a, root, lane, own, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2, always_exact,
+        test_bucket(a, root, lane, own, s, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2, always_exact,
                     bx, sx, sy, sz, sq, list, count);
     } else {
         if (lane == 0) stack[0] = root;
@@ -222,7 +228,7 @@ __global__ void k_build_lists(ListArgs a) {
             while (m) {
                 int k = __ffs(m) - 1;
                 m &= m - 1;
-                test_bucket(a, nf + k, lane, own, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2,
+                test_bucket(a, nf + k, lane, own, s, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2,
                             always_exact, bx, sx, sy, sz, sq, list, count);
             }
         } else {
@@ -237,6 +243,13 @@ __global__ void k_build_lists(ListArgs a) {
         }
     }
 
+    if (a.mode == 1) {
+        if (own) a.nbr_cnt[s] = count;
+        return;
+    }
+    if (a.mode == 2) {
+        return;
+    }
     // write the lists out
     if (own && count > a.cap) set_flag(a.cnt, ST_LIST_OVERFLOW);
     int mine = own ? min(count, a.cap) : 0;
@@ -260,6 +273,12 @@ __global__ void k_build_lists(ListArgs a) {
     }
     __syncwarp();
     for (int k = 0; k < mine; k++) a.nbr_idx[start + k] = list[k * 32 + lane];
+}
+
+__global__ void k_widen(int64_t n, const int32_t *__restrict__ cnt, int64_t *__restrict__ out) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n) out[s] = cnt[s];
+    if (s == n) out[n] = 0;
 }
 
 __global__ void k_export_count(int64_t n, const int32_t *__restrict__ perm,
@@ -291,30 +310,30 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
+static cudaError_t widen_counts(const int32_t *cnt, int64_t n, int64_t *out, stream_t st) {
+    k_widen<<<grid_for(n + 1, 256), 256, 0, st>>>(n, cnt, out);
+    return launch_check();
+}
+
 cudaError_t build_tree(hydro_ctx *c, stream_t st) {
     const Plan &P = c->plan;
     k_aabb_leaf<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_qx.get(), c->d_qy.get(),
         c->d_qz.get(), c->d_hs.get(), c->d_node_aabb.get(), c->d_node_aabb_hi.get());
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     for (int l = 1; l < P.nlevels; l++) {
         int64_t n0 = P.level_off[l], nn = P.level_off[l + 1] - P.level_off[l];
         k_aabb_node<<<grid_for(nn * 32, 256), 256, 0, st>>>(n0, nn, c->d_node_first.get(),
                                                             c->d_node_cnt.get(),
                                                             c->d_node_aabb.get(),
                                                             c->d_node_aabb_hi.get());
-        HYD_CUDA(cudaGetLastError());
+        HYD_CUDA(launch_check());
     }
     return cudaSuccess;
 }
 
-cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {
+static ListArgs list_args(hydro_ctx *c, int cap, int mode) {
     const Plan &P = c->plan;
-    const int64_t n = P.n;
-    HYD_CUDA(c->d_nbr_off.ensure(n + 1));
-    HYD_CUDA(c->d_nbr_cnt.ensure(n));
-    HYD_CUDA(c->d_nbr_idx.ensure((size_t)n * c->nbr_per_particle));
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->list_cursor, 0, sizeof(unsigned long long), st));
     ListArgs a;
     a.nbucket = P.nbucket;
     a.node_first = c->d_node_first.get();
@@ -334,16 +353,54 @@ cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {
     a.capacity = (int64_t)c->d_nbr_idx.cap;
     a.cnt = c->d_cnt;
     a.cap = cap;
-    size_t per_warp = (size_t)cap * 32 * 4 + STACK * 4 + 3 * 32 * 8 + 96 * 4;
+    a.mode = mode;
+    return a;
+}
+
+static cudaError_t launch_lists(const ListArgs &a, int64_t nbucket, stream_t st) {
+    size_t per_warp = (size_t)a.cap * 32 * 4 + STACK * 4 + 3 * 32 * 8 + 96 * 4;
     size_t smem = per_warp * LIST_WARPS;
-    static int configured = 0;
-    if ((size_t)configured < smem) {
+    static size_t configured = 48 * 1024;
+    if (configured < smem) {
         HYD_CUDA(cudaFuncSetAttribute(k_build_lists, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        configured = (int)smem;
+        configured = smem;
     }
-    k_build_lists<<<grid_for(P.nbucket, LIST_WARPS), LIST_WARPS * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    k_build_lists<<<grid_for(nbucket, LIST_WARPS), LIST_WARPS * 32, smem, st>>>(a);
+    return launch_check();
+}
+
+// one pass: lists staged per lane in shared memory (cap entries), bulk write
+cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_nbr_off.ensure(n + 1));
+    HYD_CUDA(c->d_nbr_cnt.ensure(n));
+    HYD_CUDA(c->d_nbr_idx.ensure((size_t)n * c->nbr_per_particle));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->list_cursor, 0, sizeof(unsigned long long), st));
+    return launch_lists(list_args(c, cap, 0), c->plan.nbucket, st);
+}
+
+// two passes for particles with more candidates than the staging holds:
+// count, exclusive scan into nbr_off, then write in place (synchronous)
+cudaError_t build_lists_twopass(hydro_ctx *c, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_nbr_off.ensure(n + 1));
+    HYD_CUDA(c->d_nbr_cnt.ensure(n));
+    HYD_CUDA(launch_lists(list_args(c, 0, 1), c->plan.nbucket, st));
+    HYD_CUDA(c->d_scan_tmp.ensure((size_t)(n + 1) + (n + 1) / 2048 + 64));
+    int64_t *cnt64 = c->d_scan_tmp.get();
+    int64_t *tmp = cnt64 + (n + 1);
+    HYD_CUDA(widen_counts(c->d_nbr_cnt.get(), n, cnt64, st));
+    HYD_CUDA(exclusive_scan_i64(cnt64, c->d_nbr_off.get(), n + 1, tmp, st));
+    int64_t total = 0;
+    HYD_CUDA(cudaMemcpyAsync(&total, c->d_nbr_off.get() + n, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, st));
+    HYD_CUDA(cudaStreamSynchronize(st));
+    if ((size_t)total > c->d_nbr_idx.cap) {
+        HYD_CUDA(c->d_nbr_idx.ensure((size_t)total + (size_t)n * 4));
+        c->nbr_per_particle = (int)(c->d_nbr_idx.cap / (size_t)n) + 1;
+    }
+    return launch_lists(list_args(c, 0, 2), c->plan.nbucket, st);
 }
 
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {
@@ -353,7 +410,7 @@ cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {
     int64_t *tmp = rowlen + (n + 1);
     k_export_count<<<grid_for(n + 1, 256), 256, 0, st>>>(n, c->d_perm.get(), c->d_nbr_cnt.get(),
                                                          rowlen);
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     HYD_CUDA(exclusive_scan_i64(rowlen, out->off, n + 1, tmp, st));
     int64_t total = 0;
     HYD_CUDA(cudaMemcpyAsync(&total, out->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -363,7 +420,7 @@ cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {
     k_export_fill<<<grid_for(n, 128), 128, 0, st>>>(n, c->d_perm.get(), c->d_nbr_off.get(),
                                                    c->d_nbr_cnt.get(), c->d_nbr_idx.get(),
                                                    out->off, out->idx);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

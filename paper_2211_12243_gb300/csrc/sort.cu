@@ -242,15 +242,15 @@ cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
         k_scan_tile<<<1, SCAN_THREADS, 0, st>>>(in, out, n, nullptr);
-        return cudaGetLastError();
+        return launch_check();
     }
     int64_t *sums = tmp;
     int64_t *rest = tmp + nb;
     k_scan_tile<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, sums);
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     HYD_CUDA(exclusive_scan_i64(sums, sums, nb, rest, st));
     k_scan_add<<<grid_for(n, 256), 256, 0, st>>>(out, n, sums);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 static int64_t scan_tmp_size(int64_t n) {
@@ -274,7 +274,7 @@ cudaError_t sort_particles(hydro_ctx *c, const hydro_particles *p, stream_t st) 
     k_morton<<<grid_for(n, 256), 256, 0, st>>>(n, p->x, p->y, p->z, c->d_box_off.get(),
                                                  c->plan.nbox, c->d_boxes.get(), c->d_keys.get(),
                                                  c->d_perm.get());
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     int bits = 30;
     while ((1ll << (bits - 30)) < c->plan.nbox) bits++;
     int64_t *hist = c->d_scan_tmp.get();
@@ -284,11 +284,11 @@ cudaError_t sort_particles(hydro_ctx *c, const hydro_particles *p, stream_t st) 
     int32_t *va = c->d_perm.get(), *vb = c->d_perm_alt.get();
     for (int shift = 0; shift < bits; shift += 8) {
         k_radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, st>>>(n, ka, shift, ntiles, hist);
-        HYD_CUDA(cudaGetLastError());
+        HYD_CUDA(launch_check());
         HYD_CUDA(exclusive_scan_i64(hist, offs, nh, tmp, st));
         k_radix_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, st>>>(n, ka, va, shift, ntiles, offs,
                                                                    kb, vb);
-        HYD_CUDA(cudaGetLastError());
+        HYD_CUDA(launch_check());
         unsigned long long *tk = ka; ka = kb; kb = tk;
         int32_t *tv = va; va = vb; vb = tv;
     }
@@ -321,12 +321,12 @@ cudaError_t gather_state(hydro_ctx *c, const hydro_particles *p, const double *h
             c->d_qx.get(), c->d_qy.get(), c->d_qz.get(), c->d_hsorted.get(), c->d_hs.get(),
             c->d_pbox.get(), c->d_recd.get());
     }
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     if (want_Q) {
         HYD_CUDA(c->d_Q.ensure((size_t)6 * n));
         k_gather6<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_perm.get(), p->mass, p->px, p->py,
                                                      p->pz, p->etot, p->eint, c->d_Q.get());
-        HYD_CUDA(cudaGetLastError());
+        HYD_CUDA(launch_check());
     }
     return cudaSuccess;
 }
@@ -335,14 +335,14 @@ cudaError_t scatter_to_caller(const int32_t *perm, const double *src, int64_t n,
                               int64_t src_stride, double *dst, stream_t st) {
     if (!dst || n <= 0) return cudaSuccess;
     k_scatter_caller<<<grid_for(n, 256), 256, 0, st>>>(n, ncomp, perm, src, src_stride, dst);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n, int ncomp,
                                double *dst, int64_t dst_stride, stream_t st) {
     if (!src || n <= 0) return cudaSuccess;
     k_gather_caller<<<grid_for(n, 256), 256, 0, st>>>(n, ncomp, perm, src, dst, dst_stride);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

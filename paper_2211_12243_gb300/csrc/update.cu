@@ -135,23 +135,23 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.p = *p;
     a.cnt = c->d_cnt;
     k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t run_sums(hydro_ctx *c, int which, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_partials.ensure((size_t)SUM_BLOCKS * 5));
     k_sums<<<SUM_BLOCKS, SUM_THREADS, 0, st>>>(n, c->d_Q.get(), c->d_partials.get());
-    HYD_CUDA(cudaGetLastError());
+    HYD_CUDA(launch_check());
     k_sums_final<<<1, 32, 0, st>>>(c->d_partials.get(), SUM_BLOCKS, c->d_cnt->sums[which]);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st) {
     const int64_t n = c->plan.n;
     k_export_dQ<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_perm.get(), c->d_Q.get(), c->d_dQ.get(),
                                                    dQ);
-    return cudaGetLastError();
+    return launch_check();
 }
 
 }  // namespace hyd

@@ -83,7 +83,7 @@ class Stats(C.Structure):
 EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_config",
            "hydro_set_boxes", "hydro_reserve", "hydro_build_neighbours", "hydro_density",
            "hydro_gradients", "hydro_fluxes", "hydro_step", "hydro_sync_status",
-           "hydro_get_stats", "hydro_mlp_load", "hydro_strerror"]
+           "hydro_get_stats", "hydro_mlp_load", "hydro_kernel_launches", "hydro_strerror"]
 
 
 def _load():
@@ -110,10 +110,17 @@ def _load():
         L.hydro_sync_status.argtypes = [vp, vp]
         L.hydro_get_stats.argtypes = [vp, P(Stats), vp]
         L.hydro_mlp_load.argtypes = [vp, vp, C.c_size_t]
+        L.hydro_kernel_launches.argtypes = []
+        L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
         L.hydro_strerror.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(_load().hydro_kernel_launches())
 
 
 def default_config(**kw):
