@@ -115,25 +115,43 @@ cudaError_t ensure_state(hydro_ctx *c, int64_t n) {
     return cudaSuccess;
 }
 
-// tree boxes and lists for the current search radii: one staged pass, and
-// the two-pass form when a particle has more candidates than the staging
-// holds or the list storage is too small
+// tree boxes and lists for the current search radii: one pass into the
+// fixed slots, then the count-reserve-fill passes for buckets with a list
+// longer than the slots (with a larger overflow region if it did not fit)
 int lists_all(hydro_ctx *c, cudaStream_t st) {
     API_CUDA(build_tree(c, st));
     API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-    API_CUDA(build_lists(c, 128, st));
+    API_CUDA(build_lists(c, c->nbr_per_particle, st));
     API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaStreamSynchronize(st));
-    int f = c->h_cnt->flags;
-    if (f & ST_STACK) return HYDRO_ECAPACITY;
-    if (f & (ST_LIST_OVERFLOW | ST_LIST_CAPACITY)) {
-        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-        API_CUDA(build_lists_twopass(c, st));
-        int f2 = 0;
-        API_CUDA(cudaMemcpyAsync(&f2, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (c->h_cnt->flags & ST_STACK) return HYDRO_ECAPACITY;
+    int nq = c->h_cnt->ovf_buckets;
+    const int64_t n = c->plan.n;
+    for (int attempt = 0; nq > 0; attempt++) {
+        API_CUDA(build_lists_queued(c, nq, st));
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
-        if (f2 & ST_STACK) return HYDRO_ECAPACITY;
+        int f = c->h_cnt->flags;
+        if (f & ST_STACK) return HYDRO_ECAPACITY;
+        if (!(f & ST_LIST_CAPACITY)) break;
+        if (attempt >= 2) return HYDRO_ECAPACITY;
+        // the overflow region was too small: grow it and redo the queued buckets
+        unsigned long long used = c->h_cnt->list_cursor - (unsigned long long)n * c->list_cap;
+        c->ovf_reserve = (int64_t)(used + used / 4 + 1024);
+        size_t need = (size_t)n * c->list_cap + (size_t)c->ovf_reserve;
+        API_CUDA(c->d_nbr_idx.ensure(need));
+        unsigned long long start = (unsigned long long)n * c->list_cap;
+        API_CUDA(cudaMemcpyAsync(&c->d_cnt->list_cursor, &start, sizeof(start),
+                                 cudaMemcpyHostToDevice, st));
+        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+        // the fixed slots survive a reallocation only if nothing moved; rebuild them
+        API_CUDA(build_lists(c, c->list_cap, st));
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        nq = c->h_cnt->ovf_buckets;
     }
+    // many long lists: give the next builds more fixed slots
+    if (nq > c->plan.nbucket / 16 && c->nbr_per_particle < 256) c->nbr_per_particle += 32;
     c->have_lists = true;
     return HYDRO_OK;
 }
@@ -431,11 +449,10 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     }
     if (timing) API_CUDA(cudaEventRecord(c->ev[3], st));
     const double *dt_dev = dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
-    API_CUDA(run_sums(c, 0, st));
     API_CUDA(run_fluxes(c, dt, dt_dev, st));
     if (timing) API_CUDA(cudaEventRecord(c->ev[4], st));
     API_CUDA(run_update(c, p, dt, dt_dev, st));
-    API_CUDA(run_sums(c, 1, st));
+    if (stats) API_CUDA(run_update_sums(c, st));
     if (timing) API_CUDA(cudaEventRecord(c->ev[5], st));
     c->last_stats.ngb_rounds = rounds;
     c->last_stats.list_rebuilds = rebuilds;

@@ -157,7 +157,7 @@ __device__ __forceinline__ df df_sqrt(df a) {
     float x = sqrtf(a.hi);
     df xx = two_prod(x, x);
     df r = df_sub(a, xx);
-    float corr = r.hi / (2.f * x);
+    float corr = __fdividef(r.hi, 2.f * x);
     return quick_two_sum(x, corr);
 }
 __device__ __forceinline__ df df_div(df a, df b) {
@@ -166,10 +166,16 @@ __device__ __forceinline__ df df_div(df a, df b) {
     float q2 = r.hi / b.hi;
     return quick_two_sum(q1, q2);
 }
+// float-float of a 64-bit integer |v| < 2^62 from three 21-bit pieces,
+// each converted exactly without a conversion instruction
 __device__ __forceinline__ df from_i64(long long v) {
-    float h = (float)v;
-    long long r = v - (long long)h;
-    return {h, (float)r};
+    int32_t hi = (int32_t)(v >> 42);                                   // |hi| < 2^20
+    int32_t mid = (int32_t)(((unsigned long long)v >> 21) & 0x1FFFFFull);
+    int32_t lo = (int32_t)((unsigned long long)v & 0x1FFFFFull);
+    float fh = i2f_small(hi) * 4398046511104.0f;                       // 2^42
+    float fm = i2f_small(mid) * 2097152.0f;                            // 2^21
+    df s = two_sum(fh, fm);
+    return df_add(s, {i2f_small(lo), 0.f});
 }
 
 // ---------------------------------------------------------------- mixed path
@@ -203,7 +209,8 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
             float dx = qdiff(qxi, __float_as_uint(pj.x), bx.s[0]);
             float dy = qdiff(qyi, __float_as_uint(pj.y), bx.s[1]);
             float dz = qdiff(qzi, __float_as_uint(pj.z), bx.s[2]);
-            float q = sqrtf(dx * dx + dy * dy + dz * dz) * ih;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            float q = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * ih;
             float fv, mv;
             kernel_f<float>(a.kernel, q, fv, mv);
             f += fv;

@@ -9,8 +9,18 @@
 //
 // Ownership: particle i computes the pair {i, j} found in its own list
 // (r < h_i) when i < j or when r >= h_j (then j's list does not see i), so
-// each unordered pair is computed exactly once.  The owner accumulates its
-// own -c in double registers; the partner's +c goes through double atomics.
+// each unordered pair is computed exactly once.
+//
+// Work layout: one warp per bucket of 32 owners.  The warp walks the 32
+// neighbour lists in lock-step, tests membership and ownership (cheap), and
+// compacts the owned faces into a shared-memory queue; every 32 queued
+// faces are solved one per lane, so the expensive face arithmetic runs with
+// full lanes regardless of how the faces are spread over the owners.  The
+// owner's -c is gathered back from shared memory into its own register
+// accumulator (float-float in the mixed path, double in FP64); the
+// partner's +c goes to memory through double-precision atomics.
+#include <algorithm>
+
 #include "hydro_internal.cuh"
 #include "pairgeom.cuh"
 #include "riemann.cuh"
@@ -33,7 +43,16 @@ struct FluxArgs {
     double *dQ;              // 5 n, sorted SoA
     DevCounters *cnt;
     const float *mlp;        // learned star-pressure guess (NULL: off)
+    GasK<float> Kf;          // gas constants, precomputed on the host
+    GasK<double> Kd;
+    float psi1f, psi2f, ptolf, lmin_tiny;   // float copies (no per-face conversions)
+    int64_t nbucket;
+    const int32_t *node_first, *node_cnt;
 };
+
+template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
+template <> __device__ __forceinline__ const GasK<float> &gas<float>(const FluxArgs &a) { return a.Kf; }
+template <> __device__ __forceinline__ const GasK<double> &gas<double>(const FluxArgs &a) { return a.Kd; }
 
 namespace {
 
@@ -94,9 +113,7 @@ __device__ __forceinline__ void load4(const R *p, R v[4]) {
 __device__ __forceinline__ bool member_j(float r2, float hjf, const FluxArgs &a, int64_t i,
                                          int64_t j, const Box &bx) {
     float lo = hjf * hjf * (1.0f - 1e-4f), hi = hjf * hjf * (1.0f + 1e-4f);
-    double Lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-    bool tiny = (double)hjf < Lmin * (1.0 / 4096.0);
-    if (!tiny) {
+    if (hjf >= a.lmin_tiny) {
         if (r2 < lo) return true;
         if (r2 > hi) return false;
     }
@@ -116,14 +133,16 @@ struct FaceStats {
 };
 
 // the flux c (mass, momentum, energy) that particle i gives to particle j
-template <typename R>
+template <typename R, int RIEM, int SCHEME>
 __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, const R *ri,
-                                          const R *rj, const R d[3], R r, R norm_i, R ih_i,
-                                          R dt, R c[5], FaceStats &fs) {
+                                          const R *rj, const R d[3], R r, R dt, R c[5],
+                                          FaceStats &fs) {
     c[0] = c[1] = c[2] = c[3] = c[4] = R(0);
-    const R wi = norm_i * kernel_shape<R>(a.kernel, r * ih_i);
-    const R hj = rj[R_H];
-    const R wj = kernel_norm<R>(a.kernel, hj) * kernel_shape<R>(a.kernel, r / hj);
+    const R pi = R(3.14159265358979323846);
+    const R hi_ = ri[R_H], hj = rj[R_H];
+    const R kn = a.kernel == 0 ? R(21) / (R(2) * pi) : R(8) / pi;
+    const R wi = div_(kn, hi_ * hi_ * hi_) * kernel_shape<R>(a.kernel, div_(r, hi_));
+    const R wj = div_(kn, hj * hj * hj) * kernel_shape<R>(a.kernel, div_(r, hj));
     const R *Bi = ri + R_B, *Bj = rj + R_B;
     R A[3];
     {
@@ -138,9 +157,9 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
         A[1] = oo * (ti1 * wi + tj1 * wj);
         A[2] = oo * (ti2 * wi + tj2 * wj);
     }
-    R Amag = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+    R Amag = sqrt_(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
     if (!(Amag > R(0))) return;
-    const R inA = R(1) / Amag;
+    const R inA = div_(R(1), Amag);
     const R nh[3] = {A[0] * inA, A[1] * inA, A[2] * inA};
 
     R Lf[5], Rf[5];
@@ -151,7 +170,8 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
         Rf[f] = rj[R_RHO + f] - R(0.5) * (d[0] * Gj[3 * f] + d[1] * Gj[3 * f + 1] + d[2] * Gj[3 * f + 2]);
     }
     if (a.limiter) {
-        const R p1 = (R)a.psi1, p2 = (R)a.psi2;
+        const R p1 = sizeof(R) == 4 ? (R)a.psi1f : (R)a.psi1;
+        const R p2 = sizeof(R) == 4 ? (R)a.psi2f : (R)a.psi2;
 #pragma unroll
         for (int f = 0; f < 5; f++) {
             bool pos = (f == 0 || f == 4);
@@ -166,10 +186,11 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
         R divj = Gj[3] + Gj[7] + Gj[11];
         Lf[0] -= hdt * ri[R_RHO] * divi;
         Rf[0] -= hdt * rj[R_RHO] * divj;
+        const R iri = div_(hdt, ri[R_RHO]), irj = div_(hdt, rj[R_RHO]);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            Lf[1 + q] -= hdt * Gi[12 + q] / ri[R_RHO];
-            Rf[1 + q] -= hdt * Gj[12 + q] / rj[R_RHO];
+            Lf[1 + q] -= Gi[12 + q] * iri;
+            Rf[1 + q] -= Gj[12 + q] * irj;
         }
         Lf[4] -= hdt * g * ri[R_P] * divi;
         Rf[4] -= hdt * g * rj[R_P] * divj;
@@ -192,21 +213,21 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
     const R rl = Lf[0], pl = Lf[4], rr = Rf[0], pr = Rf[4];
 
     R F[5];
-    if (a.riemann == HYDRO_RIEMANN_HLLC) {
+    if (RIEM == HYDRO_RIEMANN_HLLC) {
         R ps, ss;
         hllc_flux<R>(K, rl, ul, pl, wl, rr, ur, pr, wr, nh, F, ps, ss);
-        if (a.scheme == HYDRO_MFM) {
+        if (SCHEME == HYDRO_MFM) {
             F[0] = R(0);
             F[1] = ps * nh[0]; F[2] = ps * nh[1]; F[3] = ps * nh[2];
             F[4] = ps * ss;
         }
     } else {
         R ps, us;
-        R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)fmax(a.p_tol, 2e-6);
+        R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)a.ptolf;
         StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, R(-1), tol, a.max_newton, ps, us);
         fs.iters += so.iters;
         if (so.vacuum) { fs.vacuum++; return; }
-        if (a.scheme == HYDRO_MFM) {
+        if (SCHEME == HYDRO_MFM) {
             F[0] = R(0);
             F[1] = ps * nh[0]; F[2] = ps * nh[1]; F[3] = ps * nh[2];
             F[4] = ps * us;
@@ -214,14 +235,16 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
             R rs, uu, pp;
             int side;
             star_sample<R>(K, rl, ul, pl, rr, ur, pr, ps, us, rs, uu, pp, side);
-            const R *wt = side < 0 ? wl : wr;
-            R v2 = uu * uu + wt[0] * wt[0] + wt[1] * wt[1] + wt[2] * wt[2];
-            R et = R(0.5) * rs * v2 + pp / K.gm1;
+            R w0 = side < 0 ? wl[0] : wr[0];
+            R w1 = side < 0 ? wl[1] : wr[1];
+            R w2 = side < 0 ? wl[2] : wr[2];
+            R v2 = uu * uu + w0 * w0 + w1 * w1 + w2 * w2;
+            R et = R(0.5) * rs * v2 + div_(pp, K.gm1);
             R m = rs * uu;
             F[0] = m;
-            F[1] = m * (uu * nh[0] + wt[0]) + pp * nh[0];
-            F[2] = m * (uu * nh[1] + wt[1]) + pp * nh[1];
-            F[3] = m * (uu * nh[2] + wt[2]) + pp * nh[2];
+            F[1] = m * (uu * nh[0] + w0) + pp * nh[0];
+            F[2] = m * (uu * nh[1] + w1) + pp * nh[1];
+            F[3] = m * (uu * nh[2] + w2) + pp * nh[2];
             F[4] = uu * (et + pp);
         }
     }
@@ -236,60 +259,190 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
     c[4] = sA * Fe;
 }
 
+// float -> double from the bit pattern with integer operations (exact for
+// normal floats; the conversion instruction would use the FP64 pipe)
+__device__ __forceinline__ double widen(float f) {
+    uint32_t u = __float_as_uint(f);
+    uint32_t ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;   // zero, subnormal, inf, nan
+    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                           ((unsigned long long)(ex + 896u) << 52) |
+                           ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
+// owner accumulators: float-float (value = hi + lo) in the mixed path
+struct AccF {
+    float hi[5], lo[5];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < 5; q++) hi[q] = lo[q] = 0.f;
+    }
+    __device__ __forceinline__ void sub(int q, float v) {
+        float a = hi[q], b = -v;
+        float s = a + b;
+        float bb = s - a;
+        float e = (a - (s - bb)) + (b - bb);
+        hi[q] = s;
+        lo[q] += e;
+    }
+    __device__ __forceinline__ double get(int q) const { return (double)hi[q] + (double)lo[q]; }
+};
+struct AccD {
+    double v[5];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < 5; q++) v[q] = 0.0;
+    }
+    __device__ __forceinline__ void sub(int q, double x) { v[q] -= x; }
+    __device__ __forceinline__ double get(int q) const { return v[q]; }
+};
+template <typename R> struct AccOf;
+template <> struct AccOf<float> { using T = AccF; };
+template <> struct AccOf<double> { using T = AccD; };
+
 __device__ __forceinline__ unsigned long long wsum(unsigned long long v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
+constexpr int FLUX_WARPS = 4;
+constexpr int QCAP = 64;
+
 template <typename R>
-__global__ void __launch_bounds__(128) k_fluxes(FluxArgs a, const R *__restrict__ rec) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct FluxSmem {
+    R own[32][REC + 1];        // the bucket's records (padded: no bank conflicts)
+    R cb[32][5];               // solved faces' c, read back by the owners
+    int32_t qj[QCAP];          // queued faces: partner j
+    uint8_t qo[QCAP];          // queued faces: owner lane
+};
+
+template <typename R, int RIEM, int SCHEME>
+__global__ void __launch_bounds__(FLUX_WARPS * 32, sizeof(R) == 4 ? 4 : 2)
+k_fluxes(FluxArgs a, const R *__restrict__ rec) {
+    __shared__ FluxSmem<R> sm_all[FLUX_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FluxSmem<R> &sm = sm_all[warp];
+    const int64_t b = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
-    if (s < a.n) {
+    if (b < a.nbucket) {
+        const int f = a.node_first[b], nown = a.node_cnt[b];
+        const bool own = lane < nown;
+        const int s = f + (own ? lane : 0);
         const Box bx = a.boxes[a.pbox[s]];
-        R ri[REC];
-        load_full<R>(rec + s * REC, ri);
-        const double hd = a.h[s];
-        Member mem;
-        mem.init(a.xs, a.ys, a.zs, s, hd, bx);
-        const R h = ri[R_H];
-        const R ih = R(1) / h;
-        const R norm = kernel_norm<R>(a.kernel, h);
-        const GasK<R> K(a.gamma);
+        const GasK<R> &K = gas<R>(a);
         const R dt = (R)(a.dt_dev ? *a.dt_dev : a.dt);
-        double acc[5] = {0, 0, 0, 0, 0};
-        const int64_t o = a.nbr_off[s];
-        const int cnt = a.nbr_cnt[s];
-        for (int k = 0; k < cnt; k++) {
-            const int j = a.nbr_idx[o + k];
-            if (j == s) continue;
-            R rj[REC];
-            load4<R>(rec + (int64_t)j * REC, rj);
-            R d[3], r2;
-            rec_sep(ri, rj, bx, d, r2);
-            if (!mem(r2, j)) continue;
-            if (j < s && member_j(r2, rj[R_H], a, s, j, bx)) continue;   // j owns the pair
-            load_full<R>(rec + (int64_t)j * REC, rj);
-            R c[5];
-            face_flux<R>(a, K, ri, rj, d, sqrt(r2), norm, ih, dt, c, fs);
-            fs.pairs++;
+        // stage the owners' records
+        {
+            R v[REC];
+            load_full<R>(rec + (int64_t)s * REC, v);
 #pragma unroll
-            for (int q = 0; q < 5; q++) {
-                acc[q] -= (double)c[q];
-                atomicAdd(&a.dQ[q * a.n + j], (double)c[q]);
+            for (int k = 0; k < REC; k++) sm.own[lane][k] = v[k];
+        }
+        Member mem;
+        mem.init(a.xs, a.ys, a.zs, s, a.h[s], bx);
+        typename AccOf<R>::T acc;
+        acc.zero();
+        const int64_t o = a.nbr_off[s];
+        const int cnt = own ? a.nbr_cnt[s] : 0;
+        int maxc = cnt;
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, m));
+        const unsigned lt = (1u << lane) - 1u;
+        int qn = 0;
+        __syncwarp();
+
+        // solve the first nb queued faces, one per lane, and hand -c back
+        auto solve = [&](int nb) {
+            R c[5] = {R(0), R(0), R(0), R(0), R(0)};
+            int ol = 255;
+            if (lane < nb) {
+                ol = sm.qo[lane];
+                const int j = sm.qj[lane];
+                R rj[REC];
+                load_full<R>(rec + (int64_t)j * REC, rj);
+                const R *ri = sm.own[ol];
+                R d[3], r2;
+                rec_sep(ri, rj, bx, d, r2);
+                face_flux<R, RIEM, SCHEME>(a, K, ri, rj, d, sqrt_(r2), dt, c, fs);
+                fs.pairs++;
+#pragma unroll
+                for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + j], widen(c[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 5; q++) sm.cb[lane][q] = c[q];
+            __syncwarp();
+            for (int t = 0; t < nb; t++) {
+                if (sm.qo[t] == lane) {
+#pragma unroll
+                    for (int q = 0; q < 5; q++) acc.sub(q, sm.cb[t][q]);
+                }
+            }
+            __syncwarp();
+        };
+
+        for (int k = 0; k < maxc; k++) {
+            bool has = false;
+            int j = 0;
+            if (k < cnt) {
+                j = a.nbr_idx[o + k];
+                if (j != s) {
+                    R rj4[4];
+                    load4<R>(rec + (int64_t)j * REC, rj4);
+                    R d[3], r2;
+                    rec_sep(&sm.own[lane][0], rj4, bx, d, r2);
+                    if (mem(r2, j)) has = (j > s) || !member_j(r2, rj4[R_H], a, s, j, bx);
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            if (has) {
+                int pos = qn + __popc(m & lt);
+                sm.qj[pos] = j;
+                sm.qo[pos] = (uint8_t)lane;
+            }
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                solve(32);
+                // move the remainder to the front
+                int rest = qn - 32;
+                int tj = 0;
+                uint8_t to = 0;
+                if (lane < rest) { tj = sm.qj[32 + lane]; to = sm.qo[32 + lane]; }
+                __syncwarp();
+                if (lane < rest) { sm.qj[lane] = tj; sm.qo[lane] = to; }
+                qn = rest;
+                __syncwarp();
             }
         }
+        if (qn > 0) solve(qn);
+        if (own) {
 #pragma unroll
-        for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + s], acc[q]);
+            for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + s], acc.get(q));
+        }
     }
     unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
                        fo = wsum(fs.first_order);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         if (p) atomicAdd(&a.cnt->flux_pairs, p);
         if (it) atomicAdd(&a.cnt->newton_iters, it);
         if (va) atomicAdd(&a.cnt->vacuum, va);
         if (fo) atomicAdd(&a.cnt->first_order, fo);
     }
+}
+
+template <typename R>
+cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, stream_t st) {
+    unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if (riem == HYDRO_RIEMANN_HLLC) {
+        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    } else {
+        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFM><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    }
+    return launch_check();
 }
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -326,11 +479,23 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.dQ = c->d_dQ.get();
     a.cnt = c->d_cnt;
     a.mlp = nullptr;
+    a.psi1f = (float)c->cfg.psi1;
+    a.psi2f = (float)c->cfg.psi2;
+    a.ptolf = (float)std::max(c->cfg.p_tol, 2e-6);
+    {
+        // below h = Lmin / 4096 every membership is decided in double
+        double lmin = 1e300;
+        for (size_t k = 0; k < c->plan.box_len.size(); k++) lmin = std::min(lmin, c->plan.box_len[k]);
+        a.lmin_tiny = (float)(lmin / 4096.0);
+    }
+    a.Kf = GasK<float>(c->cfg.gamma);
+    a.Kd = GasK<double>(c->cfg.gamma);
+    a.nbucket = c->plan.nbucket;
+    a.node_first = c->d_node_first.get();
+    a.node_cnt = c->d_node_cnt.get();
     if (c->cfg.precision == HYDRO_MIXED)
-        k_fluxes<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
-    else
-        k_fluxes<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
-    return launch_check();
+        return launch_fluxes<float>(a, c->d_recf.get(), c->cfg.riemann, c->cfg.scheme, st);
+    return launch_fluxes<double>(a, c->d_recd.get(), c->cfg.riemann, c->cfg.scheme, st);
 }
 
 }  // namespace hyd

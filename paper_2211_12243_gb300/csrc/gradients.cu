@@ -140,10 +140,19 @@ __global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ r
             Bd[3] = (e00 * e22 - e02 * e02) * id;
             Bd[4] = (e02 * e01 - e00 * e12) * id;
             Bd[5] = (e00 * e11 - e01 * e01) * id;
-            double nE = e00 * e00 + e11 * e11 + e22 * e22 + 2.0 * (e01 * e01 + e02 * e02 + e12 * e12);
-            double nB = Bd[0] * Bd[0] + Bd[3] * Bd[3] + Bd[5] * Bd[5] +
-                        2.0 * (Bd[1] * Bd[1] + Bd[2] * Bd[2] + Bd[4] * Bd[4]);
-            ncond = sqrt(nB * nE) / 3.0;
+            if (sizeof(R) == 8) {
+                double nE = e00 * e00 + e11 * e11 + e22 * e22 + 2.0 * (e01 * e01 + e02 * e02 + e12 * e12);
+                double nB = Bd[0] * Bd[0] + Bd[3] * Bd[3] + Bd[5] * Bd[5] +
+                            2.0 * (Bd[1] * Bd[1] + Bd[2] * Bd[2] + Bd[4] * Bd[4]);
+                ncond = sqrt(nB * nE) / 3.0;
+            } else {
+                // N_cond only feeds the threshold test and the limiter's beta
+                float b0 = (float)Bd[0], b1 = (float)Bd[1], b2 = (float)Bd[2], b3 = (float)Bd[3],
+                      b4 = (float)Bd[4], b5 = (float)Bd[5];
+                float nE = E[0] * E[0] + E[3] * E[3] + E[5] * E[5] + 2.f * (E[1] * E[1] + E[2] * E[2] + E[4] * E[4]);
+                float nB = b0 * b0 + b3 * b3 + b5 * b5 + 2.f * (b1 * b1 + b2 * b2 + b4 * b4);
+                ncond = (double)(sqrtf(nB * nE) * (1.f / 3.f));
+            }
         } else {
             for (int k = 0; k < 6; k++) Bd[k] = 0.0;
             ncond = INFINITY;
@@ -180,9 +189,9 @@ __global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ r
                     dm[f] = e < dm[f] ? e : dm[f];
                 }
             }
-            double ratio = a.ncond_crit / ncond;
-            double beta = a.beta_max * fmin(ratio * ratio, 1.0);
-            beta = fmax(beta, a.beta_min);
+            R ratio = (R)a.ncond_crit / (R)ncond;
+            R beta = (R)a.beta_max * (ratio * ratio < R(1) ? ratio * ratio : R(1));
+            beta = beta > (R)a.beta_min ? beta : (R)a.beta_min;
 #pragma unroll
             for (int f = 0; f < 5; f++) {
                 R rp = dp[f] > R(0) ? (fmx[f] - fi[f]) / dp[f] : R(INFINITY);
@@ -211,7 +220,8 @@ __global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ r
         if (a.outN) a.outN[s] = ncond;
         // CFL timestep of Eq. 31 with the signal velocity of Eq. 32
         if (vs > R(0)) {
-            double dti = a.c_cfl * hd / (double)vs;
+            double dti = sizeof(R) == 8 ? a.c_cfl * hd / (double)vs
+                                        : (double)((float)a.c_cfl * (float)hd / (float)vs);
             atomicMin(&a.cnt->dt_min_bits, (unsigned long long)__double_as_longlong(dti));
         }
         // N_cond guard (§2.3.5)
@@ -234,17 +244,33 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
     double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
     double E = Q[4 * n + s], U = Q[5 * n + s];
     double w = om[s];
-    double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
-    double therm = U;
-    if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
     R *r = rec + s * REC;
-    r[R_H] = (R)h[s];
-    r[R_RHO] = (R)(m / w);
-    r[R_VX] = (R)(px / m);
-    r[R_VY] = (R)(py / m);
-    r[R_VZ] = (R)(pz / m);
-    r[R_P] = (R)(therm * gm1 / w);
-    r[R_OM] = (R)w;
+    if (sizeof(R) == 8) {
+        double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
+        double therm = U;
+        if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
+        r[R_H] = (R)h[s];
+        r[R_RHO] = (R)(m / w);
+        r[R_VX] = (R)(px / m);
+        r[R_VY] = (R)(py / m);
+        r[R_VZ] = (R)(pz / m);
+        r[R_P] = (R)(therm * gm1 / w);
+        r[R_OM] = (R)w;
+    } else {
+        // float record: only E - E_kin needs double (cancellation)
+        double im = 1.0 / m;
+        double ekin = 0.5 * (px * px + py * py + pz * pz) * im;
+        double therm = U;
+        if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
+        float wf = (float)w, imf = (float)im;
+        r[R_H] = (R)h[s];
+        r[R_RHO] = (R)((float)m / wf);
+        r[R_VX] = (R)((float)px * imf);
+        r[R_VY] = (R)((float)py * imf);
+        r[R_VZ] = (R)((float)pz * imf);
+        r[R_P] = (R)((float)therm * (float)gm1 / wf);
+        r[R_OM] = (R)wf;
+    }
 }
 
 // N_NGB *= grow for particles that failed the N_cond check; they (only)

@@ -64,7 +64,7 @@ struct DevCounters {
     int flags;                        // ST_* bits
     int search_fail;                  // particles whose h left the radius
     int ncond_fail;                   // particles above the N_cond threshold
-    int pad0;
+    int ovf_buckets;                  // buckets queued for the long-list passes
     unsigned long long grad_pairs;
     unsigned long long flux_pairs;
     unsigned long long newton_iters;
@@ -121,7 +121,9 @@ struct hydro_ctx {
     bool have_plan = false;
     bool have_lists = false;
     int64_t list_n = 0;
-    int nbr_per_particle = 64;
+    int nbr_per_particle = 64;        // fixed slots per particle in nbr_idx
+    int list_cap = 64;                // slots used by the current lists
+    int64_t ovf_reserve = 0;          // entries kept for the overflow region
 
     // plan on device
     hyd::DevBuf<int32_t> d_node_first, d_node_cnt, d_node_box, d_box_root;
@@ -154,6 +156,7 @@ struct hydro_ctx {
     hyd::DevBuf<int32_t> d_nbr_idx;
     hyd::DevBuf<int64_t> d_nbr_off;
     hyd::DevBuf<int32_t> d_nbr_cnt;
+    hyd::DevBuf<int32_t> d_ovf;       // bucket ids with long lists
 
     // reductions
     hyd::DevBuf<double> d_partials;
@@ -198,7 +201,7 @@ cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n
 // neighbours.cu
 cudaError_t build_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
-cudaError_t build_lists_twopass(hydro_ctx *c, stream_t st);
+cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu
@@ -220,6 +223,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
                        stream_t st);
 cudaError_t run_sums(hydro_ctx *c, int which, stream_t st);
+cudaError_t run_update_sums(hydro_ctx *c, stream_t st);
 cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st);
 
 }  // namespace hyd
@@ -245,8 +249,20 @@ __device__ __forceinline__ double r2_exact(double dx, double dy, double dz) {
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// int32 -> float for |k| < 2^22 by placing k in the mantissa of 1.5 * 2^23:
+// an integer add and a float subtract instead of a conversion instruction
+// (conversions share GB300's narrow FP64 pipe)
+__device__ __forceinline__ float i2f_small(int32_t k) {
+    return __int_as_float(0x4B400000 + k) - 12582912.0f;
+}
+
+// minimum-image separation b - a of two fixed-point coordinates, times the
+// unit s: the 32-bit difference split as hi * 2^11 + lo, each part exact
 __device__ __forceinline__ float qdiff(uint32_t a, uint32_t b, float s) {
-    return (float)(int32_t)(b - a) * s;
+    int32_t d = (int32_t)(b - a);
+    int32_t hi = d >> 11;
+    int32_t lo = d & 0x7FF;
+    return fmaf(i2f_small(hi), s * 2048.0f, i2f_small(lo) * s);
 }
 
 // Kernel normalised sums used by the density iteration:

@@ -84,22 +84,24 @@ __global__ void k_aabb_node(int64_t node0, int64_t nnode, const int32_t *__restr
     }
 }
 
-// smallest periodic gap (fixed-point units) between [a0,a1] and [b0,b1]
-__device__ __forceinline__ float axis_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
-    const long long P = 1ll << 32;
-    long long d1 = (long long)b0 - (long long)a1;
-    long long d2 = (long long)a0 - (long long)b1;
-    long long g0 = max(0ll, max(d1, d2));
-    long long g1 = max(0ll, max(d1 + P, d2 - P));
-    long long g2 = max(0ll, max(d1 - P, d2 + P));
-    return (float)min(g0, min(g1, g2));
+// Lower bound of the periodic distance (fixed-point units) between the
+// intervals [a0,a1] and [b0,b1] on the circle of 2^32 units: the circular
+// distance of the centres minus both half-widths (rounded up), in 32-bit
+// integers only (64-bit conversions would run on the FP64 pipe).
+__device__ __forceinline__ uint32_t axis_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+    uint32_t wa = (a1 - a0 + 1u) >> 1, wb = (b1 - b0 + 1u) >> 1;
+    uint32_t ca = a0 + ((a1 - a0) >> 1), cb = b0 + ((b1 - b0) >> 1);
+    int32_t dc = (int32_t)(cb - ca);
+    uint32_t d = dc < 0 ? (uint32_t)(-(int64_t)dc) : (uint32_t)dc;
+    uint32_t w = wa + wb + 2u;
+    return d > w ? d - w : 0u;
 }
 
 __device__ __forceinline__ bool boxes_near(uint4 alo, uint4 ahi, uint4 blo, uint4 bhi,
                                            const Box &bx, float rad2) {
-    float gx = axis_gap(alo.x, ahi.x, blo.x, bhi.x) * bx.s[0];
-    float gy = axis_gap(alo.y, ahi.y, blo.y, bhi.y) * bx.s[1];
-    float gz = axis_gap(alo.z, ahi.z, blo.z, bhi.z) * bx.s[2];
+    float gx = (float)axis_gap(alo.x, ahi.x, blo.x, bhi.x) * bx.s[0];
+    float gy = (float)axis_gap(alo.y, ahi.y, blo.y, bhi.y) * bx.s[1];
+    float gz = (float)axis_gap(alo.z, ahi.z, blo.z, bhi.z) * bx.s[2];
     return gx * gx + gy * gy + gz * gz <= rad2;
 }
 
@@ -117,98 +119,188 @@ struct ListArgs {
     int64_t capacity;
     DevCounters *cnt;
     int cap;   // per-lane staging entries
-    int mode;  // 0: stage in shared memory, one bulk write; 1: count only;
-               // 2: write at nbr_off (from a scan of the counts)
+    int mode;  // 0: stage in shared memory, one bulk write (buckets whose
+               //    lists overflow the staging are queued in ovf_list);
+               // 1: count and reserve storage (queued buckets);
+               // 2: write at nbr_off (queued buckets)
+    int32_t *ovf_list;      // queued bucket ids
+    int *ovf_count;
 };
 
-// stage a candidate bucket in shared memory and test it against all lanes
-__device__ __forceinline__ void test_bucket(const ListArgs &a, int cb, int lane, bool own,
-                                            int s_own, uint32_t qxi, uint32_t qyi, uint32_t qzi, double xi,
-                                            double yi, double zi, double hsi, float lo2,
-                                            float hi2, bool always_exact, const Box &bx,
-                                            double *sx, double *sy, double *sz, uint32_t *sq,
-                                            int32_t *list, int &count) {
-    int f = a.node_first[cb], c = a.node_cnt[cb];
-    __syncwarp();
-    if (lane < c) {
-        int j = f + lane;
-        sx[lane] = a.xs[j];
-        sy[lane] = a.ys[j];
-        sz[lane] = a.zs[j];
-        sq[lane] = a.qx[j];
-        sq[32 + lane] = a.qy[j];
-        sq[64 + lane] = a.qz[j];
+__device__ __forceinline__ float u2f(uint32_t v) {
+    return fmaf(i2f_small((int32_t)(v >> 11)), 2048.0f, i2f_small((int32_t)(v & 0x7FFu)));
+}
+
+// Per-lane state of the walk: the owner particle, its position relative to
+// the bucket's corner (float), and the exact-test data.
+struct Lane {
+    bool own;
+    int s;
+    uint32_t qx, qy, qz;
+    float rx, ry, rz;        // relative to the warp's origin
+    double x, y, z, hs, h2;
+    float lo2, hi2;          // float band around hs^2 (lo2 < 0 < hi2 = inf: always exact)
+    bool rel_ok;             // bucket extent + radius < L/4: relative coordinates are exact images
+};
+
+// circular gap (fixed-point units) between a point and an interval
+__device__ __forceinline__ uint32_t point_gap(uint32_t p, uint32_t b0, uint32_t b1) {
+    uint32_t w = (b1 - b0 + 1u) >> 1, c = b0 + ((b1 - b0) >> 1);
+    int32_t d = (int32_t)(c - p);
+    uint32_t e = d < 0 ? 0u - (uint32_t)d : (uint32_t)d;
+    return e > w + 2u ? e - w - 2u : 0u;
+}
+
+// does the lane's sphere reach the box?
+__device__ __forceinline__ bool sphere_near(const Lane &L, uint4 blo, uint4 bhi, const Box &bx) {
+    float gx = u2f(point_gap(L.qx, blo.x, bhi.x)) * bx.s[0];
+    float gy = u2f(point_gap(L.qy, blo.y, bhi.y)) * bx.s[1];
+    float gz = u2f(point_gap(L.qz, blo.z, bhi.z)) * bx.s[2];
+    return L.own && gx * gx + gy * gy + gz * gz <= L.hi2;
+}
+
+// one staged candidate particle (registers of the lane that loads it)
+struct Cand {
+    double x, y, z;
+    uint32_t qx, qy, qz;
+};
+
+__device__ __forceinline__ void cand_load(const ListArgs &a, int j, Cand &c) {
+    c.x = a.xs[j]; c.y = a.ys[j]; c.z = a.zs[j];
+    c.qx = a.qx[j]; c.qy = a.qy[j]; c.qz = a.qz[j];
+}
+
+struct Stage {
+    double *sx, *sy, *sz;
+    float4 *sr;
+    uint32_t *sq;
+};
+
+__device__ __forceinline__ void cand_store(const Stage &S, int lane, const Cand &c, uint32_t ox,
+                                           uint32_t oy, uint32_t oz, const Box &bx) {
+    S.sx[lane] = c.x; S.sy[lane] = c.y; S.sz[lane] = c.z;
+    S.sq[lane] = c.qx; S.sq[32 + lane] = c.qy; S.sq[64 + lane] = c.qz;
+    S.sr[lane] = make_float4(qdiff(ox, c.qx, bx.s[0]), qdiff(oy, c.qy, bx.s[1]),
+                             qdiff(oz, c.qz, bx.s[2]), 0.f);
+}
+
+// decide candidate k of the staged bucket for this lane
+__device__ __forceinline__ void decide(const ListArgs &a, const Lane &L, const Stage &S, const Box &bx,
+                                       int f, int k, float r2, int &count) {
+    bool in;
+    if (r2 < L.lo2) in = true;
+    else if (r2 > L.hi2) in = false;
+    else {
+        double ex = fold64(__dsub_rn(S.sx[k], L.x), bx.L[0]);
+        double ey = fold64(__dsub_rn(S.sy[k], L.y), bx.L[1]);
+        double ez = fold64(__dsub_rn(S.sz[k], L.z), bx.L[2]);
+        in = r2_exact(ex, ey, ez) < L.h2;
     }
-    __syncwarp();
-    if (!own) return;
-    double h2 = __dmul_rn(hsi, hsi);
-    for (int k = 0; k < c; k++) {
-        bool in;
-        if (!always_exact) {
-            float dx = qdiff(qxi, sq[k], bx.s[0]);
-            float dy = qdiff(qyi, sq[32 + k], bx.s[1]);
-            float dz = qdiff(qzi, sq[64 + k], bx.s[2]);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < lo2) in = true;
-            else if (r2 > hi2) in = false;
-            else {
-                double ex = fold64(__dsub_rn(sx[k], xi), bx.L[0]);
-                double ey = fold64(__dsub_rn(sy[k], yi), bx.L[1]);
-                double ez = fold64(__dsub_rn(sz[k], zi), bx.L[2]);
-                in = r2_exact(ex, ey, ez) < h2;
-            }
-        } else {
-            double ex = fold64(__dsub_rn(sx[k], xi), bx.L[0]);
-            double ey = fold64(__dsub_rn(sy[k], yi), bx.L[1]);
-            double ez = fold64(__dsub_rn(sz[k], zi), bx.L[2]);
-            in = r2_exact(ex, ey, ez) < h2;
+    if (in) {
+        if (a.mode == 0) {
+            if (count < a.cap) a.nbr_idx[(int64_t)L.s * a.cap + count] = f + k;
+        } else if (a.mode == 2) {
+            // storage was reserved in mode 1; a reservation that did not
+            // fit (the capacity flag is set and the host rebuilds) must
+            // not write past the buffer
+            int64_t pos = a.nbr_off[L.s] + count;
+            if (pos < a.capacity) a.nbr_idx[pos] = f + k;
         }
-        if (in) {
-            if (a.mode == 0) {
-                if (count < a.cap) list[count * 32 + lane] = f + k;
-            } else if (a.mode == 2) {
-                a.nbr_idx[a.nbr_off[s_own] + count] = f + k;
+        count++;
+    }
+}
+
+// every lane scans the c staged candidates (four at a time for overlap)
+__device__ __forceinline__ void scan_stage(const ListArgs &a, const Lane &L, const Stage &S,
+                                           const Box &bx, int f, int c, int &count) {
+    if (!L.own) return;
+    if (L.rel_ok) {
+        for (int k = 0; k < c; k += 4) {
+            float r2[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                float4 r = S.sr[k + u];
+                float dx = r.x - L.rx, dy = r.y - L.ry, dz = r.z - L.rz;
+                r2[u] = dx * dx + dy * dy + dz * dz;
             }
-            count++;
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (k + u < c) decide(a, L, S, bx, f, k + u, r2[u], count);
+        }
+    } else {
+        for (int k = 0; k < c; k++) {
+            float dx = qdiff(L.qx, S.sq[k], bx.s[0]);
+            float dy = qdiff(L.qy, S.sq[32 + k], bx.s[1]);
+            float dz = qdiff(L.qz, S.sq[64 + k], bx.s[2]);
+            decide(a, L, S, bx, f, k, dx * dx + dy * dy + dz * dz, count);
         }
     }
 }
 
-__global__ void k_build_lists(ListArgs a) {
-    extern __shared__ unsigned char smem_raw[];
+__global__ void __launch_bounds__(LIST_WARPS * 32, 6) k_build_lists(ListArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x * (int64_t)LIST_WARPS + warp;
-    // per-warp shared memory: list[cap][32] | stack[STACK] | sx sy sz [32] | sq[96]
-    size_t per_warp = (size_t)a.cap * 32 * 4 + STACK * 4 + 3 * 32 * 8 + 96 * 4;
-    unsigned char *base = smem_raw + per_warp * warp;   // cap = 0 in modes 1, 2
-    int32_t *list = (int32_t *)base;
-    int32_t *stack = (int32_t *)(base + (size_t)a.cap * 32 * 4);
-    double *sx = (double *)(base + (size_t)a.cap * 32 * 4 + STACK * 4);
-    double *sy = sx + 32;
-    double *sz = sy + 32;
-    uint32_t *sq = (uint32_t *)(sz + 32);
+    int64_t b = blockIdx.x * (int64_t)LIST_WARPS + warp;
+    // per-warp shared memory: stack[STACK] | 2 x (sr[32] float4 | sx sy sz [32] | sq[96])
+    size_t per_warp = STACK * 4 + 2 * (32 * 16 + 3 * 32 * 8 + 96 * 4);
+    unsigned char *base = smem_raw + per_warp * warp;
+    int32_t *stack = (int32_t *)base;
+    // the two staging buffers, addressed arithmetically (no local array)
+    auto stage = [&](int t) {
+        unsigned char *p = base + STACK * 4 + t * (32 * 16 + 3 * 32 * 8 + 96 * 4);
+        Stage st;
+        st.sr = (float4 *)p;
+        st.sx = (double *)(p + 32 * 16);
+        st.sy = st.sx + 32;
+        st.sz = st.sy + 32;
+        st.sq = (uint32_t *)(st.sz + 32);
+        return st;
+    };
     if (b >= a.nbucket) return;
+    if (a.mode != 0) b = a.ovf_list[b];
 
     const int f = a.node_first[b], c = a.node_cnt[b];
     const Box bx = a.boxes[a.node_box[b]];
-    const bool own = lane < c;
-    const int s = f + (own ? lane : 0);
-    uint32_t qxi = a.qx[s], qyi = a.qy[s], qzi = a.qz[s];
-    double xi = a.xs[s], yi = a.ys[s], zi = a.zs[s], hsi = a.hs[s];
-    float hf = (float)hsi;
-    float lo2 = hf * hf * (1.0f - 1e-4f), hi2 = hf * hf * (1.0f + 1e-4f);
-    const double Lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-    bool always_exact = hsi < Lmin * (1.0 / 4096.0);
     const uint4 qlo = a.lo[b], qhi = a.hi[b];
+    const uint32_t ox = qlo.x, oy = qlo.y, oz = qlo.z;   // the warp's origin
+    Lane L;
+    L.own = lane < c;
+    L.s = f + (L.own ? lane : 0);
+    L.qx = a.qx[L.s]; L.qy = a.qy[L.s]; L.qz = a.qz[L.s];
+    L.rx = qdiff(ox, L.qx, bx.s[0]);
+    L.ry = qdiff(oy, L.qy, bx.s[1]);
+    L.rz = qdiff(oz, L.qz, bx.s[2]);
+    L.x = a.xs[L.s]; L.y = a.ys[L.s]; L.z = a.zs[L.s]; L.hs = a.hs[L.s];
+    L.h2 = __dmul_rn(L.hs, L.hs);
+    {
+        float hf = (float)L.hs;
+        L.lo2 = hf * hf * (1.0f - 1e-4f);
+        L.hi2 = hf * hf * (1.0f + 1e-4f);
+        const double Lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+        if (L.hs < Lmin * (1.0 / 4096.0)) { L.lo2 = -1.0f; L.hi2 = 3.0e38f; }
+    }
     const float qh = __uint_as_float(qlo.w) * 1.00001f;
     const float rad2 = qh * qh;
+    {
+        // relative coordinates from the bucket corner give exact minimum
+        // images while every candidate that can be inside lies within L/4
+        float ex = u2f(qhi.x - qlo.x) * bx.s[0], ey = u2f(qhi.y - qlo.y) * bx.s[1],
+              ez = u2f(qhi.z - qlo.z) * bx.s[2];
+        L.rel_ok = ex + 2.f * qh < 0.25f * (float)bx.L[0] && ey + 2.f * qh < 0.25f * (float)bx.L[1] &&
+                   ez + 2.f * qh < 0.25f * (float)bx.L[2];
+    }
     int count = 0;
 
     int sp = 0;
     int root = a.box_root[a.node_box[b]];
     if (root < a.nbucket_total) {
-        test_bucket(a, root, lane, own, s, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2, always_exact,
-                    bx, sx, sy, sz, sq, list, count);
+        // the whole box is one bucket
+        Cand cd;
+        if (lane < a.node_cnt[root]) cand_load(a, a.node_first[root] + lane, cd);
+        __syncwarp();
+        if (lane < a.node_cnt[root]) cand_store(stage(0), lane, cd, ox, oy, oz, bx);
+        __syncwarp();
+        scan_stage(a, L, stage(0), bx, a.node_first[root], a.node_cnt[root], count);
     } else {
         if (lane == 0) stack[0] = root;
         sp = 1;
@@ -218,19 +310,60 @@ __global__ void k_build_lists(ListArgs a) {
         sp--;
         int node = stack[sp];
         __syncwarp();
-        int nf = a.node_first[node], nc = a.node_cnt[node];
+        const int nf = a.node_first[node], nc = a.node_cnt[node];
         bool hit = false;
-        int child = nf + lane;
-        if (lane < nc) hit = boxes_near(qlo, qhi, a.lo[child], a.hi[child], bx, rad2);
+        const int child = nf + lane;
+        uint4 clo = make_uint4(0, 0, 0, 0), chi = make_uint4(0, 0, 0, 0);
+        int cfirst = 0, ccnt = 0;
+        if (lane < nc) {
+            clo = a.lo[child];
+            chi = a.hi[child];
+            hit = boxes_near(qlo, qhi, clo, chi, bx, rad2);
+        }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (nf < a.nbucket_total) {
-            // children are buckets
-            while (m) {
-                int k = __ffs(m) - 1;
-                m &= m - 1;
-                test_bucket(a, nf + k, lane, own, s, qxi, qyi, qzi, xi, yi, zi, hsi, lo2, hi2,
-                            always_exact, bx, sx, sy, sz, sq, list, count);
+            // children are buckets: keep the ones some lane's sphere reaches,
+            // then stage bucket k+1 (global loads in flight) while scanning k
+            if (hit) { cfirst = a.node_first[child]; ccnt = a.node_cnt[child]; }
+            unsigned keep = 0;
+            unsigned mm = m;
+            while (mm) {
+                int k = __ffs(mm) - 1;
+                mm &= mm - 1;
+                uint4 blo, bhi;
+                blo.x = __shfl_sync(0xffffffffu, clo.x, k); blo.y = __shfl_sync(0xffffffffu, clo.y, k);
+                blo.z = __shfl_sync(0xffffffffu, clo.z, k);
+                bhi.x = __shfl_sync(0xffffffffu, chi.x, k); bhi.y = __shfl_sync(0xffffffffu, chi.y, k);
+                bhi.z = __shfl_sync(0xffffffffu, chi.z, k);
+                if (__any_sync(0xffffffffu, sphere_near(L, blo, bhi, bx))) keep |= 1u << k;
             }
+            if (!keep) continue;
+            int k = __ffs(keep) - 1;
+            keep &= keep - 1;
+            int cf = __shfl_sync(0xffffffffu, cfirst, k), cc = __shfl_sync(0xffffffffu, ccnt, k);
+            Cand cd;
+            if (lane < cc) cand_load(a, cf + lane, cd);
+            int buf = 0;
+            if (lane < cc) cand_store(stage(buf), lane, cd, ox, oy, oz, bx);
+            __syncwarp();
+            for (;;) {
+                int nk = keep ? __ffs(keep) - 1 : -1;
+                int nfst = 0, ncc = 0;
+                if (nk >= 0) {
+                    keep &= keep - 1;
+                    nfst = __shfl_sync(0xffffffffu, cfirst, nk);
+                    ncc = __shfl_sync(0xffffffffu, ccnt, nk);
+                    if (lane < ncc) cand_load(a, nfst + lane, cd);
+                }
+                scan_stage(a, L, stage(buf), bx, cf, cc, count);
+                if (nk < 0) break;
+                if (lane < ncc) cand_store(stage(buf ^ 1), lane, cd, ox, oy, oz, bx);
+                __syncwarp();
+                buf ^= 1;
+                cf = nfst;
+                cc = ncc;
+            }
+            __syncwarp();
         } else {
             int np = __popc(m);
             if (sp + np > STACK) {
@@ -242,17 +375,26 @@ __global__ void k_build_lists(ListArgs a) {
             __syncwarp();
         }
     }
+    const bool own = L.own;
+    const int s = L.s;
 
-    if (a.mode == 1) {
-        if (own) a.nbr_cnt[s] = count;
+    if (a.mode == 2) return;
+    if (a.mode == 0) {
+        // each particle owns cap slots at s * cap; a longer list sends the
+        // whole bucket to the count-then-fill passes (overflow region)
+        unsigned over = __ballot_sync(0xffffffffu, own && count > a.cap);
+        if (over) {
+            if (lane == 0) a.ovf_list[atomicAdd(a.ovf_count, 1)] = (int32_t)b;
+            return;
+        }
+        if (own) {
+            a.nbr_off[s] = (int64_t)s * a.cap;
+            a.nbr_cnt[s] = count;
+        }
         return;
     }
-    if (a.mode == 2) {
-        return;
-    }
-    // write the lists out
-    if (own && count > a.cap) set_flag(a.cnt, ST_LIST_OVERFLOW);
-    int mine = own ? min(count, a.cap) : 0;
+    // mode 1: reserve storage in the overflow region for the warp's lists
+    int mine = own ? count : 0;
     int incl = mine;
     for (int o = 1; o < 32; o <<= 1) {
         int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -269,16 +411,8 @@ __global__ void k_build_lists(ListArgs a) {
     }
     if ((int64_t)gbase + total > a.capacity) {
         if (lane == 0) set_flag(a.cnt, ST_LIST_CAPACITY);
-        return;
+        if (own) a.nbr_cnt[s] = 0;   // nothing stored for these lists
     }
-    __syncwarp();
-    for (int k = 0; k < mine; k++) a.nbr_idx[start + k] = list[k * 32 + lane];
-}
-
-__global__ void k_widen(int64_t n, const int32_t *__restrict__ cnt, int64_t *__restrict__ out) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s < n) out[s] = cnt[s];
-    if (s == n) out[n] = 0;
 }
 
 __global__ void k_export_count(int64_t n, const int32_t *__restrict__ perm,
@@ -310,11 +444,6 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-static cudaError_t widen_counts(const int32_t *cnt, int64_t n, int64_t *out, stream_t st) {
-    k_widen<<<grid_for(n + 1, 256), 256, 0, st>>>(n, cnt, out);
-    return launch_check();
-}
-
 cudaError_t build_tree(hydro_ctx *c, stream_t st) {
     const Plan &P = c->plan;
     k_aabb_leaf<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
@@ -333,6 +462,7 @@ cudaError_t build_tree(hydro_ctx *c, stream_t st) {
 }
 
 static ListArgs list_args(hydro_ctx *c, int cap, int mode) {
+    // cap: slots per particle in the fixed-stride part of nbr_idx
     const Plan &P = c->plan;
     ListArgs a;
     a.nbucket = P.nbucket;
@@ -354,53 +484,45 @@ static ListArgs list_args(hydro_ctx *c, int cap, int mode) {
     a.cnt = c->d_cnt;
     a.cap = cap;
     a.mode = mode;
+    a.ovf_list = c->d_ovf.get();
+    a.ovf_count = &c->d_cnt->ovf_buckets;
     return a;
 }
 
 static cudaError_t launch_lists(const ListArgs &a, int64_t nbucket, stream_t st) {
-    size_t per_warp = (size_t)a.cap * 32 * 4 + STACK * 4 + 3 * 32 * 8 + 96 * 4;
+    size_t per_warp = STACK * 4 + 2 * (32 * 16 + 3 * 32 * 8 + 96 * 4);
     size_t smem = per_warp * LIST_WARPS;
-    static size_t configured = 48 * 1024;
-    if (configured < smem) {
-        HYD_CUDA(cudaFuncSetAttribute(k_build_lists, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        configured = smem;
-    }
     k_build_lists<<<grid_for(nbucket, LIST_WARPS), LIST_WARPS * 32, smem, st>>>(a);
     return launch_check();
 }
 
-// one pass: lists staged per lane in shared memory (cap entries), bulk write
+// one pass: lists staged per lane in shared memory (cap entries), bulk
+// write; buckets with a longer list are queued for build_lists_queued()
+// Layout of nbr_idx: particle s owns the slots [s cap, s cap + cap); lists
+// longer than cap live in the overflow region that follows (n cap onwards),
+// reserved by build_lists_queued.
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_nbr_off.ensure(n + 1));
     HYD_CUDA(c->d_nbr_cnt.ensure(n));
-    HYD_CUDA(c->d_nbr_idx.ensure((size_t)n * c->nbr_per_particle));
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->list_cursor, 0, sizeof(unsigned long long), st));
+    size_t need = (size_t)n * cap + (size_t)c->ovf_reserve;
+    if (c->d_nbr_idx.cap < need) HYD_CUDA(c->d_nbr_idx.ensure(need + need / 8));
+    HYD_CUDA(c->d_ovf.ensure(c->plan.nbucket));
+    c->list_cap = cap;
+    unsigned long long start = (unsigned long long)n * cap;
+    HYD_CUDA(cudaMemcpyAsync(&c->d_cnt->list_cursor, &start, sizeof(start),
+                             cudaMemcpyHostToDevice, st));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
     return launch_lists(list_args(c, cap, 0), c->plan.nbucket, st);
 }
 
-// two passes for particles with more candidates than the staging holds:
-// count, exclusive scan into nbr_off, then write in place (synchronous)
-cudaError_t build_lists_twopass(hydro_ctx *c, stream_t st) {
-    const int64_t n = c->plan.n;
-    HYD_CUDA(c->d_nbr_off.ensure(n + 1));
-    HYD_CUDA(c->d_nbr_cnt.ensure(n));
-    HYD_CUDA(launch_lists(list_args(c, 0, 1), c->plan.nbucket, st));
-    HYD_CUDA(c->d_scan_tmp.ensure((size_t)(n + 1) + (n + 1) / 2048 + 64));
-    int64_t *cnt64 = c->d_scan_tmp.get();
-    int64_t *tmp = cnt64 + (n + 1);
-    HYD_CUDA(widen_counts(c->d_nbr_cnt.get(), n, cnt64, st));
-    HYD_CUDA(exclusive_scan_i64(cnt64, c->d_nbr_off.get(), n + 1, tmp, st));
-    int64_t total = 0;
-    HYD_CUDA(cudaMemcpyAsync(&total, c->d_nbr_off.get() + n, sizeof(int64_t),
-                             cudaMemcpyDeviceToHost, st));
-    HYD_CUDA(cudaStreamSynchronize(st));
-    if ((size_t)total > c->d_nbr_idx.cap) {
-        HYD_CUDA(c->d_nbr_idx.ensure((size_t)total + (size_t)n * 4));
-        c->nbr_per_particle = (int)(c->d_nbr_idx.cap / (size_t)n) + 1;
-    }
-    return launch_lists(list_args(c, 0, 2), c->plan.nbucket, st);
+// the queued buckets: count and reserve in the overflow region, then fill
+cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st) {
+    ListArgs a = list_args(c, c->list_cap, 1);
+    a.nbucket = nq;   // warps index the queue
+    HYD_CUDA(launch_lists(a, nq, st));
+    a.mode = 2;
+    return launch_lists(a, nq, st);
 }
 
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {

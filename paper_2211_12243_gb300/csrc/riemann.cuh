@@ -16,6 +16,13 @@ template <typename R> __device__ __forceinline__ R pow_(R a, R b);
 template <> __device__ __forceinline__ float pow_<float>(float a, float b) { return __powf(a, b); }
 template <> __device__ __forceinline__ double pow_<double>(double a, double b) { return pow(a, b); }
 
+// division and square root: IEEE in double; in float the hardware
+// approximations (a few ulp), well inside the mixed path's 1e-5 budget
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float sqrt_(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+
 // gamma-dependent constants of Toro's formulae
 template <typename R>
 struct GasK {
@@ -28,7 +35,8 @@ struct GasK {
     R g2;     // (g+1)/(2g)
     R inv_g;  // 1/g
     R mzr;    // -(g+1)/(2g)
-    __device__ explicit GasK(double gamma) {
+    GasK() = default;
+    __host__ __device__ explicit GasK(double gamma) {
         g = (R)gamma;
         gm1 = (R)(gamma - 1.0);
         gp1 = (R)(gamma + 1.0);
@@ -47,16 +55,16 @@ struct GasK {
 template <typename R>
 __device__ __forceinline__ void side_f(const GasK<R> &k, R p, R rk, R pk, R ck, R &f, R &df) {
     if (p > pk) {
-        R A = k.g5 / rk;
+        R A = div_(k.g5, rk);
         R Bk = k.g6 * pk;
-        R q = sqrt(A / (p + Bk));
+        R q = sqrt_(div_(A, p + Bk));
         f = (p - pk) * q;
-        df = q * (R(1) - R(0.5) * (p - pk) / (Bk + p));
+        df = q * (R(1) - R(0.5) * div_(p - pk, Bk + p));
     } else {
-        R pr = p / pk;
+        R pr = div_(p, pk);
         R t = pow_(pr, k.z);
         f = k.g4 * ck * (t - R(1));
-        df = t / (pr * k.g * pk) * ck;   // = (1/(rk ck)) (p/pk)^(-(g+1)/(2g))
+        df = div_(t, pr * k.g * pk) * ck;   // = (1/(rk ck)) (p/pk)^(-(g+1)/(2g))
     }
 }
 
@@ -69,15 +77,15 @@ __device__ __forceinline__ R star_guess(const GasK<R> &k, R rl, R ul, R pl, R cl
     R pmin = pl < pr ? pl : pr, pmax = pl > pr ? pl : pr;
     if (pmax <= R(2) * pmin && ppv >= pmin && ppv <= pmax) return ppv;
     if (ppv < pmin) {
-        R pq = pow_(pl / pr, k.z);
-        R um = (pq * ul / cl + ur / cr + k.g4 * (pq - R(1))) / (pq / cl + R(1) / cr);
-        R tl = R(1) + R(0.5) * k.gm1 * (ul - um) / cl;
-        R tr = R(1) + R(0.5) * k.gm1 * (um - ur) / cr;
+        R pq = pow_(div_(pl, pr), k.z);
+        R um = div_(div_(pq * ul, cl) + div_(ur, cr) + k.g4 * (pq - R(1)), div_(pq, cl) + div_(R(1), cr));
+        R tl = R(1) + R(0.5) * k.gm1 * div_(ul - um, cl);
+        R tr = R(1) + R(0.5) * k.gm1 * div_(um - ur, cr);
         return R(0.5) * (pl * pow_(tl, k.zi) + pr * pow_(tr, k.zi));
     }
-    R gl = sqrt((k.g5 / rl) / (k.g6 * pl + ppv));
-    R gr = sqrt((k.g5 / rr) / (k.g6 * pr + ppv));
-    return (gl * pl + gr * pr - (ur - ul)) / (gl + gr);
+    R gl = sqrt_(div_(div_(k.g5, rl), k.g6 * pl + ppv));
+    R gr = sqrt_(div_(div_(k.g5, rr), k.g6 * pr + ppv));
+    return div_(gl * pl + gr * pr - (ur - ul), gl + gr);
 }
 
 struct StarOut {
@@ -93,7 +101,7 @@ template <typename R>
 __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
                                               R p0, R tol, int max_newton, R &ps, R &us) {
     StarOut o{0, 0, 0};
-    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
     R du = ur - ul;
     if (k.g4 * (cl + cr) <= du) {
         o.vacuum = 1;
@@ -109,9 +117,9 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
     for (int it = 1; it <= max_newton; it++) {
         side_f(k, p, rl, pl, cl, fl, dfl);
         side_f(k, p, rr, pr, cr, fr, dfr);
-        R pn = p - (fl + fr + du) / (dfl + dfr);
+        R pn = p - div_(fl + fr + du, dfl + dfr);
         if (!(pn > pfloor)) pn = pfloor;
-        R ch = R(2) * fabs(pn - p) / (pn + p);
+        R ch = R(2) * div_(fabs(pn - p), pn + p);
         p = pn;
         o.iters = it;
         if (ch < tol) { conv = true; break; }
@@ -119,7 +127,7 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
     if (conv) {
         side_f(k, p, rl, pl, cl, fl, dfl);
         side_f(k, p, rr, pr, cr, fr, dfr);
-        R pn = p - (fl + fr + du) / (dfl + dfr);
+        R pn = p - div_(fl + fr + du, dfl + dfr);
         if (pn > pfloor) p = pn;
     } else {
         R lo = R(0), hi = pl > pr ? pl : pr;
@@ -151,21 +159,21 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
 template <typename R>
 __device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
                                             R ps, R us, R &rho, R &u, R &p, int &side) {
-    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
     if (R(0) <= us) {
         side = -1;
         if (ps > pl) {
-            R sl = ul - cl * sqrt(k.g2 * ps / pl + k.z);
+            R sl = ul - cl * sqrt_(k.g2 * div_(ps, pl) + k.z);
             if (R(0) <= sl) { rho = rl; u = ul; p = pl; }
-            else { R t = ps / pl; rho = rl * (t + k.g6) / (k.g6 * t + R(1)); u = us; p = ps; }
+            else { R t = div_(ps, pl); rho = rl * div_(t + k.g6, k.g6 * t + R(1)); u = us; p = ps; }
         } else {
             if (R(0) <= ul - cl) { rho = rl; u = ul; p = pl; }
             else {
-                R t = ps / pl;
+                R t = div_(ps, pl);
                 R cml = cl * pow_(t, k.z);
                 if (R(0) > us - cml) { rho = rl * pow_(t, k.inv_g); u = us; p = ps; }
                 else {
-                    R cc = k.g5 + k.g6 / cl * ul;
+                    R cc = k.g5 + div_(k.g6, cl) * ul;
                     rho = rl * pow_(cc, k.g4);
                     u = k.g5 * (cl + R(0.5) * k.gm1 * ul);
                     p = pl * pow_(cc, k.zi);
@@ -175,17 +183,17 @@ __device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, 
     } else {
         side = 1;
         if (ps > pr) {
-            R sr = ur + cr * sqrt(k.g2 * ps / pr + k.z);
+            R sr = ur + cr * sqrt_(k.g2 * div_(ps, pr) + k.z);
             if (R(0) >= sr) { rho = rr; u = ur; p = pr; }
-            else { R t = ps / pr; rho = rr * (t + k.g6) / (k.g6 * t + R(1)); u = us; p = ps; }
+            else { R t = div_(ps, pr); rho = rr * div_(t + k.g6, k.g6 * t + R(1)); u = us; p = ps; }
         } else {
             if (R(0) >= ur + cr) { rho = rr; u = ur; p = pr; }
             else {
-                R t = ps / pr;
+                R t = div_(ps, pr);
                 R cmr = cr * pow_(t, k.z);
                 if (R(0) <= us + cmr) { rho = rr * pow_(t, k.inv_g); u = us; p = ps; }
                 else {
-                    R cc = k.g5 - k.g6 / cr * ur;
+                    R cc = k.g5 - div_(k.g6, cr) * ur;
                     rho = rr * pow_(cc, k.g4);
                     u = k.g5 * (-cr + R(0.5) * k.gm1 * ur);
                     p = pr * pow_(cc, k.zi);
@@ -201,32 +209,32 @@ template <typename R>
 __device__ __forceinline__ void hllc_flux(const GasK<R> &k, R rl, R ul, R pl, const R *wl, R rr,
                                           R ur, R pr, const R *wr, const R *n, R *F, R &ps,
                                           R &ss) {
-    R cl = sqrt(k.g * pl / rl), cr = sqrt(k.g * pr / rr);
+    R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
     R ppv = R(0.5) * (pl + pr) - R(0.125) * (ur - ul) * (rl + rr) * (cl + cr);
     ppv = ppv > R(0) ? ppv : R(0);
-    R ql = ppv <= pl ? R(1) : sqrt(R(1) + k.g2 * (ppv / pl - R(1)));
-    R qr = ppv <= pr ? R(1) : sqrt(R(1) + k.g2 * (ppv / pr - R(1)));
+    R ql = ppv <= pl ? R(1) : sqrt_(R(1) + k.g2 * (div_(ppv, pl) - R(1)));
+    R qr = ppv <= pr ? R(1) : sqrt_(R(1) + k.g2 * (div_(ppv, pr) - R(1)));
     R sl = ul - cl * ql, sr = ur + cr * qr;
-    ss = (pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur)) / (rl * (sl - ul) - rr * (sr - ur));
+    ss = div_(pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur), rl * (sl - ul) - rr * (sr - ur));
     ps = pl + rl * (sl - ul) * (ss - ul);
     R w2l = wl[0] * wl[0] + wl[1] * wl[1] + wl[2] * wl[2];
     R w2r = wr[0] * wr[0] + wr[1] * wr[1] + wr[2] * wr[2];
-    R El = pl / k.gm1 + R(0.5) * rl * (ul * ul + w2l);
-    R Er = pr / k.gm1 + R(0.5) * rr * (ur * ur + w2r);
+    R El = div_(pl, k.gm1) + R(0.5) * rl * (ul * ul + w2l);
+    R Er = div_(pr, k.gm1) + R(0.5) * rr * (ur * ur + w2r);
     R fm, fn, fe;
     const R *wt;
     if (R(0) <= sl) {
         fm = rl * ul; fn = rl * ul * ul + pl; fe = ul * (El + pl); wt = wl;
     } else if (R(0) <= ss) {
-        R kk = rl * (sl - ul) / (sl - ss);
-        R e2 = kk * (El / rl + (ss - ul) * (ss + pl / (rl * (sl - ul))));
+        R kk = div_(rl * (sl - ul), sl - ss);
+        R e2 = kk * (div_(El, rl) + (ss - ul) * (ss + div_(pl, rl * (sl - ul))));
         fm = rl * ul + sl * (kk - rl);
         fn = rl * ul * ul + pl + sl * (kk * ss - rl * ul);
         fe = ul * (El + pl) + sl * (e2 - El);
         wt = wl;
     } else if (R(0) <= sr) {
-        R kk = rr * (sr - ur) / (sr - ss);
-        R e2 = kk * (Er / rr + (ss - ur) * (ss + pr / (rr * (sr - ur))));
+        R kk = div_(rr * (sr - ur), sr - ss);
+        R e2 = kk * (div_(Er, rr) + (ss - ur) * (ss + div_(pr, rr * (sr - ur))));
         fm = rr * ur + sr * (kk - rr);
         fn = rr * ur * ur + pr + sr * (kk * ss - rr * ur);
         fe = ur * (Er + pr) + sr * (e2 - Er);

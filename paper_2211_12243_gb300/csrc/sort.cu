@@ -48,9 +48,12 @@ __global__ void k_morton(int64_t n, const double *__restrict__ x, const double *
     if (i >= n) return;
     int b = nbox > 1 ? box_of(box_off, nbox, i) : 0;
     const Box bx = boxes[b];
-    uint32_t qx = to_fixed(x[i], bx.L[0]) >> 22;
-    uint32_t qy = to_fixed(y[i], bx.L[1]) >> 22;
-    uint32_t qz = to_fixed(z[i], bx.L[2]) >> 22;
+    // cubic cells of side Lmax / 1024 on every axis, so that a run of
+    // consecutive keys is a compact region also in elongated boxes
+    const double Lmax = fmax(bx.L[0], fmax(bx.L[1], bx.L[2]));
+    uint32_t qx = min((uint32_t)(x[i] / Lmax * 1024.0), 1023u);
+    uint32_t qy = min((uint32_t)(y[i] / Lmax * 1024.0), 1023u);
+    uint32_t qz = min((uint32_t)(z[i] / Lmax * 1024.0), 1023u);
     uint32_t m = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
     keys[i] = ((unsigned long long)b << 30) | m;
     vals[i] = (int32_t)i;

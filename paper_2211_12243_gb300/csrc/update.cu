@@ -61,6 +61,30 @@ __global__ void k_update(UpdArgs a) {
     a.p.omega[o] = a.om[s];
 }
 
+// totals before / after the update, reduced per warp and added to the
+// counters (diagnostics; the order of the block sums is not fixed)
+__global__ void k_update_sums(int64_t n, const double *__restrict__ Q, const double *__restrict__ dQ,
+                              double *__restrict__ out) {
+    double v[10];
+#pragma unroll
+    for (int q = 0; q < 10; q++) v[q] = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            double now = Q[q * n + s];
+            v[5 + q] += now;
+            v[q] += now - dQ[q * n + s];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 10; q++)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 10; q++) atomicAdd(&out[q], v[q]);
+}
+
 struct KS {
     double s, c;
 };
@@ -135,6 +159,12 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.p = *p;
     a.cnt = c->d_cnt;
     k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
+    return launch_check();
+}
+
+cudaError_t run_update_sums(hydro_ctx *c, stream_t st) {
+    k_update_sums<<<SUM_BLOCKS, SUM_THREADS, 0, st>>>(c->plan.n, c->d_Q.get(), c->d_dQ.get(),
+                                                      &c->d_cnt->sums[0][0]);
     return launch_check();
 }
 
