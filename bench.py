@@ -197,7 +197,7 @@ def main():
     cfg = hydro.default_config(gamma=w["gamma"], precision=args.precision, scheme=args.scheme)
     H = hydro.Hydro(cfg)
     H.set_boxes(*hydro.single_box(w))
-    H.reserve(n, 64)
+    H.reserve(n, 96)
     st = hydro.to_device(w)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()

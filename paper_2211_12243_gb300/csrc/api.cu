@@ -150,8 +150,8 @@ int lists_all(hydro_ctx *c, cudaStream_t st) {
         API_CUDA(cudaStreamSynchronize(st));
         nq = c->h_cnt->ovf_buckets;
     }
-    // many long lists: give the next builds more fixed slots
-    if (nq > c->plan.nbucket / 16 && c->nbr_per_particle < 256) c->nbr_per_particle += 32;
+    // long lists in more than 1/256 of the buckets: more fixed slots next time
+    if (nq > c->plan.nbucket / 256 && c->nbr_per_particle < 256) c->nbr_per_particle += 32;
     c->have_lists = true;
     return HYDRO_OK;
 }

@@ -121,7 +121,7 @@ struct hydro_ctx {
     bool have_plan = false;
     bool have_lists = false;
     int64_t list_n = 0;
-    int nbr_per_particle = 64;        // fixed slots per particle in nbr_idx
+    int nbr_per_particle = 96;        // fixed slots per particle in nbr_idx
     int list_cap = 64;                // slots used by the current lists
     int64_t ovf_reserve = 0;          // entries kept for the overflow region
 
