@@ -216,6 +216,25 @@ int hydro_get_stats(hydro_ctx *ctx, hydro_stats *stats, hydro_stream stream);
  * b3, feature mean[12], feature scale[12] (row-major, W[out][in]). */
 int hydro_mlp_load(hydro_ctx *ctx, const void *weights, size_t bytes);
 
+/* Totals over the n particles of mass, px, py, pz and etot (compensated
+ * sums), written to totals[0..4] (device), computed without allocating
+ * anything and without a context.  For callers that cannot call cudaMalloc
+ * -- a host application that owns every device allocation through its own
+ * pool, or a plugin that must not change the device memory footprint once
+ * it runs -- to check conservation around hydro_step.  No counterpart in
+ * the paper: a utility of this library.
+ * Inputs: device arrays of n doubles (caller order, any order works).
+ * Limit: n <= 2^26 (67,108,864); larger n returns HYDRO_EINVAL.
+ * Scratch: a fixed 640 KiB array in the library's static device memory,
+ * held by every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current); later calls reuse it.  All calls share
+ * the array: each overwrites the part it uses, so nothing needs clearing,
+ * but calls that overlap on the GPU race on it.  Asynchronous on stream. */
+int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const double *py,
+                         const double *pz, const double *etot, double *totals,
+                         hydro_stream stream);
+
 /* Number of kernels this library has launched in the process so far
  * (every entry point's launches, all contexts).  Diagnostics only. */
 int64_t hydro_kernel_launches(void);

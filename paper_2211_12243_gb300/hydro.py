@@ -83,7 +83,8 @@ class Stats(C.Structure):
 EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_config",
            "hydro_set_boxes", "hydro_reserve", "hydro_build_neighbours", "hydro_density",
            "hydro_gradients", "hydro_fluxes", "hydro_step", "hydro_sync_status",
-           "hydro_get_stats", "hydro_mlp_load", "hydro_kernel_launches", "hydro_strerror"]
+           "hydro_get_stats", "hydro_mlp_load", "hydro_totals_noalloc", "hydro_kernel_launches",
+           "hydro_strerror"]
 
 
 def _load():
@@ -110,12 +111,28 @@ def _load():
         L.hydro_sync_status.argtypes = [vp, vp]
         L.hydro_get_stats.argtypes = [vp, P(Stats), vp]
         L.hydro_mlp_load.argtypes = [vp, vp, C.c_size_t]
+        L.hydro_totals_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
         L.hydro_strerror.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def totals_noalloc(st, out=None, stream=None):
+    """Totals of (m, px, py, pz, E) of a state dict of CUDA tensors through
+    hydro_totals_noalloc (no allocation inside the library); returns the
+    device tensor of 5 doubles."""
+    import torch
+    if out is None:
+        out = torch.empty(5, dtype=torch.float64, device=st["x"].device)
+    n = st["m"].numel()
+    rc = _load().hydro_totals_noalloc(n, _ptr(st["m"]), _ptr(st["px"]), _ptr(st["py"]),
+                                      _ptr(st["pz"]), _ptr(st["E"]), _ptr(out), _stream(stream))
+    if rc:
+        raise HydroError(rc, "hydro_totals_noalloc")
+    return out
 
 
 def kernel_launches():
