@@ -179,6 +179,8 @@ __device__ __forceinline__ df from_i64(long long v) {
 }
 
 // ---------------------------------------------------------------- mixed path
+constexpr int DENS_THREADS = 128;
+
 __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
                                 const uint64_t *__restrict__ q64y,
                                 const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
@@ -200,17 +202,20 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     float lo = 0.f, hi = -1.f;
     bool conv = false, fail = false;
     const float ftol = 2e-6f;
+    auto sep_r = [&](int k) {
+        int j = a.nbr_idx[o + k];
+        const float *rj = rec + (int64_t)j * REC;
+        float4 pj = *reinterpret_cast<const float4 *>(rj);
+        float dx = qdiff(qxi, __float_as_uint(pj.x), bx.s[0]);
+        float dy = qdiff(qyi, __float_as_uint(pj.y), bx.s[1]);
+        float dz = qdiff(qzi, __float_as_uint(pj.z), bx.s[2]);
+        float r2 = dx * dx + dy * dy + dz * dz;
+        return r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+    };
     for (int it = 1; it <= a.max_iter; it++) {
         float f = 0.f, mq = 0.f, ih = 1.f / h;
         for (int k = 0; k < c; k++) {
-            int j = a.nbr_idx[o + k];
-            const float *rj = rec + (int64_t)j * REC;
-            float4 pj = *reinterpret_cast<const float4 *>(rj);
-            float dx = qdiff(qxi, __float_as_uint(pj.x), bx.s[0]);
-            float dy = qdiff(qyi, __float_as_uint(pj.y), bx.s[1]);
-            float dz = qdiff(qzi, __float_as_uint(pj.z), bx.s[2]);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            float q = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * ih;
+            float q = sep_r(k) * ih;
             float fv, mv;
             kernel_f<float>(a.kernel, q, fv, mv);
             f += fv;
@@ -250,7 +255,9 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     df hd = {h, 0.f};
     df ih = df_div({1.f, 0.f}, hd);
     df F = {0.f, 0.f}, MQ = {0.f, 0.f};
+    const float hcut = h * (1.f + 1e-5f);   // W = 0 beyond h: skip those (float r is good to 1e-7)
     for (int k = 0; k < c; k++) {
+        if (sep_r(k) >= hcut) continue;
         int j = a.nbr_idx[o + k];
         long long ix = (long long)(q64x[j] - xi64);
         long long iy = (long long)(q64y[j] - yi64);
@@ -368,8 +375,9 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st) {
                                                      c->d_pbox.get(), c->d_boxes.get(), q64,
                                                      q64 + n, q64 + 2 * n);
         HYD_CUDA(launch_check());
-        k_density_mixed<<<grid_for(n, 128), 128, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
-                                                          c->d_recf.get());
+        k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(a, q64, q64 + n,
+                                                                         q64 + 2 * n,
+                                                                         c->d_recf.get());
     } else {
         k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
     }

@@ -312,8 +312,8 @@ constexpr int QCAP = 64;
 
 template <typename R>
 struct FluxSmem {
-    R own[32][REC + 1];        // the bucket's records (padded: no bank conflicts)
     R cb[32][5];               // solved faces' c, read back by the owners
+    unsigned peers[32];        // per owner lane: the batch lanes holding its faces
     int32_t qj[QCAP];          // queued faces: partner j
     uint8_t qo[QCAP];          // queued faces: owner lane
 };
@@ -333,13 +333,8 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         const Box bx = a.boxes[a.pbox[s]];
         const GasK<R> &K = gas<R>(a);
         const R dt = (R)(a.dt_dev ? *a.dt_dev : a.dt);
-        // stage the owners' records
-        {
-            R v[REC];
-            load_full<R>(rec + (int64_t)s * REC, v);
-#pragma unroll
-            for (int k = 0; k < REC; k++) sm.own[lane][k] = v[k];
-        }
+        R own4[4];   // the lane's own position and h (enumeration)
+        load4<R>(rec + (int64_t)s * REC, own4);
         Member mem;
         mem.init(a.xs, a.ys, a.zs, s, a.h[s], bx);
         typename AccOf<R>::T acc;
@@ -356,13 +351,13 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         // solve the first nb queued faces, one per lane, and hand -c back
         auto solve = [&](int nb) {
             R c[5] = {R(0), R(0), R(0), R(0), R(0)};
-            int ol = 255;
+            int ol = 32 + lane;   // idle lanes: a key no owner has
             if (lane < nb) {
                 ol = sm.qo[lane];
                 const int j = sm.qj[lane];
-                R rj[REC];
+                R ri[REC], rj[REC];
+                load_full<R>(rec + (int64_t)(f + ol) * REC, ri);   // owner (L1-resident)
                 load_full<R>(rec + (int64_t)j * REC, rj);
-                const R *ri = sm.own[ol];
                 R d[3], r2;
                 rec_sep(ri, rj, bx, d, r2);
                 face_flux<R, RIEM, SCHEME>(a, K, ri, rj, d, sqrt_(r2), dt, c, fs);
@@ -372,12 +367,18 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
             }
 #pragma unroll
             for (int q = 0; q < 5; q++) sm.cb[lane][q] = c[q];
+            // hand each owner the set of batch lanes that solved its faces
+            sm.peers[lane] = 0u;
+            unsigned grp = __match_any_sync(0xffffffffu, ol);
             __syncwarp();
-            for (int t = 0; t < nb; t++) {
-                if (sm.qo[t] == lane) {
+            if (lane < nb) sm.peers[ol] = grp;   // equal values from all members
+            __syncwarp();
+            unsigned mine = sm.peers[lane];
+            while (mine) {
+                const int t = __ffs(mine) - 1;
+                mine &= mine - 1;
 #pragma unroll
-                    for (int q = 0; q < 5; q++) acc.sub(q, sm.cb[t][q]);
-                }
+                for (int q = 0; q < 5; q++) acc.sub(q, sm.cb[t][q]);
             }
             __syncwarp();
         };
@@ -391,7 +392,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                     R rj4[4];
                     load4<R>(rec + (int64_t)j * REC, rj4);
                     R d[3], r2;
-                    rec_sep(&sm.own[lane][0], rj4, bx, d, r2);
+                    rec_sep(own4, rj4, bx, d, r2);
                     if (mem(r2, j)) has = (j > s) || !member_j(r2, rj4[R_H], a, s, j, bx);
                 }
             }

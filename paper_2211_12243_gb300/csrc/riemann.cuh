@@ -53,6 +53,29 @@ struct GasK {
 
 // one side's pressure function and derivative
 template <typename R>
+__device__ __forceinline__ void side_f(const GasK<R> &k, R p, R rk, R pk, R ck, R &f, R &df);
+
+// float: both branches evaluated and selected, so that the lanes of a warp
+// (faces with shock and rarefaction sides mixed) do not diverge
+template <>
+__device__ __forceinline__ void side_f<float>(const GasK<float> &k, float p, float rk, float pk,
+                                              float ck, float &f, float &df) {
+    float A = __fdividef(k.g5, rk);
+    float Bk = k.g6 * pk;
+    float ia = __fdividef(1.f, p + Bk);
+    float q = sqrt_(A * ia);
+    float fs = (p - pk) * q;
+    float dfs = q * (1.f - 0.5f * (p - pk) * ia);
+    float pr = __fdividef(p, pk);
+    float t = __powf(pr, k.z);
+    float fr = k.g4 * ck * (t - 1.f);
+    float dfr = __fdividef(t * ck, pr * k.g * pk);
+    bool shock = p > pk;
+    f = shock ? fs : fr;
+    df = shock ? dfs : dfr;
+}
+
+template <typename R>
 __device__ __forceinline__ void side_f(const GasK<R> &k, R p, R rk, R pk, R ck, R &f, R &df) {
     if (p > pk) {
         R A = div_(k.g5, rk);
@@ -114,15 +137,25 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
     if (!(p > pfloor)) p = pfloor;
     bool conv = false;
     R fl, dfl, fr, dfr;
+    R dp_last = R(0);
     for (int it = 1; it <= max_newton; it++) {
         side_f(k, p, rl, pl, cl, fl, dfl);
         side_f(k, p, rr, pr, cr, fr, dfr);
         R pn = p - div_(fl + fr + du, dfl + dfr);
         if (!(pn > pfloor)) pn = pfloor;
         R ch = R(2) * div_(fabs(pn - p), pn + p);
+        dp_last = pn - p;
         p = pn;
         o.iters = it;
         if (ch < tol) { conv = true; break; }
+    }
+    if (conv && sizeof(R) == 4) {
+        // float: the iteration has converged to rounding; u* from the last
+        // evaluation, corrected to first order for the last Newton step
+        // (p held p_old at that evaluation, p_new - p_old = pn - p_old)
+        ps = p;
+        us = R(0.5) * (ul + ur) + R(0.5) * (fr - fl) + R(0.5) * (dfr - dfl) * dp_last;
+        return o;
     }
     if (conv) {
         side_f(k, p, rl, pl, cl, fl, dfl);
