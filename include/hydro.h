@@ -49,7 +49,8 @@ typedef enum {
     HYDRO_ENONFINITE = -7,  /* non-finite value produced or given */
     HYDRO_ECUDA = -8,       /* CUDA runtime error */
     HYDRO_ESTATE = -9,      /* call order violated (e.g. density before lists) */
-    HYDRO_ESEARCH = -10     /* a solved h exceeded the search radius of the lists */
+    HYDRO_ESEARCH = -10,    /* a solved h exceeded the search radius of the lists */
+    HYDRO_EMLP = -11        /* a tensor-core wait of the MLP gave up (result unusable) */
 } hydro_status;
 
 enum { HYDRO_KERNEL_WENDLAND_C2 = 0, HYDRO_KERNEL_CUBIC = 1 };
@@ -71,7 +72,10 @@ typedef struct {
                             HYDRO_MIXED: pair geometry, kernel sums and fluxes in
                             float; E^-1, h refinement and flux accumulation in
                             double-class precision. */
-    int learned_guess;   /* 1: MLP star-pressure guess for the exact solver */
+    int learned_guess;   /* 1: MLP starting pressure for the exact solver on hard
+                            faces (mixed precision; needs a network from
+                            hydro_mlp_load / hydro_mlp_train, else the flux
+                            calls return HYDRO_ESTATE; FP64 and HLLC ignore it) */
     int limiter;         /* 1: conditioned BJ + pairwise limiters (§2.3.6) */
     int time_extrap;     /* 1: half-step predictor of the face states (Eq. 16) */
     double ncond_crit;   /* N_cond threshold (100) */
@@ -120,7 +124,10 @@ typedef struct {
     int64_t grad_pairs;       /* directed pairs j != i, r_ij < h_i (gradient stage) */
     int64_t flux_pairs;       /* unordered pairs r_ij < max(h_i, h_j) (flux stage) */
     int64_t newton_iters;     /* Riemann Newton iterations summed over faces */
-    int64_t guess_fallbacks;  /* learned guesses rejected for the plain guess */
+    int64_t guess_fallbacks;  /* hard faces that kept the plain guess (learned guess
+                                 out of range, or no network evaluated) */
+    int64_t learned_faces;    /* faces whose Newton iteration started from the MLP */
+    int64_t hard_faces;       /* faces where Toro's guess is the two-shock value */
     int64_t vacuum_faces;
     int64_t first_order_faces;
     int ngb_rounds;           /* N_cond growth rounds taken */
@@ -207,14 +214,98 @@ int hydro_step(hydro_ctx *ctx, hydro_particles *p, double dt, hydro_stats *stats
  * returns the first error recorded by any kernel since the last read. */
 int hydro_sync_status(hydro_ctx *ctx, hydro_stream stream);
 
-/* Statistics of the last hydro_step (host copy, synchronising). */
+/* Statistics of the last hydro_step (host copy, synchronising); the flux
+ * counters (flux_pairs, newton_iters, guess_fallbacks, learned_faces,
+ * hard_faces, vacuum_faces, first_order_faces) are re-read from the device,
+ * so after hydro_fluxes they describe that call. */
 int hydro_get_stats(hydro_ctx *ctx, hydro_stats *stats, hydro_stream stream);
 
 /* Install the weights of the star-pressure MLP (12 -> 64 -> 64 -> 1) used
  * when cfg.learned_guess = 1.  `weights`: host, `bytes` = 4 * (12*64 + 64 +
- * 64*64 + 64 + 64 + 1 + 24) float32 values in the order W1, b1, W2, b2, w3,
- * b3, feature mean[12], feature scale[12] (row-major, W[out][in]). */
+ * 64*64 + 64 + 64 + 1 + 24 + 2 + 24) = 4 * 5115, float32 values in the order
+ * W1, b1, W2, b2, w3, b3, feature mean[12], feature scale[12], t_mean,
+ * t_scale, feature box xmin[12], xmax[12] (row-major, W[out][in]); output
+ * y = t_mean + t_scale (w3 . h2 + b3).  HYDRO_EINVAL on a non-finite value,
+ * a scale <= 0 or xmin > xmax.  Synchronous. */
 int hydro_mlp_load(hydro_ctx *ctx, const void *weights, size_t bytes);
+
+/* ---- Learned starting pressure of the exact Riemann solver -------------
+ * Not part of the paper's method: the paper solves each face's Riemann
+ * problem with the exact iterative solver of Toro (2009), whose Newton
+ * iteration starts from Toro's adaptive guess (PVRS, two-rarefaction or
+ * two-shock value).  These calls train and run a 12 -> 64 -> 64 -> 1 ReLU
+ * network on 12 features of the face problem (log pressure and density
+ * ratios to p_a = (p_L + p_R)/2 and rho_a, the velocity jump over the mean
+ * sound speed, sound-speed ratios, and the PVRS, two-rarefaction and
+ * two-shock values p_PVRS, p_TR, p_TS over p_a).  Its output y is a
+ * correction of the two-shock value: target ln(p* / p_TS), starting
+ * pressure p_TS exp(y).  With cfg.learned_guess = 1 (mixed precision,
+ * exact solver), the faces where Toro's guess is the two-shock value
+ * ("hard" faces: not the PVRS value, and p_PVRS >= min(p_L, p_R) so not
+ * the two-rarefaction value, which is exact for two rarefactions) start
+ * from the network's value unless it is out of range; the iteration
+ * always runs to p_tol, so the flux is unchanged beyond rounding.
+ *
+ * Face problems are float arrays in rows of n (structure of arrays):
+ * rho_L, u_L, p_L, rho_R, u_R, p_R [, p*], u along the face normal, in the
+ * frame of the face.  Inference runs on the tensor cores (BF16 operands,
+ * FP32 accumulation); training keeps FP32 master weights.
+ * ----------------------------------------------------------------------- */
+
+/* Copy the current float parameters (layout of hydro_mlp_load) to the host
+ * buffer `weights` (bytes as in hydro_mlp_load).  HYDRO_ESTATE without a
+ * network.  Synchronous. */
+int hydro_mlp_get(hydro_ctx *ctx, void *weights, size_t bytes);
+
+/* Predicted starting pressures: faces (device, 6 rows of n floats) ->
+ * p_guess (device, n floats), -1 where the prediction is out of range (a
+ * feature outside the box [xmin, xmax] of the training data, or a
+ * correction |y| > 2, or not finite).  HYDRO_ESTATE without a network. */
+int hydro_mlp_predict(hydro_ctx *ctx, const float *faces, int64_t n, float *p_guess,
+                      hydro_stream stream);
+
+/* Features x (device, n x 12 floats, row-major) and targets
+ * t = ln(p_star / p_TS) (device, n floats) of recorded faces (device, 7 rows
+ * of n floats). */
+int hydro_mlp_features(hydro_ctx *ctx, const float *faces, int64_t n, float *x, float *t,
+                       hydro_stream stream);
+
+/* Gradient of the loss 0.5 mean_i (y_i - t_i)^2 over all n samples (x:
+ * device n x 12, t: device n) with respect to the current parameters,
+ * written to grad (device, 5115 floats in the hydro_mlp_load layout; the
+ * entries of the fixed standardisations are 0) and the loss to *loss
+ * (device, 1 float).
+ * quant = 1 rounds the standardised inputs, W1, the hidden activations and
+ * W2 to bf16 in the forward pass as the tensor-core inference does (the
+ * backward pass differentiates through the rounded values as if the
+ * rounding were the identity).  HYDRO_ESTATE without a network. */
+int hydro_mlp_gradient(hydro_ctx *ctx, const float *x, const float *t, int64_t n, int quant,
+                       float *grad, float *loss, hydro_stream stream);
+
+/* Train on recorded faces (device, 7 rows of n floats): `steps` Adam steps
+ * (beta 0.9 / 0.999) on minibatches of `batch` samples drawn with a
+ * counter-based generator from `seed`, learning rate lr, bf16-rounded
+ * forward pass.  Without a loaded network, first initialises one (He
+ * normal from `seed`) and sets the feature and target standardisations and
+ * the feature box from the data; with one, continues training it.  The learning rate decays
+ * from lr to lr/20 along a cosine.  loss (device, `steps` floats, may be
+ * NULL) receives the minibatch loss of each step. */
+int hydro_mlp_train(hydro_ctx *ctx, const float *faces, int64_t n, int64_t steps,
+                    int64_t batch, double lr, uint64_t seed, float *loss,
+                    hydro_stream stream);
+
+/* Record solved face problems of the following hydro_fluxes / hydro_step
+ * calls (mixed precision, exact solver) into buf (device, 7 rows of
+ * `capacity` floats: rho_L, u_L, p_L, rho_R, u_R, p_R, p*).  A face is kept
+ * when a hash of its particle pair falls below keep_fraction (0..1], and,
+ * with hard_only = 1, only when it is a hard face.  buf = NULL stops the
+ * recording.  Resets the recorded count (synchronous). */
+int hydro_record_faces(hydro_ctx *ctx, float *buf, int64_t capacity, double keep_fraction,
+                       int hard_only);
+
+/* Number of faces that qualified since hydro_record_faces (those beyond
+ * capacity were not stored).  Synchronising. */
+int hydro_recorded_faces(hydro_ctx *ctx, int64_t *count, hydro_stream stream);
 
 /* Totals over the n particles of mass, px, py, pz and etot (compensated
  * sums), written to totals[0..4] (device), computed without allocating

@@ -1,10 +1,12 @@
 // C ABI of the hydro library (declared in include/hydro.h).
 #include <math.h>
+#include <cmath>
 #include <string.h>
 
 #include <algorithm>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "hydro_internal.cuh"
 
@@ -37,6 +39,7 @@ int flags_to_status(int f) {
     if (f & ST_NOCONV_H) return HYDRO_ENOCONV_H;
     if (f & ST_RIEMANN) return HYDRO_ERIEMANN;
     if (f & ST_NCOND) return HYDRO_ENCOND;
+    if (f & ST_MLP) return HYDRO_EMLP;
     return HYDRO_OK;
 }
 
@@ -405,6 +408,7 @@ int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *g
 int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const double *grad,
                  const double *alpha, double dt, double *dQ, hydro_stream stream) {
     if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
+    if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
     if (!valid_particles(c, p, true) || !B || !grad || !alpha || !dQ || !(dt > 0.0))
         return HYDRO_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -421,6 +425,7 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream) {
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
+    if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = p->n;
     const bool timing = stats != nullptr && c->have_events;
@@ -472,6 +477,8 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
         S.flux_pairs = (int64_t)H.flux_pairs;
         S.newton_iters = (int64_t)H.newton_iters;
         S.guess_fallbacks = (int64_t)H.guess_fallbacks;
+        S.learned_faces = (int64_t)H.learned_faces;
+        S.hard_faces = (int64_t)H.hard_faces;
         S.vacuum_faces = (int64_t)H.vacuum;
         S.first_order_faces = (int64_t)H.first_order;
         for (int w = 0; w < 2; w++) {
@@ -505,18 +512,183 @@ int hydro_sync_status(hydro_ctx *c, hydro_stream stream) {
 
 int hydro_get_stats(hydro_ctx *c, hydro_stats *stats, hydro_stream stream) {
     if (!c || !stats) return HYDRO_EINVAL;
-    API_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    *stats = c->last_stats;
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    hydro_stats &S = c->last_stats;
+    const DevCounters &H = *c->h_cnt;
+    S.flux_pairs = (int64_t)H.flux_pairs;
+    S.newton_iters = (int64_t)H.newton_iters;
+    S.guess_fallbacks = (int64_t)H.guess_fallbacks;
+    S.learned_faces = (int64_t)H.learned_faces;
+    S.hard_faces = (int64_t)H.hard_faces;
+    S.vacuum_faces = (int64_t)H.vacuum;
+    S.first_order_faces = (int64_t)H.first_order;
+    *stats = S;
     return HYDRO_OK;
 }
 
+static const size_t kMlpParams = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 24 + 2 + 24;
+static const size_t kMlpScale = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 12;   // scale[12]
+static const size_t kMlpTScale = kMlpScale + 13;
+static const size_t kMlpXmin = kMlpTScale + 1;
+
 int hydro_mlp_load(hydro_ctx *c, const void *weights, size_t bytes) {
     if (!c || !weights) return HYDRO_EINVAL;
-    const size_t nf = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 24;
-    if (bytes != nf * sizeof(float)) return HYDRO_EINVAL;
-    API_CUDA(c->d_mlp.ensure(nf));
+    if (bytes != kMlpParams * sizeof(float)) return HYDRO_EINVAL;
+    const float *w = static_cast<const float *>(weights);
+    for (size_t k = 0; k < kMlpParams; k++)
+        if (!std::isfinite(w[k])) return HYDRO_EINVAL;
+    for (size_t k = kMlpScale; k < kMlpScale + 12; k++)   // feature scales
+        if (!(w[k] > 0.f)) return HYDRO_EINVAL;
+    if (!(w[kMlpTScale] > 0.f)) return HYDRO_EINVAL;      // target scale
+    for (size_t k = 0; k < 12; k++)                       // feature box
+        if (!(w[kMlpXmin + k] <= w[kMlpXmin + 12 + k])) return HYDRO_EINVAL;
+    API_CUDA(c->d_mlp.ensure(kMlpParams));
     API_CUDA(cudaMemcpy(c->d_mlp.get(), weights, bytes, cudaMemcpyHostToDevice));
+    API_CUDA(mlp_pack(c, 0));
+    API_CUDA(cudaStreamSynchronize(0));
     c->have_mlp = true;
+    return HYDRO_OK;
+}
+
+int hydro_mlp_get(hydro_ctx *c, void *weights, size_t bytes) {
+    if (!c || !weights || bytes != kMlpParams * sizeof(float)) return HYDRO_EINVAL;
+    if (!c->have_mlp) return HYDRO_ESTATE;
+    API_CUDA(cudaDeviceSynchronize());
+    API_CUDA(cudaMemcpy(weights, c->d_mlp.get(), bytes, cudaMemcpyDeviceToHost));
+    return HYDRO_OK;
+}
+
+int hydro_mlp_predict(hydro_ctx *c, const float *faces, int64_t n, float *p_guess,
+                      hydro_stream stream) {
+    if (!c || n < 0 || (n > 0 && (!faces || !p_guess))) return HYDRO_EINVAL;
+    if (!c->have_mlp) return HYDRO_ESTATE;
+    if (n == 0) return HYDRO_OK;
+    API_CUDA(mlp_predict(c, faces, n, p_guess, (cudaStream_t)stream));
+    return HYDRO_OK;
+}
+
+int hydro_mlp_features(hydro_ctx *c, const float *faces, int64_t n, float *x, float *t,
+                       hydro_stream stream) {
+    if (!c || n < 0 || (n > 0 && (!faces || !x || !t))) return HYDRO_EINVAL;
+    if (n == 0) return HYDRO_OK;
+    API_CUDA(mlp_features(c, faces, n, x, t, (cudaStream_t)stream));
+    return HYDRO_OK;
+}
+
+int hydro_mlp_gradient(hydro_ctx *c, const float *x, const float *t, int64_t n, int quant,
+                       float *grad, float *loss, hydro_stream stream) {
+    if (!c || n <= 0 || !x || !t || !grad || !loss) return HYDRO_EINVAL;
+    if (!c->have_mlp) return HYDRO_ESTATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(cudaMemsetAsync(grad, 0, kMlpParams * sizeof(float), st));
+    API_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    API_CUDA(mlp_gradient(c, x, t, n, n, 0, 0, 0, quant ? 1 : 0, grad, loss, st));
+    return HYDRO_OK;
+}
+
+// He-normal initial parameters from a counter-based generator (splitmix64
+// of seed and index, Box-Muller); standardisation 0 / 1 until set from data
+static std::vector<float> mlp_init(uint64_t seed) {
+    auto mix = [](uint64_t z) {
+        z += 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    uint64_t ctr = 0;
+    auto normal = [&]() {
+        const double u1 = ((mix(seed ^ mix(ctr++)) >> 11) + 1.0) * 0x1.0p-53;
+        const double u2 = (mix(seed ^ mix(ctr++)) >> 11) * 0x1.0p-53;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    std::vector<float> w(kMlpParams, 0.f);
+    size_t k = 0;
+    for (int e = 0; e < 64 * 12; e++) w[k++] = (float)(normal() * std::sqrt(2.0 / 12.0));
+    k += 64;   // b1
+    for (int e = 0; e < 64 * 64; e++) w[k++] = (float)(normal() * std::sqrt(2.0 / 64.0));
+    k += 64;   // b2
+    for (int e = 0; e < 64; e++) w[k++] = (float)(normal() * std::sqrt(1.0 / 64.0));
+    k += 1;    // b3
+    k += 12;   // mean
+    for (int e = 0; e < 12; e++) w[k++] = 1.f;
+    k += 1;    // t_mean
+    w[k++] = 1.f;   // t_scale
+    for (int e = 0; e < 12; e++) w[k++] = -1e30f;   // feature box: set from data
+    for (int e = 0; e < 12; e++) w[k++] = 1e30f;
+    return w;
+}
+
+int hydro_mlp_train(hydro_ctx *c, const float *faces, int64_t n, int64_t steps, int64_t batch,
+                    double lr, uint64_t seed, float *loss, hydro_stream stream) {
+    if (!c || !faces || n <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0)) return HYDRO_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(c->d_mlp_x.ensure((size_t)12 * n));
+    API_CUDA(c->d_mlp_t.ensure((size_t)n));
+    API_CUDA(c->d_mlp_grad.ensure(kMlpParams));
+    API_CUDA(c->d_mlp_m.ensure(kMlpParams));
+    API_CUDA(c->d_mlp_v.ensure(kMlpParams));
+    API_CUDA(c->d_mlp_loss.ensure((size_t)std::max<int64_t>(steps, 1)));
+    API_CUDA(c->d_mlp_acc.ensure(26));
+    API_CUDA(mlp_features(c, faces, n, c->d_mlp_x.get(), c->d_mlp_t.get(), st));
+    if (!c->have_mlp) {
+        std::vector<float> w = mlp_init(seed);
+        API_CUDA(c->d_mlp.ensure(kMlpParams));
+        API_CUDA(cudaMemcpyAsync(c->d_mlp.get(), w.data(), w.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, st));
+        API_CUDA(c->d_mlp_box.ensure(24));
+        API_CUDA(mlp_normalise(c, c->d_mlp_x.get(), c->d_mlp_t.get(), n, c->d_mlp_acc.get(),
+                               c->d_mlp_box.get(), st));
+        API_CUDA(cudaStreamSynchronize(st));   // w is a host temporary
+    }
+    API_CUDA(cudaMemsetAsync(c->d_mlp_grad.get(), 0, kMlpParams * sizeof(float), st));
+    API_CUDA(cudaMemsetAsync(c->d_mlp_m.get(), 0, kMlpParams * sizeof(float), st));
+    API_CUDA(cudaMemsetAsync(c->d_mlp_v.get(), 0, kMlpParams * sizeof(float), st));
+    API_CUDA(cudaMemsetAsync(c->d_mlp_loss.get(), 0, std::max<int64_t>(steps, 1) * sizeof(float), st));
+    for (int64_t s = 1; s <= steps; s++) {
+        API_CUDA(mlp_gradient(c, c->d_mlp_x.get(), c->d_mlp_t.get(), n, batch, 1, seed,
+                              (uint64_t)s, 1, c->d_mlp_grad.get(), c->d_mlp_loss.get() + (s - 1),
+                              st));
+        // cosine decay of the learning rate to lr / 20 over the run
+        const double frac = steps > 1 ? (double)(s - 1) / (double)(steps - 1) : 0.0;
+        const double lr_s = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * frac)));
+        API_CUDA(mlp_adam(c, c->d_mlp_grad.get(), c->d_mlp_m.get(), c->d_mlp_v.get(), (float)lr_s,
+                          (int)std::min<int64_t>(s, 1 << 30), st));
+    }
+    if (loss && steps > 0)
+        API_CUDA(cudaMemcpyAsync(loss, c->d_mlp_loss.get(), steps * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st));
+    API_CUDA(mlp_pack(c, st));
+    c->have_mlp = true;
+    return HYDRO_OK;
+}
+
+int hydro_record_faces(hydro_ctx *c, float *buf, int64_t capacity, double keep_fraction,
+                       int hard_only) {
+    if (!c) return HYDRO_EINVAL;
+    if (buf && (capacity <= 0 || !(keep_fraction > 0.0 && keep_fraction <= 1.0)))
+        return HYDRO_EINVAL;
+    API_CUDA(c->d_rec_cursor.ensure(1));
+    API_CUDA(cudaDeviceSynchronize());
+    API_CUDA(cudaMemset(c->d_rec_cursor.get(), 0, sizeof(unsigned long long)));
+    c->rec_faces = buf;
+    c->rec_cap = buf ? capacity : 0;
+    c->rec_keep = (uint32_t)std::min(4294967295.0, std::floor(keep_fraction * 4294967296.0));
+    if (buf && c->rec_keep == 0) c->rec_keep = 1;
+    c->rec_hard_only = hard_only ? 1 : 0;
+    return HYDRO_OK;
+}
+
+int hydro_recorded_faces(hydro_ctx *c, int64_t *count, hydro_stream stream) {
+    if (!c || !count) return HYDRO_EINVAL;
+    unsigned long long v = 0;
+    if (c->d_rec_cursor.get()) {
+        cudaStream_t st = (cudaStream_t)stream;
+        API_CUDA(cudaMemcpyAsync(&v, c->d_rec_cursor.get(), sizeof(v), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+    }
+    *count = (int64_t)v;
     return HYDRO_OK;
 }
 
@@ -535,6 +707,7 @@ const char *hydro_strerror(int s) {
     case HYDRO_ECUDA: return "CUDA runtime error";
     case HYDRO_ESTATE: return "call order violated";
     case HYDRO_ESEARCH: return "smoothing length beyond the neighbour search radius";
+    case HYDRO_EMLP: return "tensor-core MLP wait gave up";
     default: return "unknown status";
     }
 }

@@ -24,6 +24,7 @@
 #include "hydro_internal.cuh"
 #include "pairgeom.cuh"
 #include "riemann.cuh"
+#include "mlp.cuh"
 
 namespace hyd {
 
@@ -42,7 +43,15 @@ struct FluxArgs {
     const double *dt_dev;
     double *dQ;              // 5 n, sorted SoA
     DevCounters *cnt;
-    const float *mlp;        // learned star-pressure guess (NULL: off)
+    const unsigned char *mlp_blob;   // packed network (hard-face kernel)
+    float *hard;             // deferred hard faces: FaceState fields [HF_N][hard_cap]
+    int32_t *hard_idx;       // their owner and partner (sorted indices) [2][hard_cap]
+    int64_t hard_cap;
+    float *rec_faces;        // face recording [7][rec_cap] (NULL: off)
+    unsigned long long *rec_cursor;
+    int64_t rec_cap;
+    uint32_t rec_keep;
+    int rec_hard_only;
     GasK<float> Kf;          // gas constants, precomputed on the host
     GasK<double> Kd;
     float psi1f, psi2f, ptolf, lmin_tiny;   // float copies (no per-face conversions)
@@ -132,12 +141,21 @@ struct FaceStats {
     unsigned long long pairs, iters, vacuum, first_order;
 };
 
-// the flux c (mass, momentum, energy) that particle i gives to particle j
-template <typename R, int RIEM, int SCHEME>
-__device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, const R *ri,
-                                          const R *rj, const R d[3], R r, R dt, R c[5],
-                                          FaceStats &fs) {
-    c[0] = c[1] = c[2] = c[3] = c[4] = R(0);
+// Riemann problem of one face in the frame moving with (v_i + v_j)/2:
+// normal n, left/right normal velocities and densities/pressures,
+// tangential velocities, the frame velocity and dt |A_ij|
+template <typename R>
+struct FaceState {
+    R rl, ul, pl, rr, ur, pr;
+    R wl[3], wr[3], nh[3], vf[3];
+    R sA;
+};
+
+// face vector, extrapolated and limited states; false when A_ij = 0 (no flux)
+template <typename R>
+__device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, const R *ri,
+                                           const R *rj, const R d[3], R r, R dt,
+                                           FaceState<R> &st, FaceStats &fs) {
     const R pi = R(3.14159265358979323846);
     const R hi_ = ri[R_H], hj = rj[R_H];
     const R kn = a.kernel == 0 ? R(21) / (R(2) * pi) : R(8) / pi;
@@ -158,9 +176,9 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
         A[2] = oo * (ti2 * wi + tj2 * wj);
     }
     R Amag = sqrt_(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
-    if (!(Amag > R(0))) return;
+    if (!(Amag > R(0))) return false;
     const R inA = div_(R(1), Amag);
-    const R nh[3] = {A[0] * inA, A[1] * inA, A[2] * inA};
+    st.nh[0] = A[0] * inA; st.nh[1] = A[1] * inA; st.nh[2] = A[2] * inA;
 
     R Lf[5], Rf[5];
     const R *Gi = ri + R_G, *Gj = rj + R_G;
@@ -200,18 +218,47 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
         for (int f = 0; f < 5; f++) { Lf[f] = ri[R_RHO + f]; Rf[f] = rj[R_RHO + f]; }
         fs.first_order++;
     }
-    const R vf[3] = {R(0.5) * (ri[R_VX] + rj[R_VX]), R(0.5) * (ri[R_VY] + rj[R_VY]),
-                     R(0.5) * (ri[R_VZ] + rj[R_VZ])};
+    st.vf[0] = R(0.5) * (ri[R_VX] + rj[R_VX]);
+    st.vf[1] = R(0.5) * (ri[R_VY] + rj[R_VY]);
+    st.vf[2] = R(0.5) * (ri[R_VZ] + rj[R_VZ]);
     R vl[3], vr[3];
 #pragma unroll
-    for (int q = 0; q < 3; q++) { vl[q] = Lf[1 + q] - vf[q]; vr[q] = Rf[1 + q] - vf[q]; }
-    const R ul = vl[0] * nh[0] + vl[1] * nh[1] + vl[2] * nh[2];
-    const R ur = vr[0] * nh[0] + vr[1] * nh[1] + vr[2] * nh[2];
-    R wl[3], wr[3];
+    for (int q = 0; q < 3; q++) { vl[q] = Lf[1 + q] - st.vf[q]; vr[q] = Rf[1 + q] - st.vf[q]; }
+    st.ul = vl[0] * st.nh[0] + vl[1] * st.nh[1] + vl[2] * st.nh[2];
+    st.ur = vr[0] * st.nh[0] + vr[1] * st.nh[1] + vr[2] * st.nh[2];
 #pragma unroll
-    for (int q = 0; q < 3; q++) { wl[q] = vl[q] - ul * nh[q]; wr[q] = vr[q] - ur * nh[q]; }
-    const R rl = Lf[0], pl = Lf[4], rr = Rf[0], pr = Rf[4];
+    for (int q = 0; q < 3; q++) { st.wl[q] = vl[q] - st.ul * st.nh[q]; st.wr[q] = vr[q] - st.ur * st.nh[q]; }
+    st.rl = Lf[0]; st.pl = Lf[4]; st.rr = Rf[0]; st.pr = Rf[4];
+    st.sA = dt * Amag;
+    return true;
+}
 
+// Toro's adaptive guess falls back to the two-shock value on this face (the
+// same tests as star_guess: not the PVRS value, and p_PVRS >= p_min so not
+// the two-rarefaction value, which is exact for two rarefactions).  These
+// "hard" faces are the ones where the guess is only approximate.
+template <typename R>
+__device__ __forceinline__ bool two_shock_guess(const GasK<R> &k, const FaceState<R> &st) {
+    R cl = sqrt_(div_(k.g * st.pl, st.rl)), cr = sqrt_(div_(k.g * st.pr, st.rr));
+    R ppv = R(0.5) * (st.pl + st.pr) - R(0.125) * (st.ur - st.ul) * (st.rl + st.rr) * (cl + cr);
+    ppv = ppv > R(0) ? ppv : R(0);
+    R pmin = st.pl < st.pr ? st.pl : st.pr, pmax = st.pl > st.pr ? st.pl : st.pr;
+    const bool pvrs = pmax <= R(2) * pmin && ppv >= pmin && ppv <= pmax;
+    return !pvrs && !(ppv < pmin);
+}
+
+// the flux c (mass, momentum, energy) that particle i gives to particle j,
+// from the face's Riemann problem; p0 > 0 is the exact solver's starting
+// pressure (else its adaptive guess).  ps: the star pressure (exact solver,
+// 0 on vacuum or HLLC).
+template <typename R, int RIEM, int SCHEME>
+__device__ __forceinline__ void face_finish(const FluxArgs &a, const GasK<R> &K,
+                                            const FaceState<R> &st, R p0, R c[5], FaceStats &fs,
+                                            R &ps_out) {
+    c[0] = c[1] = c[2] = c[3] = c[4] = R(0);
+    ps_out = R(0);
+    const R rl = st.rl, ul = st.ul, pl = st.pl, rr = st.rr, ur = st.ur, pr = st.pr;
+    const R *nh = st.nh, *wl = st.wl, *wr = st.wr, *vf = st.vf;
     R F[5];
     if (RIEM == HYDRO_RIEMANN_HLLC) {
         R ps, ss;
@@ -224,9 +271,10 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
     } else {
         R ps, us;
         R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)a.ptolf;
-        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, R(-1), tol, a.max_newton, ps, us);
+        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, p0, tol, a.max_newton, ps, us);
         fs.iters += so.iters;
         if (so.vacuum) { fs.vacuum++; return; }
+        ps_out = ps;
         if (SCHEME == HYDRO_MFM) {
             F[0] = R(0);
             F[1] = ps * nh[0]; F[2] = ps * nh[1]; F[3] = ps * nh[2];
@@ -251,12 +299,70 @@ __device__ __forceinline__ void face_flux(const FluxArgs &a, const GasK<R> &K, c
     // back to the lab frame
     const R vf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
     const R Fe = F[4] + (F[1] * vf[0] + F[2] * vf[1] + F[3] * vf[2]) + R(0.5) * F[0] * vf2;
-    const R sA = dt * Amag;
+    const R sA = st.sA;
     c[0] = sA * F[0];
     c[1] = sA * (F[1] + F[0] * vf[0]);
     c[2] = sA * (F[2] + F[0] * vf[1]);
     c[3] = sA * (F[3] + F[0] * vf[2]);
     c[4] = sA * Fe;
+}
+
+// append a solved face problem (rho_L, u_L, p_L, rho_R, u_R, p_R, p*) to the
+// recording buffer when the pair's hash falls under the keep threshold
+template <typename R>
+__device__ __forceinline__ void record_face(const FluxArgs &a, const GasK<R> &K,
+                                            const FaceState<R> &st, R ps, int64_t s, int64_t j) {
+    if (!(ps > R(0))) return;
+    uint64_t z = (uint64_t)s * 0x9E3779B97F4A7C15ull ^ ((uint64_t)j + 0x632BE59BD9B4E019ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    if ((uint32_t)(z >> 32) >= a.rec_keep) return;
+    if (a.rec_hard_only && !two_shock_guess<R>(K, st)) return;
+    const unsigned long long k = atomicAdd(a.rec_cursor, 1ull);
+    if ((int64_t)k >= a.rec_cap) return;
+    float *o = a.rec_faces + k;
+    const int64_t c = a.rec_cap;
+    o[0] = (float)st.rl; o[c] = (float)st.ul; o[2 * c] = (float)st.pl;
+    o[3 * c] = (float)st.rr; o[4 * c] = (float)st.ur; o[5 * c] = (float)st.pr;
+    o[6 * c] = (float)ps;
+}
+
+// deferred hard faces: the FaceState fields, structure of arrays
+constexpr int HF_N = 19;
+
+template <typename R>
+__device__ __forceinline__ void store_hard(const FluxArgs &a, const FaceState<R> &st, int64_t k,
+                                           int32_t s, int32_t j) {
+    float *o = a.hard + k;
+    const int64_t c = a.hard_cap;
+    const float v[HF_N] = {(float)st.rl, (float)st.ul, (float)st.pl, (float)st.rr, (float)st.ur,
+                           (float)st.pr, (float)st.wl[0], (float)st.wl[1], (float)st.wl[2],
+                           (float)st.wr[0], (float)st.wr[1], (float)st.wr[2], (float)st.nh[0],
+                           (float)st.nh[1], (float)st.nh[2], (float)st.vf[0], (float)st.vf[1],
+                           (float)st.vf[2], (float)st.sA};
+#pragma unroll
+    for (int q = 0; q < HF_N; q++) o[q * c] = v[q];
+    a.hard_idx[k] = s;
+    a.hard_idx[c + k] = j;
+}
+
+__device__ __forceinline__ void load_hard(const FluxArgs &a, int64_t k, FaceState<float> &st,
+                                          int32_t &s, int32_t &j) {
+    const float *o = a.hard + k;
+    const int64_t c = a.hard_cap;
+    st.rl = o[0]; st.ul = o[c]; st.pl = o[2 * c]; st.rr = o[3 * c]; st.ur = o[4 * c];
+    st.pr = o[5 * c];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        st.wl[q] = o[(6 + q) * c];
+        st.wr[q] = o[(9 + q) * c];
+        st.nh[q] = o[(12 + q) * c];
+        st.vf[q] = o[(15 + q) * c];
+    }
+    st.sA = o[18 * c];
+    s = a.hard_idx[k];
+    j = a.hard_idx[c + k];
 }
 
 // float -> double from the bit pattern with integer operations (exact for
@@ -318,7 +424,7 @@ struct FluxSmem {
     uint8_t qo[QCAP];          // queued faces: owner lane
 };
 
-template <typename R, int RIEM, int SCHEME>
+template <typename R, int RIEM, int SCHEME, bool DEFER>
 __global__ void __launch_bounds__(FLUX_WARPS * 32, sizeof(R) == 4 ? 4 : 2)
 k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     __shared__ FluxSmem<R> sm_all[FLUX_WARPS];
@@ -326,6 +432,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     FluxSmem<R> &sm = sm_all[warp];
     const int64_t b = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
+    unsigned long long n_fallback = 0;
     if (b < a.nbucket) {
         const int f = a.node_first[b], nown = a.node_cnt[b];
         const bool own = lane < nown;
@@ -360,10 +467,40 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 load_full<R>(rec + (int64_t)j * REC, rj);
                 R d[3], r2;
                 rec_sep(ri, rj, bx, d, r2);
-                face_flux<R, RIEM, SCHEME>(a, K, ri, rj, d, sqrt_(r2), dt, c, fs);
-                fs.pairs++;
+                FaceState<R> st;
+                if (face_state<R>(a, K, ri, rj, d, sqrt_(r2), dt, st, fs)) {
+                    bool deferred = false;
+                    if constexpr (DEFER) {
+                        // hard faces go to the learned-guess pass, which
+                        // applies both sides of their flux; the lanes that
+                        // defer together take their slots with one atomic.
+                        // Beyond the buffer's capacity a face is solved here
+                        // from the plain guess.
+                        if (two_shock_guess<R>(K, st)) {
+                            const unsigned am = __activemask();
+                            const int lead = __ffs(am) - 1;
+                            unsigned long long base = 0;
+                            if (lane == lead)
+                                base = atomicAdd(&a.cnt->hard_faces, (unsigned long long)__popc(am));
+                            base = __shfl_sync(am, base, lead);
+                            const int64_t slot = (int64_t)(base + __popc(am & lt));
+                            if (slot < a.hard_cap) {
+                                store_hard(a, st, slot, f + ol, j);
+                                deferred = true;
+                            } else {
+                                n_fallback++;
+                            }
+                        }
+                    }
+                    if (!deferred) {
+                        R ps;
+                        face_finish<R, RIEM, SCHEME>(a, K, st, R(-1), c, fs, ps);
+                        if (RIEM == HYDRO_RIEMANN_EXACT && a.rec_faces) record_face<R>(a, K, st, ps, f + ol, j);
 #pragma unroll
-                for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + j], widen(c[q]));
+                        for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + j], widen(c[q]));
+                    }
+                }
+                fs.pairs++;
             }
 #pragma unroll
             for (int q = 0; q < 5; q++) sm.cb[lane][q] = c[q];
@@ -424,25 +561,119 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         }
     }
     unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
-                       fo = wsum(fs.first_order);
+                       fo = wsum(fs.first_order), fb = DEFER ? wsum(n_fallback) : 0ull;
     if (lane == 0) {
         if (p) atomicAdd(&a.cnt->flux_pairs, p);
         if (it) atomicAdd(&a.cnt->newton_iters, it);
         if (va) atomicAdd(&a.cnt->vacuum, va);
         if (fo) atomicAdd(&a.cnt->first_order, fo);
+        if (fb) atomicAdd(&a.cnt->guess_fallbacks, fb);
     }
+}
+
+// Hard faces deferred by the flux kernel, solved from the learned starting
+// pressure.  Each CTA evaluates the network on tiles of 128 faces with
+// tcgen05.mma (mlp.cuh), one face per thread (row = thread), then runs the
+// exact solver from p_TS exp(y) -- or from Toro's guess when the prediction
+// is out of range -- and applies c to both sides (dQ_i -= c, dQ_j += c).
+// The iteration always runs to the same tolerance, so the guess changes the
+// iteration count, not the flux beyond rounding.
+template <int SCHEME>
+__global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
+    extern __shared__ unsigned char dyn_raw[];
+    MlpTile &T = *reinterpret_cast<MlpTile *>(
+        (reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, lane = tid & 31;
+    bool ok = mlp_tile_setup(T, a.mlp_blob);
+    uint32_t phase = 0;
+    const GasK<float> &K = a.Kf;
+    const int64_t cnt = min((int64_t)a.cnt->hard_faces, a.hard_cap);
+    const int64_t ntile = (cnt + 127) / 128;
+    FaceStats fs{0, 0, 0, 0};
+    unsigned long long n_learned = 0, n_fallback = 0;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t i = tile * 128 + tid;
+        const bool active = i < cnt;
+        FaceState<float> st;
+        int32_t s = 0, j = 0;
+        if (active) load_hard(a, i, st, s, j);
+        float p0 = -1.f;
+        if (ok) {
+            float x[MLP_NF], pa = 1.f, lts = 0.f;
+            bool in = false;
+            if (active) {
+                mlp_features(K, st.rl, st.ul, st.pl, st.rr, st.ur, st.pr, x, pa);
+                lts = x[9];
+                in = mlp_standardise(T, x);
+            } else {
+#pragma unroll
+                for (int q = 0; q < MLP_NF; q++) x[q] = 0.f;
+            }
+            mlp_put_row(T, tid, x);
+            const float y = mlp_tile_eval(T, phase, &ok);
+            const float pg = mlp_guess(in, pa, lts, y);
+            if (active && ok && pg > 0.f) p0 = pg;
+        }
+        if (active) {
+            if (p0 > 0.f) n_learned++; else n_fallback++;
+            float c[5], ps;
+            face_finish<float, HYDRO_RIEMANN_EXACT, SCHEME>(a, K, st, p0, c, fs, ps);
+            if (a.rec_faces) record_face<float>(a, K, st, ps, s, j);
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                const double v = widen(c[q]);
+                atomicAdd(&a.dQ[q * a.n + s], -v);
+                atomicAdd(&a.dQ[q * a.n + j], v);
+            }
+        }
+    }
+    const unsigned long long it = wsum(fs.iters), va = wsum(fs.vacuum), le = wsum(n_learned),
+                             fb = wsum(n_fallback);
+    if (lane == 0) {
+        if (it) atomicAdd(&a.cnt->newton_iters, it);
+        if (va) atomicAdd(&a.cnt->vacuum, va);
+        if (le) atomicAdd(&a.cnt->learned_faces, le);
+        if (fb) atomicAdd(&a.cnt->guess_fallbacks, fb);
+    }
+    if (!ok && tid == 0) atomicOr(&a.cnt->flags, ST_MLP);
+    mlp_tile_teardown(T);
 }
 
 template <typename R>
 cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, stream_t st) {
     unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
     if (riem == HYDRO_RIEMANN_HLLC) {
-        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-        else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     } else {
-        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFM><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-        else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     }
+    return launch_check();
+}
+
+// mixed precision, exact solver, learned guess: the flux kernel defers the
+// hard faces, then the hard-face kernel solves them from the network
+cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int scheme, stream_t st) {
+    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if (scheme == HYDRO_MFM)
+        k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFM, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    else
+        k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFV, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    HYD_CUDA(launch_check());
+    const size_t smem = sizeof(MlpTile) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        HYD_CUDA(cudaFuncSetAttribute(k_hard_faces<HYDRO_MFM>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HYD_CUDA(cudaFuncSetAttribute(k_hard_faces<HYDRO_MFV>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    // persistent: the count of hard faces is known on the device only
+    const unsigned hgrid = 152 * 4;
+    if (scheme == HYDRO_MFM) k_hard_faces<HYDRO_MFM><<<hgrid, 128, smem, st>>>(a);
+    else k_hard_faces<HYDRO_MFV><<<hgrid, 128, smem, st>>>(a);
     return launch_check();
 }
 
@@ -454,8 +685,9 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
     HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
-    // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 5 * sizeof(unsigned long long), st));
+    // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
+    // learned_faces, hard_faces (also the deferred-face cursor)
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 7 * sizeof(unsigned long long), st));
     FluxArgs a;
     a.n = n;
     a.nbr_off = c->d_nbr_off.get();
@@ -479,7 +711,30 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.dt_dev = dt_dev;
     a.dQ = c->d_dQ.get();
     a.cnt = c->d_cnt;
-    a.mlp = nullptr;
+    a.mlp_blob = c->d_mlp_blob.get();
+    a.hard = nullptr;
+    a.hard_idx = nullptr;
+    a.hard_cap = 0;
+    const bool learned = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
+                         c->cfg.learned_guess && c->have_mlp;
+    if (learned) {
+        // room for 8 hard faces per particle; beyond it faces are solved in
+        // the flux kernel from the plain guess
+        const int64_t cap = 8 * n + 65536;
+        if (c->hard_cap < cap) {
+            HYD_CUDA(c->d_hard.ensure((size_t)HF_N * cap));
+            HYD_CUDA(c->d_hard_idx.ensure((size_t)2 * cap));
+            c->hard_cap = cap;
+        }
+        a.hard = c->d_hard.get();
+        a.hard_idx = c->d_hard_idx.get();
+        a.hard_cap = c->hard_cap;
+    }
+    a.rec_faces = c->rec_faces;
+    a.rec_cursor = c->d_rec_cursor.get();
+    a.rec_cap = c->rec_cap;
+    a.rec_keep = c->rec_keep;
+    a.rec_hard_only = c->rec_hard_only;
     a.psi1f = (float)c->cfg.psi1;
     a.psi2f = (float)c->cfg.psi2;
     a.ptolf = (float)std::max(c->cfg.p_tol, 2e-6);
@@ -494,6 +749,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.nbucket = c->plan.nbucket;
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
+    if (learned) return launch_fluxes_learned(a, c->d_recf.get(), c->cfg.scheme, st);
     if (c->cfg.precision == HYDRO_MIXED)
         return launch_fluxes<float>(a, c->d_recf.get(), c->cfg.riemann, c->cfg.scheme, st);
     return launch_fluxes<double>(a, c->d_recd.get(), c->cfg.riemann, c->cfg.scheme, st);

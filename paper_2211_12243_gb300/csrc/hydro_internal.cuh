@@ -48,6 +48,7 @@ enum : int {
     ST_RIEMANN = 32,
     ST_NONFINITE = 64,
     ST_STACK = 128,
+    ST_MLP = 256,             // a tensor-core wait of the MLP gave up
 };
 
 struct Box {
@@ -71,6 +72,9 @@ struct DevCounters {
     unsigned long long guess_fallbacks;
     unsigned long long vacuum;
     unsigned long long first_order;
+    unsigned long long learned_faces;  // faces solved from the learned guess
+    unsigned long long hard_faces;     // faces where Toro's guess is the two-shock value
+                                       // (the cursor of the deferred-face buffer)
     double sums[2][5];                // totals before / after (m, px, py, pz, E)
 };
 
@@ -161,9 +165,26 @@ struct hydro_ctx {
     // reductions
     hyd::DevBuf<double> d_partials;
 
-    // MLP
+    // MLP: float parameters, the packed bf16 tiles the kernels copy into
+    // shared memory, and training scratch
     hyd::DevBuf<float> d_mlp;
+    hyd::DevBuf<unsigned char> d_mlp_blob;
+    hyd::DevBuf<float> d_mlp_x, d_mlp_t, d_mlp_grad, d_mlp_m, d_mlp_v, d_mlp_loss;
+    hyd::DevBuf<double> d_mlp_acc;
+    hyd::DevBuf<int> d_mlp_box;       // feature min / max as ordered integers
     bool have_mlp = false;
+
+    // hard faces deferred to the learned-guess pass (FaceState fields, owner/partner)
+    hyd::DevBuf<float> d_hard;
+    hyd::DevBuf<int32_t> d_hard_idx;
+    int64_t hard_cap = 0;
+
+    // face recording (training data for the MLP), mixed exact path
+    float *rec_faces = nullptr;       // caller's device buffer [7][rec_cap]
+    hyd::DevBuf<unsigned long long> d_rec_cursor;   // faces seen (may exceed rec_cap)
+    int64_t rec_cap = 0;
+    uint32_t rec_keep = 0;            // keep a face when its hash < rec_keep
+    int rec_hard_only = 0;
 
     // device counters + pinned host mirror
     hyd::DevCounters *d_cnt = nullptr;
@@ -218,6 +239,20 @@ cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
 
 // fluxes.cu
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st);
+
+// mlp.cu (bytes of the packed weight tiles; faces are float [6 or 7][n])
+constexpr size_t MLP_BLOB_BYTES = 11264;
+cudaError_t mlp_pack(hydro_ctx *c, stream_t st);
+cudaError_t mlp_predict(hydro_ctx *c, const float *faces, int64_t n, float *out, stream_t st);
+cudaError_t mlp_features(hydro_ctx *c, const float *faces, int64_t n, float *x, float *t,
+                         stream_t st);
+cudaError_t mlp_gradient(hydro_ctx *c, const float *x, const float *t, int64_t n, int64_t nb,
+                         int random, uint64_t seed, uint64_t step, int quant, float *grad,
+                         float *loss, stream_t st);
+cudaError_t mlp_adam(hydro_ctx *c, float *grad, float *m, float *v, float lr, int step,
+                     stream_t st);
+cudaError_t mlp_normalise(hydro_ctx *c, const float *x, const float *t, int64_t n, double *acc,
+                          int *box, stream_t st);
 
 // update.cu
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,

@@ -23,7 +23,10 @@ PRECISION = {"fp64": 0, "mixed": 1}
 
 STATUS = {0: "HYDRO_OK", -1: "HYDRO_EINVAL", -2: "HYDRO_ENOMEM", -3: "HYDRO_ECAPACITY",
           -4: "HYDRO_ENOCONV_H", -5: "HYDRO_ENCOND", -6: "HYDRO_ERIEMANN",
-          -7: "HYDRO_ENONFINITE", -8: "HYDRO_ECUDA", -9: "HYDRO_ESTATE", -10: "HYDRO_ESEARCH"}
+          -7: "HYDRO_ENONFINITE", -8: "HYDRO_ECUDA", -9: "HYDRO_ESTATE", -10: "HYDRO_ESEARCH",
+          -11: "HYDRO_EMLP"}
+
+MLP_NPARAM = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 24 + 2 + 24
 
 
 class HydroError(RuntimeError):
@@ -60,7 +63,8 @@ class Stats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("dt", C.c_double), ("dt_next", C.c_double),
         ("grad_pairs", C.c_int64), ("flux_pairs", C.c_int64), ("newton_iters", C.c_int64),
-        ("guess_fallbacks", C.c_int64), ("vacuum_faces", C.c_int64),
+        ("guess_fallbacks", C.c_int64), ("learned_faces", C.c_int64),
+        ("hard_faces", C.c_int64), ("vacuum_faces", C.c_int64),
         ("first_order_faces", C.c_int64), ("ngb_rounds", C.c_int), ("ncond_fail", C.c_int64),
         ("list_rebuilds", C.c_int), ("mass", C.c_double * 2), ("mom", (C.c_double * 3) * 2),
         ("energy", C.c_double * 2), ("ms_sort", C.c_float), ("ms_neighbours", C.c_float),
@@ -83,7 +87,9 @@ class Stats(C.Structure):
 EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_config",
            "hydro_set_boxes", "hydro_reserve", "hydro_build_neighbours", "hydro_density",
            "hydro_gradients", "hydro_fluxes", "hydro_step", "hydro_sync_status",
-           "hydro_get_stats", "hydro_mlp_load", "hydro_totals_noalloc", "hydro_kernel_launches",
+           "hydro_get_stats", "hydro_mlp_load", "hydro_mlp_get", "hydro_mlp_predict",
+           "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
+           "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
            "hydro_strerror"]
 
 
@@ -111,6 +117,13 @@ def _load():
         L.hydro_sync_status.argtypes = [vp, vp]
         L.hydro_get_stats.argtypes = [vp, P(Stats), vp]
         L.hydro_mlp_load.argtypes = [vp, vp, C.c_size_t]
+        L.hydro_mlp_get.argtypes = [vp, vp, C.c_size_t]
+        L.hydro_mlp_predict.argtypes = [vp, vp, i64, vp, vp]
+        L.hydro_mlp_features.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.hydro_mlp_gradient.argtypes = [vp, vp, vp, i64, C.c_int, vp, vp, vp]
+        L.hydro_mlp_train.argtypes = [vp, vp, i64, i64, i64, C.c_double, C.c_uint64, vp, vp]
+        L.hydro_record_faces.argtypes = [vp, vp, i64, C.c_double, C.c_int]
+        L.hydro_recorded_faces.argtypes = [vp, P(i64), vp]
         L.hydro_totals_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
@@ -310,6 +323,85 @@ class Hydro:
         rc = self.lib.hydro_mlp_load(self.h, w.ctypes.data_as(C.c_void_p), w.nbytes)
         if rc:
             raise HydroError(rc, "hydro_mlp_load")
+
+    def mlp_get(self):
+        w = np.zeros(MLP_NPARAM, dtype=np.float32)
+        rc = self.lib.hydro_mlp_get(self.h, w.ctypes.data_as(C.c_void_p), w.nbytes)
+        if rc:
+            raise HydroError(rc, "hydro_mlp_get")
+        return w
+
+    @staticmethod
+    def _faces(faces, rows):
+        assert faces.dtype.itemsize == 4 and faces.is_cuda and faces.is_contiguous()
+        assert faces.dim() == 2 and faces.shape[0] >= rows
+        return faces.shape[1]
+
+    def mlp_predict(self, faces, stream=None):
+        """faces: float32 CUDA tensor [6 (or 7), n] -> p_guess [n] (-1: out of range)."""
+        import torch
+        n = self._faces(faces, 6)
+        out = torch.empty(n, dtype=torch.float32, device=faces.device)
+        rc = self.lib.hydro_mlp_predict(self.h, _ptr(faces), n, _ptr(out), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_mlp_predict")
+        return out
+
+    def mlp_features(self, faces, stream=None):
+        import torch
+        n = self._faces(faces, 7)
+        x = torch.empty((n, 12), dtype=torch.float32, device=faces.device)
+        t = torch.empty(n, dtype=torch.float32, device=faces.device)
+        rc = self.lib.hydro_mlp_features(self.h, _ptr(faces), n, _ptr(x), _ptr(t),
+                                         _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_mlp_features")
+        return x, t
+
+    def mlp_gradient(self, x, t, quant=False, stream=None):
+        import torch
+        assert x.dtype == torch.float32 and x.is_contiguous() and x.shape[1] == 12
+        assert t.dtype == torch.float32 and t.is_contiguous() and t.numel() == x.shape[0]
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        rc = self.lib.hydro_mlp_gradient(self.h, _ptr(x), _ptr(t), x.shape[0], int(quant),
+                                         _ptr(g), _ptr(loss), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_mlp_gradient")
+        return g, loss
+
+    def mlp_train(self, faces, steps, batch=1024, lr=1e-3, seed=0, stream=None):
+        """Train on recorded faces [7, n]; returns the per-step loss tensor."""
+        import torch
+        n = self._faces(faces, 7)
+        loss = torch.zeros(max(int(steps), 1), dtype=torch.float32, device=faces.device)
+        rc = self.lib.hydro_mlp_train(self.h, _ptr(faces), n, int(steps), int(batch), float(lr),
+                                      int(seed), _ptr(loss), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_mlp_train")
+        return loss[: int(steps)]
+
+    def record_faces(self, buf, keep=1.0, hard_only=False):
+        """Record solved faces of the next flux calls into buf (float32 CUDA
+        tensor [7, capacity]); buf=None stops recording."""
+        cap = 0 if buf is None else self._faces(buf, 7)
+        rc = self.lib.hydro_record_faces(self.h, _ptr(buf), cap, float(keep), int(hard_only))
+        if rc:
+            raise HydroError(rc, "hydro_record_faces")
+
+    def recorded_faces(self, stream=None):
+        v = C.c_int64()
+        rc = self.lib.hydro_recorded_faces(self.h, C.byref(v), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_recorded_faces")
+        return v.value
+
+    def get_stats(self, stream=None):
+        s = Stats()
+        rc = self.lib.hydro_get_stats(self.h, C.byref(s), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_get_stats")
+        return s.as_dict()
 
 
 def to_device(w, device="cuda", keys=("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")):

@@ -7,7 +7,8 @@ import pytest
 
 from paper_2211_12243_gb300 import workloads as W
 
-from parity_util import compare, conservation, flux_scale, gpu_stages, oracle_stages
+from parity_util import (compare, compare_masked as _compare_masked, conservation, flux_scale,
+                         gpu_stages, oracle_stages)
 
 pytestmark = pytest.mark.gpu
 
@@ -62,48 +63,6 @@ def test_neighbour_lists_bit_exact(orc, hyd, name):
     off_o, idx_o = orc.neighbours(w["x"], w["y"], w["z"], w["L"], hs)
     assert np.array_equal(off.cpu().numpy(), off_o)
     assert np.array_equal(idx.cpu().numpy(), idx_o)
-
-
-def _well_conditioned(orc, w, o, crit=100.0):
-    """Particles whose own E and whose neighbours' E are well conditioned
-    (N_cond <= crit): the staged calls run without the N_cond guard, and for
-    a (near-)singular E the inverse is rounding noise in any precision."""
-    ok = o["ncond"] <= crit
-    off, idx = orc.neighbours(w["x"], w["y"], w["z"], w["L"], o["h"] * 1.0000001)
-    good = ok.copy()
-    for i in np.nonzero(ok)[0]:
-        good[i] = ok[idx[off[i]:off[i + 1]]].all()
-    return ok, good
-
-
-def _mask(o, g, ok, good):
-    o2, g2 = dict(o), dict(g)
-    for k in ("B", "grad", "alpha", "ncond"):
-        o2[k], g2[k] = o[k][ok], g[k][ok]
-    o2["prims"] = tuple(p[ok] for p in o["prims"])
-    o2["h_m"] = o["h"][ok]
-    for k in ("dQ", "dQabs"):
-        o2[k] = o[k][good]
-    g2["dQ"] = g["dQ"][good]
-    o2["prims_g"] = tuple(p[good] for p in o["prims"])
-    return o2, g2
-
-
-def _compare_masked(orc, w, o, g, tol, what):
-    ok, good = _well_conditioned(orc, w, o)
-    assert good.mean() > 0.9
-    o2, g2 = _mask(o, g, ok, good)
-    errs, bad = {}, {}
-    e, b = compare(g, o, tol, what=tuple(k for k in what if k in ("h", "omega")))
-    errs.update(e); bad.update(b)
-    oh = dict(o2, h=o2["h_m"])
-    e, b = compare(g2, oh, tol, what=tuple(k for k in what if k in ("B", "grad", "ncond")))
-    errs.update(e); bad.update(b)
-    if "dQ" in what:
-        od = dict(o2, prims=o2["prims_g"])
-        e, b = compare(g2, od, tol, what=("dQ",))
-        errs.update(e); bad.update(b)
-    return errs, bad
 
 
 @pytest.mark.parametrize("name", list(CASES))
