@@ -124,8 +124,9 @@ typedef struct {
     int64_t grad_pairs;       /* directed pairs j != i, r_ij < h_i (gradient stage) */
     int64_t flux_pairs;       /* unordered pairs r_ij < max(h_i, h_j) (flux stage) */
     int64_t newton_iters;     /* Riemann Newton iterations summed over faces */
-    int64_t guess_fallbacks;  /* hard faces that kept the plain guess (learned guess
-                                 out of range, or no network evaluated) */
+    int64_t guess_fallbacks;  /* hard faces that kept the plain guess: learned value
+                                 out of range, a correction |y| < 1e-3 (kept at the
+                                 two-shock value), or no room to defer the face */
     int64_t learned_faces;    /* faces whose Newton iteration started from the MLP */
     int64_t hard_faces;       /* faces where Toro's guess is the two-shock value */
     int64_t vacuum_faces;
@@ -135,6 +136,8 @@ typedef struct {
     int list_rebuilds;        /* neighbour-list rebuilds for h beyond the radius */
     double mass[2], mom[2][3], energy[2];   /* totals before / after the step */
     float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
+    float ms_flux_kernel;     /* the pair-flux kernel alone (CUDA events on the stream) */
+    float ms_hard_faces;      /* the learned-guess hard-face kernel (0 when off) */
 } hydro_stats;
 
 /* Defaults described above.  Always succeeds. */
@@ -287,7 +290,8 @@ int hydro_mlp_gradient(hydro_ctx *ctx, const float *x, const float *t, int64_t n
  * counter-based generator from `seed`, learning rate lr, bf16-rounded
  * forward pass.  Without a loaded network, first initialises one (He
  * normal from `seed`) and sets the feature and target standardisations and
- * the feature box from the data; with one, continues training it.  The learning rate decays
+ * the feature box from the data; with one, continues training it.  Samples
+ * with a non-finite feature or target are skipped.  The learning rate decays
  * from lr to lr/20 along a cosine.  loss (device, `steps` floats, may be
  * NULL) receives the minibatch loss of each step. */
 int hydro_mlp_train(hydro_ctx *ctx, const float *faces, int64_t n, int64_t steps,
@@ -299,7 +303,8 @@ int hydro_mlp_train(hydro_ctx *ctx, const float *faces, int64_t n, int64_t steps
  * `capacity` floats: rho_L, u_L, p_L, rho_R, u_R, p_R, p*).  A face is kept
  * when a hash of its particle pair falls below keep_fraction (0..1], and,
  * with hard_only = 1, only when it is a hard face.  buf = NULL stops the
- * recording.  Resets the recorded count (synchronous). */
+ * recording.  Only faces with positive densities and pressures on both
+ * sides and p* > 0 are recorded.  Resets the recorded count (synchronous). */
 int hydro_record_faces(hydro_ctx *ctx, float *buf, int64_t capacity, double keep_fraction,
                        int hard_only);
 

@@ -85,6 +85,13 @@ def in_range(theta, x, y):
     return inside & (np.abs(y) <= 2.0)
 
 
+def use_learned(theta, x, y):
+    """Faces that start the solver from the learned value: in range and a
+    correction |y| >= 1e-3 (a smaller one keeps the two-shock value, which
+    then starts within 1e-3 of p* anyway)."""
+    return in_range(theta, x, y) & (np.abs(y) >= 1e-3)
+
+
 def unpack(theta):
     theta = np.asarray(theta, dtype=np.float64)
     out, k = {}, 0

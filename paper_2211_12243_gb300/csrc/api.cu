@@ -242,7 +242,7 @@ int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_cnt, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters));
     if (e == cudaSuccess) {
-        for (int k = 0; k < 8 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
+        for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
         c->have_events = e == cudaSuccess;
     }
     if (e != cudaSuccess) {
@@ -259,7 +259,7 @@ void hydro_destroy(hydro_ctx *c) {
     if (c->d_cnt) cudaFree(c->d_cnt);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->have_events)
-        for (int k = 0; k < 8; k++) cudaEventDestroy(c->ev[k]);
+        for (int k = 0; k < 10; k++) cudaEventDestroy(c->ev[k]);
     delete c;
 }
 
@@ -454,7 +454,10 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     }
     if (timing) API_CUDA(cudaEventRecord(c->ev[3], st));
     const double *dt_dev = dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
-    API_CUDA(run_fluxes(c, dt, dt_dev, st));
+    c->timing = timing;
+    rc = run_fluxes(c, dt, dt_dev, st);
+    c->timing = false;
+    API_CUDA((cudaError_t)rc);
     if (timing) API_CUDA(cudaEventRecord(c->ev[4], st));
     API_CUDA(run_update(c, p, dt, dt_dev, st));
     if (stats) API_CUDA(run_update_sums(c, st));
@@ -492,6 +495,11 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
             cudaEventElapsedTime(&S.ms_gradients, c->ev[2], c->ev[3]);
             cudaEventElapsedTime(&S.ms_fluxes, c->ev[3], c->ev[4]);
             cudaEventElapsedTime(&S.ms_update, c->ev[4], c->ev[5]);
+            cudaEventElapsedTime(&S.ms_flux_kernel, c->ev[6], c->ev[7]);
+            S.ms_hard_faces = 0.f;
+            if (c->cfg.learned_guess && c->cfg.precision == HYDRO_MIXED &&
+                c->cfg.riemann == HYDRO_RIEMANN_EXACT)
+                cudaEventElapsedTime(&S.ms_hard_faces, c->ev[7], c->ev[8]);
             S.ms_sort = 0.f;
         }
         *stats = S;
@@ -630,7 +638,7 @@ int hydro_mlp_train(hydro_ctx *c, const float *faces, int64_t n, int64_t steps, 
     API_CUDA(c->d_mlp_m.ensure(kMlpParams));
     API_CUDA(c->d_mlp_v.ensure(kMlpParams));
     API_CUDA(c->d_mlp_loss.ensure((size_t)std::max<int64_t>(steps, 1)));
-    API_CUDA(c->d_mlp_acc.ensure(26));
+    API_CUDA(c->d_mlp_acc.ensure(27));
     API_CUDA(mlp_features(c, faces, n, c->d_mlp_x.get(), c->d_mlp_t.get(), st));
     if (!c->have_mlp) {
         std::vector<float> w = mlp_init(seed);

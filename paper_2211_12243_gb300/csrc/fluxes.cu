@@ -46,7 +46,8 @@ struct FluxArgs {
     const unsigned char *mlp_blob;   // packed network (hard-face kernel)
     float *hard;             // deferred hard faces: FaceState fields [HF_N][hard_cap]
     int32_t *hard_idx;       // their owner and partner (sorted indices) [2][hard_cap]
-    int64_t hard_cap;
+    unsigned long long *hard_cursor;   // faces taken in each of the HARD_SUB sub-buffers
+    int64_t hard_cap;        // HARD_SUB sub-buffers of hard_cap / HARD_SUB slots
     float *rec_faces;        // face recording [7][rec_cap] (NULL: off)
     unsigned long long *rec_cursor;
     int64_t rec_cap;
@@ -312,7 +313,8 @@ __device__ __forceinline__ void face_finish(const FluxArgs &a, const GasK<R> &K,
 template <typename R>
 __device__ __forceinline__ void record_face(const FluxArgs &a, const GasK<R> &K,
                                             const FaceState<R> &st, R ps, int64_t s, int64_t j) {
-    if (!(ps > R(0))) return;
+    // only physical problems (a cell with negative pressure can reach here)
+    if (!(ps > R(0) && st.rl > R(0) && st.pl > R(0) && st.rr > R(0) && st.pr > R(0))) return;
     uint64_t z = (uint64_t)s * 0x9E3779B97F4A7C15ull ^ ((uint64_t)j + 0x632BE59BD9B4E019ull);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -328,8 +330,10 @@ __device__ __forceinline__ void record_face(const FluxArgs &a, const GasK<R> &K,
     o[6 * c] = (float)ps;
 }
 
-// deferred hard faces: the FaceState fields, structure of arrays
+// deferred hard faces: the FaceState fields, structure of arrays, in
+// HARD_SUB sub-buffers with a cursor each (CTA b writes sub-buffer b mod HARD_SUB)
 constexpr int HF_N = 19;
+constexpr int HARD_SUB = 256;
 
 template <typename R>
 __device__ __forceinline__ void store_hard(const FluxArgs &a, const FaceState<R> &st, int64_t k,
@@ -365,15 +369,16 @@ __device__ __forceinline__ void load_hard(const FluxArgs &a, int64_t k, FaceStat
     j = a.hard_idx[c + k];
 }
 
-// float -> double from the bit pattern with integer operations (exact for
-// normal floats; the conversion instruction would use the FP64 pipe)
+// float -> double from the bit pattern with integer operations only (the
+// conversion instruction runs on the FP64 pipe): exact for normal floats,
+// infinities and NaNs; zeros and subnormals (below 1.2e-38) become signed 0
 __device__ __forceinline__ double widen(float f) {
-    uint32_t u = __float_as_uint(f);
-    uint32_t ex = (u >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return (double)f;   // zero, subnormal, inf, nan
-    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                           ((unsigned long long)(ex + 896u) << 52) |
-                           ((unsigned long long)(u & 0x7fffffu) << 29);
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);
+    const unsigned long long b = ex == 0u ? sign : (sign | (e64 << 52) | man);
     return __longlong_as_double((long long)b);
 }
 __device__ __forceinline__ double widen(double f) { return f; }
@@ -432,7 +437,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     FluxSmem<R> &sm = sm_all[warp];
     const int64_t b = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
-    unsigned long long n_fallback = 0;
+    unsigned long long n_fallback = 0, n_hard = 0;
     if (b < a.nbucket) {
         const int f = a.node_first[b], nown = a.node_cnt[b];
         const bool own = lane < nown;
@@ -477,15 +482,19 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                         // Beyond the buffer's capacity a face is solved here
                         // from the plain guess.
                         if (two_shock_guess<R>(K, st)) {
+                            n_hard++;
+                            // the CTA's sub-buffer (spreads the cursor atomics)
+                            const int sub = blockIdx.x & (HARD_SUB - 1);
+                            const int64_t subcap = a.hard_cap / HARD_SUB;
                             const unsigned am = __activemask();
                             const int lead = __ffs(am) - 1;
                             unsigned long long base = 0;
                             if (lane == lead)
-                                base = atomicAdd(&a.cnt->hard_faces, (unsigned long long)__popc(am));
+                                base = atomicAdd(&a.hard_cursor[sub], (unsigned long long)__popc(am));
                             base = __shfl_sync(am, base, lead);
-                            const int64_t slot = (int64_t)(base + __popc(am & lt));
-                            if (slot < a.hard_cap) {
-                                store_hard(a, st, slot, f + ol, j);
+                            const int64_t k = (int64_t)(base + __popc(am & lt));
+                            if (k < subcap) {
+                                store_hard(a, st, sub * subcap + k, f + ol, j);
                                 deferred = true;
                             } else {
                                 n_fallback++;
@@ -561,9 +570,11 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         }
     }
     unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
-                       fo = wsum(fs.first_order), fb = DEFER ? wsum(n_fallback) : 0ull;
+                       fo = wsum(fs.first_order), fb = DEFER ? wsum(n_fallback) : 0ull,
+                       ha = DEFER ? wsum(n_hard) : 0ull;
     if (lane == 0) {
         if (p) atomicAdd(&a.cnt->flux_pairs, p);
+        if (ha) atomicAdd(&a.cnt->hard_faces, ha);
         if (it) atomicAdd(&a.cnt->newton_iters, it);
         if (va) atomicAdd(&a.cnt->vacuum, va);
         if (fo) atomicAdd(&a.cnt->first_order, fo);
@@ -587,13 +598,19 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
     bool ok = mlp_tile_setup(T, a.mlp_blob);
     uint32_t phase = 0;
     const GasK<float> &K = a.Kf;
-    const int64_t cnt = min((int64_t)a.cnt->hard_faces, a.hard_cap);
-    const int64_t ntile = (cnt + 127) / 128;
+    // tiles of 128 slots never straddle sub-buffers (their size is a
+    // multiple of 128); tiles past a sub-buffer's count are skipped whole
+    const int64_t subcap = a.hard_cap / HARD_SUB;
+    const int64_t ntile = a.hard_cap / 128;
     FaceStats fs{0, 0, 0, 0};
     unsigned long long n_learned = 0, n_fallback = 0;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const int64_t i = tile * 128 + tid;
-        const bool active = i < cnt;
+        const int64_t sub = (tile * 128) / subcap;
+        const int64_t cnt = min((int64_t)a.hard_cursor[sub], subcap);
+        const int64_t first = tile * 128 - sub * subcap;
+        if (first >= cnt) continue;   // uniform over the CTA
+        const bool active = i - sub * subcap < cnt;
         FaceState<float> st;
         int32_t s = 0, j = 0;
         if (active) load_hard(a, i, st, s, j);
@@ -612,7 +629,10 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
             mlp_put_row(T, tid, x);
             const float y = mlp_tile_eval(T, phase, &ok);
             const float pg = mlp_guess(in, pa, lts, y);
-            if (active && ok && pg > 0.f) p0 = pg;
+            // a correction below 1e-3 is kept at the two-shock value: a
+            // start within 1e-3 converges in as few iterations either way,
+            // and the two-shock value may be nearly exact (weak shocks)
+            if (active && ok && pg > 0.f && fabsf(y) >= 1e-3f) p0 = pg;
         }
         if (active) {
             if (p0 > 0.f) n_learned++; else n_fallback++;
@@ -640,8 +660,10 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
 }
 
 template <typename R>
-cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, stream_t st) {
+cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, stream_t st,
+                          cudaEvent_t *ev) {
     unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
     if (riem == HYDRO_RIEMANN_HLLC) {
         if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
         else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
@@ -649,18 +671,23 @@ cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme,
         if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
         else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     }
-    return launch_check();
+    HYD_CUDA(launch_check());
+    if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
+    return cudaSuccess;
 }
 
 // mixed precision, exact solver, learned guess: the flux kernel defers the
 // hard faces, then the hard-face kernel solves them from the network
-cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int scheme, stream_t st) {
+cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int scheme, stream_t st,
+                                  cudaEvent_t *ev) {
     const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
     if (scheme == HYDRO_MFM)
         k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFM, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     else
         k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFV, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     HYD_CUDA(launch_check());
+    if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
     const size_t smem = sizeof(MlpTile) + 1024;
     static bool configured = false;
     if (!configured) {
@@ -674,7 +701,9 @@ cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int schem
     const unsigned hgrid = 152 * 4;
     if (scheme == HYDRO_MFM) k_hard_faces<HYDRO_MFM><<<hgrid, 128, smem, st>>>(a);
     else k_hard_faces<HYDRO_MFV><<<hgrid, 128, smem, st>>>(a);
-    return launch_check();
+    HYD_CUDA(launch_check());
+    if (ev) HYD_CUDA(cudaEventRecord(ev[2], st));
+    return cudaSuccess;
 }
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -686,7 +715,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
     HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
     // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
-    // learned_faces, hard_faces (also the deferred-face cursor)
+    // learned_faces, hard_faces
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 7 * sizeof(unsigned long long), st));
     FluxArgs a;
     a.n = n;
@@ -714,20 +743,25 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.mlp_blob = c->d_mlp_blob.get();
     a.hard = nullptr;
     a.hard_idx = nullptr;
+    a.hard_cursor = nullptr;
     a.hard_cap = 0;
     const bool learned = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
                          c->cfg.learned_guess && c->have_mlp;
     if (learned) {
         // room for 8 hard faces per particle; beyond it faces are solved in
         // the flux kernel from the plain guess
-        const int64_t cap = 8 * n + 65536;
+        const int64_t unit = (int64_t)HARD_SUB * 128;
+        const int64_t cap = (8 * n + 65536 + unit - 1) / unit * unit;
         if (c->hard_cap < cap) {
             HYD_CUDA(c->d_hard.ensure((size_t)HF_N * cap));
             HYD_CUDA(c->d_hard_idx.ensure((size_t)2 * cap));
             c->hard_cap = cap;
         }
+        HYD_CUDA(c->d_hard_cursor.ensure(HARD_SUB));
+        HYD_CUDA(cudaMemsetAsync(c->d_hard_cursor.get(), 0, HARD_SUB * sizeof(unsigned long long), st));
         a.hard = c->d_hard.get();
         a.hard_idx = c->d_hard_idx.get();
+        a.hard_cursor = c->d_hard_cursor.get();
         a.hard_cap = c->hard_cap;
     }
     a.rec_faces = c->rec_faces;
@@ -749,10 +783,11 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.nbucket = c->plan.nbucket;
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
-    if (learned) return launch_fluxes_learned(a, c->d_recf.get(), c->cfg.scheme, st);
+    cudaEvent_t *ev = c->timing ? c->ev + 6 : nullptr;
+    if (learned) return launch_fluxes_learned(a, c->d_recf.get(), c->cfg.scheme, st, ev);
     if (c->cfg.precision == HYDRO_MIXED)
-        return launch_fluxes<float>(a, c->d_recf.get(), c->cfg.riemann, c->cfg.scheme, st);
-    return launch_fluxes<double>(a, c->d_recd.get(), c->cfg.riemann, c->cfg.scheme, st);
+        return launch_fluxes<float>(a, c->d_recf.get(), c->cfg.riemann, c->cfg.scheme, st, ev);
+    return launch_fluxes<double>(a, c->d_recd.get(), c->cfg.riemann, c->cfg.scheme, st, ev);
 }
 
 }  // namespace hyd

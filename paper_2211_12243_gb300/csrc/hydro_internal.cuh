@@ -74,7 +74,6 @@ struct DevCounters {
     unsigned long long first_order;
     unsigned long long learned_faces;  // faces solved from the learned guess
     unsigned long long hard_faces;     // faces where Toro's guess is the two-shock value
-                                       // (the cursor of the deferred-face buffer)
     double sums[2][5];                // totals before / after (m, px, py, pz, E)
 };
 
@@ -177,6 +176,7 @@ struct hydro_ctx {
     // hard faces deferred to the learned-guess pass (FaceState fields, owner/partner)
     hyd::DevBuf<float> d_hard;
     hyd::DevBuf<int32_t> d_hard_idx;
+    hyd::DevBuf<unsigned long long> d_hard_cursor;
     int64_t hard_cap = 0;
 
     // face recording (training data for the MLP), mixed exact path
@@ -192,8 +192,9 @@ struct hydro_ctx {
     int pending_status = 0;
 
     hydro_stats last_stats;
-    cudaEvent_t ev[8];
+    cudaEvent_t ev[10];               // 0-5 stage boundaries, 6-9 around the flux kernels
     bool have_events = false;
+    bool timing = false;              // record ev[6..9] in the flux launcher
 };
 
 namespace hyd {

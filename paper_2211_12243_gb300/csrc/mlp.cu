@@ -149,8 +149,12 @@ __global__ void __launch_bounds__(GRAD_THREADS) k_mlp_grad(const float *__restri
     const float *mean = pb + 3 * MLP_NH + 1, *scale = mean + MLP_NF;
     const float tmean = pb[3 * MLP_NH + 1 + 2 * MLP_NF], tscale = pb[3 * MLP_NH + 2 + 2 * MLP_NF];
     const int64_t slot = blockIdx.x * (int64_t)GRAD_THREADS + tid;
-    const bool active = slot < nb;
+    bool active = slot < nb;
     const int64_t idx = active ? (random ? sample_index(seed, step, slot, n) : slot) : 0;
+    // samples with a non-finite feature or target (an unphysical face) are skipped
+    bool finite = active && isfinite(t[idx]);
+    for (int k = 0; k < MLP_NF; k++) finite = finite && isfinite(x[idx * MLP_NF + k]);
+    active = finite;
     float target = active ? t[idx] : 0.f;
     for (int k = 0; k < MLP_NF; k++)
         xs[tid * 13 + k] = active ? bfr((x[idx * MLP_NF + k] - mean[k]) / scale[k], q) : 0.f;
@@ -254,16 +258,22 @@ __device__ __forceinline__ float ord_val(int k) {
 }
 
 // per-feature and target mean and standard deviation (double accumulators:
-// acc[0..11] sums, [12..23] sums of squares, [24], [25] the target's) and
-// the feature box (box[0..11] min keys, [12..23] max keys)
+// acc[0..11] sums, [12..23] sums of squares, [24], [25] the target's, [26]
+// the count) and the feature box (box[0..11] min keys, [12..23] max keys),
+// over the samples whose features and target are all finite
 __global__ void k_mlp_stats(int64_t n, const float *__restrict__ x, const float *__restrict__ t,
                             double *__restrict__ acc, int *__restrict__ box) {
     double s[MLP_NF + 1], s2[MLP_NF + 1];
     float lo[MLP_NF], hi[MLP_NF];
     for (int k = 0; k <= MLP_NF; k++) s[k] = s2[k] = 0.0;
     for (int k = 0; k < MLP_NF; k++) { lo[k] = 3.0e38f; hi[k] = -3.0e38f; }
+    double cnt = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = isfinite(t[i]);
+        for (int k = 0; k < MLP_NF; k++) ok = ok && isfinite(x[i * MLP_NF + k]);
+        if (!ok) continue;
+        cnt += 1.0;
         for (int k = 0; k <= MLP_NF; k++) {
             const float f = k < MLP_NF ? x[i * MLP_NF + k] : t[i];
             const double v = f;
@@ -271,6 +281,8 @@ __global__ void k_mlp_stats(int64_t n, const float *__restrict__ x, const float 
             s2[k] += v * v;
             if (k < MLP_NF) { lo[k] = fminf(lo[k], f); hi[k] = fmaxf(hi[k], f); }
         }
+    }
+    atomicAdd(&acc[2 * MLP_NF + 2], cnt);
     for (int k = 0; k < MLP_NF; k++) {
         atomicAdd(&acc[k], s[k]);
         atomicAdd(&acc[MLP_NF + k], s2[k]);
@@ -293,10 +305,11 @@ __global__ void k_mlp_set_norm(int64_t n, const double *__restrict__ acc, const 
                                float *__restrict__ theta) {
     int k = threadIdx.x;
     if (k > MLP_NF) return;
+    const double cnt = acc[2 * MLP_NF + 2] > 0.0 ? acc[2 * MLP_NF + 2] : 1.0;
     const double sum = k < MLP_NF ? acc[k] : acc[2 * MLP_NF];
     const double sq = k < MLP_NF ? acc[MLP_NF + k] : acc[2 * MLP_NF + 1];
-    const double mu = sum / (double)n;
-    const double var = sq / (double)n - mu * mu;
+    const double mu = sum / cnt;
+    const double var = sq / cnt - mu * mu;
     const double sd = sqrt(var > 0.0 ? var : 0.0);
     if (k < MLP_NF) {
         theta[MLP_OFF_MEAN + k] = (float)mu;
@@ -370,7 +383,7 @@ cudaError_t mlp_adam(hydro_ctx *c, float *grad, float *m, float *v, float lr, in
 
 cudaError_t mlp_normalise(hydro_ctx *c, const float *x, const float *t, int64_t n, double *acc,
                           int *box, stream_t st) {
-    HYD_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (2 * MLP_NF + 2), st));
+    HYD_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (2 * MLP_NF + 3), st));
     k_mlp_box_init<<<1, 32, 0, st>>>(box);
     HYD_CUDA(launch_check());
     k_mlp_stats<<<256, 256, 0, st>>>(n, x, t, acc, box);

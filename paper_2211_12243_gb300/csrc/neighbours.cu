@@ -1,9 +1,11 @@
 // Bucketed neighbour search (§2.2.3).  The Morton-sorted particles are cut
 // into buckets of 32 (one warp each); buckets are grouped 32 at a time into
 // a fixed-arity bounding-box tree per periodic box.  One warp walks the tree
-// once for its whole bucket (the paper's single search per bucket), tests
-// every candidate particle against each of its 32 particles, and appends
-// the matches to per-lane lists in shared memory before one bulk write.
+// once for its whole bucket (the paper's single search per bucket).  Each
+// candidate bucket is staged in shared memory -- only its particles within
+// the search radius of the warp's bucket box, compacted -- and every lane
+// tests the staged particles against its own, appending matches to its
+// fixed-stride row of the list (or, for long lists, the overflow region).
 //
 // Membership r_ij < h_search,i is decided exactly as the definition states
 // in double precision: a float test on the fixed-point separation settles
@@ -118,9 +120,9 @@ struct ListArgs {
     int32_t *nbr_cnt;
     int64_t capacity;
     DevCounters *cnt;
-    int cap;   // per-lane staging entries
-    int mode;  // 0: stage in shared memory, one bulk write (buckets whose
-               //    lists overflow the staging are queued in ovf_list);
+    int cap;   // fixed slots per particle (row s at s cap)
+    int mode;  // 0: write the fixed-stride rows (buckets with a row longer
+               //    than cap are queued in ovf_list);
                // 1: count and reserve storage (queued buckets);
                // 2: write at nbr_off (queued buckets)
     int32_t *ovf_list;      // queued bucket ids
@@ -172,47 +174,64 @@ __device__ __forceinline__ void cand_load(const ListArgs &a, int j, Cand &c) {
 
 struct Stage {
     double *sx, *sy, *sz;
-    float4 *sr;
+    float4 *sr;              // position relative to the warp's origin; .w = index bits
     uint32_t *sq;
 };
 
-__device__ __forceinline__ void cand_store(const Stage &S, int lane, const Cand &c, uint32_t ox,
-                                           uint32_t oy, uint32_t oz, const Box &bx) {
-    S.sx[lane] = c.x; S.sy[lane] = c.y; S.sz[lane] = c.z;
-    S.sq[lane] = c.qx; S.sq[32 + lane] = c.qy; S.sq[64 + lane] = c.qz;
-    S.sr[lane] = make_float4(qdiff(ox, c.qx, bx.s[0]), qdiff(oy, c.qy, bx.s[1]),
-                             qdiff(oz, c.qz, bx.s[2]), 0.f);
+// per-stage bytes: sr[32] float4 | sx sy sz [32] double | sq[96]
+constexpr size_t STAGE_BYTES = 32 * 16 + 3 * 32 * 8 + 96 * 4;
+
+// Stage this lane's candidate (keep = it can lie within the search radius
+// of some particle of the warp's bucket): the kept candidates are compacted
+// to the front in their original order; returns their number.
+__device__ __forceinline__ int cand_stage(const Stage &S, bool keep, int lane, const Cand &c, int j,
+                                          uint32_t ox, uint32_t oy, uint32_t oz, const Box &bx) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+        const int pos = __popc(m & ((1u << lane) - 1u));
+        S.sx[pos] = c.x; S.sy[pos] = c.y; S.sz[pos] = c.z;
+        S.sq[pos] = c.qx; S.sq[32 + pos] = c.qy; S.sq[64 + pos] = c.qz;
+        S.sr[pos] = make_float4(qdiff(ox, c.qx, bx.s[0]), qdiff(oy, c.qy, bx.s[1]),
+                                qdiff(oz, c.qz, bx.s[2]), __int_as_float(j));
+    }
+    return __popc(m);
 }
 
-// decide candidate k of the staged bucket for this lane
-__device__ __forceinline__ void decide(const ListArgs &a, const Lane &L, const Stage &S, const Box &bx,
-                                       int f, int k, float r2, int &count) {
-    bool in;
-    if (r2 < L.lo2) in = true;
-    else if (r2 > L.hi2) in = false;
-    else {
+// can candidate c lie within rad2 of a point of the bucket box [lo, hi]?
+// (a lower bound of the periodic distance, as in sphere_near)
+__device__ __forceinline__ bool cand_near(const Cand &c, uint4 lo, uint4 hi, const Box &bx,
+                                          float rad2) {
+    float gx = u2f(point_gap(c.qx, lo.x, hi.x)) * bx.s[0];
+    float gy = u2f(point_gap(c.qy, lo.y, hi.y)) * bx.s[1];
+    float gz = u2f(point_gap(c.qz, lo.z, hi.z)) * bx.s[2];
+    return gx * gx + gy * gy + gz * gz <= rad2;
+}
+
+// Output row of a lane: where its matches go and how many fit.
+struct Row {
+    int32_t *out;
+    int lim;
+};
+
+// decide staged candidate k for this lane
+__device__ __forceinline__ void decide(const Lane &L, const Row &R, const Stage &S, const Box &bx,
+                                       int k, float r2, int &count) {
+    bool in = r2 < L.lo2;
+    if (!in && r2 <= L.hi2) {   // within the float band: decide in double
         double ex = fold64(__dsub_rn(S.sx[k], L.x), bx.L[0]);
         double ey = fold64(__dsub_rn(S.sy[k], L.y), bx.L[1]);
         double ez = fold64(__dsub_rn(S.sz[k], L.z), bx.L[2]);
         in = r2_exact(ex, ey, ez) < L.h2;
     }
     if (in) {
-        if (a.mode == 0) {
-            if (count < a.cap) a.nbr_idx[(int64_t)L.s * a.cap + count] = f + k;
-        } else if (a.mode == 2) {
-            // storage was reserved in mode 1; a reservation that did not
-            // fit (the capacity flag is set and the host rebuilds) must
-            // not write past the buffer
-            int64_t pos = a.nbr_off[L.s] + count;
-            if (pos < a.capacity) a.nbr_idx[pos] = f + k;
-        }
+        if (count < R.lim) R.out[count] = __float_as_int(S.sr[k].w);
         count++;
     }
 }
 
 // every lane scans the c staged candidates (four at a time for overlap)
-__device__ __forceinline__ void scan_stage(const ListArgs &a, const Lane &L, const Stage &S,
-                                           const Box &bx, int f, int c, int &count) {
+__device__ __forceinline__ void scan_stage(const Lane &L, const Row &R, const Stage &S,
+                                           const Box &bx, int c, int &count) {
     if (!L.own) return;
     if (L.rel_ok) {
         for (int k = 0; k < c; k += 4) {
@@ -225,29 +244,29 @@ __device__ __forceinline__ void scan_stage(const ListArgs &a, const Lane &L, con
             }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (k + u < c) decide(a, L, S, bx, f, k + u, r2[u], count);
+                if (k + u < c) decide(L, R, S, bx, k + u, r2[u], count);
         }
     } else {
         for (int k = 0; k < c; k++) {
             float dx = qdiff(L.qx, S.sq[k], bx.s[0]);
             float dy = qdiff(L.qy, S.sq[32 + k], bx.s[1]);
             float dz = qdiff(L.qz, S.sq[64 + k], bx.s[2]);
-            decide(a, L, S, bx, f, k, dx * dx + dy * dy + dz * dz, count);
+            decide(L, R, S, bx, k, dx * dx + dy * dy + dz * dz, count);
         }
     }
 }
 
-__global__ void __launch_bounds__(LIST_WARPS * 32, 6) k_build_lists(ListArgs a) {
+__global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_build_lists(ListArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t b = blockIdx.x * (int64_t)LIST_WARPS + warp;
-    // per-warp shared memory: stack[STACK] | 2 x (sr[32] float4 | sx sy sz [32] | sq[96])
-    size_t per_warp = STACK * 4 + 2 * (32 * 16 + 3 * 32 * 8 + 96 * 4);
+    // per-warp shared memory: stack[STACK] | 2 stages
+    size_t per_warp = STACK * 4 + 2 * STAGE_BYTES;
     unsigned char *base = smem_raw + per_warp * warp;
     int32_t *stack = (int32_t *)base;
     // the two staging buffers, addressed arithmetically (no local array)
     auto stage = [&](int t) {
-        unsigned char *p = base + STACK * 4 + t * (32 * 16 + 3 * 32 * 8 + 96 * 4);
+        unsigned char *p = base + STACK * 4 + t * STAGE_BYTES;
         Stage st;
         st.sr = (float4 *)p;
         st.sx = (double *)(p + 32 * 16);
@@ -290,17 +309,33 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 6) k_build_lists(ListArgs a) 
                    ez + 2.f * qh < 0.25f * (float)bx.L[2];
     }
     int count = 0;
+    Row R;
+    R.out = nullptr;
+    R.lim = 0;
+    if (a.mode == 0) {
+        R.out = a.nbr_idx + (int64_t)L.s * a.cap;
+        R.lim = a.cap;
+    } else if (a.mode == 2) {
+        // storage was reserved in mode 1; a reservation that did not fit
+        // (the capacity flag is set and the host rebuilds) must not write
+        // past the buffer
+        const int64_t o = a.nbr_off[L.s];
+        R.out = a.nbr_idx + o;
+        R.lim = (int)max((int64_t)0, min(a.capacity - o, (int64_t)0x7fffffff));
+    }
 
     int sp = 0;
     int root = a.box_root[a.node_box[b]];
     if (root < a.nbucket_total) {
         // the whole box is one bucket
         Cand cd;
-        if (lane < a.node_cnt[root]) cand_load(a, a.node_first[root] + lane, cd);
+        const int rf = a.node_first[root], rc = a.node_cnt[root];
+        if (lane < rc) cand_load(a, rf + lane, cd);
         __syncwarp();
-        if (lane < a.node_cnt[root]) cand_store(stage(0), lane, cd, ox, oy, oz, bx);
+        const int kc = cand_stage(stage(0), lane < rc && cand_near(cd, qlo, qhi, bx, rad2), lane, cd,
+                                  rf + lane, ox, oy, oz, bx);
         __syncwarp();
-        scan_stage(a, L, stage(0), bx, a.node_first[root], a.node_cnt[root], count);
+        scan_stage(L, R, stage(0), bx, kc, count);
     } else {
         if (lane == 0) stack[0] = root;
         sp = 1;
@@ -344,7 +379,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 6) k_build_lists(ListArgs a) 
             Cand cd;
             if (lane < cc) cand_load(a, cf + lane, cd);
             int buf = 0;
-            if (lane < cc) cand_store(stage(buf), lane, cd, ox, oy, oz, bx);
+            int kc = cand_stage(stage(buf), lane < cc && cand_near(cd, qlo, qhi, bx, rad2), lane, cd,
+                                cf + lane, ox, oy, oz, bx);
             __syncwarp();
             for (;;) {
                 int nk = keep ? __ffs(keep) - 1 : -1;
@@ -355,13 +391,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 6) k_build_lists(ListArgs a) 
                     ncc = __shfl_sync(0xffffffffu, ccnt, nk);
                     if (lane < ncc) cand_load(a, nfst + lane, cd);
                 }
-                scan_stage(a, L, stage(buf), bx, cf, cc, count);
+                scan_stage(L, R, stage(buf), bx, kc, count);
                 if (nk < 0) break;
-                if (lane < ncc) cand_store(stage(buf ^ 1), lane, cd, ox, oy, oz, bx);
+                kc = cand_stage(stage(buf ^ 1), lane < ncc && cand_near(cd, qlo, qhi, bx, rad2), lane,
+                                cd, nfst + lane, ox, oy, oz, bx);
                 __syncwarp();
                 buf ^= 1;
-                cf = nfst;
-                cc = ncc;
             }
             __syncwarp();
         } else {
@@ -490,15 +525,14 @@ static ListArgs list_args(hydro_ctx *c, int cap, int mode) {
 }
 
 static cudaError_t launch_lists(const ListArgs &a, int64_t nbucket, stream_t st) {
-    size_t per_warp = STACK * 4 + 2 * (32 * 16 + 3 * 32 * 8 + 96 * 4);
+    size_t per_warp = STACK * 4 + 2 * STAGE_BYTES;
     size_t smem = per_warp * LIST_WARPS;
     k_build_lists<<<grid_for(nbucket, LIST_WARPS), LIST_WARPS * 32, smem, st>>>(a);
     return launch_check();
 }
 
-// one pass: lists staged per lane in shared memory (cap entries), bulk
-// write; buckets with a longer list are queued for build_lists_queued()
-// Layout of nbr_idx: particle s owns the slots [s cap, s cap + cap); lists
+// one pass over all buckets; buckets with a row longer than cap are queued
+// for build_lists_queued().  Layout of nbr_idx: particle s owns the slots [s cap, s cap + cap); lists
 // longer than cap live in the overflow region that follows (n cap onwards),
 // reserved by build_lists_queued.
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {

@@ -69,7 +69,7 @@ class Stats(C.Structure):
         ("list_rebuilds", C.c_int), ("mass", C.c_double * 2), ("mom", (C.c_double * 3) * 2),
         ("energy", C.c_double * 2), ("ms_sort", C.c_float), ("ms_neighbours", C.c_float),
         ("ms_density", C.c_float), ("ms_gradients", C.c_float), ("ms_fluxes", C.c_float),
-        ("ms_update", C.c_float),
+        ("ms_update", C.c_float), ("ms_flux_kernel", C.c_float), ("ms_hard_faces", C.c_float),
     ]
 
     def as_dict(self):
