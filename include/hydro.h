@@ -72,10 +72,15 @@ typedef struct {
                             HYDRO_MIXED: pair geometry, kernel sums and fluxes in
                             float; E^-1, h refinement and flux accumulation in
                             double-class precision. */
-    int learned_guess;   /* 1: MLP starting pressure for the exact solver on hard
+    int learned_guess;   /* MLP starting pressure for the exact solver on hard
                             faces (mixed precision; needs a network from
                             hydro_mlp_load / hydro_mlp_train, else the flux
-                            calls return HYDRO_ESTATE; FP64 and HLLC ignore it) */
+                            calls return HYDRO_ESTATE; FP64 and HLLC ignore it):
+                            0 off; 2 on in every flux call; 1 adaptive: on,
+                            but when at most 10% of the hard faces of a call
+                            started from the network, the next 15 flux calls
+                            (hydro_fluxes or hydro_step) use the plain guess
+                            (no deferral cost) before trying again */
     int limiter;         /* 1: conditioned BJ + pairwise limiters (§2.3.6) */
     int time_extrap;     /* 1: half-step predictor of the face states (Eq. 16) */
     double ncond_crit;   /* N_cond threshold (100) */
@@ -128,7 +133,9 @@ typedef struct {
                                  out of range, a correction |y| < 1e-3 (kept at the
                                  two-shock value), or no room to defer the face */
     int64_t learned_faces;    /* faces whose Newton iteration started from the MLP */
-    int64_t hard_faces;       /* faces where Toro's guess is the two-shock value */
+    int64_t hard_faces;       /* faces where Toro's guess is the two-shock value
+                                 (counted when the learned path ran) */
+    int learned_active;       /* 1 if the step's fluxes ran the learned path */
     int64_t vacuum_faces;
     int64_t first_order_faces;
     int ngb_rounds;           /* N_cond growth rounds taken */

@@ -52,6 +52,7 @@ bool valid_config(const hydro_config *c) {
     if (c->scheme != HYDRO_MFV && c->scheme != HYDRO_MFM) return false;
     if (c->riemann != HYDRO_RIEMANN_EXACT && c->riemann != HYDRO_RIEMANN_HLLC) return false;
     if (c->precision != HYDRO_FP64 && c->precision != HYDRO_MIXED) return false;
+    if (c->learned_guess < 0 || c->learned_guess > 2) return false;
     if (!(c->search_margin >= 1.0)) return false;
     if (c->max_h_iter < 1 || c->max_newton < 1 || c->max_ngb_grow < 0) return false;
     return true;
@@ -240,6 +241,7 @@ int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_cnt, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_cnt, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_learn, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters));
     if (e == cudaSuccess) {
         for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
@@ -258,6 +260,7 @@ void hydro_destroy(hydro_ctx *c) {
     if (!c) return;
     if (c->d_cnt) cudaFree(c->d_cnt);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
+    if (c->h_learn) cudaFreeHost(c->h_learn);
     if (c->have_events)
         for (int k = 0; k < 10; k++) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -482,6 +485,7 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
         S.guess_fallbacks = (int64_t)H.guess_fallbacks;
         S.learned_faces = (int64_t)H.learned_faces;
         S.hard_faces = (int64_t)H.hard_faces;
+        S.learned_active = c->learned_active ? 1 : 0;
         S.vacuum_faces = (int64_t)H.vacuum;
         S.first_order_faces = (int64_t)H.first_order;
         for (int w = 0; w < 2; w++) {
@@ -497,9 +501,7 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
             cudaEventElapsedTime(&S.ms_update, c->ev[4], c->ev[5]);
             cudaEventElapsedTime(&S.ms_flux_kernel, c->ev[6], c->ev[7]);
             S.ms_hard_faces = 0.f;
-            if (c->cfg.learned_guess && c->cfg.precision == HYDRO_MIXED &&
-                c->cfg.riemann == HYDRO_RIEMANN_EXACT)
-                cudaEventElapsedTime(&S.ms_hard_faces, c->ev[7], c->ev[8]);
+            if (c->learned_active) cudaEventElapsedTime(&S.ms_hard_faces, c->ev[7], c->ev[8]);
             S.ms_sort = 0.f;
         }
         *stats = S;
@@ -530,6 +532,7 @@ int hydro_get_stats(hydro_ctx *c, hydro_stats *stats, hydro_stream stream) {
     S.guess_fallbacks = (int64_t)H.guess_fallbacks;
     S.learned_faces = (int64_t)H.learned_faces;
     S.hard_faces = (int64_t)H.hard_faces;
+    S.learned_active = c->learned_active ? 1 : 0;
     S.vacuum_faces = (int64_t)H.vacuum;
     S.first_order_faces = (int64_t)H.first_order;
     *stats = S;

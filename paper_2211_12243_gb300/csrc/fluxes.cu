@@ -429,15 +429,29 @@ struct FluxSmem {
     uint8_t qo[QCAP];          // queued faces: owner lane
 };
 
+// per-warp queue of hard faces waiting to be written to the deferred-face
+// buffer (32 at a time, one cursor atomic per 32)
+constexpr int HQ = 64;
+struct HardQ {
+    float v[HF_N][HQ];
+    int32_t s[HQ], j[HQ];
+    int cnt;   // faces queued (slots taken with shared-memory atomics)
+};
+
 template <typename R, int RIEM, int SCHEME, bool DEFER>
 __global__ void __launch_bounds__(FLUX_WARPS * 32, sizeof(R) == 4 ? 4 : 2)
 k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     __shared__ FluxSmem<R> sm_all[FLUX_WARPS];
+    __shared__ HardQ hq_all[DEFER ? FLUX_WARPS : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FluxSmem<R> &sm = sm_all[warp];
+    HardQ &hq = hq_all[DEFER ? warp : 0];
+    int hh = 0;   // the oldest entry of the warp's hard queue (a ring of HQ)
+    if (DEFER && lane == 0) hq.cnt = 0;
+    __syncwarp();
     const int64_t b = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
-    unsigned long long n_fallback = 0, n_hard = 0;
+    unsigned long long n_hard = 0;
     if (b < a.nbucket) {
         const int f = a.node_first[b], nown = a.node_cnt[b];
         const bool own = lane < nown;
@@ -460,6 +474,36 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         int qn = 0;
         __syncwarp();
 
+        // write the k oldest queued hard faces (a ring of HQ entries from hh)
+        // to the deferred-face buffer: the CTA's sub-buffer; a full
+        // sub-buffer sets hard_ovf and the host redoes the flux stage with a
+        // larger buffer
+        auto flush_hard = [&](int k) {
+            __syncwarp();
+            const int sub = blockIdx.x & (HARD_SUB - 1);
+            const int64_t subcap = a.hard_cap / HARD_SUB;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.hard_cursor[sub], (unsigned long long)k);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (lane < k) {
+                const int e = (hh + lane) & (HQ - 1);
+                const int64_t slot = (int64_t)base + lane;
+                if (slot < subcap) {
+                    const int64_t g = sub * subcap + slot, c = a.hard_cap;
+#pragma unroll
+                    for (int q = 0; q < HF_N; q++) a.hard[q * c + g] = hq.v[q][e];
+                    a.hard_idx[g] = hq.s[e];
+                    a.hard_idx[c + g] = hq.j[e];
+                } else {
+                    atomicOr(&a.cnt->hard_ovf, 1ull);
+                }
+            }
+            hh = (hh + k) & (HQ - 1);
+            __syncwarp();
+            if (lane == 0) hq.cnt -= k;
+            __syncwarp();
+        };
+
         // solve the first nb queued faces, one per lane, and hand -c back
         auto solve = [&](int nb) {
             R c[5] = {R(0), R(0), R(0), R(0), R(0)};
@@ -476,29 +520,20 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 if (face_state<R>(a, K, ri, rj, d, sqrt_(r2), dt, st, fs)) {
                     bool deferred = false;
                     if constexpr (DEFER) {
-                        // hard faces go to the learned-guess pass, which
-                        // applies both sides of their flux; the lanes that
-                        // defer together take their slots with one atomic.
-                        // Beyond the buffer's capacity a face is solved here
-                        // from the plain guess.
+                        // hard faces are queued for the learned-guess pass,
+                        // which applies both sides of their flux
                         if (two_shock_guess<R>(K, st)) {
                             n_hard++;
-                            // the CTA's sub-buffer (spreads the cursor atomics)
-                            const int sub = blockIdx.x & (HARD_SUB - 1);
-                            const int64_t subcap = a.hard_cap / HARD_SUB;
-                            const unsigned am = __activemask();
-                            const int lead = __ffs(am) - 1;
-                            unsigned long long base = 0;
-                            if (lane == lead)
-                                base = atomicAdd(&a.hard_cursor[sub], (unsigned long long)__popc(am));
-                            base = __shfl_sync(am, base, lead);
-                            const int64_t k = (int64_t)(base + __popc(am & lt));
-                            if (k < subcap) {
-                                store_hard(a, st, sub * subcap + k, f + ol, j);
-                                deferred = true;
-                            } else {
-                                n_fallback++;
-                            }
+                            const int e = (hh + atomicAdd(&hq.cnt, 1)) & (HQ - 1);
+                            const float v[HF_N] = {st.rl, st.ul, st.pl, st.rr, st.ur, st.pr,
+                                                   st.wl[0], st.wl[1], st.wl[2], st.wr[0],
+                                                   st.wr[1], st.wr[2], st.nh[0], st.nh[1],
+                                                   st.nh[2], st.vf[0], st.vf[1], st.vf[2], st.sA};
+#pragma unroll
+                            for (int q = 0; q < HF_N; q++) hq.v[q][e] = v[q];
+                            hq.s[e] = f + ol;
+                            hq.j[e] = j;
+                            deferred = true;
                         }
                     }
                     if (!deferred) {
@@ -527,6 +562,9 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 for (int q = 0; q < 5; q++) acc.sub(q, sm.cb[t][q]);
             }
             __syncwarp();
+            if constexpr (DEFER) {
+                if (hq.cnt >= 32) flush_hard(32);   // read after the warp sync above
+            }
         };
 
         for (int k = 0; k < maxc; k++) {
@@ -564,21 +602,23 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
             }
         }
         if (qn > 0) solve(qn);
+        if constexpr (DEFER) {
+            const int rest = hq.cnt;
+            if (rest > 0) flush_hard(rest);
+        }
         if (own) {
 #pragma unroll
             for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + s], acc.get(q));
         }
     }
     unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
-                       fo = wsum(fs.first_order), fb = DEFER ? wsum(n_fallback) : 0ull,
-                       ha = DEFER ? wsum(n_hard) : 0ull;
+                       fo = wsum(fs.first_order), ha = DEFER ? wsum(n_hard) : 0ull;
     if (lane == 0) {
         if (p) atomicAdd(&a.cnt->flux_pairs, p);
         if (ha) atomicAdd(&a.cnt->hard_faces, ha);
         if (it) atomicAdd(&a.cnt->newton_iters, it);
         if (va) atomicAdd(&a.cnt->vacuum, va);
         if (fo) atomicAdd(&a.cnt->first_order, fo);
-        if (fb) atomicAdd(&a.cnt->guess_fallbacks, fb);
     }
 }
 
@@ -678,16 +718,19 @@ cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme,
 
 // mixed precision, exact solver, learned guess: the flux kernel defers the
 // hard faces, then the hard-face kernel solves them from the network
-cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int scheme, stream_t st,
-                                  cudaEvent_t *ev) {
+// mixed precision, exact solver, learned guess: the flux kernel defers the
+// hard faces (pass 1) ...
+cudaError_t launch_fluxes_defer(const FluxArgs &a, const float *rec, int scheme, stream_t st) {
     const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
-    if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
     if (scheme == HYDRO_MFM)
         k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFM, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     else
         k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFV, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-    HYD_CUDA(launch_check());
-    if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
+    return launch_check();
+}
+
+// ... then the hard-face kernel solves them from the network (pass 2)
+cudaError_t launch_hard_faces(const FluxArgs &a, int scheme, stream_t st) {
     const size_t smem = sizeof(MlpTile) + 1024;
     static bool configured = false;
     if (!configured) {
@@ -701,9 +744,7 @@ cudaError_t launch_fluxes_learned(const FluxArgs &a, const float *rec, int schem
     const unsigned hgrid = 152 * 4;
     if (scheme == HYDRO_MFM) k_hard_faces<HYDRO_MFM><<<hgrid, 128, smem, st>>>(a);
     else k_hard_faces<HYDRO_MFV><<<hgrid, 128, smem, st>>>(a);
-    HYD_CUDA(launch_check());
-    if (ev) HYD_CUDA(cudaEventRecord(ev[2], st));
-    return cudaSuccess;
+    return launch_check();
 }
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -713,10 +754,13 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
-    HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
-    // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
-    // learned_faces, hard_faces
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 7 * sizeof(unsigned long long), st));
+    auto clear = [&]() -> cudaError_t {
+        HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
+        // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
+        // learned_faces, hard_faces, hard_ovf
+        return cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 8 * sizeof(unsigned long long), st);
+    };
+    HYD_CUDA(clear());
     FluxArgs a;
     a.n = n;
     a.nbr_off = c->d_nbr_off.get();
@@ -745,25 +789,43 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.hard_idx = nullptr;
     a.hard_cursor = nullptr;
     a.hard_cap = 0;
-    const bool learned = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
-                         c->cfg.learned_guess && c->have_mlp;
-    if (learned) {
-        // room for 8 hard faces per particle; beyond it faces are solved in
-        // the flux kernel from the plain guess
-        const int64_t unit = (int64_t)HARD_SUB * 128;
-        const int64_t cap = (8 * n + 65536 + unit - 1) / unit * unit;
+    const bool want = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
+                      c->cfg.learned_guess && c->have_mlp;
+    bool learned = false;
+    if (want) {
+        // adaptive mode: after a learned call in which under 10% of the hard
+        // faces started from the network, the next 15 calls skip the
+        // deferral (its cost buys nothing there) before probing again
+        if (c->learn_probe_pending) {
+            HYD_CUDA(cudaEventSynchronize(c->ev[9]));
+            const unsigned long long used = c->h_learn[0], hard = c->h_learn[1];
+            c->learn_probe_pending = false;
+            if (c->cfg.learned_guess == 1 && used * 10 <= hard) c->learn_skip = 15;
+        }
+        if (c->cfg.learned_guess == 2 || c->learn_skip == 0) learned = true;
+        else c->learn_skip--;
+    }
+    c->learned_active = learned;
+    // room for 4 hard faces per particle to start with (sub-buffer sizes a
+    // multiple of 128); a pass that fills a sub-buffer is redone with twice
+    // the room
+    const int64_t unit = (int64_t)HARD_SUB * 128;
+    auto reserve_hard = [&](int64_t want) -> cudaError_t {
+        const int64_t cap = (want + unit - 1) / unit * unit;
         if (c->hard_cap < cap) {
+            c->hard_cap = 0;
             HYD_CUDA(c->d_hard.ensure((size_t)HF_N * cap));
             HYD_CUDA(c->d_hard_idx.ensure((size_t)2 * cap));
             c->hard_cap = cap;
         }
         HYD_CUDA(c->d_hard_cursor.ensure(HARD_SUB));
-        HYD_CUDA(cudaMemsetAsync(c->d_hard_cursor.get(), 0, HARD_SUB * sizeof(unsigned long long), st));
         a.hard = c->d_hard.get();
         a.hard_idx = c->d_hard_idx.get();
         a.hard_cursor = c->d_hard_cursor.get();
         a.hard_cap = c->hard_cap;
-    }
+        return cudaSuccess;
+    };
+    if (learned) HYD_CUDA(reserve_hard(4 * n + 65536));
     a.rec_faces = c->rec_faces;
     a.rec_cursor = c->d_rec_cursor.get();
     a.rec_cap = c->rec_cap;
@@ -784,7 +846,29 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
     cudaEvent_t *ev = c->timing ? c->ev + 6 : nullptr;
-    if (learned) return launch_fluxes_learned(a, c->d_recf.get(), c->cfg.scheme, st, ev);
+    if (learned) {
+        for (int attempt = 0;; attempt++) {
+            HYD_CUDA(cudaMemsetAsync(a.hard_cursor, 0, HARD_SUB * sizeof(unsigned long long), st));
+            if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
+            HYD_CUDA(launch_fluxes_defer(a, c->d_recf.get(), c->cfg.scheme, st));
+            if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
+            unsigned long long ovf = 0;
+            HYD_CUDA(cudaMemcpyAsync(&ovf, &c->d_cnt->hard_ovf, sizeof(ovf), cudaMemcpyDeviceToHost, st));
+            HYD_CUDA(cudaStreamSynchronize(st));
+            if (!ovf) break;
+            if (attempt >= 6) return cudaErrorMemoryAllocation;
+            HYD_CUDA(reserve_hard(2 * a.hard_cap));
+            HYD_CUDA(clear());
+        }
+        HYD_CUDA(launch_hard_faces(a, c->cfg.scheme, st));
+        if (ev) HYD_CUDA(cudaEventRecord(ev[2], st));
+        // learned_faces and hard_faces (adjacent) for the adaptive decision
+        HYD_CUDA(cudaMemcpyAsync(c->h_learn, &c->d_cnt->learned_faces, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        HYD_CUDA(cudaEventRecord(c->ev[9], st));
+        c->learn_probe_pending = true;
+        return cudaSuccess;
+    }
     if (c->cfg.precision == HYDRO_MIXED)
         return launch_fluxes<float>(a, c->d_recf.get(), c->cfg.riemann, c->cfg.scheme, st, ev);
     return launch_fluxes<double>(a, c->d_recd.get(), c->cfg.riemann, c->cfg.scheme, st, ev);

@@ -74,6 +74,7 @@ struct DevCounters {
     unsigned long long first_order;
     unsigned long long learned_faces;  // faces solved from the learned guess
     unsigned long long hard_faces;     // faces where Toro's guess is the two-shock value
+    unsigned long long hard_ovf;       // a deferred-face sub-buffer was full (pass redone)
     double sums[2][5];                // totals before / after (m, px, py, pz, E)
 };
 
@@ -177,6 +178,13 @@ struct hydro_ctx {
     hyd::DevBuf<float> d_hard;
     hyd::DevBuf<int32_t> d_hard_idx;
     hyd::DevBuf<unsigned long long> d_hard_cursor;
+    // adaptive learned path: plain-guess steps left before the next probe,
+    // and whether the last flux call ran the learned path (its counts then
+    // sit in h_learn[0..1] = hard, learned once the stream passes them)
+    int learn_skip = 0;
+    bool learn_probe_pending = false;
+    bool learned_active = false;
+    unsigned long long *h_learn = nullptr;   // pinned
     int64_t hard_cap = 0;
 
     // face recording (training data for the MLP), mixed exact path
@@ -192,7 +200,8 @@ struct hydro_ctx {
     int pending_status = 0;
 
     hydro_stats last_stats;
-    cudaEvent_t ev[10];               // 0-5 stage boundaries, 6-9 around the flux kernels
+    cudaEvent_t ev[10];               // 0-5 stage boundaries, 6-8 around the flux kernels,
+                                      // 9 after the learned-path counters' readback
     bool have_events = false;
     bool timing = false;              // record ev[6..9] in the flux launcher
 };

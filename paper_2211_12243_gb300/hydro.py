@@ -64,7 +64,7 @@ class Stats(C.Structure):
         ("status", C.c_int), ("dt", C.c_double), ("dt_next", C.c_double),
         ("grad_pairs", C.c_int64), ("flux_pairs", C.c_int64), ("newton_iters", C.c_int64),
         ("guess_fallbacks", C.c_int64), ("learned_faces", C.c_int64),
-        ("hard_faces", C.c_int64), ("vacuum_faces", C.c_int64),
+        ("hard_faces", C.c_int64), ("learned_active", C.c_int), ("vacuum_faces", C.c_int64),
         ("first_order_faces", C.c_int64), ("ngb_rounds", C.c_int), ("ncond_fail", C.c_int64),
         ("list_rebuilds", C.c_int), ("mass", C.c_double * 2), ("mom", (C.c_double * 3) * 2),
         ("energy", C.c_double * 2), ("ms_sort", C.c_float), ("ms_neighbours", C.c_float),

@@ -340,3 +340,27 @@ def test_learned_flux_matches_oracle(orc, hyd, trained, name):
     assert s1["learned_faces"] + s1["guess_fallbacks"] == s1["hard_faces"]
     assert s1["flux_pairs"] == s0["flux_pairs"]
     assert s1["newton_iters"] < s0["newton_iters"], (s0, s1)
+
+
+def test_adaptive_learned_path_pauses_when_unused(hyd):
+    """learned_guess = 1: a network whose corrections all fall below 1e-3
+    starts no face, so after one learned step the next 15 run the plain
+    guess, then the path is tried again; learned_guess = 2 never pauses."""
+    p = mlp.unpack(mlp.init(1))
+    p["w3"][:] = 0.0                     # y = t_mean + t_scale b3 = 0
+    p["xmin"], p["xmax"] = np.full(mlp.NF, -1e30), np.full(mlp.NF, 1e30)
+    theta = mlp.pack(p).astype(np.float32)
+    w = W.sod(12)
+    for mode, want in ((1, [1] + [0] * 15 + [1]), (2, [1] * 17)):
+        H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision="mixed", learned_guess=mode))
+        H.mlp_load(theta)
+        H.set_boxes(*hyd.single_box(w))
+        st = hyd.to_device(w)
+        seen = []
+        for _ in range(17):
+            s = H.step(st)
+            seen.append(s["learned_active"])
+            if s["learned_active"]:
+                assert s["hard_faces"] > 0 and s["learned_faces"] == 0
+                assert s["guess_fallbacks"] == s["hard_faces"]
+        assert seen == want, (mode, seen)
