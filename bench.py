@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sod", choices=["sod", "sedov", "lognormal"],
+    ap.add_argument("--workload", default="sod", choices=["sod", "sedov", "lognormal", "batch"],
                     help="sod: 3D Sod tube (default); sedov: Sedov-Taylor blast on an n^3 "
-                         "lattice; lognormal: clustered log-normal box of n particles")
+                         "lattice; lognormal: clustered log-normal box of n particles; batch: n "
+                         "independent periodic boxes of 4k-64k particles in one launch")
     ap.add_argument("--n", type=int, default=None,
                     help="size: Sod resolution (78: 1,067,742), Sedov lattice side (128), "
-                         "log-normal particle count (2^24)")
+                         "log-normal particle count (2^24), number of boxes (512)")
     ap.add_argument("--scheme", default="mfv")
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
@@ -136,6 +137,9 @@ def make_workload(kind, n):
     if kind == "lognormal":
         n = n or (1 << 24)
         return W.lognormal(n), f"lognormal3d_{n}_mfv_exact"
+    if kind == "batch":
+        n = n or 512
+        return W.batch(n), f"batch_{n}_boxes_4k_64k_mfv_exact"
     n = n or 78
     return W.sod(n), (WORKLOAD if n == 78 else f"sod3d_n{n}")
 
@@ -146,27 +150,41 @@ def oracle_sample_rate(kind, n, reps):
     metric."""
     import oracle
     if n is None:
-        n = {"sod": 40, "sedov": 32, "lognormal": 1 << 15}[kind]
+        n = {"sod": 40, "sedov": 32, "lognormal": 1 << 15, "batch": 6}[kind]
     w, _ = make_workload(kind, n)
+    if kind == "batch":   # the oracle takes one periodic box at a time
+        off, bl = w["box_off"], w["box_len"].reshape(-1, 3)
+        boxes = [({k: w[k][off[b]:off[b + 1]] for k in ("x", "y", "z", "m", "px", "py", "pz",
+                                                          "E", "U", "h")}, bl[b])
+                 for b in range(len(off) - 1)]
+    else:
+        boxes = [(w, w["L"])]
     cfg = oracle.config(gamma=w["gamma"])
-    x, y, z, L = w["x"], w["y"], w["z"], w["L"]
-    h, om, _, _ = oracle.density(cfg, x, y, z, L, w["h"])
-    prims = oracle.primitives(cfg, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"], om)
-    off, idx = oracle.neighbours(x, y, z, L, h)
-    gpairs = int(idx.size - x.size)
+    prep = []
+    gpairs = 0
+    for wb, L in boxes:
+        x, y, z = wb["x"], wb["y"], wb["z"]
+        h, om, _, _ = oracle.density(cfg, x, y, z, L, wb["h"])
+        prims = oracle.primitives(cfg, wb["m"], wb["px"], wb["py"], wb["pz"], wb["E"], wb["U"], om)
+        off_l, idx = oracle.neighbours(x, y, z, L, h)
+        gpairs += int(idx.size - x.size)
+        prep.append((x, y, z, L, h, om, prims))
     t = 0.0
     fpairs = 0
     for _ in range(reps):
-        t0 = time.perf_counter()
-        B6, _, nc = oracle.matrices(cfg, x, y, z, L, h, om)
-        grad, alpha, _ = oracle.gradients(cfg, x, y, z, L, h, om, prims, B6, nc)
-        pairs = oracle.flux_pairs(x, y, z, L, h)
-        oracle.fluxes(cfg, x, y, z, L, h, om, B6, prims, grad, alpha, 1e-4, pairs=pairs)
-        t += time.perf_counter() - t0
-        fpairs = len(pairs)
+        fpairs = 0
+        for x, y, z, L, h, om, prims in prep:
+            t0 = time.perf_counter()
+            B6, _, nc = oracle.matrices(cfg, x, y, z, L, h, om)
+            grad, alpha, _ = oracle.gradients(cfg, x, y, z, L, h, om, prims, B6, nc)
+            pairs = oracle.flux_pairs(x, y, z, L, h)
+            oracle.fluxes(cfg, x, y, z, L, h, om, B6, prims, grad, alpha, 1e-4, pairs=pairs)
+            t += time.perf_counter() - t0
+            fpairs += len(pairs)
     total = reps * (gpairs + fpairs)
+    npart = sum(len(p[0]) for p in prep)
     return dict(value=total / t, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                sample=f"{kind} generator at n={n} ({x.size} particles), oracle gradient+flux stages "
+                sample=f"{kind} generator at n={n} ({npart} particles), oracle gradient+flux stages "
                        f"(E/B/N_cond, gradients+limiter, pair enumeration, fluxes), {reps} passes, "
                        f"{total} pair-interactions in {t:.2f} s"), t
 
@@ -204,6 +222,13 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def boxes_of(hydro, w):
+    """(box_off, box_len) of a workload: its own for a batch, else one box."""
+    if w.get("box_off") is not None:
+        return w["box_off"], w["box_len"]
+    return hydro.single_box(w)
+
+
 def train_network(hydro, workloads, w, steps):
     """Record the hard faces of a few mixed steps of the workload itself, a
     log-normal field and a Sedov blast, and train the starting-pressure
@@ -217,7 +242,7 @@ def train_network(hydro, workloads, w, steps):
     for wk, nstep, keep in sets:
         Hr = hydro.Hydro(hydro.default_config(gamma=wk["gamma"], precision="mixed",
                                               search_margin=2.0))
-        Hr.set_boxes(*hydro.single_box(wk))
+        Hr.set_boxes(*boxes_of(hydro, wk))
         s = hydro.to_device(wk)
         cap = 1 << 21
         buf = torch.zeros((7, cap), dtype=torch.float32, device="cuda")
@@ -263,13 +288,13 @@ def main():
     learned = args.precision == "mixed" and not args.no_learned
     training = train_network(hydro, workloads, w, args.train_steps) if learned else None
     # the log-normal initial h are rough guesses: search wider in the first step
-    margin = 2.0 if args.workload == "lognormal" else 1.15
+    margin = 1.15
     cfg = hydro.default_config(gamma=w["gamma"], precision=args.precision, scheme=args.scheme,
                                learned_guess=int(learned), search_margin=margin)
     H = hydro.Hydro(cfg)
     if learned:
         H.mlp_load(training["theta"])
-    H.set_boxes(*hydro.single_box(w))
+    H.set_boxes(*boxes_of(hydro, w))
     H.reserve(n, 96)
     st = hydro.to_device(w)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -279,7 +304,7 @@ def main():
     # after the N_NGB growths; the step completes and reports them (ENCOND)
     ok_status = (0, -5) if args.workload == "lognormal" else (0,)
 
-    restart = args.restart or args.workload == "lognormal"
+    restart = args.restart or args.workload in ("lognormal", "batch")
 
     def timed_steps(Hc, state, k, warm):
         saved = {kk: v.clone() for kk, v in state.items()} if restart else None
@@ -379,7 +404,7 @@ def main():
     if learned:
         Hp = hydro.Hydro(hydro.default_config(gamma=w["gamma"], precision=args.precision,
                                               scheme=args.scheme, search_margin=margin))
-        Hp.set_boxes(*hydro.single_box(w))
+        Hp.set_boxes(*boxes_of(hydro, w))
         stp = hydro.to_device(w)
         kp = max(2, min(args.steps, 5))
         rp = timed_steps(Hp, stp, kp, 1)
@@ -395,7 +420,7 @@ def main():
         cfg64 = hydro.default_config(gamma=w["gamma"], precision="fp64", scheme=args.scheme,
                                      search_margin=margin)
         H64 = hydro.Hydro(cfg64)
-        H64.set_boxes(*hydro.single_box(w))
+        H64.set_boxes(*boxes_of(hydro, w))
         st64 = hydro.to_device(w)
         k64 = max(2, min(args.steps, 5))
         r64 = timed_steps(H64, st64, k64, 1)

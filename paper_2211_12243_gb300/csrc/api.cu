@@ -168,22 +168,30 @@ int build_all(hydro_ctx *c, const hydro_particles *p, const double *h_in, const 
     return lists_all(c, st);
 }
 
-// density with re-searches when a root leaves the list radius
+// density with re-searches when a root leaves the list radius: the failed
+// particles' radii grow and only their buckets get new lists (a full
+// rebuild when the overflow region is too small)
 int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &rebuilds,
                 cudaStream_t st) {
-    API_CUDA(run_density(c, only_active, st));
-    for (;;) {
+    API_CUDA(run_density(c, only_active, true, st));
+    for (int round = 0;; round++) {
         int sf = 0;
         API_CUDA(cudaMemcpyAsync(&sf, &c->d_cnt->search_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
         if (sf == 0) return HYDRO_OK;
-        if (rebuilds >= 4) return HYDRO_ESEARCH;
+        if (round >= 8) return HYDRO_ESEARCH;
         rebuilds++;
-        // widen the radius of the failed particles and search again
         API_CUDA(grow_search_radius(c, st));
-        int rc = lists_all(c, st);
-        if (rc) return rc;
-        API_CUDA(run_density(c, true, st));
+        int nq = 0;
+        API_CUDA(rebuild_active_lists(c, &nq, st));
+        int fl = 0;
+        API_CUDA(cudaMemcpyAsync(&fl, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        if (fl & (ST_LIST_CAPACITY | ST_STACK)) {
+            int rc = lists_all(c, st);
+            if (rc) return rc;
+        }
+        API_CUDA(run_density(c, true, true, st));
     }
 }
 
@@ -361,7 +369,7 @@ int hydro_density(hydro_ctx *c, hydro_particles *p, hydro_stream stream) {
     API_CUDA(gather_from_caller(c->d_perm.get(), p->h, p->n, 1, c->d_hsorted.get(), p->n, st));
     API_CUDA(reset_guard(c, st));
     API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-    API_CUDA(run_density(c, false, st));
+    API_CUDA(run_density(c, false, false, st));
     int sf = 0, fl = 0;
     API_CUDA(cudaMemcpyAsync(&sf, &c->d_cnt->search_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaMemcpyAsync(&fl, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -14,6 +14,16 @@
 // double-float (pairs of floats, Dekker/Knuth error-free transformations)
 // on the exact 64-bit separations refines h to double-class accuracy
 // without the GPU's scarce FP64 pipe; omega is taken from that evaluation.
+//
+// Tight lists (hydro_step only): once an upper bracket hi of the root is
+// known, no later iterate exceeds it, so the particle's list is compacted in
+// place to the entries within hi (plus a relative slack that covers the
+// float separation's error) and the last pass compacts it to the final h.
+// The search radius hs is lowered to the radius the compacted list is
+// complete for; the gradient and flux kernels, which test r_ij < h_i
+// exactly on every entry, then walk only the members.  Compaction keeps the
+// order of the entries, so the members are summed in the same order as in
+// the full list.
 #include "hydro_internal.cuh"
 
 namespace hyd {
@@ -23,9 +33,9 @@ namespace {
 struct DensArgs {
     int64_t n;
     const int64_t *nbr_off;
-    const int32_t *nbr_cnt;
-    const int32_t *nbr_idx;
-    const double *hs;
+    int32_t *nbr_cnt;         // rewritten when lists are compacted
+    int32_t *nbr_idx;
+    double *hs;               // lowered to the compacted lists' radius
     const double *xs, *ys, *zs;
     const int32_t *pbox;
     const Box *boxes;
@@ -36,6 +46,7 @@ struct DensArgs {
     double tol;
     int max_iter;
     bool only_active;
+    bool compact;             // compact the lists to the root (see above)
     double *h;                // sorted, in: guess, out: solution
     double *om;               // sorted out
     DevCounters *cnt;
@@ -48,28 +59,39 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
     if (a.only_active && !(a.active[s] & 1)) return;
     const Box bx = a.boxes[a.pbox[s]];
     const double xi = a.xs[s], yi = a.ys[s], zi = a.zs[s];
-    const double hsi = a.hs[s];
+    double hsi = a.hs[s];
     const double N = a.nngb ? a.nngb[s] : a.n_ngb;
     const int64_t o = a.nbr_off[s];
-    const int c = a.nbr_cnt[s];
+    int32_t *idx = a.nbr_idx + o;
+    int c = a.nbr_cnt[s];
     const double Kn = kernel_Kn<double>(a.kernel);
     double h = a.h[s];
     if (!(h > 0.0) || h > hsi) h = hsi;
     double lo = 0.0, hi = -1.0;
     bool conv = false, fail = false;
+    auto sep = [&](int j) {
+        double dx = fold64(a.xs[j] - xi, bx.L[0]);
+        double dy = fold64(a.ys[j] - yi, bx.L[1]);
+        double dz = fold64(a.zs[j] - zi, bx.L[2]);
+        return sqrt(dx * dx + dy * dy + dz * dz);
+    };
     for (int it = 1; it <= a.max_iter; it++) {
         double f = 0.0, mq = 0.0, ih = 1.0 / h;
+        // an upper bracket well inside the list radius: drop the entries
+        // beyond it (relative slack 1e-9 >> the rounding of r)
+        const bool shrink = a.compact && hi > 0.0 && hi < 0.8 * hsi;
+        const double keep = hi * (1.0 + 1e-9);
+        int w = 0;
         for (int k = 0; k < c; k++) {
-            int j = a.nbr_idx[o + k];
-            double dx = fold64(a.xs[j] - xi, bx.L[0]);
-            double dy = fold64(a.ys[j] - yi, bx.L[1]);
-            double dz = fold64(a.zs[j] - zi, bx.L[2]);
-            double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
+            const int j = idx[k];
+            const double r = sep(j);
+            if (shrink && r < keep) idx[w++] = j;
             double fv, mv;
-            kernel_f<double>(a.kernel, q, fv, mv);
+            kernel_f<double>(a.kernel, r * ih, fv, mv);
             f += fv;
             mq += mv;
         }
+        if (shrink) { c = w; hsi = hi * (1.0 + 5e-10); }   // complete below this
         double g = Kn * f - N;
         double dg = Kn * mq * ih;
         if (g == 0.0) { conv = true; break; }
@@ -89,7 +111,7 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
         }
         h = hn;
     }
-    if (fail) {
+    if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
         a.active[s] = 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
@@ -97,13 +119,18 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
     }
     if (!conv) set_flag(a.cnt, ST_NOCONV_H);
     double sw = 0.0, ih = 1.0 / h;
+    const double keep = h * (1.0 + 1e-9);
+    int w = 0;
     for (int k = 0; k < c; k++) {
-        int j = a.nbr_idx[o + k];
-        double dx = fold64(a.xs[j] - xi, bx.L[0]);
-        double dy = fold64(a.ys[j] - yi, bx.L[1]);
-        double dz = fold64(a.zs[j] - zi, bx.L[2]);
-        double q = sqrt(dx * dx + dy * dy + dz * dz) * ih;
-        sw += kernel_shape<double>(a.kernel, q);
+        const int j = idx[k];
+        const double r = sep(j);
+        if (a.compact && r < keep) idx[w++] = j;
+        sw += kernel_shape<double>(a.kernel, r * ih);
+    }
+    if (a.compact) {
+        // complete for every r < h (1 + 5e-10)
+        a.nbr_cnt[s] = w;
+        a.hs[s] = h * (1.0 + 5e-10);
     }
     sw *= kernel_norm<double>(a.kernel, h);
     double om = 1.0 / sw;
@@ -192,18 +219,24 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     const uint32_t qxi = __float_as_uint(ri[R_X]), qyi = __float_as_uint(ri[R_Y]),
                    qzi = __float_as_uint(ri[R_Z]);
     const double hsi_d = a.hs[s];
-    const float hsi = (float)hsi_d;
+    float hsi = (float)hsi_d;
     const float N = (float)(a.nngb ? a.nngb[s] : a.n_ngb);
     const int64_t o = a.nbr_off[s];
-    const int c = a.nbr_cnt[s];
+    int32_t *idx = a.nbr_idx + o;
+    int c = a.nbr_cnt[s];
     const float Kn = kernel_Kn<float>(a.kernel);
     float h = (float)a.h[s];
     if (!(h > 0.f) || h > hsi) h = hsi;
     float lo = 0.f, hi = -1.f;
     bool conv = false, fail = false;
+    float comp = -1.f;   // radius the compacted list is complete for (none yet)
     const float ftol = 2e-6f;
-    auto sep_r = [&](int k) {
-        int j = a.nbr_idx[o + k];
+    // The float separation from the fixed-point positions is within
+    // 4e-7 r + 4e-10 L of the exact one, so keeping the entries with float
+    // r < X (1 + 1e-4) leaves the list complete for every r < X (1 + 5e-5)
+    // when X > L / 65536 (compaction is skipped below that).
+    const float xmin = (float)(fmin(bx.L[0], fmin(bx.L[1], bx.L[2])) * (1.0 / 65536.0));
+    auto sep_r = [&](int j) {
         const float *rj = rec + (int64_t)j * REC;
         float4 pj = *reinterpret_cast<const float4 *>(rj);
         float dx = qdiff(qxi, __float_as_uint(pj.x), bx.s[0]);
@@ -214,13 +247,21 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     };
     for (int it = 1; it <= a.max_iter; it++) {
         float f = 0.f, mq = 0.f, ih = 1.f / h;
+        // an upper bracket well inside the list radius: drop the entries
+        // beyond it (no later iterate exceeds hi)
+        const bool shrink = a.compact && hi > xmin && hi < 0.8f * hsi;
+        const float keep = hi * 1.0001f;
+        int w = 0;
         for (int k = 0; k < c; k++) {
-            float q = sep_r(k) * ih;
+            const int j = idx[k];
+            const float r = sep_r(j);
+            if (shrink && r < keep) idx[w++] = j;
             float fv, mv;
-            kernel_f<float>(a.kernel, q, fv, mv);
+            kernel_f<float>(a.kernel, r * ih, fv, mv);
             f += fv;
             mq += mv;
         }
+        if (shrink) { c = w; comp = hi * 1.00005f; hsi = comp; }
         float g = Kn * f - N;
         float dg = Kn * mq * ih;
         if (g == 0.f) { conv = true; break; }
@@ -240,7 +281,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         }
         h = hn;
     }
-    if (fail) {
+    if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
         a.active[s] = 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
@@ -256,9 +297,14 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     df ih = df_div({1.f, 0.f}, hd);
     df F = {0.f, 0.f}, MQ = {0.f, 0.f};
     const float hcut = h * (1.f + 1e-5f);   // W = 0 beyond h: skip those (float r is good to 1e-7)
+    const bool fin = a.compact && h > xmin;
+    const float keep = h * 1.0001f;
+    int w = 0;
     for (int k = 0; k < c; k++) {
-        if (sep_r(k) >= hcut) continue;
-        int j = a.nbr_idx[o + k];
+        const int j = idx[k];
+        const float rf = sep_r(j);
+        if (fin && rf < keep) idx[w++] = j;
+        if (rf >= hcut) continue;
         long long ix = (long long)(q64x[j] - xi64);
         long long iy = (long long)(q64y[j] - yi64);
         long long iz = (long long)(q64z[j] - zi64);
@@ -291,12 +337,26 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
             MQ = df_add(MQ, mv);
         }
     }
-    // g = Kn F - N, dg = Kn MQ / h  ->  h_new = h - g / dg = h - (F - N/Kn) h / MQ
+    // g = Kn F - N, dg = Kn MQ / h  ->  h_new = h - (F - N/Kn) h / MQ
     double Fd = (double)F.hi + (double)F.lo;
     double MQd = (double)MQ.hi + (double)MQ.lo;
     double hN = (double)h;
     double Kd = a.kernel == 0 ? 14.0 : 32.0 / 3.0;
     double hnew = MQd > 0.0 ? hN - (Fd - (double)N / Kd) * hN / MQd : hN;
+    if (fin || comp > 0.f) {
+        // the compacted list is complete for r < crad
+        const double crad = fin ? hN * (1.0 + 5e-5) : (double)comp;
+        a.nbr_cnt[s] = fin ? w : c;
+        a.hs[s] = crad;
+        if (!(hnew < crad)) {
+            // the refinement left the compacted radius (an unconverged float
+            // root): search again from a rebuilt list
+            a.active[s] = 3;
+            atomicAdd(&a.cnt->search_fail, 1);
+            set_flag(a.cnt, ST_SEARCH);
+            return;
+        }
+    }
     // omega from the sum at h (first order in the small correction)
     // sum_j W(r, hnew) = norm(hnew) sum f(q_new); d/dh [h^3 sum W] = Kn MQ / h * 3/(4 pi)
     double normh = kernel_norm<double>(a.kernel, hnew);
@@ -320,7 +380,7 @@ __global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *_
     if (a & 2) {
         const Box bx = boxes[pbox[s]];
         double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-        hs[s] = fmin(fmax(hs[s] * 1.5, h[s] * margin), half);
+        hs[s] = fmin(fmax(hs[s] * 2.0, h[s] * margin), half);
         active[s] = 1;
     } else {
         active[s] = 0;
@@ -345,7 +405,7 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st) {
+cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st) {
     const int64_t n = c->plan.n;
     DensArgs a;
     a.n = n;
@@ -363,6 +423,7 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st) {
     a.tol = c->cfg.h_tol;
     a.max_iter = c->cfg.max_h_iter;
     a.only_active = only_active;
+    a.compact = compact;
     a.h = c->d_hsorted.get();
     a.om = c->d_omsorted.get();
     a.cnt = c->d_cnt;

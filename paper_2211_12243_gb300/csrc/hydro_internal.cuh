@@ -233,10 +233,12 @@ cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n
 cudaError_t build_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
 cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
+cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu
-cudaError_t run_density(hydro_ctx *c, bool only_active, stream_t st);
+// compact: shrink each solved particle's list to its root (hydro_step only)
+cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st);
 cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
 
 // gradients.cu

@@ -475,6 +475,20 @@ __global__ void k_export_fill(int64_t n, const int32_t *__restrict__ perm,
     }
 }
 
+// queue the buckets holding a particle to search again (active bit 0), and
+// clear the search-failure flag that the rebuild answers
+__global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ first,
+                               const int32_t *__restrict__ cnt, const uint8_t *__restrict__ active,
+                               int32_t *__restrict__ queue, int *__restrict__ nqueue,
+                               DevCounters *counters) {
+    int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (b == 0 && lane == 0) atomicAnd(&counters->flags, ~ST_SEARCH);
+    if (b >= nbucket) return;
+    bool act = lane < cnt[b] && (active[first[b] + lane] & 1);
+    if (__any_sync(0xffffffffu, act) && lane == 0) queue[atomicAdd(nqueue, 1)] = (int32_t)b;
+}
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -557,6 +571,24 @@ cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st) {
     HYD_CUDA(launch_lists(a, nq, st));
     a.mode = 2;
     return launch_lists(a, nq, st);
+}
+
+// new lists (in the overflow region) for the buckets that hold a particle
+// whose search radius grew; every other list stays as it is.  *nq receives
+// the number of buckets rebuilt (the host waits for it).
+cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st) {
+    const Plan &P = c->plan;
+    HYD_CUDA(c->d_ovf.ensure(P.nbucket));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
+    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+        P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
+        &c->d_cnt->ovf_buckets, c->d_cnt);
+    HYD_CUDA(launch_check());
+    HYD_CUDA(cudaMemcpyAsync(nq, &c->d_cnt->ovf_buckets, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HYD_CUDA(cudaStreamSynchronize(st));
+    if (*nq == 0) return cudaSuccess;
+    HYD_CUDA(build_tree(c, st));   // the buckets' search radii changed
+    return build_lists_queued(c, *nq, st);
 }
 
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {
