@@ -408,7 +408,7 @@ int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *g
     API_CUDA(c->d_out.ensure((size_t)27 * n));
     double *stg = c->d_out.get();
     API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
-    API_CUDA(run_gradients(c, stg, stg + 6 * n, stg + 21 * n, stg + 26 * n, st));
+    API_CUDA(run_gradients(c, stg, stg + 6 * n, stg + 21 * n, stg + 26 * n, false, st));
     API_CUDA(scatter_to_caller(c->d_perm.get(), stg, n, 6, n, B, st));
     API_CUDA(scatter_to_caller(c->d_perm.get(), stg + 6 * n, n, 15, n, grad, st));
     API_CUDA(scatter_to_caller(c->d_perm.get(), stg + 21 * n, n, 5, n, alpha, st));
@@ -454,7 +454,8 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
         if (rc) return rc;
         if (first && timing) API_CUDA(cudaEventRecord(c->ev[2], st));
         API_CUDA(run_primitives(c, st));
-        API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, st));
+        // a guard round recomputes only the gradients its re-solved densities change
+        API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
         API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));

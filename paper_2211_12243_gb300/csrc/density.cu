@@ -112,7 +112,7 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
         h = hn;
     }
     if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
-        a.active[s] = 3;
+        a.active[s] = (a.active[s] & ACT_GUARD) | 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
         return;
@@ -282,7 +282,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         h = hn;
     }
     if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
-        a.active[s] = 3;
+        a.active[s] = (a.active[s] & ACT_GUARD) | 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
         return;
@@ -351,7 +351,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         if (!(hnew < crad)) {
             // the refinement left the compacted radius (an unconverged float
             // root): search again from a rebuilt list
-            a.active[s] = 3;
+            a.active[s] = (a.active[s] & ACT_GUARD) | 3;
             atomicAdd(&a.cnt->search_fail, 1);
             set_flag(a.cnt, ST_SEARCH);
             return;
@@ -381,9 +381,9 @@ __global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *_
         const Box bx = boxes[pbox[s]];
         double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
         hs[s] = fmin(fmax(hs[s] * 2.0, h[s] * margin), half);
-        active[s] = 1;
+        active[s] = (a & ACT_GUARD) | 1;
     } else {
-        active[s] = 0;
+        active[s] = a & ACT_GUARD;
     }
 }
 

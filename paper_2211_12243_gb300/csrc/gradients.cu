@@ -31,7 +31,10 @@ struct GradArgs {
     double ncond_crit, beta_min, beta_max, c_cfl;
     int limiter;
     double *outB, *outG, *outA, *outN;   // sorted staging (may be NULL)
-    uint8_t *active;                     // bit 2 set when N_cond fails
+    uint8_t *active;                     // ACT_NCOND set when N_cond fails
+    bool only_redo;                      // only the particles flagged ACT_REDO
+    double *dt_part;                     // per-particle CFL dt (+inf: no signal)
+    int32_t *npair;                      // per-particle gradient pairs
     DevCounters *cnt;
 };
 
@@ -58,16 +61,11 @@ __device__ __forceinline__ void load10<double>(const double *p, double v[10]) {
     }
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long mypairs = 0;
-    if (s < a.n) {
+    int mypairs = 0;
+    if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO))) {
         const Box bx = a.boxes[a.pbox[s]];
         R ri[10];
         load10<R>(rec + s * REC, ri);
@@ -218,20 +216,67 @@ __global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ r
             for (int f = 0; f < 5; f++) a.outA[f * a.n + s] = (double)alpha[f];
         }
         if (a.outN) a.outN[s] = ncond;
-        // CFL timestep of Eq. 31 with the signal velocity of Eq. 32
-        if (vs > R(0)) {
-            double dti = sizeof(R) == 8 ? a.c_cfl * hd / (double)vs
-                                        : (double)((float)a.c_cfl * (float)hd / (float)vs);
-            atomicMin(&a.cnt->dt_min_bits, (unsigned long long)__double_as_longlong(dti));
-        }
+        // CFL timestep of Eq. 31 with the signal velocity of Eq. 32 (the
+        // minimum over particles is taken by k_grad_reduce)
+        double dti = INFINITY;
+        if (vs > R(0))
+            dti = sizeof(R) == 8 ? a.c_cfl * hd / (double)vs
+                                 : (double)((float)a.c_cfl * (float)hd / (float)vs);
+        a.dt_part[s] = dti;
+        a.npair[s] = mypairs;
         // N_cond guard (§2.3.5)
         if (!(ncond <= a.ncond_crit)) {
-            a.active[s] |= 4;
+            a.active[s] |= ACT_NCOND;
             atomicAdd(&a.cnt->ncond_fail, 1);
         }
     }
-    unsigned long long tot = warp_sum_ull(mypairs);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&a.cnt->grad_pairs, tot);
+}
+
+// global CFL dt (minimum of the per-particle values, Eq. 31) and the count
+// of gradient pairs; dt_min_bits and grad_pairs were reset by the launcher
+__global__ void __launch_bounds__(256) k_grad_reduce(int64_t n, const double *__restrict__ dt_part,
+                                                     const int32_t *__restrict__ npair,
+                                                     DevCounters *cnt) {
+    __shared__ double smin[8];
+    __shared__ unsigned long long ssum[8];
+    double m = INFINITY;
+    unsigned long long t = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        m = fmin(m, dt_part[s]);
+        t += (unsigned long long)npair[s];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { smin[w] = m; ssum[w] = t; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        m = smin[0];
+        t = ssum[0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) { m = fmin(m, smin[k]); t += ssum[k]; }
+        // positive doubles order like their bit patterns
+        atomicMin(&cnt->dt_min_bits, (unsigned long long)__double_as_longlong(m));
+        if (t) atomicAdd(&cnt->grad_pairs, t);
+    }
+}
+
+// particles whose gradients change when the guard re-solved some densities:
+// the re-solved ones and every particle with one of them in its list
+__global__ void k_mark_redo(int64_t n, const int64_t *__restrict__ nbr_off,
+                            const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
+                            uint8_t *__restrict__ active) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint8_t me = active[s];
+    bool redo = (me & ACT_GUARD) != 0;
+    const int64_t o = nbr_off[s];
+    const int c = nbr_cnt[s];
+    for (int k = 0; k < c && !redo; k++) redo = (active[nbr_idx[o + k]] & ACT_GUARD) != 0;
+    // only this thread writes its byte, and ACT_GUARD (read by the others) is kept
+    if (redo) active[s] = me | ACT_REDO;
 }
 
 // primitives from the sorted conserved state and omega (§2.3.2, Eq. 23)
@@ -280,9 +325,9 @@ __global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint8_t a = active[s];
-    if (a & 4) {
+    if (a & ACT_NCOND) {
         nngb[s] *= grow;
-        active[s] = 1;
+        active[s] = ACT_SOLVE | ACT_GUARD;
     } else {
         active[s] = 0;
     }
@@ -321,8 +366,10 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st) {
 }
 
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
-                          double *ncond_out, stream_t st) {
+                          double *ncond_out, bool only_redo, stream_t st) {
     const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_vsig_dt.ensure(n));
+    HYD_CUDA(c->d_gpairs.ensure(n));
     GradArgs a;
     a.n = n;
     a.nbr_off = c->d_nbr_off.get();
@@ -341,7 +388,14 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.limiter = c->cfg.limiter;
     a.outB = B_out; a.outG = grad_out; a.outA = alpha_out; a.outN = ncond_out;
     a.active = c->d_active.get();
+    a.only_redo = only_redo;
+    a.dt_part = c->d_vsig_dt.get();
+    a.npair = c->d_gpairs.get();
     a.cnt = c->d_cnt;
+    if (only_redo) {
+        k_mark_redo<<<grid_for(n, 256), 256, 0, st>>>(n, a.nbr_off, a.nbr_cnt, a.nbr_idx, a.active);
+        HYD_CUDA(launch_check());
+    }
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
     const unsigned long long inf_bits = 0x7FF0000000000000ull;
@@ -351,6 +405,8 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         k_gradients<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
     else
         k_gradients<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
+    HYD_CUDA(launch_check());
+    k_grad_reduce<<<152 * 2, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
     return launch_check();
 }
 

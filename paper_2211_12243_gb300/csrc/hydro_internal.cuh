@@ -51,6 +51,15 @@ enum : int {
     ST_MLP = 256,             // a tensor-core wait of the MLP gave up
 };
 
+// per-particle flag bits (d_active)
+enum : uint8_t {
+    ACT_SOLVE = 1,     // solve the density of this particle
+    ACT_SEARCH = 2,    // its root lay beyond the list radius
+    ACT_NCOND = 4,     // N_cond above the threshold (guard)
+    ACT_REDO = 8,      // recompute its gradients (a neighbour's h changed)
+    ACT_GUARD = 16,    // its N_NGB grew in the current guard round
+};
+
 struct Box {
     double L[3];      // lengths
     float s[3];       // L / 2^32 (metres per fixed-point unit)
@@ -155,6 +164,7 @@ struct hydro_ctx {
     hyd::DevBuf<double> d_nngb;       // per-particle N_NGB
     hyd::DevBuf<uint8_t> d_active;    // density / guard flags
     hyd::DevBuf<double> d_vsig_dt;    // per-particle CFL dt
+    hyd::DevBuf<int32_t> d_gpairs;    // per-particle gradient pairs
 
     // neighbour lists
     hyd::DevBuf<int32_t> d_nbr_idx;
@@ -243,8 +253,10 @@ cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
 
 // gradients.cu
 cudaError_t run_primitives(hydro_ctx *c, stream_t st);
+// only_redo: recompute only the particles whose list holds a particle that
+// the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
-                          double *ncond_out, stream_t st);
+                          double *ncond_out, bool only_redo, stream_t st);
 cudaError_t guard_grow(hydro_ctx *c, stream_t st);
 cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
                            const double *alpha, stream_t st);

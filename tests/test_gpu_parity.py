@@ -149,6 +149,40 @@ def test_full_step_matches_oracle(orc, hyd, name, precision, tol):
     assert err < tol, err
 
 
+@pytest.mark.parametrize("crit", [4.0, 3.0])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_guard_rounds_match_oracle(orc, hyd, crit, precision, tol):
+    """The N_cond guard (§2.3.5) with a low threshold takes all five growth
+    rounds (crit 4: every particle passes in the end; crit 3: seven still
+    fail, status ENCOND).  A round re-solves the grown particles' densities
+    and recomputes only the gradients those change; the step must end where
+    the oracle, which recomputes every particle each round, ends."""
+    import torch
+    w = W.lognormal(4096, seed=2, grid=16)
+    co, cg = _cfgs(orc, hyd, w, dict(ncond_crit=crit), precision)
+    so, _, info_o = orc.step(co, w, -1.0)
+    assert info_o["ngb_rounds"] == 5
+    H = hyd.Hydro(cg)
+    H.set_boxes(*hyd.single_box(w))
+    st = hyd.to_device(w)
+    stats = H.step(st, -1.0, check=False)
+    torch.cuda.synchronize()
+    sg = {k: v.cpu().numpy() for k, v in st.items()}
+    assert stats["status"] == info_o["status"]
+    assert stats["ngb_rounds"] == info_o["ngb_rounds"]
+    assert stats["ncond_fail"] == info_o["ncond_fail"]
+    assert stats["grad_pairs"] == info_o["grad_pairs"]
+    assert stats["flux_pairs"] == info_o["flux"]["pairs"]
+    assert stats["dt"] == pytest.approx(info_o["dt"], rel=tol)
+    for k in ("h", "omega"):
+        assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol, k
+    for k in ("m", "px", "py", "pz", "E", "U"):
+        d_o = so[k] - w[k]
+        d_g = sg[k] - w[k]
+        scale = np.abs(d_o).max() + 1e-300
+        assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, k
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_conserves_and_reports(hyd, precision):
     import torch
