@@ -95,6 +95,11 @@ typedef struct {
     int max_h_iter;      /* cap on the h iteration (60) */
     int max_newton;      /* cap on Riemann Newton iterations (100) */
     double search_margin;/* hydro_step: search radius = margin * h_in (1.15) */
+    int graph;           /* hydro_step: 1 (default) runs the step as one captured
+                            CUDA graph whose re-search and N_cond loops are
+                            device-side WHILE nodes (no host waits inside the
+                            step); the first step of a context, and a step that
+                            must grow a buffer, run host-driven.  0: host-driven. */
 } hydro_config;
 
 /* Caller-owned particle state, caller order, all device pointers, n each.
@@ -145,6 +150,11 @@ typedef struct {
     float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
     float ms_flux_kernel;     /* the pair-flux kernel alone (CUDA events on the stream) */
     float ms_hard_faces;      /* the learned-guess hard-face kernel (0 when off) */
+    int graph;                /* 1: the step ran as the captured graph; 0: host-driven
+                                 (graph off, or the context's first step); 2: the
+                                 graph step needed a larger buffer, the host-driven
+                                 step redid it and grew the buffer; 3: a capture
+                                 failed, this context runs host-driven from now on */
 } hydro_stats;
 
 /* Defaults described above.  Always succeeds. */

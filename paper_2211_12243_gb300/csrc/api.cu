@@ -18,6 +18,8 @@ cudaError_t launch_check() {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace hyd
 
 namespace {
@@ -30,19 +32,6 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? HYDRO_OK : (e == cuda
         if (e__ != cudaSuccess) return cuda_status(e__); \
     } while (0)
 
-int flags_to_status(int f) {
-    if (f & ST_NONFINITE) return HYDRO_ENONFINITE;
-    if (f & ST_LIST_CAPACITY) return HYDRO_ECAPACITY;
-    if (f & ST_LIST_OVERFLOW) return HYDRO_ECAPACITY;
-    if (f & ST_STACK) return HYDRO_ECAPACITY;
-    if (f & ST_SEARCH) return HYDRO_ESEARCH;
-    if (f & ST_NOCONV_H) return HYDRO_ENOCONV_H;
-    if (f & ST_RIEMANN) return HYDRO_ERIEMANN;
-    if (f & ST_NCOND) return HYDRO_ENCOND;
-    if (f & ST_MLP) return HYDRO_EMLP;
-    return HYDRO_OK;
-}
-
 bool valid_config(const hydro_config *c) {
     if (!c) return false;
     if (!(c->gamma > 1.0)) return false;
@@ -54,6 +43,7 @@ bool valid_config(const hydro_config *c) {
     if (c->precision != HYDRO_FP64 && c->precision != HYDRO_MIXED) return false;
     if (c->learned_guess < 0 || c->learned_guess > 2) return false;
     if (!(c->search_margin >= 1.0)) return false;
+    if (c->graph != 0 && c->graph != 1) return false;
     if (c->max_h_iter < 1 || c->max_newton < 1 || c->max_ngb_grow < 0) return false;
     return true;
 }
@@ -140,13 +130,10 @@ int lists_all(hydro_ctx *c, cudaStream_t st) {
         if (!(f & ST_LIST_CAPACITY)) break;
         if (attempt >= 2) return HYDRO_ECAPACITY;
         // the overflow region was too small: grow it and redo the queued buckets
-        unsigned long long used = c->h_cnt->list_cursor - (unsigned long long)n * c->list_cap;
-        c->ovf_reserve = (int64_t)(used + used / 4 + 1024);
+        grow_overflow(c, c->h_cnt->list_cursor);
         size_t need = (size_t)n * c->list_cap + (size_t)c->ovf_reserve;
         API_CUDA(c->d_nbr_idx.ensure(need));
-        unsigned long long start = (unsigned long long)n * c->list_cap;
-        API_CUDA(cudaMemcpyAsync(&c->d_cnt->list_cursor, &start, sizeof(start),
-                                 cudaMemcpyHostToDevice, st));
+        API_CUDA(set_u64(&c->d_cnt->list_cursor, (unsigned long long)n * c->list_cap, st));
         API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
         // the fixed slots survive a reallocation only if nothing moved; rebuild them
         API_CUDA(build_lists(c, c->list_cap, st));
@@ -184,15 +171,33 @@ int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &r
         API_CUDA(grow_search_radius(c, st));
         int nq = 0;
         API_CUDA(rebuild_active_lists(c, &nq, st));
-        int fl = 0;
-        API_CUDA(cudaMemcpyAsync(&fl, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
+        const int fl = c->h_cnt->flags;
         if (fl & (ST_LIST_CAPACITY | ST_STACK)) {
+            if (fl & ST_LIST_CAPACITY) grow_overflow(c, c->h_cnt->list_cursor);
             int rc = lists_all(c, st);
             if (rc) return rc;
         }
         API_CUDA(run_density(c, true, true, st));
     }
+}
+
+}  // namespace
+
+namespace hyd {
+
+int flags_to_status(int f) {
+    if (f & ST_NONFINITE) return HYDRO_ENONFINITE;
+    if (f & ST_LIST_CAPACITY) return HYDRO_ECAPACITY;
+    if (f & ST_LIST_OVERFLOW) return HYDRO_ECAPACITY;
+    if (f & ST_STACK) return HYDRO_ECAPACITY;
+    if (f & ST_SEARCH) return HYDRO_ESEARCH;
+    if (f & ST_NOCONV_H) return HYDRO_ENOCONV_H;
+    if (f & ST_RIEMANN) return HYDRO_ERIEMANN;
+    if (f & ST_NCOND) return HYDRO_ENCOND;
+    if (f & ST_MLP) return HYDRO_EMLP;
+    return HYDRO_OK;
 }
 
 __global__ void k_fill(int64_t n, double *a, double v, uint8_t *act) {
@@ -207,7 +212,55 @@ cudaError_t reset_guard(hydro_ctx *c, cudaStream_t st) {
     return launch_check();
 }
 
-}  // namespace
+void grow_overflow(hydro_ctx *c, unsigned long long cursor) {
+    const unsigned long long base = (unsigned long long)c->plan.n * c->list_cap;
+    const unsigned long long used = cursor > base ? cursor - base : 0ull;
+    const int64_t want = (int64_t)(used + used / 4 + 4096);
+    if (want > c->ovf_reserve) c->ovf_reserve = want;
+}
+
+// last_stats from the counters already copied to h_cnt (the stream is idle)
+void fill_stats(hydro_ctx *c, double dt, bool timing) {
+    hydro_stats &S = c->last_stats;
+    const DevCounters &H = *c->h_cnt;
+    double dtmin;
+    memcpy(&dtmin, &H.dt_min_bits, sizeof(double));
+    S.dt_next = dtmin;
+    S.dt = dt > 0.0 ? dt : dtmin;
+    S.grad_pairs = (int64_t)H.grad_pairs;
+    S.flux_pairs = (int64_t)H.flux_pairs;
+    S.newton_iters = (int64_t)H.newton_iters;
+    S.guess_fallbacks = (int64_t)H.guess_fallbacks;
+    S.learned_faces = (int64_t)H.learned_faces;
+    S.hard_faces = (int64_t)H.hard_faces;
+    S.learned_active = c->learned_active ? 1 : 0;
+    S.vacuum_faces = (int64_t)H.vacuum;
+    S.first_order_faces = (int64_t)H.first_order;
+    for (int w = 0; w < 2; w++) {
+        S.mass[w] = H.sums[w][0];
+        for (int a = 0; a < 3; a++) S.mom[w][a] = H.sums[w][1 + a];
+        S.energy[w] = H.sums[w][4];
+    }
+    if (timing) {
+        auto el = [&](float &out, int e0, int e1) {
+            if (cudaEventElapsedTime(&out, c->ev[e0], c->ev[e1]) != cudaSuccess) {
+                out = 0.f;
+                (void)cudaGetLastError();
+            }
+        };
+        el(S.ms_neighbours, 0, 1);
+        el(S.ms_density, 1, 2);
+        el(S.ms_gradients, 2, 3);
+        el(S.ms_fluxes, 3, 4);
+        el(S.ms_update, 4, 5);
+        el(S.ms_flux_kernel, 6, 7);
+        S.ms_hard_faces = 0.f;
+        if (c->learned_active) el(S.ms_hard_faces, 7, 8);
+        S.ms_sort = 0.f;
+    }
+}
+
+}  // namespace hyd
 
 extern "C" {
 
@@ -237,6 +290,7 @@ void hydro_config_default(hydro_config *c) {
     c->max_h_iter = 60;
     c->max_newton = 100;
     c->search_margin = 1.15;
+    c->graph = 1;
 }
 
 int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
@@ -266,6 +320,7 @@ int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
 
 void hydro_destroy(hydro_ctx *c) {
     if (!c) return;
+    graph_release(c);
     if (c->d_cnt) cudaFree(c->d_cnt);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_learn) cudaFreeHost(c->h_learn);
@@ -441,18 +496,30 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     const int64_t n = p->n;
     const bool timing = stats != nullptr && c->have_events;
     API_CUDA(ensure_state(c, n));
+    // the first step of a context runs host-driven (it sizes every buffer);
+    // later ones replay the captured graph unless it asks for the host path
+    int how = 0;   // hydro_stats.graph of a host-driven step
+    if (c->cfg.graph && !c->graph_off && c->steps_done > 0) {
+        int rg = graph_step(c, p, dt, stats, st);
+        if (rg <= 0) {
+            c->steps_done++;
+            return rg;
+        }
+        how = c->graph_off ? 3 : 2;
+    }
+    c->last_stats.graph = how;
     API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
-    if (timing) API_CUDA(cudaEventRecord(c->ev[0], st));
+    if (timing) API_CUDA(record_event(c->ev[0], st));
     int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
     if (rc) return rc;
-    if (timing) API_CUDA(cudaEventRecord(c->ev[1], st));
+    if (timing) API_CUDA(record_event(c->ev[1], st));
     API_CUDA(reset_guard(c, st));
     int rebuilds = 0, rounds = 0, ncond_fail = 0;
     bool first = true;
     for (;;) {
         rc = density_all(c, p, !first, rebuilds, st);
         if (rc) return rc;
-        if (first && timing) API_CUDA(cudaEventRecord(c->ev[2], st));
+        if (first && timing) API_CUDA(record_event(c->ev[2], st));
         API_CUDA(run_primitives(c, st));
         // a guard round recomputes only the gradients its re-solved densities change
         API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
@@ -464,55 +531,27 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
         API_CUDA(guard_grow(c, st));
         rounds++;
     }
-    if (timing) API_CUDA(cudaEventRecord(c->ev[3], st));
+    if (timing) API_CUDA(record_event(c->ev[3], st));
     const double *dt_dev = dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
     c->timing = timing;
     rc = run_fluxes(c, dt, dt_dev, st);
     c->timing = false;
     API_CUDA((cudaError_t)rc);
-    if (timing) API_CUDA(cudaEventRecord(c->ev[4], st));
-    API_CUDA(run_update(c, p, dt, dt_dev, st));
+    if (timing) API_CUDA(record_event(c->ev[4], st));
+    API_CUDA(run_update(c, p, dt, dt_dev, false, st));
     if (stats) API_CUDA(run_update_sums(c, st));
-    if (timing) API_CUDA(cudaEventRecord(c->ev[5], st));
+    if (timing) API_CUDA(record_event(c->ev[5], st));
     c->last_stats.ngb_rounds = rounds;
     c->last_stats.list_rebuilds = rebuilds;
     c->last_stats.ncond_fail = ncond_fail;
+    c->steps_done++;
     if (stats) {
         API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
         hydro_stats &S = c->last_stats;
-        const DevCounters &H = *c->h_cnt;
-        S.status = flags_to_status(H.flags);
+        S.status = flags_to_status(c->h_cnt->flags);
         if (ncond_fail && S.status == HYDRO_OK) S.status = HYDRO_ENCOND;
-        double dtmin;
-        memcpy(&dtmin, &H.dt_min_bits, sizeof(double));
-        S.dt_next = dtmin;
-        S.dt = dt > 0.0 ? dt : dtmin;
-        S.grad_pairs = (int64_t)H.grad_pairs;
-        S.flux_pairs = (int64_t)H.flux_pairs;
-        S.newton_iters = (int64_t)H.newton_iters;
-        S.guess_fallbacks = (int64_t)H.guess_fallbacks;
-        S.learned_faces = (int64_t)H.learned_faces;
-        S.hard_faces = (int64_t)H.hard_faces;
-        S.learned_active = c->learned_active ? 1 : 0;
-        S.vacuum_faces = (int64_t)H.vacuum;
-        S.first_order_faces = (int64_t)H.first_order;
-        for (int w = 0; w < 2; w++) {
-            S.mass[w] = H.sums[w][0];
-            for (int a = 0; a < 3; a++) S.mom[w][a] = H.sums[w][1 + a];
-            S.energy[w] = H.sums[w][4];
-        }
-        if (timing) {
-            cudaEventElapsedTime(&S.ms_neighbours, c->ev[0], c->ev[1]);
-            cudaEventElapsedTime(&S.ms_density, c->ev[1], c->ev[2]);
-            cudaEventElapsedTime(&S.ms_gradients, c->ev[2], c->ev[3]);
-            cudaEventElapsedTime(&S.ms_fluxes, c->ev[3], c->ev[4]);
-            cudaEventElapsedTime(&S.ms_update, c->ev[4], c->ev[5]);
-            cudaEventElapsedTime(&S.ms_flux_kernel, c->ev[6], c->ev[7]);
-            S.ms_hard_faces = 0.f;
-            if (c->learned_active) cudaEventElapsedTime(&S.ms_hard_faces, c->ev[7], c->ev[8]);
-            S.ms_sort = 0.f;
-        }
+        fill_stats(c, dt, timing);
         *stats = S;
         return S.status;
     }

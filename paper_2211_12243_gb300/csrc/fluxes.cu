@@ -703,7 +703,7 @@ template <typename R>
 cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, stream_t st,
                           cudaEvent_t *ev) {
     unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
-    if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
+    if (ev) HYD_CUDA(record_event(ev[0], st));
     if (riem == HYDRO_RIEMANN_HLLC) {
         if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
         else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
@@ -712,7 +712,7 @@ cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme,
         else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     }
     HYD_CUDA(launch_check());
-    if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
+    if (ev) HYD_CUDA(record_event(ev[1], st));
     return cudaSuccess;
 }
 
@@ -750,6 +750,25 @@ cudaError_t launch_hard_faces(const FluxArgs &a, int scheme, stream_t st) {
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+bool decide_learned(hydro_ctx *c) {
+    const bool want = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
+                      c->cfg.learned_guess && c->have_mlp;
+    if (!want) return false;
+    // adaptive mode: after a learned call in which under 10% of the hard
+    // faces started from the network, the next 15 calls skip the deferral
+    // (its cost buys nothing there) before probing again
+    if (c->learn_probe_pending) {
+        if (cudaEventSynchronize(c->ev[9]) == cudaSuccess) {
+            const unsigned long long used = c->h_learn[0], hard = c->h_learn[1];
+            if (c->cfg.learned_guess == 1 && used * 10 <= hard) c->learn_skip = 15;
+        }
+        c->learn_probe_pending = false;
+    }
+    if (c->cfg.learned_guess == 2 || c->learn_skip == 0) return true;
+    c->learn_skip--;
+    return false;
+}
 
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st) {
     const int64_t n = c->plan.n;
@@ -789,22 +808,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.hard_idx = nullptr;
     a.hard_cursor = nullptr;
     a.hard_cap = 0;
-    const bool want = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
-                      c->cfg.learned_guess && c->have_mlp;
-    bool learned = false;
-    if (want) {
-        // adaptive mode: after a learned call in which under 10% of the hard
-        // faces started from the network, the next 15 calls skip the
-        // deferral (its cost buys nothing there) before probing again
-        if (c->learn_probe_pending) {
-            HYD_CUDA(cudaEventSynchronize(c->ev[9]));
-            const unsigned long long used = c->h_learn[0], hard = c->h_learn[1];
-            c->learn_probe_pending = false;
-            if (c->cfg.learned_guess == 1 && used * 10 <= hard) c->learn_skip = 15;
-        }
-        if (c->cfg.learned_guess == 2 || c->learn_skip == 0) learned = true;
-        else c->learn_skip--;
-    }
+    const bool learned = c->learned_decision >= 0 ? c->learned_decision != 0 : decide_learned(c);
     c->learned_active = learned;
     // room for 4 hard faces per particle to start with (sub-buffer sizes a
     // multiple of 128); a pass that fills a sub-buffer is redone with twice
@@ -849,9 +853,12 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     if (learned) {
         for (int attempt = 0;; attempt++) {
             HYD_CUDA(cudaMemsetAsync(a.hard_cursor, 0, HARD_SUB * sizeof(unsigned long long), st));
-            if (ev) HYD_CUDA(cudaEventRecord(ev[0], st));
+            if (ev) HYD_CUDA(record_event(ev[0], st));
             HYD_CUDA(launch_fluxes_defer(a, c->d_recf.get(), c->cfg.scheme, st));
-            if (ev) HYD_CUDA(cudaEventRecord(ev[1], st));
+            if (ev) HYD_CUDA(record_event(ev[1], st));
+            // a graph step cannot wait here: a full sub-buffer (hard_ovf)
+            // stops its update and the host redoes the step
+            if (c->capturing) break;
             unsigned long long ovf = 0;
             HYD_CUDA(cudaMemcpyAsync(&ovf, &c->d_cnt->hard_ovf, sizeof(ovf), cudaMemcpyDeviceToHost, st));
             HYD_CUDA(cudaStreamSynchronize(st));
@@ -861,11 +868,11 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
             HYD_CUDA(clear());
         }
         HYD_CUDA(launch_hard_faces(a, c->cfg.scheme, st));
-        if (ev) HYD_CUDA(cudaEventRecord(ev[2], st));
+        if (ev) HYD_CUDA(record_event(ev[2], st));
         // learned_faces and hard_faces (adjacent) for the adaptive decision
         HYD_CUDA(cudaMemcpyAsync(c->h_learn, &c->d_cnt->learned_faces, 2 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, st));
-        HYD_CUDA(cudaEventRecord(c->ev[9], st));
+        HYD_CUDA(record_event(c->ev[9], st));
         c->learn_probe_pending = true;
         return cudaSuccess;
     }

@@ -398,9 +398,7 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     }
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
-    const unsigned long long inf_bits = 0x7FF0000000000000ull;
-    HYD_CUDA(cudaMemcpyAsync(&c->d_cnt->dt_min_bits, &inf_bits, sizeof(inf_bits),
-                             cudaMemcpyHostToDevice, st));
+    HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
     if (c->cfg.precision == HYDRO_MIXED)
         k_gradients<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
     else

@@ -85,6 +85,12 @@ struct DevCounters {
     unsigned long long hard_faces;     // faces where Toro's guess is the two-shock value
     unsigned long long hard_ovf;       // a deferred-face sub-buffer was full (pass redone)
     double sums[2][5];                // totals before / after (m, px, py, pz, E)
+    // device-driven loops of the graph step (graph.cu)
+    int search_round;                 // re-search rounds of the current density solve
+    int guard_round;                  // N_cond growth rounds taken
+    int rebuilds;                     // re-search rounds in the step
+    int abort;                        // the step cannot finish on the device: no update
+    int ovf_first;                    // buckets of the first list pass with long lists
 };
 
 // bucket tree topology (host plan, mirrored on the device)
@@ -214,6 +220,21 @@ struct hydro_ctx {
                                       // 9 after the learned-path counters' readback
     bool have_events = false;
     bool timing = false;              // record ev[6..9] in the flux launcher
+
+    // graph step (graph.cu): one executable graph per learned-path choice,
+    // with the launch parameters it was captured with
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<unsigned long long> key;
+        // kernels per run: top level, one re-search round, one guard round
+        // (without its re-search rounds)
+        long long k_top = 0, k_search = 0, k_guard = 0;
+    } graph_slot[2];
+    cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};   // capture streams (top, bodies)
+    int learned_decision = -1;        // >= 0: run_fluxes takes this choice (graph capture)
+    bool capturing = false;           // enqueue without host synchronisation
+    bool graph_off = false;           // a capture failed: host-driven steps only
+    int64_t steps_done = 0;           // hydro_step calls completed
 };
 
 namespace hyd {
@@ -221,6 +242,20 @@ namespace hyd {
 // every kernel launch is followed by launch_check(): it returns the launch
 // error and counts the launch (process-wide, see hydro_kernel_launches)
 cudaError_t launch_check();
+// an event record that a stream capture turns into a graph node (a plain
+// record during capture only orders captured work and is never timed)
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(st, &cs);
+    if (r != cudaSuccess) return r;
+    if (cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    return cudaEventRecord(e, st);
+}
+// the process-wide count behind hydro_kernel_launches: a kernel enqueued
+// while a graph is captured is counted when the graph runs (graph.cu)
+long long launch_count();
+void add_launches(long long k);
 
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
@@ -244,6 +279,10 @@ cudaError_t build_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
 cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
 cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st);
+// the same two passes with the bucket count read on the device (no host
+// wait): the queued overflow buckets, and the re-search rebuild
+cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);
+cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu
@@ -263,6 +302,21 @@ cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
 
 // fluxes.cu
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st);
+// the adaptive learned-path choice for the next flux call (host state)
+bool decide_learned(hydro_ctx *c);
+
+// api.cu: shared by the host-driven and the graph step
+int flags_to_status(int flags);
+cudaError_t reset_guard(hydro_ctx *c, stream_t st);   // N_NGB = n_ngb, every particle active
+void fill_stats(hydro_ctx *c, double dt, bool timing); // last_stats from h_cnt and the events
+// the overflow region of the lists asked for entries up to `cursor`: keep
+// room for that (and a quarter more) from the next list build on
+void grow_overflow(hydro_ctx *c, unsigned long long cursor);
+
+// graph.cu: hydro_step as one captured graph; returns HYDRO_* (a positive
+// value asks the caller to run the host-driven step instead)
+int graph_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats, stream_t st);
+void graph_release(hydro_ctx *c);
 
 // mlp.cu (bytes of the packed weight tiles; faces are float [6 or 7][n])
 constexpr size_t MLP_BLOB_BYTES = 11264;
@@ -278,9 +332,13 @@ cudaError_t mlp_adam(hydro_ctx *c, float *grad, float *m, float *v, float lr, in
 cudaError_t mlp_normalise(hydro_ctx *c, const float *x, const float *t, int64_t n, double *acc,
                           int *box, stream_t st);
 
-// update.cu
+// update.cu (abort_check: skip the update when the device step set an abort
+// condition -- see graph.cu)
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
-                       stream_t st);
+                       bool abort_check, stream_t st);
+// *p = v on the stream (a kernel: no host memory is referenced, so the call
+// can be captured into a graph)
+cudaError_t set_u64(unsigned long long *p, unsigned long long v, stream_t st);
 cudaError_t run_sums(hydro_ctx *c, int which, stream_t st);
 cudaError_t run_update_sums(hydro_ctx *c, stream_t st);
 cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st);

@@ -127,6 +127,7 @@ struct ListArgs {
                // 2: write at nbr_off (queued buckets)
     int32_t *ovf_list;      // queued bucket ids
     int *ovf_count;
+    bool nq_dev;            // modes 1, 2: warps past *ovf_count have no bucket
 };
 
 __device__ __forceinline__ float u2f(uint32_t v) {
@@ -276,7 +277,10 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_build_lists(ListArgs a) 
         return st;
     };
     if (b >= a.nbucket) return;
-    if (a.mode != 0) b = a.ovf_list[b];
+    if (a.mode != 0) {
+        if (a.nq_dev && b >= *a.ovf_count) return;
+        b = a.ovf_list[b];
+    }
 
     const int f = a.node_first[b], c = a.node_cnt[b];
     const Box bx = a.boxes[a.node_box[b]];
@@ -535,6 +539,7 @@ static ListArgs list_args(hydro_ctx *c, int cap, int mode) {
     a.mode = mode;
     a.ovf_list = c->d_ovf.get();
     a.ovf_count = &c->d_cnt->ovf_buckets;
+    a.nq_dev = false;
     return a;
 }
 
@@ -557,9 +562,7 @@ cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st) {
     if (c->d_nbr_idx.cap < need) HYD_CUDA(c->d_nbr_idx.ensure(need + need / 8));
     HYD_CUDA(c->d_ovf.ensure(c->plan.nbucket));
     c->list_cap = cap;
-    unsigned long long start = (unsigned long long)n * cap;
-    HYD_CUDA(cudaMemcpyAsync(&c->d_cnt->list_cursor, &start, sizeof(start),
-                             cudaMemcpyHostToDevice, st));
+    HYD_CUDA(set_u64(&c->d_cnt->list_cursor, (unsigned long long)n * cap, st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
     return launch_lists(list_args(c, cap, 0), c->plan.nbucket, st);
 }
@@ -571,6 +574,27 @@ cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st) {
     HYD_CUDA(launch_lists(a, nq, st));
     a.mode = 2;
     return launch_lists(a, nq, st);
+}
+
+// the queued passes over as many warps as there are buckets; the count of
+// queued buckets is read by the warps themselves
+cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st) {
+    ListArgs a = list_args(c, c->list_cap, 1);
+    a.nq_dev = true;
+    HYD_CUDA(launch_lists(a, c->plan.nbucket, st));
+    a.mode = 2;
+    return launch_lists(a, c->plan.nbucket, st);
+}
+
+cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st) {
+    const Plan &P = c->plan;
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
+    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+        P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
+        &c->d_cnt->ovf_buckets, c->d_cnt);
+    HYD_CUDA(launch_check());
+    HYD_CUDA(build_tree(c, st));
+    return build_lists_queued_dev(c, st);
 }
 
 // new lists (in the overflow region) for the buckets that hold a particle

@@ -22,11 +22,18 @@ struct UpdArgs {
     const double *dt_dev;
     hydro_particles p;
     DevCounters *cnt;
+    bool abort_check;
 };
 
 __global__ void k_update(UpdArgs a) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= a.n) return;
+    if (a.abort_check) {
+        // the graph step found a condition it cannot resolve on the device:
+        // leave the caller's state as it was (the host redoes the step)
+        const DevCounters &k = *a.cnt;
+        if (k.abort || k.hard_ovf || (k.flags & (ST_LIST_CAPACITY | ST_STACK))) return;
+    }
     const int64_t n = a.n;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     double m0 = a.Q[s], px0 = a.Q[n + s], py0 = a.Q[2 * n + s], pz0 = a.Q[3 * n + s];
@@ -138,12 +145,19 @@ __global__ void k_export_dQ(int64_t n, const int32_t *__restrict__ perm,
     out[6 * o + 5] = dU;
 }
 
+__global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+cudaError_t set_u64(unsigned long long *p, unsigned long long v, stream_t st) {
+    k_set_u64<<<1, 1, 0, st>>>(p, v);
+    return launch_check();
+}
+
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
-                       stream_t st) {
+                       bool abort_check, stream_t st) {
     UpdArgs a;
     a.n = c->plan.n;
     a.perm = c->d_perm.get();
@@ -158,6 +172,7 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.dt_dev = dt_dev;
     a.p = *p;
     a.cnt = c->d_cnt;
+    a.abort_check = abort_check;
     k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
     return launch_check();
 }

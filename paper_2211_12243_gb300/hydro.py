@@ -45,7 +45,7 @@ class Config(C.Structure):
         ("psi1", C.c_double), ("psi2", C.c_double), ("beta_min", C.c_double),
         ("beta_max", C.c_double), ("c_cfl", C.c_double), ("alpha1", C.c_double),
         ("h_tol", C.c_double), ("p_tol", C.c_double), ("max_h_iter", C.c_int),
-        ("max_newton", C.c_int), ("search_margin", C.c_double),
+        ("max_newton", C.c_int), ("search_margin", C.c_double), ("graph", C.c_int),
     ]
 
 
@@ -70,6 +70,7 @@ class Stats(C.Structure):
         ("energy", C.c_double * 2), ("ms_sort", C.c_float), ("ms_neighbours", C.c_float),
         ("ms_density", C.c_float), ("ms_gradients", C.c_float), ("ms_fluxes", C.c_float),
         ("ms_update", C.c_float), ("ms_flux_kernel", C.c_float), ("ms_hard_faces", C.c_float),
+        ("graph", C.c_int),
     ]
 
     def as_dict(self):
