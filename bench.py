@@ -49,13 +49,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sod", choices=["sod", "sedov", "lognormal", "batch"],
+    ap.add_argument("--workload", default="sod",
+                    choices=["sod", "sedov", "lognormal", "batch", "wave"],
                     help="sod: 3D Sod tube (default); sedov: Sedov-Taylor blast on an n^3 "
                          "lattice; lognormal: clustered log-normal box of n particles; batch: n "
-                         "independent periodic boxes of 4k-64k particles in one launch")
+                         "independent periodic boxes of 4k-64k particles in one launch; wave: "
+                         "n^3 jittered lattice with a density wave (HLLC)")
     ap.add_argument("--n", type=int, default=None,
                     help="size: Sod resolution (78: 1,067,742), Sedov lattice side (128), "
-                         "log-normal particle count (2^24), number of boxes (512)")
+                         "log-normal particle count (2^24), number of boxes (512), wave "
+                         "lattice side (32)")
+    ap.add_argument("--riemann", default=None, choices=["exact", "hllc"],
+                    help="Riemann solver (default: exact; hllc for the wave)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch parameters (no hydro_autotune)")
+    ap.add_argument("--no-graph", action="store_true", help="host-driven steps (no CUDA graph)")
     ap.add_argument("--scheme", default="mfv")
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
@@ -140,6 +148,9 @@ def make_workload(kind, n):
     if kind == "batch":
         n = n or 512
         return W.batch(n), f"batch_{n}_boxes_4k_64k_mfv_exact"
+    if kind == "wave":
+        n = n or 32
+        return W.lattice_wave(n), f"wave3d_{n}cubed_mfv_hllc"
     n = n or 78
     return W.sod(n), (WORKLOAD if n == 78 else f"sod3d_n{n}")
 
@@ -150,7 +161,7 @@ def oracle_sample_rate(kind, n, reps):
     metric."""
     import oracle
     if n is None:
-        n = {"sod": 40, "sedov": 32, "lognormal": 1 << 15, "batch": 6}[kind]
+        n = {"sod": 40, "sedov": 32, "lognormal": 1 << 15, "batch": 6, "wave": 32}[kind]
     w, _ = make_workload(kind, n)
     if kind == "batch":   # the oracle takes one periodic box at a time
         off, bl = w["box_off"], w["box_len"].reshape(-1, 3)
@@ -287,10 +298,13 @@ def main():
     n = w["x"].size
     learned = args.precision == "mixed" and not args.no_learned
     training = train_network(hydro, workloads, w, args.train_steps) if learned else None
-    # the log-normal initial h are rough guesses: search wider in the first step
+    riemann = args.riemann or ("hllc" if args.workload == "wave" else "exact")
+    learned = learned and riemann == "exact"
     margin = 1.15
-    cfg = hydro.default_config(gamma=w["gamma"], precision=args.precision, scheme=args.scheme,
-                               learned_guess=int(learned), search_margin=margin)
+    graph = 0 if args.no_graph else 1
+    common = dict(gamma=w["gamma"], scheme=args.scheme, riemann=riemann, search_margin=margin,
+                  graph=graph)
+    cfg = hydro.default_config(precision=args.precision, learned_guess=int(learned), **common)
     H = hydro.Hydro(cfg)
     if learned:
         H.mlp_load(training["theta"])
@@ -317,6 +331,12 @@ def main():
         w["h"] = tmp["h"].cpu().numpy()
         del tmp
 
+    def tune(Hc, state):
+        # launch parameters timed on this state (untimed; state untouched)
+        return None if args.no_autotune else Hc.autotune(state)
+
+    tuning = tune(H, st)
+
     def timed_steps(Hc, state, k, warm):
         saved = {kk: v.clone() for kk, v in state.items()} if restart else None
         for _ in range(warm):
@@ -334,7 +354,7 @@ def main():
         hard_ms = 0.0
         flux_pairs = 0
         iters = 0
-        hard = learned_faces = fallbacks = active = 0
+        hard = learned_faces = fallbacks = active = graph_steps = 0
         launches0 = hydro.kernel_launches()
         stats = None
         for i in range(k):
@@ -357,13 +377,15 @@ def main():
             learned_faces += stats["learned_faces"]
             fallbacks += stats["guess_fallbacks"]
             active += stats["learned_active"]
+            graph_steps += stats["graph"] == 1
         torch.cuda.synchronize()
         launches = hydro.kernel_launches() - launches0 - 0
         ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
         return dict(ms=ms, pairs=pairs, flux_ms=flux_ms, grad_ms=grad_ms, kern_ms=kern_ms,
                     hard_ms=hard_ms, gf_ms=grad_ms + flux_ms,
                     flux_pairs=flux_pairs, iters=iters, hard=hard, learned=learned_faces,
-                    fallbacks=fallbacks, active=active, launches=launches, last=stats)
+                    fallbacks=fallbacks, active=active, launches=launches, last=stats,
+                    graph_steps=graph_steps)
 
     # ---- timed region: the mixed step
     if world > 1:
@@ -413,10 +435,11 @@ def main():
     # ---- the same mixed step with the plain (Toro) guess, same starting state
     plain_guess = None
     if learned:
-        Hp = hydro.Hydro(hydro.default_config(gamma=w["gamma"], precision=args.precision,
-                                              scheme=args.scheme, search_margin=margin))
+        Hp = hydro.Hydro(hydro.default_config(precision=args.precision, **common))
         Hp.set_boxes(*boxes_of(hydro, w))
         stp = hydro.to_device(w)
+        if tuning:
+            Hp.set_tuning(tuning)
         kp = max(2, min(args.steps, 5))
         rp = timed_steps(Hp, stp, kp, 1)
         plain_guess = {"value": rp["pairs"] / (rp["gf_ms"] / 1000.0),
@@ -428,16 +451,20 @@ def main():
     # ---- plain FP64 step on the same starting state
     fp64 = None
     if not args.no_fp64:
-        cfg64 = hydro.default_config(gamma=w["gamma"], precision="fp64", scheme=args.scheme,
-                                     search_margin=margin)
-        H64 = hydro.Hydro(cfg64)
+        H64 = hydro.Hydro(hydro.default_config(precision="fp64", **common))
         H64.set_boxes(*boxes_of(hydro, w))
         st64 = hydro.to_device(w)
+        # the list radius and slots found for the mixed step; default kernels
+        tuning64 = None if tuning is None else dict(tuning, grad_min_ctas=1, flux_min_ctas=4)
+        if tuning64:
+            H64.set_tuning(tuning64)
         k64 = max(2, min(args.steps, 5))
         r64 = timed_steps(H64, st64, k64, 1)
         fp64 = {"value": r64["pairs"] / (r64["gf_ms"] / 1000.0),
                 "step_rate": r64["pairs"] / (r64["ms"] / 1000.0), "ms_per_step": r64["ms"] / k64,
-                "flux_kernel_ms": r64["flux_ms"] / k64}
+                "flux_kernel_ms": r64["flux_ms"] / k64,
+                "tuning": None if tuning64 is None else {k: tuning64[k] for k in (
+                    "search_margin", "nbr_slots", "grad_min_ctas")}}
         H64.close()
 
     # ---- roofline of the dominant kernel (pair fluxes, float ALU bound):
@@ -453,10 +480,15 @@ def main():
     iters_own = iters * solved / max(faces, 1.0)
     achieved = (solved * FLOPS_PER_FACE + iters_own * FLOPS_PER_NEWTON) / (kern_ms / 1000.0) / 1e12
     peak = FP32_PEAK_TFLOPS
+    if riemann != "exact":
+        achieved = None   # the flop count below is the exact solver's
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak,
-            "traffic": FLUX_TRAFFIC_BYTES_PER_FACE * faces if args.workload == "sod" else None,
-            "kernel": "k_fluxes<float,exact,mfv>", "kernel_ms": kern_ms,
+            "frac": None if achieved is None else achieved / peak,
+            # measured for the default register bound (4 CTAs per SM) on the tube
+            "traffic": (FLUX_TRAFFIC_BYTES_PER_FACE * faces
+                        if args.workload == "sod" and (tuning is None or
+                                                       tuning["flux_min_ctas"] == 4) else None),
+            "kernel": f"k_fluxes<float,{riemann},{args.scheme}>", "kernel_ms": kern_ms,
             "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     cpu = None
@@ -472,7 +504,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": wname, "particles": n,
                    "timed_steps": "each from the initial state (h: its converged smoothing lengths)" if restart else "consecutive",
-                   "precision": args.precision, "scheme": args.scheme, "riemann": "exact",
+                   "precision": args.precision, "scheme": args.scheme, "riemann": riemann,
+                   "cuda_graph": bool(graph), "graph_steps": r["graph_steps"],
+                   "tuning": tuning,
                    "kernel": "wendland_c2", "n_ngb": 32,
                    "l2": "flushed before every timed step (256 MB write)",
                    "pairs_per_step": r["pairs"] / args.steps,
@@ -511,9 +545,10 @@ FLOPS_PER_NEWTON = 38.0
 # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
-# of the current kernel (Sod tube n = 60: 249.4 MB for 6,385,500 faces);
-# a launch's traffic scales with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = 39.05
+# of the current kernel on the Sod tube at n = 60 (181.9 MB for 6,385,500
+# faces, lists compacted by the density stage); a launch's traffic scales
+# with its faces
+FLUX_TRAFFIC_BYTES_PER_FACE = 28.49
 
 if __name__ == "__main__":
     sys.exit(main())

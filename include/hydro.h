@@ -348,6 +348,41 @@ int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const 
                          const double *pz, const double *etot, double *totals,
                          hydro_stream stream);
 
+/* Launch parameters of the step that hydro_autotune chooses by timing the
+ * candidates on the caller's own particles (no counterpart in the paper:
+ * a property of this GPU implementation).  Candidates:
+ *   search_margin x nbr_slots: the neighbour-list radius factor of
+ *     hydro_step {1.05, 1.1, 1.15, 1.25} and the fixed list slots per
+ *     particle {64, 96, 128} (longer lists take two extra passes into an
+ *     overflow region), timed over sort + lists + density;
+ *   grad_min_ctas: register bound of the gradient kernel (1: none; 5, 6
+ *     resident 128-thread CTAs per SM), timed over the gradient stage;
+ *   flux_min_ctas: register bound of the float flux kernel (4, 5, 6),
+ *     timed over the plain-guess flux stage (mixed precision only).
+ * The times (ms, best of two) are returned beside the choices. */
+typedef struct {
+    double search_margin;
+    int nbr_slots;
+    int grad_min_ctas;
+    int flux_min_ctas;
+    float front_ms[4][3];     /* [margin][slots] */
+    float grad_ms[3];         /* [1, 5, 6] */
+    float flux_ms[3];         /* [4, 5, 6]; 0 in FP64 */
+} hydro_tuning;
+
+/* Time the candidates above on the particles p (device, caller order; state
+ * as for hydro_step) and keep the fastest in the context (search_margin
+ * replaces the configured one).  The particles are read, never written.
+ * `out` (host, may be NULL) receives the choices and times.  Synchronous.
+ * Errors: HYDRO_EINVAL (no boxes / bad particles), HYDRO_ESTATE (learned
+ * guess configured without a network), or any error a step would report. */
+int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_stream stream);
+
+/* Apply choices saved from an earlier hydro_autotune (search_margin >= 1,
+ * nbr_slots in [32, 256], grad_min_ctas in {1, 5, 6}, flux_min_ctas in
+ * {4, 5, 6}; the time fields are ignored).  HYDRO_EINVAL otherwise. */
+int hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *t);
+
 /* Number of kernels this library has launched in the process so far
  * (every entry point's launches, all contexts).  Diagnostics only. */
 int64_t hydro_kernel_launches(void);

@@ -751,6 +751,119 @@ int hydro_recorded_faces(hydro_ctx *c, int64_t *count, hydro_stream stream) {
     return HYDRO_OK;
 }
 
+int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
+    if (!c || !t) return HYDRO_EINVAL;
+    if (!(t->search_margin >= 1.0) || t->nbr_slots < 32 || t->nbr_slots > 256) return HYDRO_EINVAL;
+    if (t->grad_min_ctas != 1 && t->grad_min_ctas != 5 && t->grad_min_ctas != 6) return HYDRO_EINVAL;
+    if (t->flux_min_ctas < 4 || t->flux_min_ctas > 6) return HYDRO_EINVAL;
+    c->cfg.search_margin = t->search_margin;
+    c->nbr_per_particle = t->nbr_slots;
+    c->grad_minb = t->grad_min_ctas;
+    c->flux_minb = t->flux_min_ctas;
+    return HYDRO_OK;
+}
+
+int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_stream stream) {
+    if (!c || !c->have_plan) return HYDRO_EINVAL;
+    if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
+    if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(ensure_state(c, p->n));
+    static const double margins[4] = {1.05, 1.1, 1.15, 1.25};
+    static const int slots[3] = {64, 96, 128};
+    static const int gminb[3] = {1, 5, 6};
+    static const int fminb[3] = {4, 5, 6};
+    hydro_tuning T;
+    memset(&T, 0, sizeof(T));
+    float ms = 0.f;
+    // sort, lists and density (the part the radius and the slots change),
+    // from the caller's particles each time
+    auto front = [&](double margin, int nslots) -> int {
+        c->cfg.search_margin = margin;
+        c->nbr_per_particle = nslots;
+        API_CUDA(record_event(c->ev[0], st));
+        API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
+        int rc = build_all(c, p, p->h, nullptr, margin, true, st);
+        if (rc) return rc;
+        API_CUDA(reset_guard(c, st));
+        int rebuilds = 0;
+        rc = density_all(c, p, false, rebuilds, st);
+        if (rc) return rc;
+        API_CUDA(record_event(c->ev[1], st));
+        API_CUDA(cudaEventSynchronize(c->ev[1]));
+        API_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->nbr_per_particle = nslots;   // (lists_all may have grown it)
+        return HYDRO_OK;
+    };
+    float best = 1e30f;
+    double bm = c->cfg.search_margin;
+    int bs = c->nbr_per_particle;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 3; j++) {
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                int rc = front(margins[i], slots[j]);
+                if (rc) return rc;
+                t = std::min(t, ms);
+            }
+            T.front_ms[i][j] = t;
+            if (t < best) { best = t; bm = margins[i]; bs = slots[j]; }
+        }
+    int rc = front(bm, bs);
+    if (rc) return rc;
+    API_CUDA(run_primitives(c, st));
+    // gradient stage
+    best = 1e30f;
+    int bg = 1;
+    for (int k = 0; k < 3; k++) {
+        c->grad_minb = gminb[k];
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            API_CUDA(record_event(c->ev[0], st));
+            API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, false, st));
+            API_CUDA(record_event(c->ev[1], st));
+            API_CUDA(cudaEventSynchronize(c->ev[1]));
+            API_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            t = std::min(t, ms);
+        }
+        T.grad_ms[k] = t;
+        if (t < best) { best = t; bg = gminb[k]; }
+    }
+    c->grad_minb = bg;
+    // flux stage, plain guess (the dt the gradients found)
+    int bf = 4;
+    if (c->cfg.precision == HYDRO_MIXED) {
+        const double *dt_dev = reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
+        best = 1e30f;
+        c->learned_decision = 0;
+        for (int k = 0; k < 3; k++) {
+            c->flux_minb = fminb[k];
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                API_CUDA(record_event(c->ev[0], st));
+                cudaError_t e = run_fluxes(c, -1.0, dt_dev, st);
+                if (e != cudaSuccess) { c->learned_decision = -1; return cuda_status(e); }
+                API_CUDA(record_event(c->ev[1], st));
+                API_CUDA(cudaEventSynchronize(c->ev[1]));
+                API_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+                t = std::min(t, ms);
+            }
+            T.flux_ms[k] = t;
+            if (t < best) { best = t; bf = fminb[k]; }
+        }
+        c->learned_decision = -1;
+    }
+    c->flux_minb = bf;
+    c->cfg.search_margin = bm;
+    c->nbr_per_particle = bs;
+    T.search_margin = bm;
+    T.nbr_slots = bs;
+    T.grad_min_ctas = bg;
+    T.flux_min_ctas = bf;
+    if (out) *out = T;
+    return HYDRO_OK;
+}
+
 int64_t hydro_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 const char *hydro_strerror(int s) {

@@ -1,0 +1,39 @@
+// The float flux kernel (flux_kernel.cuh) compiled for 5 and 6 resident
+// CTAs of 128 threads per SM (at most 96 and 80 registers per thread, with
+// spills), the launch-bounds variants the autotuner times against the
+// default of 4 CTAs (128 registers).  A translation unit of its own so that
+// the variants compile in parallel with fluxes.cu.
+#include "flux_kernel.cuh"
+
+namespace hyd {
+
+namespace {
+
+template <int MINB>
+cudaError_t launch_minb(const FluxArgs &a, const float *rec, int riem, int scheme, bool defer,
+                        stream_t st) {
+    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    constexpr int E = HYDRO_RIEMANN_EXACT, H = HYDRO_RIEMANN_HLLC;
+    if (defer) {
+        if (scheme == HYDRO_MFM) k_fluxes<float, E, HYDRO_MFM, true, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<float, E, HYDRO_MFV, true, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    } else if (riem == H) {
+        if (scheme == HYDRO_MFM) k_fluxes<float, H, HYDRO_MFM, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<float, H, HYDRO_MFV, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    } else {
+        if (scheme == HYDRO_MFM) k_fluxes<float, E, HYDRO_MFM, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        else k_fluxes<float, E, HYDRO_MFV, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    }
+    return launch_check();
+}
+
+}  // namespace
+
+cudaError_t launch_fluxes_occ(int minb, const FluxArgs &a, const float *rec, int riem, int scheme,
+                              bool defer, stream_t st) {
+    if (minb == 5) return launch_minb<5>(a, rec, riem, scheme, defer, st);
+    if (minb == 6) return launch_minb<6>(a, rec, riem, scheme, defer, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hyd

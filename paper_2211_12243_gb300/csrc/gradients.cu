@@ -61,8 +61,10 @@ __device__ __forceinline__ void load10<double>(const double *p, double v[10]) {
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_gradients(GradArgs a, R *__restrict__ rec) {
+// MINB: resident CTAs per SM the register allocation must allow (1: no
+// bound; 5, 6: the variants hydro_autotune times)
+template <typename R, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int mypairs = 0;
     if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO))) {
@@ -399,10 +401,18 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
     HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
-    if (c->cfg.precision == HYDRO_MIXED)
-        k_gradients<float><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recf.get());
-    else
-        k_gradients<double><<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
+    const unsigned grid = grid_for(n, 128);
+    if (c->cfg.precision == HYDRO_MIXED) {
+        float *r = c->d_recf.get();
+        if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, 0, st>>>(a, r);
+        else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, 0, st>>>(a, r);
+        else k_gradients<float, 1><<<grid, 128, 0, st>>>(a, r);
+    } else {
+        double *r = c->d_recd.get();
+        if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, 0, st>>>(a, r);
+        else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, 0, st>>>(a, r);
+        else k_gradients<double, 1><<<grid, 128, 0, st>>>(a, r);
+    }
     HYD_CUDA(launch_check());
     k_grad_reduce<<<152 * 2, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
     return launch_check();

@@ -234,6 +234,11 @@ struct hydro_ctx {
     int learned_decision = -1;        // >= 0: run_fluxes takes this choice (graph capture)
     bool capturing = false;           // enqueue without host synchronisation
     bool graph_off = false;           // a capture failed: host-driven steps only
+    // launch-bounds variants chosen by hydro_autotune (resident CTAs per SM
+    // the register allocation allows): float flux kernel 4, 5 or 6;
+    // gradient kernel 1 (no bound), 5 or 6
+    int flux_minb = 4;
+    int grad_minb = 1;
     int64_t steps_done = 0;           // hydro_step calls completed
 };
 

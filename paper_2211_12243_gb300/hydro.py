@@ -85,13 +85,27 @@ class Stats(C.Structure):
         return d
 
 
+class Tuning(C.Structure):
+    _fields_ = [
+        ("search_margin", C.c_double), ("nbr_slots", C.c_int), ("grad_min_ctas", C.c_int),
+        ("flux_min_ctas", C.c_int), ("front_ms", (C.c_float * 3) * 4), ("grad_ms", C.c_float * 3),
+        ("flux_ms", C.c_float * 3),
+    ]
+
+    def as_dict(self):
+        return {"search_margin": self.search_margin, "nbr_slots": self.nbr_slots,
+                "grad_min_ctas": self.grad_min_ctas, "flux_min_ctas": self.flux_min_ctas,
+                "front_ms": [[self.front_ms[i][j] for j in range(3)] for i in range(4)],
+                "grad_ms": list(self.grad_ms), "flux_ms": list(self.flux_ms)}
+
+
 EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_config",
            "hydro_set_boxes", "hydro_reserve", "hydro_build_neighbours", "hydro_density",
            "hydro_gradients", "hydro_fluxes", "hydro_step", "hydro_sync_status",
            "hydro_get_stats", "hydro_mlp_load", "hydro_mlp_get", "hydro_mlp_predict",
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
-           "hydro_strerror"]
+           "hydro_strerror", "hydro_autotune", "hydro_set_tuning"]
 
 
 def _load():
@@ -126,6 +140,8 @@ def _load():
         L.hydro_record_faces.argtypes = [vp, vp, i64, C.c_double, C.c_int]
         L.hydro_recorded_faces.argtypes = [vp, P(i64), vp]
         L.hydro_totals_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
+        L.hydro_autotune.argtypes = [vp, P(Particles), P(Tuning), vp]
+        L.hydro_set_tuning.argtypes = [vp, P(Tuning)]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
@@ -315,6 +331,26 @@ class Hydro:
         if rc and check:
             raise HydroError(rc, "hydro_step")
         return s.as_dict() if stats else rc
+
+    def autotune(self, st, stream=None):
+        """Time the launch-parameter candidates on the state st and keep the
+        fastest (hydro_autotune); returns the choices and times."""
+        p = particles_struct(st)
+        t = Tuning()
+        rc = self.lib.hydro_autotune(self.h, C.byref(p), C.byref(t), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_autotune")
+        return t.as_dict()
+
+    def set_tuning(self, d):
+        t = Tuning()
+        t.search_margin = d["search_margin"]
+        t.nbr_slots = d["nbr_slots"]
+        t.grad_min_ctas = d["grad_min_ctas"]
+        t.flux_min_ctas = d["flux_min_ctas"]
+        rc = self.lib.hydro_set_tuning(self.h, C.byref(t))
+        if rc:
+            raise HydroError(rc, "hydro_set_tuning")
 
     def sync_status(self, stream=None):
         return self.lib.hydro_sync_status(self.h, _stream(stream))

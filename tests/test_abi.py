@@ -46,8 +46,8 @@ def test_struct_sizes_match_header(lib):
 #include <stdio.h>
 #include "hydro.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(hydro_config), sizeof(hydro_particles),
-         sizeof(hydro_nbrlist), sizeof(hydro_stats));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(hydro_config), sizeof(hydro_particles),
+         sizeof(hydro_nbrlist), sizeof(hydro_stats), sizeof(hydro_tuning));
   return 0;
 }
 '''
@@ -59,7 +59,8 @@ int main(void) {
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     sizes = list(map(int, out))
     assert sizes == [ctypes.sizeof(hydro.Config), ctypes.sizeof(hydro.Particles),
-                     ctypes.sizeof(hydro.NbrList), ctypes.sizeof(hydro.Stats)]
+                     ctypes.sizeof(hydro.NbrList), ctypes.sizeof(hydro.Stats),
+                     ctypes.sizeof(hydro.Tuning)]
 
 
 def test_defaults_and_strerror(lib):
