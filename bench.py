@@ -524,7 +524,8 @@ def main():
                                active_steps=r["active"], hard_faces_per_step=hard,
                                learned_faces_per_step=r["learned"] / args.steps,
                                fallbacks_per_step=r["fallbacks"] / args.steps,
-                               hard_kernel_ms=r["hard_ms"] / args.steps)
+                               hard_kernel_ms=r["hard_ms"] / args.steps,
+                               probe_ms_plain_learned=last["learned_probe_ms"])
         line["learned"].pop("theta")
     if rank == 0:
         print(json.dumps(line), flush=True)

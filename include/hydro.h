@@ -76,11 +76,13 @@ typedef struct {
                             faces (mixed precision; needs a network from
                             hydro_mlp_load / hydro_mlp_train, else the flux
                             calls return HYDRO_ESTATE; FP64 and HLLC ignore it):
-                            0 off; 2 on in every flux call; 1 adaptive: on,
-                            but when at most 10% of the hard faces of a call
-                            started from the network, the next 15 flux calls
-                            (hydro_fluxes or hydro_step) use the plain guess
-                            (no deferral cost) before trying again */
+                            0 off; 2 on in every flux call; 1 adaptive: one
+                            flux call (hydro_fluxes or hydro_step) with the
+                            learned path, one with the plain guess, both timed
+                            with CUDA events, then 15 calls with the learned
+                            path if more than 10% of its hard faces started
+                            from the network and it was the faster, else with
+                            the plain guess; then the two probes again */
     int limiter;         /* 1: conditioned BJ + pairwise limiters (§2.3.6) */
     int time_extrap;     /* 1: half-step predictor of the face states (Eq. 16) */
     double ncond_crit;   /* N_cond threshold (100) */
@@ -155,6 +157,8 @@ typedef struct {
                                  graph step needed a larger buffer, the host-driven
                                  step redid it and grew the buffer; 3: a capture
                                  failed, this context runs host-driven from now on */
+    float learned_probe_ms[2];/* learned_guess = 1: flux-stage times of the last plain
+                                 and learned probe calls (CUDA events; 0 before) */
 } hydro_stats;
 
 /* Defaults described above.  Always succeeds. */

@@ -234,6 +234,8 @@ void fill_stats(hydro_ctx *c, double dt, bool timing) {
     S.learned_faces = (int64_t)H.learned_faces;
     S.hard_faces = (int64_t)H.hard_faces;
     S.learned_active = c->learned_active ? 1 : 0;
+    S.learned_probe_ms[0] = c->learn_t[0];
+    S.learned_probe_ms[1] = c->learn_t[1];
     S.vacuum_faces = (int64_t)H.vacuum;
     S.first_order_faces = (int64_t)H.first_order;
     for (int w = 0; w < 2; w++) {
@@ -487,8 +489,20 @@ int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const 
     return HYDRO_OK;
 }
 
+static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
+                     hydro_stream stream);
+
 int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream) {
+    if (stats) memset(stats, 0, sizeof(*stats));
+    const int rc = step_impl(c, p, dt, stats, stream);
+    // a step that stopped early reports its error in the statistics too
+    if (stats && rc != HYDRO_OK && stats->status == HYDRO_OK) stats->status = rc;
+    return rc;
+}
+
+static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
+                     hydro_stream stream) {
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
@@ -520,8 +534,9 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
         rc = density_all(c, p, !first, rebuilds, st);
         if (rc) return rc;
         if (first && timing) API_CUDA(record_event(c->ev[2], st));
-        API_CUDA(run_primitives(c, st));
-        // a guard round recomputes only the gradients its re-solved densities change
+        // a guard round recomputes the primitives of its re-solved particles
+        // and only the gradients their new densities change
+        API_CUDA(run_primitives(c, st, !first));
         API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
         API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
@@ -835,6 +850,7 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
     if (c->cfg.precision == HYDRO_MIXED) {
         const double *dt_dev = reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
         best = 1e30f;
+        read_learn_probe(c);   // (the trials below reuse the probe events)
         c->learned_decision = 0;
         for (int k = 0; k < 3; k++) {
             c->flux_minb = fminb[k];

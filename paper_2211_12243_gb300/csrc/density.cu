@@ -52,6 +52,17 @@ struct DensArgs {
     DevCounters *cnt;
 };
 
+// Growth of the search radius hs after a failed solve.  First failure
+// (hs within 1.3 of the particle's h guess): the weighted count at the
+// radius, kf = N_enc(hs), grows about as hs^3 in a locally uniform
+// distribution, so the root lies near hs (N / kf)^(1/3): take 10% beyond
+// that, at least 5% and at most a doubling.  A radius grown before: double.
+__device__ __forceinline__ double search_growth(double N, double kf, double hs, double h) {
+    if (!(hs <= 1.3 * h)) return 2.0;
+    double g = kf > 0.0 ? 1.1 * cbrt(N / kf) : 2.0;
+    return fmin(fmax(g, 1.05), 2.0);
+}
+
 // ---------------------------------------------------------------- FP64 path
 __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -69,6 +80,7 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
     if (!(h > 0.0) || h > hsi) h = hsi;
     double lo = 0.0, hi = -1.0;
     bool conv = false, fail = false;
+    double kf_fail = 0.0;   // N_enc(hsi) = Kn sum f at a failure
     auto sep = [&](int j) {
         double dx = fold64(a.xs[j] - xi, bx.L[0]);
         double dy = fold64(a.ys[j] - yi, bx.L[1]);
@@ -96,7 +108,7 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
         double dg = Kn * mq * ih;
         if (g == 0.0) { conv = true; break; }
         if (g < 0.0) {
-            if (h >= hsi) { fail = true; break; }
+            if (h >= hsi) { fail = true; kf_fail = Kn * f; break; }
             lo = fmax(lo, h);
         } else {
             hi = (hi < 0.0 || h < hi) ? h : hi;
@@ -112,6 +124,7 @@ __global__ void k_density_f64(DensArgs a, double *__restrict__ rec) {
         h = hn;
     }
     if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
+        a.hs[s] = hsi * search_growth(N, kf_fail, hsi, a.h[s]);
         a.active[s] = (a.active[s] & ACT_GUARD) | 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
@@ -230,6 +243,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     float lo = 0.f, hi = -1.f;
     bool conv = false, fail = false;
     float comp = -1.f;   // radius the compacted list is complete for (none yet)
+    float kf_fail = 0.f;  // N_enc(hsi) = Kn sum f at a failure
     const float ftol = 2e-6f;
     // The float separation from the fixed-point positions is within
     // 4e-7 r + 4e-10 L of the exact one, so keeping the entries with float
@@ -266,7 +280,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         float dg = Kn * mq * ih;
         if (g == 0.f) { conv = true; break; }
         if (g < 0.f) {
-            if (h >= hsi) { fail = true; break; }
+            if (h >= hsi) { fail = true; kf_fail = Kn * f; break; }
             lo = fmaxf(lo, h);
         } else {
             hi = (hi < 0.f || h < hi) ? h : hi;
@@ -282,6 +296,7 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         h = hn;
     }
     if (fail) {   // (no compaction happened: failing needs h >= hsi, below any bracket)
+        a.hs[s] = hsi_d * search_growth((double)N, (double)kf_fail, hsi_d, a.h[s]);
         a.active[s] = (a.active[s] & ACT_GUARD) | 3;
         atomicAdd(&a.cnt->search_fail, 1);
         set_flag(a.cnt, ST_SEARCH);
@@ -369,8 +384,9 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     rr[R_OM] = (float)om;
 }
 
-// widen the search radius of particles whose root lay beyond it; the
-// radius never exceeds half the shortest box side (one periodic image)
+// the search radius of particles whose root lay beyond it, as the density
+// kernel grew it (not below margin h); never beyond half the shortest box
+// side (one periodic image)
 __global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *__restrict__ hs,
                               const double *__restrict__ h, double margin,
                               const int32_t *__restrict__ pbox, const Box *__restrict__ boxes) {
@@ -380,7 +396,7 @@ __global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *_
     if (a & 2) {
         const Box bx = boxes[pbox[s]];
         double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-        hs[s] = fmin(fmax(hs[s] * 2.0, h[s] * margin), half);
+        hs[s] = fmin(fmax(hs[s], h[s] * margin), half);   // (grown by the density kernel)
         active[s] = (a & ACT_GUARD) | 1;
     } else {
         active[s] = a & ACT_GUARD;
@@ -430,12 +446,16 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_fail, 0, sizeof(int), st));
     if (c->cfg.precision == HYDRO_MIXED) {
         // 64-bit fixed-point copies for the refinement step (xs.. are sorted)
+        // (positions are fixed within a step: the solves of selected
+        // particles reuse the copies of the step's first, full solve)
         HYD_CUDA(c->d_q64.ensure((size_t)3 * n));
         uint64_t *q64 = c->d_q64.get();
-        k_fixed64<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
-                                                     c->d_pbox.get(), c->d_boxes.get(), q64,
-                                                     q64 + n, q64 + 2 * n);
-        HYD_CUDA(launch_check());
+        if (!only_active) {
+            k_fixed64<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_xs.get(), c->d_ys.get(),
+                                                         c->d_zs.get(), c->d_pbox.get(),
+                                                         c->d_boxes.get(), q64, q64 + n, q64 + 2 * n);
+            HYD_CUDA(launch_check());
+        }
         k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(a, q64, q64 + n,
                                                                          q64 + 2 * n,
                                                                          c->d_recf.get());

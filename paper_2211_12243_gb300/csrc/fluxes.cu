@@ -76,23 +76,52 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
+void read_learn_probe(hydro_ctx *c) {
+    if (!c->learn_probe) return;
+    const bool lp = c->learn_probe == 1;
+    float ms = 0.f;
+    if (cudaEventSynchronize(c->ev[lp ? 8 : 7]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, c->ev[6], c->ev[lp ? 8 : 7]) == cudaSuccess && ms > 0.f) {
+        c->learn_t[lp ? 1 : 0] = ms;
+    } else {
+        (void)cudaGetLastError();
+        c->learn_t[lp ? 1 : 0] = lp ? 1e30f : 0.f;   // unknown: prefer the plain path
+    }
+    if (lp) {
+        c->learn_used = false;
+        if (cudaEventSynchronize(c->ev[9]) == cudaSuccess)
+            c->learn_used = c->h_learn[0] * 10 > c->h_learn[1];
+    }
+    c->learn_probe = 0;
+}
+
 bool decide_learned(hydro_ctx *c) {
     const bool want = c->cfg.precision == HYDRO_MIXED && c->cfg.riemann == HYDRO_RIEMANN_EXACT &&
                       c->cfg.learned_guess && c->have_mlp;
     if (!want) return false;
-    // adaptive mode: after a learned call in which under 10% of the hard
-    // faces started from the network, the next 15 calls skip the deferral
-    // (its cost buys nothing there) before probing again
-    if (c->learn_probe_pending) {
-        if (cudaEventSynchronize(c->ev[9]) == cudaSuccess) {
-            const unsigned long long used = c->h_learn[0], hard = c->h_learn[1];
-            if (c->cfg.learned_guess == 1 && used * 10 <= hard) c->learn_skip = 15;
-        }
-        c->learn_probe_pending = false;
+    if (c->cfg.learned_guess == 2) return true;
+    // adaptive: the previous call was a probe -> collect its time (and, for
+    // the learned probe, how many hard faces started from the network)
+    read_learn_probe(c);
+    if (c->learn_phase == 0) {
+        c->learn_phase = 1;
+        c->learn_probe = 1;
+        return true;
     }
-    if (c->cfg.learned_guess == 2 || c->learn_skip == 0) return true;
-    c->learn_skip--;
-    return false;
+    if (c->learn_phase == 1) {
+        c->learn_phase = 2;
+        c->learn_probe = 2;
+        c->learn_skip = 0;
+        return false;
+    }
+    if (c->learn_skip == 0) {
+        // the network must start more than 10% of the hard faces and the
+        // learned path must be the faster of the two probes
+        c->learn_winner = c->learn_used && c->learn_t[1] < c->learn_t[0];
+        c->learn_skip = 15;
+    }
+    if (--c->learn_skip == 0) c->learn_phase = 0;
+    return c->learn_winner;
 }
 
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st) {
@@ -174,7 +203,10 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.nbucket = c->plan.nbucket;
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
-    cudaEvent_t *ev = c->timing ? c->ev + 6 : nullptr;
+    // the adaptive learned path times its probes with the same events
+    const bool adapt = c->cfg.learned_guess == 1 && c->cfg.precision == HYDRO_MIXED &&
+                       c->cfg.riemann == HYDRO_RIEMANN_EXACT && c->have_mlp;
+    cudaEvent_t *ev = (c->timing || adapt) ? c->ev + 6 : nullptr;
     if (learned) {
         for (int attempt = 0;; attempt++) {
             HYD_CUDA(cudaMemsetAsync(a.hard_cursor, 0, HARD_SUB * sizeof(unsigned long long), st));
@@ -198,7 +230,6 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
         HYD_CUDA(cudaMemcpyAsync(c->h_learn, &c->d_cnt->learned_faces, 2 * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, st));
         HYD_CUDA(record_event(c->ev[9], st));
-        c->learn_probe_pending = true;
         return cudaSuccess;
     }
     if (c->cfg.precision == HYDRO_MIXED)

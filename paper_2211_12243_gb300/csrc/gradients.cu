@@ -265,29 +265,15 @@ __global__ void __launch_bounds__(256) k_grad_reduce(int64_t n, const double *__
     }
 }
 
-// particles whose gradients change when the guard re-solved some densities:
-// the re-solved ones and every particle with one of them in its list
-__global__ void k_mark_redo(int64_t n, const int64_t *__restrict__ nbr_off,
-                            const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
-                            uint8_t *__restrict__ active) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const uint8_t me = active[s];
-    bool redo = (me & ACT_GUARD) != 0;
-    const int64_t o = nbr_off[s];
-    const int c = nbr_cnt[s];
-    for (int k = 0; k < c && !redo; k++) redo = (active[nbr_idx[o + k]] & ACT_GUARD) != 0;
-    // only this thread writes its byte, and ACT_GUARD (read by the others) is kept
-    if (redo) active[s] = me | ACT_REDO;
-}
-
 // primitives from the sorted conserved state and omega (§2.3.2, Eq. 23)
 template <typename R>
 __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
                              const double *__restrict__ om, const double *__restrict__ h,
-                             double gm1, double alpha1, R *__restrict__ rec) {
+                             double gm1, double alpha1, const uint8_t *__restrict__ active,
+                             bool only_guard, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
+    if (only_guard && !(active[s] & ACT_GUARD)) return;
     double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
     double E = Q[4 * n + s], U = Q[5 * n + s];
     double w = om[s];
@@ -323,13 +309,14 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
 // N_NGB *= grow for particles that failed the N_cond check; they (only)
 // get their density solved again
 __global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__restrict__ nngb,
-                             double grow) {
+                             double grow, int32_t *__restrict__ guard_idx, int *__restrict__ nguard) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint8_t a = active[s];
     if (a & ACT_NCOND) {
         nngb[s] *= grow;
         active[s] = ACT_SOLVE | ACT_GUARD;
+        guard_idx[atomicAdd(nguard, 1)] = (int32_t)s;
     } else {
         active[s] = 0;
     }
@@ -353,17 +340,20 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-cudaError_t run_primitives(hydro_ctx *c, stream_t st) {
+cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
     const int64_t n = c->plan.n;
     double gm1 = c->cfg.gamma - 1.0;
+    const uint8_t *act = c->d_active.get();
     if (c->cfg.precision == HYDRO_MIXED)
         k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                               c->d_hsorted.get(), gm1,
-                                                              c->cfg.alpha1, c->d_recf.get());
+                                                              c->cfg.alpha1, act, only_guard,
+                                                              c->d_recf.get());
     else
         k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
-                                                               c->cfg.alpha1, c->d_recd.get());
+                                                               c->cfg.alpha1, act, only_guard,
+                                                               c->d_recd.get());
     return launch_check();
 }
 
@@ -394,10 +384,7 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.dt_part = c->d_vsig_dt.get();
     a.npair = c->d_gpairs.get();
     a.cnt = c->d_cnt;
-    if (only_redo) {
-        k_mark_redo<<<grid_for(n, 256), 256, 0, st>>>(n, a.nbr_off, a.nbr_cnt, a.nbr_idx, a.active);
-        HYD_CUDA(launch_check());
-    }
+    if (only_redo) HYD_CUDA(mark_reverse(c, st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
     HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
@@ -420,8 +407,11 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
 
 cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_guard_idx.ensure(n));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nguard, 0, sizeof(int), st));
     k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_nngb.get(),
-                                                   c->cfg.ngb_grow);
+                                                   c->cfg.ngb_grow, c->d_guard_idx.get(),
+                                                   &c->d_cnt->nguard);
     return launch_check();
 }
 

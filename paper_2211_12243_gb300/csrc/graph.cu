@@ -131,7 +131,7 @@ cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
     HYD_CUDA(guard_grow(c, s));
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(search_loop(c, 2, s));
-    HYD_CUDA(run_primitives(c, s));
+    HYD_CUDA(run_primitives(c, s, true));
     HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, true, s));
     HYD_CUDA(cond_guard(c, s, h));
     g_cap_guard = launch_count() - k0 - g_cap_search;   // its re-search body runs per round
@@ -267,7 +267,6 @@ int graph_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats, 
         if (slot.exec) cudaGraphExecDestroy(slot.exec);
         slot.exec = nullptr;
         slot.key.clear();
-        const bool probe = c->learn_probe_pending;
         c->learned_decision = learned ? 1 : 0;
         c->capturing = true;
         cudaGraph_t g = nullptr;
@@ -288,7 +287,6 @@ int graph_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats, 
         slot.k_top = captured - 2 * g_cap_search - g_cap_guard;
         c->capturing = false;
         c->learned_decision = -1;
-        c->learn_probe_pending = probe;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&slot.exec, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -302,7 +300,6 @@ int graph_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats, 
     cudaError_t e = cudaGraphLaunch(slot.exec, st);
     if (e != cudaSuccess) return HYDRO_ECUDA;
     c->learned_active = learned;
-    if (learned) c->learn_probe_pending = true;
     e = cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return HYDRO_ECUDA;

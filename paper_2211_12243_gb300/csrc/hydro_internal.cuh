@@ -91,6 +91,7 @@ struct DevCounters {
     int rebuilds;                     // re-search rounds in the step
     int abort;                        // the step cannot finish on the device: no update
     int ovf_first;                    // buckets of the first list pass with long lists
+    int nguard;                       // particles whose N_NGB grew in this guard round
 };
 
 // bucket tree topology (host plan, mirrored on the device)
@@ -171,6 +172,7 @@ struct hydro_ctx {
     hyd::DevBuf<uint8_t> d_active;    // density / guard flags
     hyd::DevBuf<double> d_vsig_dt;    // per-particle CFL dt
     hyd::DevBuf<int32_t> d_gpairs;    // per-particle gradient pairs
+    hyd::DevBuf<int32_t> d_guard_idx; // the guard round's grown particles (nguard of them)
 
     // neighbour lists
     hyd::DevBuf<int32_t> d_nbr_idx;
@@ -194,11 +196,16 @@ struct hydro_ctx {
     hyd::DevBuf<float> d_hard;
     hyd::DevBuf<int32_t> d_hard_idx;
     hyd::DevBuf<unsigned long long> d_hard_cursor;
-    // adaptive learned path: plain-guess steps left before the next probe,
-    // and whether the last flux call ran the learned path (its counts then
-    // sit in h_learn[0..1] = hard, learned once the stream passes them)
-    int learn_skip = 0;
-    bool learn_probe_pending = false;
+    // adaptive learned path (learned_guess = 1): a learned probe call, a
+    // plain probe call, then the faster of the two for 15 calls.  The probe
+    // times come from events 6-8 around the flux kernels, the learned probe's
+    // counts from h_learn[0..1] (learned, hard faces; event 9)
+    int learn_phase = 0;              // 0: probe learned next; 1: probe plain next; 2: run the winner
+    int learn_skip = 0;               // winner calls left
+    bool learn_winner = false;        // the learned path won the last comparison
+    int learn_probe = 0;              // the last call was a probe: 1 learned, 2 plain
+    float learn_t[2] = {0.f, 0.f};    // flux-stage time of the last probes: plain, learned
+    bool learn_used = false;          // > 10% of the learned probe's hard faces used the network
     bool learned_active = false;
     unsigned long long *h_learn = nullptr;   // pinned
     int64_t hard_cap = 0;
@@ -284,6 +291,9 @@ cudaError_t build_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
 cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
 cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st);
+// ACT_REDO on the guard round's particles and on every particle i with one
+// of them in its list (r_ia < h_i), found by walks of the bucket tree
+cudaError_t mark_reverse(hydro_ctx *c, stream_t st);
 // the same two passes with the bucket count read on the device (no host
 // wait): the queued overflow buckets, and the re-search rebuild
 cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);
@@ -296,7 +306,8 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
 cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
 
 // gradients.cu
-cudaError_t run_primitives(hydro_ctx *c, stream_t st);
+// only_guard: the particles of the current guard round (their omega changed)
+cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard = false);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
@@ -309,6 +320,9 @@ cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st);
 // the adaptive learned-path choice for the next flux call (host state)
 bool decide_learned(hydro_ctx *c);
+// collect the time of a pending probe call before other flux calls reuse
+// its events (waits for the probe's events)
+void read_learn_probe(hydro_ctx *c);
 
 // api.cu: shared by the host-driven and the graph step
 int flags_to_status(int flags);

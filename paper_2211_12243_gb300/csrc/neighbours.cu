@@ -493,9 +493,96 @@ __global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ firs
     if (__any_sync(0xffffffffu, act) && lane == 0) queue[atomicAdd(nqueue, 1)] = (int32_t)b;
 }
 
+// The particles that hold a guard particle a in their list, i.e. r_ia < h_i
+// (the list's own radius: the reverse of a's list), by one walk of the
+// bucket tree per guard particle and warp.  The lanes test the children of
+// a node at once: a child is entered when the lower bound of its periodic
+// distance from a is within the largest search radius of its particles
+// (hs >= h); the particles of an entered bucket are tested exactly, one per
+// lane (the double-precision membership of the lists).  Marks ACT_REDO on
+// them and on a itself.  Warps stride over the guard particles, whose count
+// is read on the device.
+constexpr int RSTACK = 320;   // 32-ary tree of at most MAX_LEVELS levels
+constexpr int RWARPS = 4;
+
+__global__ void __launch_bounds__(RWARPS * 32)
+k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ nguard,
+               const int32_t *__restrict__ node_first, const int32_t *__restrict__ node_cnt,
+               const int32_t *__restrict__ box_root, int64_t nbucket,
+               const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
+               const uint32_t *__restrict__ qx, const uint32_t *__restrict__ qy,
+               const uint32_t *__restrict__ qz, const double *__restrict__ xs,
+               const double *__restrict__ ys, const double *__restrict__ zs,
+               const double *__restrict__ h, const int32_t *__restrict__ pbox,
+               const Box *__restrict__ boxes, uint8_t *__restrict__ active, DevCounters *cnt) {
+    __shared__ int stack_all[RWARPS][RSTACK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *stack = stack_all[warp];
+    const int ng = *nguard;
+    const int nwarps = gridDim.x * RWARPS;
+    for (int g = blockIdx.x * RWARPS + warp; g < ng; g += nwarps) {
+        const int a = guard_idx[g];
+        const Box bx = boxes[pbox[a]];
+        const uint32_t pax = qx[a], pay = qy[a], paz = qz[a];
+        const double xa = xs[a], ya = ys[a], za = zs[a];
+        if (lane == 0) {
+            active[a] |= ACT_REDO;
+            stack[0] = box_root[pbox[a]];
+        }
+        int sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            const int node = stack[--sp];
+            __syncwarp();
+            const int f = node_first[node], c = node_cnt[node];
+            if (node < nbucket) {
+                // a bucket: lane k tests its particle f + k
+                const int i = f + lane;
+                if (lane < c && i != a) {
+                    const double ex = fold64(__dsub_rn(xa, xs[i]), bx.L[0]);
+                    const double ey = fold64(__dsub_rn(ya, ys[i]), bx.L[1]);
+                    const double ez = fold64(__dsub_rn(za, zs[i]), bx.L[2]);
+                    const double hi_ = h[i];
+                    if (r2_exact(ex, ey, ez) < __dmul_rn(hi_, hi_)) active[i] |= ACT_REDO;
+                }
+                continue;
+            }
+            bool hit = false;
+            if (lane < c) {
+                const uint4 l = lo[f + lane], u = hi[f + lane];
+                const float rmax = __uint_as_float(l.w) * 1.0001f;
+                const float gx = u2f(point_gap(pax, l.x, u.x)) * bx.s[0];
+                const float gy = u2f(point_gap(pay, l.y, u.y)) * bx.s[1];
+                const float gz = u2f(point_gap(paz, l.z, u.z)) * bx.s[2];
+                hit = gx * gx + gy * gy + gz * gz <= rmax * rmax;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            const int np = __popc(m);
+            if (sp + np > RSTACK) {   // (cannot happen for trees of MAX_LEVELS levels)
+                if (lane == 0) set_flag(cnt, ST_STACK);
+                break;
+            }
+            if (hit) stack[sp + __popc(m & ((1u << lane) - 1u))] = f + lane;
+            sp += np;
+            __syncwarp();
+        }
+        __syncwarp();
+    }
+}
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t mark_reverse(hydro_ctx *c, stream_t st) {
+    const Plan &P = c->plan;
+    k_mark_reverse<<<152 * 4, RWARPS * 32, 0, st>>>(
+        c->d_guard_idx.get(), &c->d_cnt->nguard, c->d_node_first.get(), c->d_node_cnt.get(),
+        c->d_box_root.get(), P.nbucket, c->d_node_aabb.get(), c->d_node_aabb_hi.get(),
+        c->d_qx.get(), c->d_qy.get(), c->d_qz.get(), c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
+        c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(), c->d_active.get(), c->d_cnt);
+    return launch_check();
+}
 
 cudaError_t build_tree(hydro_ctx *c, stream_t st) {
     const Plan &P = c->plan;

@@ -70,7 +70,7 @@ class Stats(C.Structure):
         ("energy", C.c_double * 2), ("ms_sort", C.c_float), ("ms_neighbours", C.c_float),
         ("ms_density", C.c_float), ("ms_gradients", C.c_float), ("ms_fluxes", C.c_float),
         ("ms_update", C.c_float), ("ms_flux_kernel", C.c_float), ("ms_hard_faces", C.c_float),
-        ("graph", C.c_int),
+        ("graph", C.c_int), ("learned_probe_ms", C.c_float * 2),
     ]
 
     def as_dict(self):
@@ -79,7 +79,7 @@ class Stats(C.Structure):
             v = getattr(self, k)
             if k == "mom":
                 v = [[v[w][a] for a in range(3)] for w in range(2)]
-            elif k in ("mass", "energy"):
+            elif k in ("mass", "energy", "learned_probe_ms"):
                 v = [v[0], v[1]]
             d[k] = v
         return d

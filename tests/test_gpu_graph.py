@@ -121,10 +121,15 @@ def test_graph_step_matches_oracle(orc, hyd, precision, tol):
     st = hyd.to_device(w)
     init = {k: v.clone() for k, v in st.items()}
     H.step(st, -1.0, check=False)          # host-driven first step
-    for k, v in init.items():
-        st[k].copy_(v)
-    stats = H.step(st, -1.0, check=False)  # graph step
-    torch.cuda.synchronize()
+    for attempt in range(3):
+        # graph steps from the same state; the first may hand over to the
+        # host path once to grow the overflow region of the lists (graph 2)
+        for k, v in init.items():
+            st[k].copy_(v)
+        stats = H.step(st, -1.0, check=False)
+        torch.cuda.synchronize()
+        if stats["graph"] == 1:
+            break
     assert stats["graph"] == 1
     assert stats["list_rebuilds"] > 0
     sg = {k: v.cpu().numpy() for k, v in st.items()}

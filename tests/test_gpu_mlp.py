@@ -343,21 +343,22 @@ def test_learned_flux_matches_oracle(orc, hyd, trained, name):
 
 
 def test_adaptive_learned_path_pauses_when_unused(hyd):
-    """learned_guess = 1: a network whose corrections all fall below 1e-3
-    starts no face, so after one learned step the next 15 run the plain
-    guess, then the path is tried again; learned_guess = 2 never pauses."""
+    """learned_guess = 1: a learned probe call, a plain probe call, then 15
+    calls with the winner, then the probes again.  A network whose
+    corrections all fall below 1e-3 starts no face, so the plain guess wins
+    whatever the times; learned_guess = 2 never pauses."""
     p = mlp.unpack(mlp.init(1))
     p["w3"][:] = 0.0                     # y = t_mean + t_scale b3 = 0
     p["xmin"], p["xmax"] = np.full(mlp.NF, -1e30), np.full(mlp.NF, 1e30)
     theta = mlp.pack(p).astype(np.float32)
     w = W.sod(12)
-    for mode, want in ((1, [1] + [0] * 15 + [1]), (2, [1] * 17)):
+    for mode, want in ((1, [1, 0] + [0] * 15 + [1, 0]), (2, [1] * 19)):
         H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision="mixed", learned_guess=mode))
         H.mlp_load(theta)
         H.set_boxes(*hyd.single_box(w))
         st = hyd.to_device(w)
         seen = []
-        for _ in range(17):
+        for _ in range(19):
             s = H.step(st)
             seen.append(s["learned_active"])
             if s["learned_active"]:
