@@ -137,22 +137,30 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle baseline (test infrastructure, timed as it stands)
 # --------------------------------------------------------------------------
+def workload_name(kind, n):
+    if kind == "sedov":
+        return f"sedov3d_{n or 128}cubed_mfv_exact"
+    if kind == "lognormal":
+        return f"lognormal3d_{n or (1 << 24)}_mfv_exact"
+    if kind == "batch":
+        return f"batch_{n or 512}_boxes_4k_64k_mfv_exact"
+    if kind == "wave":
+        return f"wave3d_{n or 32}cubed_mfv_hllc"
+    return WORKLOAD if (n or 78) == 78 else f"sod3d_n{n}"
+
+
 def make_workload(kind, n):
     from paper_2211_12243_gb300 import workloads as W
+    name = workload_name(kind, n)
     if kind == "sedov":
-        n = n or 128
-        return W.sedov(n), f"sedov3d_{n}cubed_mfv_exact"
+        return W.sedov(n or 128), name
     if kind == "lognormal":
-        n = n or (1 << 24)
-        return W.lognormal(n), f"lognormal3d_{n}_mfv_exact"
+        return W.lognormal(n or (1 << 24)), name
     if kind == "batch":
-        n = n or 512
-        return W.batch(n), f"batch_{n}_boxes_4k_64k_mfv_exact"
+        return W.batch(n or 512), name
     if kind == "wave":
-        n = n or 32
-        return W.lattice_wave(n), f"wave3d_{n}cubed_mfv_hllc"
-    n = n or 78
-    return W.sod(n), (WORKLOAD if n == 78 else f"sod3d_n{n}")
+        return W.lattice_wave(n or 32), name
+    return W.sod(n or 78), name
 
 
 def oracle_sample_rate(kind, n, reps):
@@ -219,8 +227,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}_oracle_sample", "sample": rate["sample"],
-                   "l2": "inputs fit in host caches; CPU"},
+        "config": {"workload": workload_name(args.workload, args.n), "sample": rate["sample"],
+                   "l2": "CPU run (no device caches)"},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": rate["sample"]},
