@@ -571,19 +571,27 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
             }
         };
 
+        // software pipeline over the list: the index two entries ahead and
+        // the record of the next entry are in flight while an entry is tested
+        int jc = 0 < cnt ? a.nbr_idx[o] : 0;
+        int jn = 1 < cnt ? a.nbr_idx[o + 1] : 0;
+        R rc4[4] = {R(0), R(0), R(0), R(0)};
+        if (0 < cnt) load4<R>(rec + (int64_t)jc * REC, rc4);
         for (int k = 0; k < maxc; k++) {
+            R rn4[4] = {R(0), R(0), R(0), R(0)};
+            if (k + 1 < cnt) load4<R>(rec + (int64_t)jn * REC, rn4);
+            const int jnn = k + 2 < cnt ? a.nbr_idx[o + k + 2] : 0;
             bool has = false;
-            int j = 0;
-            if (k < cnt) {
-                j = a.nbr_idx[o + k];
-                if (j != s) {
-                    R rj4[4];
-                    load4<R>(rec + (int64_t)j * REC, rj4);
-                    R d[3], r2;
-                    rec_sep(own4, rj4, bx, d, r2);
-                    if (mem(r2, j)) has = (j > s) || !member_j(r2, rj4[R_H], a, s, j, bx);
-                }
+            const int j = jc;
+            if (k < cnt && j != s) {
+                R d[3], r2;
+                rec_sep(own4, rc4, bx, d, r2);
+                if (mem(r2, j)) has = (j > s) || !member_j(r2, rc4[R_H], a, s, j, bx);
             }
+            jc = jn;
+            jn = jnn;
+#pragma unroll
+            for (int q = 0; q < 4; q++) rc4[q] = rn4[q];
             unsigned m = __ballot_sync(0xffffffffu, has);
             if (has) {
                 int pos = qn + __popc(m & lt);

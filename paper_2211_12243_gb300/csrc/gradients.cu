@@ -91,11 +91,21 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
         R vs = R(0);
         const int64_t o = a.nbr_off[s];
         const int c = a.nbr_cnt[s];
+        // software pipeline: the index two entries ahead and the record of
+        // the next entry are in flight while an entry is summed
+        int jc = 0 < c ? a.nbr_idx[o] : 0;
+        int jn = 1 < c ? a.nbr_idx[o + 1] : 0;
+        R rn[10];
+        if (0 < c) load10<R>(rec + (int64_t)jc * REC, rn);
         for (int k = 0; k < c; k++) {
-            int j = a.nbr_idx[o + k];
-            if (j == s) continue;
+            const int j = jc;
             R rj[10];
-            load10<R>(rec + (int64_t)j * REC, rj);
+#pragma unroll
+            for (int q = 0; q < 10; q++) rj[q] = rn[q];
+            if (k + 1 < c) load10<R>(rec + (int64_t)jn * REC, rn);
+            jc = jn;
+            jn = k + 2 < c ? a.nbr_idx[o + k + 2] : 0;
+            if (j == s) continue;
             R d[3], r2;
             rec_sep(ri, rj, bx, d, r2);
             if (!mem(r2, j)) continue;
@@ -168,17 +178,27 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
         R alpha[5] = {R(1), R(1), R(1), R(1), R(1)};
         if (a.limiter) {
             R dp[5] = {0, 0, 0, 0, 0}, dm[5] = {0, 0, 0, 0, 0};
-            for (int k = 0; k < c; k++) {
-                int j = a.nbr_idx[o + k];
-                if (j == s) continue;
+            auto pos4 = [&](int j, R v[4]) {
                 const R *pj = rec + (int64_t)j * REC;
-                R rj[4];
                 if (sizeof(R) == 4) {
                     float4 t = *reinterpret_cast<const float4 *>(pj);
-                    rj[0] = t.x; rj[1] = t.y; rj[2] = t.z; rj[3] = t.w;
+                    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
                 } else {
-                    rj[0] = pj[0]; rj[1] = pj[1]; rj[2] = pj[2]; rj[3] = pj[3];
+                    v[0] = pj[0]; v[1] = pj[1]; v[2] = pj[2]; v[3] = pj[3];
                 }
+            };
+            // (same pipeline as pass 1)
+            int jc2 = 0 < c ? a.nbr_idx[o] : 0;
+            int jn2 = 1 < c ? a.nbr_idx[o + 1] : 0;
+            R rn4[4];
+            if (0 < c) pos4(jc2, rn4);
+            for (int k = 0; k < c; k++) {
+                const int j = jc2;
+                R rj[4] = {rn4[0], rn4[1], rn4[2], rn4[3]};
+                if (k + 1 < c) pos4(jn2, rn4);
+                jc2 = jn2;
+                jn2 = k + 2 < c ? a.nbr_idx[o + k + 2] : 0;
+                if (j == s) continue;
                 R d[3], r2;
                 rec_sep(ri, rj, bx, d, r2);
                 if (!mem(r2, j)) continue;
