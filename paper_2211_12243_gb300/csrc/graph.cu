@@ -39,8 +39,6 @@ namespace {
 
 constexpr int MAX_SEARCH_ROUNDS = 8;   // as the host-driven density solve
 
-// kernels enqueued while capturing one re-search body and one guard body
-long long g_cap_search = 0, g_cap_guard = 0;
 
 __global__ void k_cond_search(cudaGraphConditionalHandle h, DevCounters *c) {
     const bool fail = c->search_fail > 0;
@@ -109,7 +107,7 @@ cudaError_t search_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle
     HYD_CUDA(rebuild_active_lists_dev(c, s));
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(cond_search(c, s, h));
-    g_cap_search = launch_count() - k0;
+    c->cap_k_search = launch_count() - k0;
     return cudaSuccess;
 }
 
@@ -134,7 +132,7 @@ cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
     HYD_CUDA(run_primitives(c, s, true));
     HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, true, s));
     HYD_CUDA(cond_guard(c, s, h));
-    g_cap_guard = launch_count() - k0 - g_cap_search;   // its re-search body runs per round
+    c->cap_k_guard = launch_count() - k0 - c->cap_k_search;   // its re-search body runs per round
     return cudaSuccess;
 }
 
@@ -280,11 +278,11 @@ int graph_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats, 
         // nothing ran yet: count the kernels when the graph runs
         const long long captured = launch_count() - k0;
         add_launches(-captured);
-        slot.k_search = g_cap_search;
-        slot.k_guard = g_cap_guard;
+        slot.k_search = c->cap_k_search;
+        slot.k_guard = c->cap_k_guard;
         // captured: the top level, two re-search bodies (top level and inside
         // the guard body) and one guard body
-        slot.k_top = captured - 2 * g_cap_search - g_cap_guard;
+        slot.k_top = captured - 2 * c->cap_k_search - c->cap_k_guard;
         c->capturing = false;
         c->learned_decision = -1;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&slot.exec, g, 0);

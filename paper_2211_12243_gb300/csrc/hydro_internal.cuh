@@ -238,6 +238,7 @@ struct hydro_ctx {
         long long k_top = 0, k_search = 0, k_guard = 0;
     } graph_slot[2];
     cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};   // capture streams (top, bodies)
+    long long cap_k_search = 0, cap_k_guard = 0;   // kernels in one captured loop body
     int learned_decision = -1;        // >= 0: run_fluxes takes this choice (graph capture)
     bool capturing = false;           // enqueue without host synchronisation
     bool graph_off = false;           // a capture failed: host-driven steps only
