@@ -352,6 +352,20 @@ int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const 
                          const double *pz, const double *etot, double *totals,
                          hydro_stream stream);
 
+/* An external (gravitational) acceleration for the following hydro_step
+ * calls (§2.3.8): acc is a device array of 3 doubles per particle (ax, ay,
+ * az; caller order), read at every step and held by pointer until replaced
+ * (NULL: none; the caller keeps it alive).  The step, with a held fixed over
+ * it, adds to the state the fluxes updated the sources integrated by the
+ * trapezoidal rule of §2.3.4 between the start-of-step state U^n and that
+ * state U~: momentum dt/2 (m^n + m~) a; total energy dt/2 (P^n + P~).a plus
+ * the work on the exchanged mass, (1/2) a . sum_j dm_ij r_ij (dm_ij the mass
+ * i gains from j through their face, r_ij = x_i - x_j; zero for MFM).  The
+ * internal energy takes no source.  E_grav = m |a| h enters the
+ * total-energy pressure switch (§2.3.7).  The totals in hydro_stats then
+ * include the work of the external force.  Always HYDRO_OK for a context. */
+int hydro_set_gravity(hydro_ctx *ctx, const double *acc);
+
 /* Launch parameters of the step that hydro_autotune chooses by timing the
  * candidates on the caller's own particles (no counterpart in the paper:
  * a property of this GPU implementation).  Candidates:

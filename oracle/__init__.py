@@ -86,7 +86,7 @@ def lib():
         L.orc_density.restype = i32
         L.orc_density.argtypes = [P(Config), i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_primitives.restype = None
-        L.orc_primitives.argtypes = [P(Config), i64] + [vp] * 12
+        L.orc_primitives.argtypes = [P(Config), i64] + [vp] * 14
         L.orc_matrices.restype = None
         L.orc_matrices.argtypes = [P(Config), i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_gradients.restype = None
@@ -95,7 +95,7 @@ def lib():
         L.orc_flux_pairs.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp]
         L.orc_fluxes.restype = None
         L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 14 + [d, i64, vp, vp, vp,
-                                 P(FluxStats), vp, vp])
+                                 P(FluxStats), vp, vp, vp])
         L.orc_riemann_guess.restype = d
         L.orc_riemann_guess.argtypes = [d] * 7
         L.orc_riemann_star.restype = i32
@@ -107,7 +107,7 @@ def lib():
         L.orc_pair_limit.restype = d
         L.orc_pair_limit.argtypes = [d] * 5 + [i32]
         L.orc_step.restype = i32
-        L.orc_step.argtypes = ([P(Config), i64] + [vp] * 12 + [d] + [vp] * 5 + [P(StepInfo)])
+        L.orc_step.argtypes = ([P(Config), i64] + [vp] * 13 + [d] + [vp] * 5 + [P(StepInfo)])
         L.orc_num_threads.restype = i32
         L.orc_set_num_threads.argtypes = [i32]
         _lib = L
@@ -170,11 +170,16 @@ def density(cfg, x, y, z, L, h_guess, n_ngb=None, active=None):
     return h, om, it, st
 
 
-def primitives(cfg, m, px, py, pz, E, U, omega):
+def primitives(cfg, m, px, py, pz, E, U, omega, h=None, acc=None):
+    """rho, vx, vy, vz, p (§2.3.7); acc[n,3] (with h) enters the pressure
+    switch through E_grav = m |a| h."""
     arrs = list(map(_f64, (m, px, py, pz, E, U, omega)))
     n = arrs[0].size
     out = [np.zeros(n) for _ in range(5)]
-    lib().orc_primitives(C.byref(cfg), n, *[_p(a) for a in arrs], *[_p(o) for o in out])
+    hh = None if acc is None else _f64(h)
+    aa = None if acc is None else _f64(acc).reshape(n, 3)
+    lib().orc_primitives(C.byref(cfg), n, *[_p(a) for a in arrs], _p(hh), _p(aa),
+                         *[_p(o) for o in out])
     return tuple(out)  # rho, vx, vy, vz, p
 
 
@@ -215,9 +220,10 @@ def flux_pairs(x, y, z, L, h):
 
 
 def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
-           pair_guess=None, want_faces=False, want_abs=False):
+           pair_guess=None, want_faces=False, want_abs=False, want_dM=False):
     """dQ[n,6] = (dm, dpx, dpy, dpz, dE, dU) of Eqs. 16 and 24; (dQ, stats, faces)
-    or, with want_abs, (dQ, stats, faces, dQabs[n,5] = sum over faces of |c|)."""
+    or, with want_abs, (dQ, stats, faces, dQabs[n,5] = sum over faces of |c|);
+    with want_dM the last element is dM[n,3] = sum_j dm_ij r_ij (§2.3.8)."""
     x, y, z, L, h, omega, B6 = map(_f64, (x, y, z, L, h, omega, B6))
     grad, alpha = _f64(grad), _f64(alpha)
     rho, vx, vy, vz, p = map(_f64, prims)
@@ -231,12 +237,13 @@ def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
     faces = np.zeros((npairs, 9)) if want_faces else None
     pg = None if pair_guess is None else _f64(pair_guess)
     dQabs = np.zeros((n, 5)) if want_abs else None
+    dM = np.zeros((n, 3)) if want_dM else None
     lib().orc_fluxes(C.byref(cfg), n, _p(x), _p(y), _p(z), _p(L), _p(h), _p(omega), _p(B6),
                      _p(rho), _p(vx), _p(vy), _p(vz), _p(p), _p(grad), _p(alpha), float(dt),
-                     npairs, _p(pairs), _p(pg), _p(dQ), C.byref(st), _p(faces), _p(dQabs))
-    if want_abs:
-        return dQ, st.as_dict(), faces, dQabs
-    return dQ, st.as_dict(), faces
+                     npairs, _p(pairs), _p(pg), _p(dQ), C.byref(st), _p(faces), _p(dQabs),
+                     _p(dM))
+    out = (dQ, st.as_dict(), faces) + ((dQabs,) if want_abs else ()) + ((dM,) if want_dM else ())
+    return out
 
 
 def riemann_guess(rl, ul, pl, rr, ur, pr, g):
@@ -272,9 +279,10 @@ def pair_limit(e, a, b, psi1=0.5, psi2=0.25, positive=False):
     return lib().orc_pair_limit(e, a, b, psi1, psi2, int(bool(positive)))
 
 
-def step(cfg, state, dt=-1.0):
+def step(cfg, state, dt=-1.0, acc=None):
     """One full step on a copy of ``state`` (workload dict).  Returns
-    (new_state, outputs, info) where outputs has B6, grad, alpha, ncond, dQ."""
+    (new_state, outputs, info) where outputs has B6, grad, alpha, ncond, dQ.
+    acc[n,3]: an external acceleration held over the step (§2.3.8)."""
     s = {k: _f64(state[k]).copy() for k in ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")}
     L = _f64(state["L"])
     n = s["x"].size
@@ -284,7 +292,9 @@ def step(cfg, state, dt=-1.0):
     info = StepInfo()
     st = lib().orc_step(C.byref(cfg), n, _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(L), _p(s["m"]),
                         _p(s["px"]), _p(s["py"]), _p(s["pz"]), _p(s["E"]), _p(s["U"]),
-                        _p(s["h"]), _p(s["omega"]), float(dt), _p(out["B6"]), _p(out["grad"]),
+                        _p(s["h"]), _p(s["omega"]),
+                        _p(None if acc is None else _f64(acc).reshape(n, 3)), float(dt),
+                        _p(out["B6"]), _p(out["grad"]),
                         _p(out["alpha"]), _p(out["ncond"]), _p(out["dQ"]), C.byref(info))
     inf = dict(status=st, dt=info.dt, dt_next=info.dt_next, ngb_rounds=info.ngb_rounds,
                ncond_fail=info.ncond_fail, grad_pairs=info.grad_pairs, flux=info.flux.as_dict())

@@ -447,13 +447,15 @@ int orc_density(const orc_config *c, int64_t n, const double *x, const double *y
 /* ------------------------------------------------------------------------ */
 
 /* rho = m/omega (= m omega^-1, §2.3.2), v = P/m, and the pressure from the
- * total energy (Eq. 23) when U_i > alpha1 E_kin,i, else from the separately
- * integrated internal energy U_i (p = (gamma-1) U_i / omega_i).  The total
- * energy route also requires E - E_kin > 0. */
+ * total energy (Eq. 23) when U_i > alpha1 (E_grav,i + E_kin,i), else from
+ * the separately integrated internal energy U_i (p = (gamma-1) U_i / omega_i).
+ * E_kin = P.P / 2m; E_grav = m |a_grav| h (§2.3.7), zero without an
+ * acceleration (acc NULL; h may then be NULL too).  The total energy route
+ * also requires E - E_kin > 0.  acc: 3 per particle (ax, ay, az). */
 void orc_primitives(const orc_config *c, int64_t n, const double *m, const double *px,
                     const double *py, const double *pz, const double *E, const double *U,
-                    const double *omega, double *rho, double *vx, double *vy, double *vz,
-                    double *p)
+                    const double *omega, const double *h, const double *acc, double *rho,
+                    double *vx, double *vy, double *vz, double *p)
 {
     for (int64_t i = 0; i < n; i++) {
         rho[i] = m[i] / omega[i];
@@ -461,8 +463,13 @@ void orc_primitives(const orc_config *c, int64_t n, const double *m, const doubl
         vy[i] = py[i] / m[i];
         vz[i] = pz[i] / m[i];
         double ekin = (px[i] * px[i] + py[i] * py[i] + pz[i] * pz[i]) / (2.0 * m[i]);
+        double egrav = 0.0;
+        if (acc) {
+            const double *a = acc + 3 * i;
+            egrav = m[i] * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * h[i];
+        }
         double therm = U[i];
-        if (U[i] > c->alpha1 * ekin && E[i] - ekin > 0.0) therm = E[i] - ekin;
+        if (U[i] > c->alpha1 * (egrav + ekin) && E[i] - ekin > 0.0) therm = E[i] - ekin;
         p[i] = therm * (c->gamma - 1.0) / omega[i];
     }
 }
@@ -1106,7 +1113,7 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
                 const double *B6, const double *rho, const double *vx, const double *vy,
                 const double *vz, const double *p, const double *grad, const double *alpha,
                 double dt, int64_t npairs, const int64_t *pairs, const double *pair_guess,
-                double *dQ, orc_flux_stats *st, double *face_out, double *dQabs)
+                double *dQ, orc_flux_stats *st, double *face_out, double *dQabs, double *dM)
 {
     const double *Wp[5] = {rho, vx, vy, vz, p};
     double *cf = (double *)malloc((size_t)(npairs > 0 ? npairs : 1) * 5 * sizeof(double));
@@ -1161,6 +1168,24 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
         dQ[6 * i + 5] = dU;
     }
     free(acc);
+    /* the mass exchanged through the faces times the separation, for the
+     * gravitational work of §2.3.8: sum_j dm_ij r_ij with dm_ij the mass i
+     * gains from j and r_ij = x_i - x_j.  A face gives c_m from i to j, so
+     * both particles add c_m (x_j - x_i) (compensated sums) */
+    if (dM) {
+        orc_ksum *am = (orc_ksum *)calloc((size_t)n * 3, sizeof(orc_ksum));
+        for (int64_t k = 0; k < npairs; k++) {
+            int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+            double d[3];
+            orc_sep(x, y, z, L, i, j, d);
+            for (int q = 0; q < 3; q++) {
+                ks_add(&am[3 * i + q], cf[5 * k] * d[q]);
+                ks_add(&am[3 * j + q], cf[5 * k] * d[q]);
+            }
+        }
+        for (int64_t i = 0; i < 3 * n; i++) dM[i] = am[i].s + am[i].c;
+        free(am);
+    }
     /* scale of the per-particle flux error (sum over the particle's faces of
      * |c| per component), used to normalise comparisons of dQ whose net
      * value may cancel */
@@ -1195,13 +1220,20 @@ typedef struct {
  * min_i C_CFL h_i / v_sig,i (Eqs. 31-32).  Steps: density (Eq. 18), N_cond
  * guard (§2.3.5), primitives, gradients + limiter, fluxes (Eq. 16),
  * conserved update, internal energy (Eq. 24), drift with the mean of the
- * old and new velocity.  Optional outputs (NULL to skip): B6, grad, alpha,
- * ncond, dQ. */
+ * old and new velocity.  acc (3 per particle, may be NULL): an external
+ * (gravitational) acceleration held fixed over the step; its sources are
+ * added to the updated state by the trapezoidal rule of §2.3.4 between the
+ * start-of-step state and the state the fluxes updated: momentum
+ * dt/2 (m^n + m~) a, energy dt/2 (P^n + P~).a plus the work of the
+ * exchanged mass, (1/2) a . sum_j dm_ij r_ij (§2.3.8); it also enters the
+ * pressure switch through E_grav = m |a| h (§2.3.7).  The internal energy
+ * takes no gravitational source.  Optional outputs (NULL to skip): B6,
+ * grad, alpha, ncond, dQ (the hydrodynamic change only). */
 int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
              const double *L, double *m, double *px, double *py, double *pz, double *E,
-             double *U, double *h, double *omega, double dt, double *B6_out,
-             double *grad_out, double *alpha_out, double *ncond_out, double *dQ_out,
-             orc_step_info *info)
+             double *U, double *h, double *omega, const double *acc, double dt,
+             double *B6_out, double *grad_out, double *alpha_out, double *ncond_out,
+             double *dQ_out, orc_step_info *info)
 {
     int status = ORC_OK;
     double *nngb = (double *)malloc((size_t)n * sizeof(double));
@@ -1234,7 +1266,7 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
         rounds++;
     }
     if (fail && status == ORC_OK) status = ORC_ENCOND;
-    orc_primitives(c, n, m, px, py, pz, E, U, omega, rho, vx, vy, vz, p);
+    orc_primitives(c, n, m, px, py, pz, E, U, omega, h, acc, rho, vx, vy, vz, p);
     orc_gradients(c, n, x, y, z, L, h, omega, rho, vx, vy, vz, p, B6, nc, grad, alpha, vsig);
     double dtc = INFINITY;
     for (int64_t i = 0; i < n; i++) {
@@ -1253,8 +1285,9 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
         np = orc_flux_pairs(n, x, y, z, L, h, cap, pairs);
     }
     orc_flux_stats fst;
+    double *dM = acc ? (double *)malloc((size_t)n * 3 * sizeof(double)) : NULL;
     orc_fluxes(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, dt, np, pairs,
-               NULL, dQ, &fst, NULL, NULL);
+               NULL, dQ, &fst, NULL, NULL, dM);
     free(pairs);
     /* directed gradient pairs */
     if (info) {
@@ -1266,12 +1299,27 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     /* update */
     for (int64_t i = 0; i < n; i++) {
         double vox = vx[i], voy = vy[i], voz = vz[i];
+        const double m0 = m[i], p0[3] = {px[i], py[i], pz[i]};
         m[i] += dQ[6 * i + 0];
         px[i] += dQ[6 * i + 1];
         py[i] += dQ[6 * i + 2];
         pz[i] += dQ[6 * i + 3];
         E[i] += dQ[6 * i + 4];
         U[i] += dQ[6 * i + 5];
+        if (acc) {
+            const double *a = acc + 3 * i;
+            const double ph[3] = {px[i], py[i], pz[i]};   /* hydro-updated */
+            const double w = 0.5 * dt * (m0 + m[i]);
+            double eg = 0.0, ex = 0.0;
+            for (int q = 0; q < 3; q++) {
+                eg += (p0[q] + ph[q]) * a[q];
+                ex += a[q] * dM[3 * i + q];
+            }
+            px[i] += w * a[0];
+            py[i] += w * a[1];
+            pz[i] += w * a[2];
+            E[i] += 0.5 * dt * eg + 0.5 * ex;
+        }
         double nx = px[i] / m[i], ny = py[i] / m[i], nz = pz[i] / m[i];
         double xs[3] = {x[i] + dt * 0.5 * (vox + nx), y[i] + dt * 0.5 * (voy + ny),
                         z[i] + dt * 0.5 * (voz + nz)};
@@ -1285,6 +1333,7 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     if (grad_out) memcpy(grad_out, grad, (size_t)n * 15 * sizeof(double));
     if (alpha_out) memcpy(alpha_out, alpha, (size_t)n * 5 * sizeof(double));
     if (ncond_out) memcpy(ncond_out, nc, (size_t)n * sizeof(double));
+    free(dM);
     if (dQ_out) memcpy(dQ_out, dQ, (size_t)n * 6 * sizeof(double));
     if (info) {
         info->dt = dt;

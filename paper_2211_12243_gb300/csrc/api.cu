@@ -454,6 +454,7 @@ static int stage_state(hydro_ctx *c, const hydro_particles *p, cudaStream_t st) 
 
 int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *grad,
                     double *alpha, double *ncond, hydro_stream stream) {
+    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
     if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -475,6 +476,7 @@ int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *g
 
 int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const double *grad,
                  const double *alpha, double dt, double *dQ, hydro_stream stream) {
+    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
     if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
     if (!valid_particles(c, p, true) || !B || !grad || !alpha || !dQ || !(dt > 0.0))
@@ -526,6 +528,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     if (timing) API_CUDA(record_event(c->ev[0], st));
     int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
     if (rc) return rc;
+    API_CUDA(gather_gravity(c, st));
     if (timing) API_CUDA(record_event(c->ev[1], st));
     API_CUDA(reset_guard(c, st));
     int rebuilds = 0, rounds = 0, ncond_fail = 0;
@@ -766,6 +769,12 @@ int hydro_recorded_faces(hydro_ctx *c, int64_t *count, hydro_stream stream) {
     return HYDRO_OK;
 }
 
+int hydro_set_gravity(hydro_ctx *c, const double *acc) {
+    if (!c) return HYDRO_EINVAL;
+    c->grav = acc;
+    return HYDRO_OK;
+}
+
 int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (!c || !t) return HYDRO_EINVAL;
     if (!(t->search_margin >= 1.0) || t->nbr_slots < 32 || t->nbr_slots > 256) return HYDRO_EINVAL;
@@ -779,6 +788,7 @@ int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
 }
 
 int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_stream stream) {
+    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;

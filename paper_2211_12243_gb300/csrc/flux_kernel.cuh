@@ -60,6 +60,11 @@ struct FluxArgs {
     float psi1f, psi2f, ptolf, lmin_tiny;   // float copies (no per-face conversions)
     int64_t nbucket;
     const int32_t *node_first, *node_cnt;
+    // gravity (§2.3.8): sum_j dm_ij r_ij, 3 n sorted SoA (NULL: no gravity);
+    // both particles of a face add c_m (x_j - x_i).  recf: the float
+    // records, for the hard-face kernel's separations
+    double *dM;
+    const float *recf;
 };
 
 template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
@@ -546,6 +551,13 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                         if (RIEM == HYDRO_RIEMANN_EXACT && a.rec_faces) record_face<R>(a, K, st, ps, f + ol, j);
 #pragma unroll
                         for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + j], widen(c[q]));
+                        if (a.dM && c[0] != R(0)) {
+                            const double cm = widen(c[0]);
+                            for (int q = 0; q < 3; q++) {
+                                atomicAdd(&a.dM[q * a.n + f + ol], cm * (double)d[q]);
+                                atomicAdd(&a.dM[q * a.n + j], cm * (double)d[q]);
+                            }
+                        }
                     }
                 }
                 fs.pairs++;
@@ -696,6 +708,17 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
                 const double v = widen(c[q]);
                 atomicAdd(&a.dQ[q * a.n + s], -v);
                 atomicAdd(&a.dQ[q * a.n + j], v);
+            }
+            if (a.dM && c[0] != 0.f) {
+                float ri4[4], rj4[4], d[3], r2;
+                load4<float>(a.recf + (int64_t)s * REC, ri4);
+                load4<float>(a.recf + (int64_t)j * REC, rj4);
+                rec_sep(ri4, rj4, a.boxes[a.pbox[s]], d, r2);
+                const double cm = widen(c[0]);
+                for (int q = 0; q < 3; q++) {
+                    atomicAdd(&a.dM[q * a.n + s], cm * (double)d[q]);
+                    atomicAdd(&a.dM[q * a.n + j], cm * (double)d[q]);
+                }
             }
         }
     }

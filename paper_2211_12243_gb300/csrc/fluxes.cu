@@ -127,8 +127,10 @@ bool decide_learned(hydro_ctx *c) {
 cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
+    if (c->grav_live) HYD_CUDA(c->d_dM.ensure((size_t)3 * n));
     auto clear = [&]() -> cudaError_t {
         HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
+        if (c->grav_live) HYD_CUDA(cudaMemsetAsync(c->d_dM.get(), 0, sizeof(double) * 3 * n, st));
         // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
         // learned_faces, hard_faces, hard_ovf
         return cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 8 * sizeof(unsigned long long), st);
@@ -203,6 +205,8 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.nbucket = c->plan.nbucket;
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
+    a.recf = c->d_recf.get();
+    a.dM = c->grav_live ? c->d_dM.get() : nullptr;
     // the adaptive learned path times its probes with the same events
     const bool adapt = c->cfg.learned_guess == 1 && c->cfg.precision == HYDRO_MIXED &&
                        c->cfg.riemann == HYDRO_RIEMANN_EXACT && c->have_mlp;

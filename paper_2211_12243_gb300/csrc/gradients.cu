@@ -290,18 +290,25 @@ template <typename R>
 __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
                              const double *__restrict__ om, const double *__restrict__ h,
                              double gm1, double alpha1, const uint8_t *__restrict__ active,
-                             bool only_guard, R *__restrict__ rec) {
+                             bool only_guard, const double *__restrict__ agrav,
+                             R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     if (only_guard && !(active[s] & ACT_GUARD)) return;
     double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
     double E = Q[4 * n + s], U = Q[5 * n + s];
     double w = om[s];
+    // E_grav = m |a| h enters the total-energy switch (§2.3.7)
+    double egrav = 0.0;
+    if (agrav) {
+        const double ax = agrav[s], ay = agrav[n + s], az = agrav[2 * n + s];
+        egrav = m * sqrt(ax * ax + ay * ay + az * az) * h[s];
+    }
     R *r = rec + s * REC;
     if (sizeof(R) == 8) {
         double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
         double therm = U;
-        if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
+        if (U > alpha1 * (egrav + ekin) && E - ekin > 0.0) therm = E - ekin;
         r[R_H] = (R)h[s];
         r[R_RHO] = (R)(m / w);
         r[R_VX] = (R)(px / m);
@@ -314,7 +321,7 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
         double im = 1.0 / m;
         double ekin = 0.5 * (px * px + py * py + pz * pz) * im;
         double therm = U;
-        if (U > alpha1 * ekin && E - ekin > 0.0) therm = E - ekin;
+        if (U > alpha1 * (egrav + ekin) && E - ekin > 0.0) therm = E - ekin;
         float wf = (float)w, imf = (float)im;
         r[R_H] = (R)h[s];
         r[R_RHO] = (R)((float)m / wf);
@@ -364,17 +371,27 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
     const int64_t n = c->plan.n;
     double gm1 = c->cfg.gamma - 1.0;
     const uint8_t *act = c->d_active.get();
+    const double *ag = c->grav_live ? c->d_agrav.get() : nullptr;
     if (c->cfg.precision == HYDRO_MIXED)
         k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                               c->d_hsorted.get(), gm1,
-                                                              c->cfg.alpha1, act, only_guard,
+                                                              c->cfg.alpha1, act, only_guard, ag,
                                                               c->d_recf.get());
     else
         k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
-                                                               c->cfg.alpha1, act, only_guard,
+                                                               c->cfg.alpha1, act, only_guard, ag,
                                                                c->d_recd.get());
     return launch_check();
+}
+
+cudaError_t gather_gravity(hydro_ctx *c, stream_t st) {
+    c->grav_live = c->grav != nullptr;
+    if (!c->grav) return cudaSuccess;
+    const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_agrav.ensure((size_t)3 * n));
+    HYD_CUDA(c->d_dM.ensure((size_t)3 * n));
+    return gather_from_caller(c->d_perm.get(), c->grav, n, 3, c->d_agrav.get(), n, st);
 }
 
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,

@@ -142,6 +142,7 @@ cudaError_t enqueue_step(hydro_ctx *c, hydro_particles *p, double dt, bool sums,
     if (timing) HYD_CUDA(record_event(c->ev[0], st));
     HYD_CUDA(sort_particles(c, p, st));
     HYD_CUDA(gather_state(c, p, p->h, nullptr, c->cfg.search_margin, true, st));
+    HYD_CUDA(gather_gravity(c, st));
     HYD_CUDA(build_tree(c, st));
     HYD_CUDA(build_lists(c, c->nbr_per_particle, st));
     k_note_ovf<<<1, 1, 0, st>>>(c->d_cnt);
@@ -203,6 +204,9 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
     k.push_back((unsigned long long)c->plan.nbucket);
     k.push_back((unsigned long long)c->plan.nlevels);
     put(c->rec_faces);
+    put(c->grav);
+    put(c->d_agrav.get());
+    put(c->d_dM.get());
     k.push_back((unsigned long long)c->rec_cap);
     k.push_back((unsigned long long)c->rec_keep | ((unsigned long long)c->rec_hard_only << 32));
     for (const void *q :

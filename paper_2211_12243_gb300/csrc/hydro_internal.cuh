@@ -180,6 +180,13 @@ struct hydro_ctx {
     hyd::DevBuf<int32_t> d_nbr_cnt;
     hyd::DevBuf<int32_t> d_ovf;       // bucket ids with long lists
 
+    // external (gravitational) acceleration: the caller's array (3 per
+    // particle, caller order) or NULL; sorted SoA copy; sum_j dm_ij r_ij
+    const double *grav = nullptr;
+    bool grav_live = false;           // d_agrav holds this step's sorted copy (hydro_step only)
+    hyd::DevBuf<double> d_agrav;      // 3 n
+    hyd::DevBuf<double> d_dM;         // 3 n
+
     // reductions
     hyd::DevBuf<double> d_partials;
 
@@ -309,6 +316,8 @@ cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
 // gradients.cu
 // only_guard: the particles of the current guard round (their omega changed)
 cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard = false);
+// the caller's acceleration into sorted order (no-op without one)
+cudaError_t gather_gravity(hydro_ctx *c, stream_t st);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,

@@ -23,6 +23,8 @@ struct UpdArgs {
     hydro_particles p;
     DevCounters *cnt;
     bool abort_check;
+    const double *agrav;   // sorted SoA 3 n (NULL: no gravity)
+    const double *dM;      // sum_j dm_ij r_ij, sorted SoA 3 n
 };
 
 __global__ void k_update(UpdArgs a) {
@@ -44,6 +46,20 @@ __global__ void k_update(UpdArgs a) {
     double dU = dE - (vx0 * dpx + vy0 * dpy + vz0 * dpz) + 0.5 * (vx0 * vx0 + vy0 * vy0 + vz0 * vz0) * dm;
     double m1 = m0 + dm, px1 = px0 + dpx, py1 = py0 + dpy, pz1 = pz0 + dpz;
     double E1 = E0 + dE, U1 = U0 + dU;
+    if (a.agrav) {
+        // gravity (§2.3.8), trapezoidal between the start-of-step state and
+        // the state the fluxes updated (§2.3.4): momentum dt/2 (m^n + m~) a,
+        // energy dt/2 (P^n + P~).a + (1/2) a . sum_j dm_ij r_ij; the internal
+        // energy takes no source
+        const double ax = a.agrav[s], ay = a.agrav[n + s], az = a.agrav[2 * n + s];
+        const double w = 0.5 * dt * (m0 + m1);
+        const double eg = (px0 + px1) * ax + (py0 + py1) * ay + (pz0 + pz1) * az;
+        const double ex = ax * a.dM[s] + ay * a.dM[n + s] + az * a.dM[2 * n + s];
+        E1 += 0.5 * dt * eg + 0.5 * ex;
+        px1 += w * ax;
+        py1 += w * ay;
+        pz1 += w * az;
+    }
     double vx1 = px1 / m1, vy1 = py1 / m1, vz1 = pz1 / m1;
     const Box bx = a.boxes[a.pbox[s]];
     double x = a.xs[s] + dt * 0.5 * (vx0 + vx1);
@@ -173,6 +189,8 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.p = *p;
     a.cnt = c->d_cnt;
     a.abort_check = abort_check;
+    a.agrav = c->grav_live ? c->d_agrav.get() : nullptr;
+    a.dM = c->grav_live ? c->d_dM.get() : nullptr;
     k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
     return launch_check();
 }

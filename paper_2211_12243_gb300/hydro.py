@@ -105,7 +105,7 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_get_stats", "hydro_mlp_load", "hydro_mlp_get", "hydro_mlp_predict",
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
-           "hydro_strerror", "hydro_autotune", "hydro_set_tuning"]
+           "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity"]
 
 
 def _load():
@@ -142,6 +142,7 @@ def _load():
         L.hydro_totals_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         L.hydro_autotune.argtypes = [vp, P(Particles), P(Tuning), vp]
         L.hydro_set_tuning.argtypes = [vp, P(Tuning)]
+        L.hydro_set_gravity.argtypes = [vp, vp]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
@@ -341,6 +342,14 @@ class Hydro:
         if rc:
             raise HydroError(rc, "hydro_autotune")
         return t.as_dict()
+
+    def set_gravity(self, acc):
+        """acc: CUDA float64 tensor [n, 3] (caller order) kept alive by the
+        caller, or None (hydro_set_gravity)."""
+        self._grav = acc
+        rc = self.lib.hydro_set_gravity(self.h, _ptr(acc) if acc is not None else None)
+        if rc:
+            raise HydroError(rc, "hydro_set_gravity")
 
     def set_tuning(self, d):
         t = Tuning()

@@ -262,3 +262,38 @@ def test_degenerate_inputs_report_status(hyd):
     # bad config
     with pytest.raises(hyd.HydroError):
         hyd.Hydro(hyd.default_config(gamma=0.5))
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_gravity_step_matches_oracle(orc, hyd, scheme, precision, tol):
+    """hydro_set_gravity (§2.3.8): a random acceleration field on a Sod tube;
+    the host-driven and the graph step end where the oracle's step ends."""
+    import torch
+    w = W.sod(8)
+    n = w["x"].size
+    acc = np.random.default_rng(3).normal(0.0, 0.5, (n, 3))
+    co = orc.config(gamma=w["gamma"], scheme=scheme)
+    so, _, info_o = orc.step(co, w, -1.0, acc=acc)
+    H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision=precision, scheme=scheme))
+    H.set_boxes(*hyd.single_box(w))
+    acc_d = torch.as_tensor(acc, device="cuda").contiguous()
+    H.set_gravity(acc_d)
+    st = hyd.to_device(w)
+    init = {k: v.clone() for k, v in st.items()}
+    for graph in (0, 1):
+        for k, v in init.items():
+            st[k].copy_(v)
+        stats = H.step(st, -1.0)
+        torch.cuda.synchronize()
+        assert stats["status"] == 0 and stats["graph"] == graph, stats
+        assert stats["dt"] == pytest.approx(info_o["dt"], rel=tol)
+        sg = {k: v.cpu().numpy() for k, v in st.items()}
+        for k in ("h", "omega"):
+            assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol, (graph, k)
+        for k in ("m", "px", "py", "pz", "E", "U"):
+            d_o = so[k] - w[k]
+            d_g = sg[k] - w[k]
+            scale = np.abs(d_o).max() + 1e-300
+            assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, (graph, k)
+    H.set_gravity(None)

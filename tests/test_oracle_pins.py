@@ -539,3 +539,88 @@ def test_sod_tube_follows_exact_solution(orc, scheme):
         assert l1 < (0.6, 0.3, 0.5)[k] * l1_frozen, (k, l1, l1_frozen)
     # transverse motion stays negligible (§3.1.2)
     assert np.abs(prims[2][sel]).max() < 1e-2 and np.abs(prims[3][sel]).max() < 1e-2
+
+
+# --------------------------------------------------------------------------
+# external acceleration (§2.3.8) integrated by the rule of §2.3.4
+# --------------------------------------------------------------------------
+def _uniform_moving(v0, n=8):
+    w = dict(W.lattice_wave(n, jitter=0.0))
+    m = np.full(w["x"].size, 1.0 / n ** 3)
+    w["m"] = m
+    w["px"], w["py"], w["pz"] = m * v0[0], m * v0[1], m * v0[2]
+    w["U"] = m * 1.0 / (w["gamma"] - 1)
+    w["E"] = w["U"] + 0.5 * m * float(np.dot(v0, v0))
+    return w
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_gravity_on_a_uniform_state_closed_form(orc, scheme):
+    """A uniform lattice moving with v0 in a uniform acceleration a: the
+    fluxes vanish (Galilean-invariant uniform state), so the step is the
+    source rule alone: P += m a dt, E += dt P.a (the trapezoid between the
+    start state and the flux-updated state, which equals the start state
+    here), U unchanged, x += dt v0 + a dt^2 / 2 (the mean of the old and new
+    velocity), masses unchanged."""
+    v0 = np.array([0.3, -0.2, 0.1])
+    a = np.array([0.5, 1.5, -2.0])
+    w = _uniform_moving(v0)
+    n = w["x"].size
+    dt = 1e-3
+    cfg = orc.config(scheme=scheme)
+    s, out, info = orc.step(cfg, w, dt, acc=np.tile(a, (n, 1)))
+    assert info["status"] == 0
+    m = w["m"]
+    assert np.array_equal(s["m"], m)
+    for q, k in enumerate(("px", "py", "pz")):
+        want = w[k] + m * a[q] * dt
+        assert np.allclose(s[k], want, rtol=1e-13, atol=1e-16 * np.abs(want).max()), k
+    dE = dt * m * float(np.dot(v0, a))
+    assert np.allclose(s["E"] - w["E"], dE, rtol=1e-9, atol=1e-18)
+    assert np.allclose(s["U"], w["U"], rtol=1e-13)
+    for q, k in enumerate(("x", "y", "z")):
+        d = s[k] - w[k] - (dt * v0[q] + 0.5 * a[q] * dt * dt)
+        d -= np.round(d)          # unit periodic box
+        assert np.abs(d).max() < 1e-14, k
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_gravity_momentum_and_exchange_term(orc, scheme):
+    """A pressure bump in the middle of a tube at rest (uniform state at the
+    periodic seam, so no face across it carries mass): the flux conserves
+    momentum, so the total momentum changes by exactly sum_i dt/2 (m^n + m^{n+1})
+    a_i for any field a_i; the exchange sums sum_j dm_ij r_ij over all
+    particles equal twice the change of sum_k m_k x_k that the mass exchange
+    alone makes (each face moves c_m from x_i to x_j), and vanish for MFM."""
+    rng = np.random.default_rng(7)
+    w = _uniform_moving(np.zeros(3), n=12)
+    x = w["x"]
+    bump = np.exp(-((x - 0.5) / 0.08) ** 2)     # 1e-17 at the seam
+    w["U"] = w["m"] * (1.0 + 2.0 * bump) / (w["gamma"] - 1)
+    w["E"] = w["U"].copy()
+    n = x.size
+    acc = rng.normal(0.0, 0.5, (n, 3))
+    cfg = orc.config(scheme=scheme)
+    s, out, info = orc.step(cfg, w, 1e-3, acc=acc)
+    assert info["status"] == 0
+    dt = info["dt"]
+    w_ = 0.5 * dt * (w["m"] + s["m"])
+    for q, k in enumerate(("px", "py", "pz")):
+        want = math.fsum(w_ * acc[:, q])
+        got = math.fsum(s[k]) - math.fsum(w[k])
+        assert abs(got - want) < 1e-12 * math.fsum(np.abs(w_ * acc[:, q])), k
+    # exchange sums from the oracle's flux routine on the same start state
+    co = cfg
+    h, om, _, _ = orc.density(co, w["x"], w["y"], w["z"], w["L"], w["h"])
+    prims = orc.primitives(co, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"], om)
+    B6, _, nc = orc.matrices(co, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, _ = orc.gradients(co, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    dQ, _, _, dM = orc.fluxes(co, w["x"], w["y"], w["z"], w["L"], h, om, B6, prims, grad,
+                              alpha, dt, want_dM=True)
+    if scheme == "mfm":
+        assert np.all(dM == 0.0)
+        return
+    moved = np.array([math.fsum(dQ[:, 0] * c) for c in (w["x"], w["y"], w["z"])])
+    total = np.array([math.fsum(dM[:, q]) for q in range(3)])
+    assert np.abs(moved[0]) > 0
+    assert np.allclose(total, 2.0 * moved, rtol=1e-9, atol=1e-12 * np.abs(dQ[:, 0]).sum())
