@@ -149,15 +149,18 @@ def workload_name(kind, n):
     return WORKLOAD if (n or 78) == 78 else f"sod3d_n{n}"
 
 
-def make_workload(kind, n):
+def make_workload(kind, n, seed=0):
+    """The workload of one rank: the seeded generators (log-normal, batch)
+    draw a different realisation per seed, the lattice problems are the same
+    on every rank."""
     from paper_2211_12243_gb300 import workloads as W
     name = workload_name(kind, n)
     if kind == "sedov":
         return W.sedov(n or 128), name
     if kind == "lognormal":
-        return W.lognormal(n or (1 << 24)), name
+        return W.lognormal(n or (1 << 24), seed=seed), name
     if kind == "batch":
-        return W.batch(n or 512), name
+        return W.batch(n or 512, seed=seed), name
     if kind == "wave":
         return W.lattice_wave(n or 32), name
     return W.sod(n or 78), name
@@ -206,6 +209,21 @@ def oracle_sample_rate(kind, n, reps):
                 sample=f"{kind} generator at n={n} ({npart} particles), oracle gradient+flux stages "
                        f"(E/B/N_cond, gradients+limiter, pair enumeration, fluxes), {reps} passes, "
                        f"{total} pair-interactions in {t:.2f} s"), t
+
+
+def aggregate(world, pairs, ms, gf_ms, device):
+    """Whole-job figures of a multi-rank run (one process per GPU, each on
+    its own boxes, no data-path collective): pair-interactions summed over
+    the ranks, step and stage times the maximum over the ranks."""
+    if world <= 1:
+        return float(pairs), float(ms), float(gf_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, gf_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(p[0].item()), float(t[0].item()), float(t[1].item())
 
 
 def run_reference(args):
@@ -302,7 +320,7 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-    w, wname = make_workload(args.workload, args.n)
+    w, wname = make_workload(args.workload, args.n, seed=rank)
     n = w["x"].size
     learned = args.precision == "mixed" and not args.no_learned
     training = train_network(hydro, workloads, w, args.train_steps) if learned else None
@@ -403,15 +421,11 @@ def main():
     clk.start()
     r = timed_steps(H, st, args.steps, args.warmup)
     clocks = clk.stop()
-    ms_max, gf_max = r["ms"], r["gf_ms"]
-    if world > 1:
-        t = torch.tensor([r["ms"], r["gf_ms"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max, gf_max = float(t[0].item()), float(t[1].item())
+    pairs_all, ms_max, gf_max = aggregate(world, r["pairs"], r["ms"], r["gf_ms"], "cuda")
     ms_per_step = ms_max / args.steps
     # the metric: pairs over the gradient + flux stage time; whole-step rate beside it
-    value = world * r["pairs"] / (gf_max / 1000.0)
-    step_rate = world * r["pairs"] / (ms_max / 1000.0)
+    value = pairs_all / (gf_max / 1000.0)
+    step_rate = pairs_all / (ms_max / 1000.0)
 
     # ---- end to end through the public API with host buffers
     keys = ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")
