@@ -41,7 +41,8 @@ class Config(C.Structure):
         ("max_ngb_grow", C.c_int), ("psi1", C.c_double), ("psi2", C.c_double),
         ("beta_min", C.c_double), ("beta_max", C.c_double), ("c_cfl", C.c_double),
         ("alpha1", C.c_double), ("h_tol", C.c_double), ("p_tol", C.c_double),
-        ("max_h_iter", C.c_int), ("max_newton", C.c_int),
+        ("max_h_iter", C.c_int), ("max_newton", C.c_int), ("entropy", C.c_int),
+        ("alpha2", C.c_double), ("alpha3", C.c_double),
     ]
 
 
@@ -62,12 +63,13 @@ class StepInfo(C.Structure):
 def config(gamma=5.0 / 3.0, kernel="wendland", n_ngb=32.0, scheme="mfv", riemann="exact",
            limiter=True, time_extrap=True, ncond_crit=100.0, ngb_grow=1.2, max_ngb_grow=5,
            psi1=0.5, psi2=0.25, beta_min=1.0, beta_max=2.0, c_cfl=0.2, alpha1=0.01,
-           h_tol=1e-10, p_tol=1e-12, max_h_iter=60, max_newton=100):
+           h_tol=1e-10, p_tol=1e-12, max_h_iter=60, max_newton=100, entropy=False,
+           alpha2=1e-3, alpha3=1e-3):
     return Config(gamma, {"wendland": 0, "cubic": 1}[kernel], n_ngb,
                   {"mfv": 0, "mfm": 1}[scheme], {"exact": 0, "hllc": 1}[riemann],
                   int(bool(limiter)), int(bool(time_extrap)), ncond_crit, ngb_grow,
                   max_ngb_grow, psi1, psi2, beta_min, beta_max, c_cfl, alpha1, h_tol, p_tol,
-                  max_h_iter, max_newton)
+                  max_h_iter, max_newton, int(bool(entropy)), alpha2, alpha3)
 
 
 def lib():
@@ -86,7 +88,7 @@ def lib():
         L.orc_density.restype = i32
         L.orc_density.argtypes = [P(Config), i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_primitives.restype = None
-        L.orc_primitives.argtypes = [P(Config), i64] + [vp] * 14
+        L.orc_primitives.argtypes = [P(Config), i64] + [vp] * 17
         L.orc_matrices.restype = None
         L.orc_matrices.argtypes = [P(Config), i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_gradients.restype = None
@@ -95,7 +97,7 @@ def lib():
         L.orc_flux_pairs.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp]
         L.orc_fluxes.restype = None
         L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 14 + [d, i64, vp, vp, vp,
-                                 P(FluxStats), vp, vp, vp])
+                                 P(FluxStats), vp, vp, vp, vp, vp])
         L.orc_riemann_guess.restype = d
         L.orc_riemann_guess.argtypes = [d] * 7
         L.orc_riemann_star.restype = i32
@@ -107,7 +109,9 @@ def lib():
         L.orc_pair_limit.restype = d
         L.orc_pair_limit.argtypes = [d] * 5 + [i32]
         L.orc_step.restype = i32
-        L.orc_step.argtypes = ([P(Config), i64] + [vp] * 13 + [d] + [vp] * 5 + [P(StepInfo)])
+        L.orc_step.argtypes = ([P(Config), i64] + [vp] * 14 + [d] + [vp] * 5 + [P(StepInfo)])
+        L.orc_ekin_max.restype = None
+        L.orc_ekin_max.argtypes = [i64] + [vp] * 10
         L.orc_num_threads.restype = i32
         L.orc_set_num_threads.argtypes = [i32]
         _lib = L
@@ -170,17 +174,32 @@ def density(cfg, x, y, z, L, h_guess, n_ngb=None, active=None):
     return h, om, it, st
 
 
-def primitives(cfg, m, px, py, pz, E, U, omega, h=None, acc=None):
+def primitives(cfg, m, px, py, pz, E, U, omega, h=None, acc=None, A=None, ekmax=None,
+               want_src=False):
     """rho, vx, vy, vz, p (§2.3.7); acc[n,3] (with h) enters the pressure
-    switch through E_grav = m |a| h."""
+    switch through E_grav = m |a| h; with the entropy switch (cfg.entropy),
+    A (entropic function) and ekmax (E_kin^max) select the entropy route.
+    want_src appends the pressure source per particle (0 total energy,
+    1 entropy, 2 internal energy)."""
     arrs = list(map(_f64, (m, px, py, pz, E, U, omega)))
     n = arrs[0].size
     out = [np.zeros(n) for _ in range(5)]
-    hh = None if acc is None else _f64(h)
+    hh = None if h is None else _f64(h)
     aa = None if acc is None else _f64(acc).reshape(n, 3)
-    lib().orc_primitives(C.byref(cfg), n, *[_p(a) for a in arrs], _p(hh), _p(aa),
-                         *[_p(o) for o in out])
-    return tuple(out)  # rho, vx, vy, vz, p
+    AA = None if A is None else _f64(A)
+    ek = None if ekmax is None else _f64(ekmax)
+    src = np.zeros(n, dtype=np.int32) if want_src else None
+    lib().orc_primitives(C.byref(cfg), n, *[_p(a) for a in arrs], _p(hh), _p(aa), _p(AA), _p(ek),
+                         _p(src), *[_p(o) for o in out])
+    return tuple(out) + ((src,) if want_src else ())  # rho, vx, vy, vz, p[, src]
+
+
+def ekin_max(x, y, z, L, h, m, px, py, pz):
+    """max_j (1/2) m_i |v_j - v_i|^2 over j != i with r_ij < h_i (§2.3.7)."""
+    arrs = list(map(_f64, (x, y, z, L, h, m, px, py, pz)))
+    out = np.zeros(arrs[0].size)
+    lib().orc_ekin_max(arrs[0].size, *[_p(a) for a in arrs], _p(out))
+    return out
 
 
 def matrices(cfg, x, y, z, L, h, omega):
@@ -220,10 +239,11 @@ def flux_pairs(x, y, z, L, h):
 
 
 def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
-           pair_guess=None, want_faces=False, want_abs=False, want_dM=False):
+           pair_guess=None, want_faces=False, want_abs=False, want_dM=False, A=None):
     """dQ[n,6] = (dm, dpx, dpy, dpz, dE, dU) of Eqs. 16 and 24; (dQ, stats, faces)
     or, with want_abs, (dQ, stats, faces, dQabs[n,5] = sum over faces of |c|);
-    with want_dM the last element is dM[n,3] = sum_j dm_ij r_ij (§2.3.8)."""
+    with want_dM then dM[n,3] = sum_j dm_ij r_ij (§2.3.8); with A (entropic
+    function) last dS[n], the upwind entropy the mass fluxes carry (§2.3.7)."""
     x, y, z, L, h, omega, B6 = map(_f64, (x, y, z, L, h, omega, B6))
     grad, alpha = _f64(grad), _f64(alpha)
     rho, vx, vy, vz, p = map(_f64, prims)
@@ -238,12 +258,14 @@ def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
     pg = None if pair_guess is None else _f64(pair_guess)
     dQabs = np.zeros((n, 5)) if want_abs else None
     dM = np.zeros((n, 3)) if want_dM else None
+    AA = None if A is None else _f64(A)
+    dS = np.zeros(n) if A is not None else None
     lib().orc_fluxes(C.byref(cfg), n, _p(x), _p(y), _p(z), _p(L), _p(h), _p(omega), _p(B6),
                      _p(rho), _p(vx), _p(vy), _p(vz), _p(p), _p(grad), _p(alpha), float(dt),
                      npairs, _p(pairs), _p(pg), _p(dQ), C.byref(st), _p(faces), _p(dQabs),
-                     _p(dM))
+                     _p(dM), _p(AA), _p(dS))
     out = (dQ, st.as_dict(), faces) + ((dQabs,) if want_abs else ()) + ((dM,) if want_dM else ())
-    return out
+    return out + ((dS,) if A is not None else ())
 
 
 def riemann_guess(rl, ul, pl, rr, ur, pr, g):
@@ -282,18 +304,23 @@ def pair_limit(e, a, b, psi1=0.5, psi2=0.25, positive=False):
 def step(cfg, state, dt=-1.0, acc=None):
     """One full step on a copy of ``state`` (workload dict).  Returns
     (new_state, outputs, info) where outputs has B6, grad, alpha, ncond, dQ.
-    acc[n,3]: an external acceleration held over the step (§2.3.8)."""
+    acc[n,3]: an external acceleration held over the step (§2.3.8).  With
+    cfg.entropy the entropic function state["A"] (entries <= 0 unset) is
+    evolved and returned in new_state["A"] (§2.3.7)."""
     s = {k: _f64(state[k]).copy() for k in ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")}
     L = _f64(state["L"])
     n = s["x"].size
     s["omega"] = np.zeros(n)
+    if cfg.entropy:
+        s["A"] = _f64(state["A"]).copy() if "A" in state else np.zeros(n)
     out = dict(B6=np.zeros((n, 6)), grad=np.zeros((n, 5, 3)), alpha=np.zeros((n, 5)),
                ncond=np.zeros(n), dQ=np.zeros((n, 6)))
     info = StepInfo()
     st = lib().orc_step(C.byref(cfg), n, _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(L), _p(s["m"]),
                         _p(s["px"]), _p(s["py"]), _p(s["pz"]), _p(s["E"]), _p(s["U"]),
                         _p(s["h"]), _p(s["omega"]),
-                        _p(None if acc is None else _f64(acc).reshape(n, 3)), float(dt),
+                        _p(None if acc is None else _f64(acc).reshape(n, 3)),
+                        _p(s["A"] if cfg.entropy else None), float(dt),
                         _p(out["B6"]), _p(out["grad"]),
                         _p(out["alpha"]), _p(out["ncond"]), _p(out["dQ"]), C.byref(info))
     inf = dict(status=st, dt=info.dt, dt_next=info.dt_next, ngb_rounds=info.ngb_rounds,

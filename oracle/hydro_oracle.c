@@ -63,6 +63,8 @@ typedef struct {
     double p_tol;        /* relative Newton tolerance on p* */
     int max_h_iter;      /* cap on the h iteration */
     int max_newton;      /* cap on the Riemann Newton iteration */
+    int entropy;         /* 1 = entropy switch of §2.3.7 (entropic function evolved) */
+    double alpha2, alpha3; /* entropy switch thresholds, §2.3.7 (1/1000 each) */
 } orc_config;
 
 typedef struct {
@@ -454,8 +456,9 @@ int orc_density(const orc_config *c, int64_t n, const double *x, const double *y
  * also requires E - E_kin > 0.  acc: 3 per particle (ax, ay, az). */
 void orc_primitives(const orc_config *c, int64_t n, const double *m, const double *px,
                     const double *py, const double *pz, const double *E, const double *U,
-                    const double *omega, const double *h, const double *acc, double *rho,
-                    double *vx, double *vy, double *vz, double *p)
+                    const double *omega, const double *h, const double *acc, const double *A,
+                    const double *ekmax, int32_t *src, double *rho, double *vx, double *vy,
+                    double *vz, double *p)
 {
     for (int64_t i = 0; i < n; i++) {
         rho[i] = m[i] / omega[i];
@@ -469,9 +472,48 @@ void orc_primitives(const orc_config *c, int64_t n, const double *m, const doubl
             egrav = m[i] * sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) * h[i];
         }
         double therm = U[i];
-        if (U[i] > c->alpha1 * (egrav + ekin) && E[i] - ekin > 0.0) therm = E[i] - ekin;
-        p[i] = therm * (c->gamma - 1.0) / omega[i];
+        int from = 2;   /* 0 total energy, 1 entropy, 2 internal energy */
+        if (U[i] > c->alpha1 * (egrav + ekin) && E[i] - ekin > 0.0) {
+            therm = E[i] - ekin;
+            from = 0;
+        } else if (c->entropy && A && A[i] > 0.0 &&
+                   (U[i] < c->alpha2 * (ekmax[i] + U[i]) || U[i] < c->alpha3 * egrav)) {
+            from = 1;
+        }
+        if (from == 1)
+            p[i] = A[i] * pow(rho[i], c->gamma);   /* the entropic function p = A rho^gamma */
+        else
+            p[i] = therm * (c->gamma - 1.0) / omega[i];
+        if (src) src[i] = from;
     }
+}
+
+/* The largest kinetic energy of particle i relative to a neighbour,
+ * max_j (1/2) m_i |v_j - v_i|^2 over j != i with r_ij < h_i (§2.3.7: the
+ * smoothness measure of the entropy switch; 0 without neighbours). */
+void orc_ekin_max(int64_t n, const double *x, const double *y, const double *z,
+                  const double *L, const double *h, const double *m, const double *px,
+                  const double *py, const double *pz, double *out)
+{
+    int64_t *off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t tot = orc_neighbours(n, x, y, z, L, h, 1, 0, off, NULL);
+    int32_t *idx = (int32_t *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int32_t));
+    orc_neighbours(n, x, y, z, L, h, 1, tot, off, idx);
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; i++) {
+        const double vix = px[i] / m[i], viy = py[i] / m[i], viz = pz[i] / m[i];
+        double best = 0.0;
+        for (int64_t k = off[i]; k < off[i + 1]; k++) {
+            const int64_t j = idx[k];
+            if (j == i) continue;
+            const double dx = px[j] / m[j] - vix, dy = py[j] / m[j] - viy, dz = pz[j] / m[j] - viz;
+            const double e = 0.5 * m[i] * ((dx * dx + dy * dy) + dz * dz);
+            if (e > best) best = e;
+        }
+        out[i] = best;
+    }
+    free(idx);
+    free(off);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1113,7 +1155,8 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
                 const double *B6, const double *rho, const double *vx, const double *vy,
                 const double *vz, const double *p, const double *grad, const double *alpha,
                 double dt, int64_t npairs, const int64_t *pairs, const double *pair_guess,
-                double *dQ, orc_flux_stats *st, double *face_out, double *dQabs, double *dM)
+                double *dQ, orc_flux_stats *st, double *face_out, double *dQabs, double *dM,
+                const double *A, double *dS)
 {
     const double *Wp[5] = {rho, vx, vy, vz, p};
     double *cf = (double *)malloc((size_t)(npairs > 0 ? npairs : 1) * 5 * sizeof(double));
@@ -1186,6 +1229,21 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
         for (int64_t i = 0; i < 3 * n; i++) dM[i] = am[i].s + am[i].c;
         free(am);
     }
+    /* the extensive entropy m A carried by the mass fluxes (§2.3.7, the MFV
+     * entropy advection): a face giving c_m > 0 from i to j carries
+     * c_m A_i, one with c_m < 0 carries c_m A_j (the upwind entropic function) */
+    if (dS && A) {
+        orc_ksum *as = (orc_ksum *)calloc((size_t)n, sizeof(orc_ksum));
+        for (int64_t k = 0; k < npairs; k++) {
+            int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+            const double cm = cf[5 * k];
+            const double sflux = cm * (cm > 0.0 ? A[i] : A[j]);
+            ks_add(&as[i], -sflux);
+            ks_add(&as[j], sflux);
+        }
+        for (int64_t i = 0; i < n; i++) dS[i] = as[i].s + as[i].c;
+        free(as);
+    }
     /* scale of the per-particle flux error (sum over the particle's faces of
      * |c| per component), used to normalise comparisons of dQ whose net
      * value may cancel */
@@ -1231,7 +1289,7 @@ typedef struct {
  * grad, alpha, ncond, dQ (the hydrodynamic change only). */
 int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
              const double *L, double *m, double *px, double *py, double *pz, double *E,
-             double *U, double *h, double *omega, const double *acc, double dt,
+             double *U, double *h, double *omega, const double *acc, double *A, double dt,
              double *B6_out, double *grad_out, double *alpha_out, double *ncond_out,
              double *dQ_out, orc_step_info *info)
 {
@@ -1266,7 +1324,18 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
         rounds++;
     }
     if (fail && status == ORC_OK) status = ORC_ENCOND;
-    orc_primitives(c, n, m, px, py, pz, E, U, omega, h, acc, rho, vx, vy, vz, p);
+    /* entropy switch (§2.3.7): E_kin^max at the solved h; the entropic
+     * function A follows the pressure actually used (resynchronised where it
+     * came from the energies; entries <= 0 are unset and resynchronised) */
+    const int ent = c->entropy && A;
+    double *ekm = ent ? (double *)malloc((size_t)n * sizeof(double)) : NULL;
+    int32_t *src = ent ? (int32_t *)malloc((size_t)n * sizeof(int32_t)) : NULL;
+    if (ent) orc_ekin_max(n, x, y, z, L, h, m, px, py, pz, ekm);
+    orc_primitives(c, n, m, px, py, pz, E, U, omega, h, acc, ent ? A : NULL, ekm, src, rho, vx,
+                   vy, vz, p);
+    if (ent)
+        for (int64_t i = 0; i < n; i++)
+            if (src[i] != 1) A[i] = p[i] / pow(rho[i], c->gamma);
     orc_gradients(c, n, x, y, z, L, h, omega, rho, vx, vy, vz, p, B6, nc, grad, alpha, vsig);
     double dtc = INFINITY;
     for (int64_t i = 0; i < n; i++) {
@@ -1286,8 +1355,9 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     }
     orc_flux_stats fst;
     double *dM = acc ? (double *)malloc((size_t)n * 3 * sizeof(double)) : NULL;
+    double *dS = ent ? (double *)malloc((size_t)n * sizeof(double)) : NULL;
     orc_fluxes(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, dt, np, pairs,
-               NULL, dQ, &fst, NULL, NULL, dM);
+               NULL, dQ, &fst, NULL, NULL, dM, ent ? A : NULL, dS);
     free(pairs);
     /* directed gradient pairs */
     if (info) {
@@ -1301,6 +1371,9 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
         double vox = vx[i], voy = vy[i], voz = vz[i];
         const double m0 = m[i], p0[3] = {px[i], py[i], pz[i]};
         m[i] += dQ[6 * i + 0];
+        /* entropy: constant along MFM particles (no mass flux); MFV carries
+         * m A with the mass fluxes */
+        if (ent && c->scheme == 0) A[i] = (m0 * A[i] + dS[i]) / m[i];
         px[i] += dQ[6 * i + 1];
         py[i] += dQ[6 * i + 2];
         pz[i] += dQ[6 * i + 3];
@@ -1334,6 +1407,9 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     if (alpha_out) memcpy(alpha_out, alpha, (size_t)n * 5 * sizeof(double));
     if (ncond_out) memcpy(ncond_out, nc, (size_t)n * sizeof(double));
     free(dM);
+    free(dS);
+    free(ekm);
+    free(src);
     if (dQ_out) memcpy(dQ_out, dQ, (size_t)n * 6 * sizeof(double));
     if (info) {
         info->dt = dt;

@@ -624,3 +624,101 @@ def test_gravity_momentum_and_exchange_term(orc, scheme):
     total = np.array([math.fsum(dM[:, q]) for q in range(3)])
     assert np.abs(moved[0]) > 0
     assert np.allclose(total, 2.0 * moved, rtol=1e-9, atol=1e-12 * np.abs(dQ[:, 0]).sum())
+
+
+# --------------------------------------------------------------------------
+# entropy switch (§2.3.7)
+# --------------------------------------------------------------------------
+def test_entropy_switch_regimes(orc):
+    """The three pressure routes: total energy when U > alpha1 (E_grav +
+    E_kin); else the entropic function (p = A rho^gamma) when U < alpha2
+    (E_kin^max + U) or U < alpha3 E_grav; else the internal energy."""
+    g = 5.0 / 3.0
+    m = np.ones(6)
+    om = np.full(6, 0.5)                     # rho = 2
+    v = np.array([0.0, 1.0, 1.0, 1.0, 1.0, 1.0])
+    px, py, pz = m * v, np.zeros(6), np.zeros(6)
+    U = np.array([1.0, 1e-6, 5e-3, 1e-6, 5e-3, 5e-3])
+    E = U + 0.5 * m * v * v
+    ekmax = np.array([0.0, 1.0, 1.0, 1.0, 1e-3, 1e-3])
+    A = np.array([0.3, 0.3, 0.3, -1.0, 0.3, 0.3])
+    h = np.ones(6)
+    acc = np.zeros((6, 3))
+    acc[5, 2] = 10.0                          # E_grav = 10 > U / alpha3 = 5
+    cfg = orc.config(gamma=g, entropy=True)
+    rho, _, _, _, p, src = orc.primitives(cfg, m, px, py, pz, E, U, om, h=h, acc=acc, A=A,
+                                          ekmax=ekmax, want_src=True)
+    # 0: hot; 1: cold, large relative motion; 2: cold, relative motion small
+    # vs U / alpha2; 3: entropy route but A unset; 4: U > alpha2 (ekmax + U);
+    # 5: E_grav large: the first test fails (U < alpha1 (E_grav + E_kin)),
+    # the entropy route through U < alpha3 E_grav
+    assert list(src) == [0, 1, 2, 2, 2, 1]
+    assert p[0] == pytest.approx((E[0] - 0.0) * (g - 1) / 0.5, rel=1e-15)
+    assert p[1] == pytest.approx(0.3 * 2.0 ** g, rel=1e-15)
+    assert p[2] == pytest.approx(5e-3 * (g - 1) / 0.5, rel=1e-15)
+    assert p[5] == pytest.approx(0.3 * 2.0 ** g, rel=1e-15)
+    # switched off: never the entropy route
+    cfg0 = orc.config(gamma=g, entropy=False)
+    *_, src0 = orc.primitives(cfg0, m, px, py, pz, E, U, om, h=h, acc=acc, A=A, ekmax=ekmax,
+                              want_src=True)
+    assert 1 not in list(src0)
+
+
+def test_ekin_max_brute_force(orc):
+    rng = np.random.default_rng(4)
+    n = 300
+    x, y, z = rng.random(n), rng.random(n), rng.random(n)
+    L = np.array([1.0, 1.0, 1.0])
+    h = rng.uniform(0.1, 0.2, n)
+    m = rng.uniform(0.5, 1.5, n)
+    vel = rng.normal(0, 1, (n, 3))
+    got = orc.ekin_max(x, y, z, L, h, m, m * vel[:, 0], m * vel[:, 1], m * vel[:, 2])
+    for i in range(0, n, 7):
+        d = np.stack([x - x[i], y - y[i], z - z[i]], 1)
+        d -= np.round(d)
+        r2 = (d[:, 0] ** 2 + d[:, 1] ** 2) + d[:, 2] ** 2
+        sel = (r2 < h[i] ** 2) & (np.arange(n) != i)
+        want = (0.5 * m[i] * np.sum((vel[sel] - vel[i]) ** 2, 1)).max() if sel.any() else 0.0
+        assert got[i] == pytest.approx(want, rel=1e-14), i
+
+
+def _cold_streams(n=10):
+    """Two cold streams colliding along x (|v| = 2, c_s ~ 0.03): the relative
+    kinetic energy of neighbours dwarfs U."""
+    w = dict(W.lattice_wave(n, jitter=0.0))
+    m = np.full(w["x"].size, 1.0 / n ** 3)
+    vx = np.where(w["x"] < 0.5, 2.0, -2.0)
+    w["m"] = m
+    w["px"], w["py"], w["pz"] = m * vx, 0.0 * m, 0.0 * m
+    w["U"] = m * 1e-3 / (w["gamma"] - 1)
+    w["E"] = w["U"] + 0.5 * m * vx * vx
+    w["A"] = np.zeros(w["x"].size)
+    return w
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_entropy_constant_in_mfm_and_carried_in_mfv(orc, scheme):
+    """The entropic function follows the pressure used at the start of the
+    step (re-set from the energies where they gave the pressure); MFM keeps it
+    constant along the particles, MFV carries m A with the mass fluxes, so
+    sum m A is conserved to rounding."""
+    w = _cold_streams()
+    cfg = orc.config(gamma=w["gamma"], scheme=scheme, entropy=True)
+    # two steps: the first sets A from the energies, the second may use it
+    s1, _, i1 = orc.step(cfg, w, 1e-3)
+    assert i1["status"] == 0 and np.all(s1["A"] > 0)
+    s2, _, i2 = orc.step(cfg, s1, 1e-3)
+    assert i2["status"] == 0
+    # the A the second step started from: re-set where the energies gave p
+    h, om = s2["h"], s2["omega"]
+    ek = orc.ekin_max(s1["x"], s1["y"], s1["z"], s1["L"], h, s1["m"], s1["px"], s1["py"], s1["pz"])
+    rho, _, _, _, p, src = orc.primitives(cfg, s1["m"], s1["px"], s1["py"], s1["pz"], s1["E"],
+                                          s1["U"], om, h=h, A=s1["A"], ekmax=ek, want_src=True)
+    assert (src == 1).sum() > 0           # the cold streams take the entropy route
+    A_used = np.where(src == 1, s1["A"], p / rho ** w["gamma"])
+    if scheme == "mfm":
+        assert np.allclose(s2["A"], A_used, rtol=1e-14, atol=0.0)   # (numpy vs C pow: ulps)
+    else:
+        before = math.fsum(s1["m"] * A_used)
+        after = math.fsum(s2["m"] * s2["A"])
+        assert abs(after - before) < 1e-13 * math.fsum(np.abs(s1["m"] * A_used))
