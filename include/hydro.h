@@ -60,7 +60,8 @@ enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1 };
 
 /* Method parameters.  hydro_config_default() fills the values used by the
  * paper where it states them (N_cond threshold 100 and growth 1.2, §2.3.5;
- * pairwise limiter psi1 = 0.5, psi2 = 0.25, §2.3.6; alpha1 = 1/100, §2.3.7)
+ * pairwise limiter psi1 = 0.5, psi2 = 0.25, §2.3.6; alpha1 = 1/100 and
+ * alpha2 = alpha3 = 1/1000, §2.3.7)
  * and this library's readings elsewhere. */
 typedef struct {
     double gamma;        /* adiabatic index */
@@ -102,6 +103,12 @@ typedef struct {
                             device-side WHILE nodes (no host waits inside the
                             step); the first step of a context, and a step that
                             must grow a buffer, run host-driven.  0: host-driven. */
+    int entropy_switch;  /* hydro_step: 1 evolves the entropic function A of
+                            §2.3.7 (held by hydro_set_entropy) and takes the
+                            pressure from it where the flow is cold relative
+                            to its kinetic or gravitational energy (0: off) */
+    double alpha2;       /* entropy route when U < alpha2 (E_kin^max + U) (1/1000) */
+    double alpha3;       /* ... or when U < alpha3 E_grav (1/1000) */
 } hydro_config;
 
 /* Caller-owned particle state, caller order, all device pointers, n each.
@@ -365,6 +372,28 @@ int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const 
  * total-energy pressure switch (§2.3.7).  The totals in hydro_stats then
  * include the work of the external force.  Always HYDRO_OK for a context. */
 int hydro_set_gravity(hydro_ctx *ctx, const double *acc);
+
+/* The entropic function A of the entropy switch (§2.3.7) for the following
+ * hydro_step calls with cfg.entropy_switch = 1: A is a device array of n
+ * doubles (caller order), read and rewritten by every step and held by
+ * pointer until replaced (NULL: none; the caller keeps it alive).  Each
+ * step takes the pressure of particle i from
+ *   the total energy,     when U_i > alpha1 (E_grav,i + E_kin,i) and
+ *                         E_i - E_kin,i > 0 (as without the switch);
+ *   p = A_i rho_i^gamma,  else when A_i > 0 and U_i < alpha2 (E_kin^max,i +
+ *                         U_i) or U_i < alpha3 E_grav,i;
+ *   the internal energy,  otherwise;
+ * with E_kin^max,i = max_j (1/2) m_i |v_j - v_i|^2 over the neighbours
+ * j != i with r_ij < h_i at the step's h (0 without neighbours) and E_grav
+ * as in hydro_set_gravity.  Where the energies gave the pressure, A_i is set
+ * to p_i / rho_i^gamma (an entry <= 0 is unset and is set so).  A then stays
+ * constant along MFM particles; in MFV the mass flux of each face carries
+ * m A with the upwind value (the donor particle's A), so sum_i m_i A_i is
+ * conserved and A_i^(n+1) = (m_i^n A_i + sum_j c_m,ij A_upwind) / m_i^(n+1).
+ * The updated A is written back when the step completes.  hydro_step returns
+ * HYDRO_ESTATE when the switch is on and no array is held.  Always HYDRO_OK
+ * for a context. */
+int hydro_set_entropy(hydro_ctx *ctx, double *A);
 
 /* Launch parameters of the step that hydro_autotune chooses by timing the
  * candidates on the caller's own particles (no counterpart in the paper:

@@ -45,6 +45,9 @@ bool valid_config(const hydro_config *c) {
     if (!(c->search_margin >= 1.0)) return false;
     if (c->graph != 0 && c->graph != 1) return false;
     if (c->max_h_iter < 1 || c->max_newton < 1 || c->max_ngb_grow < 0) return false;
+    if (c->entropy_switch != 0 && c->entropy_switch != 1) return false;
+    if (!(c->alpha2 >= 0.0) || !(c->alpha3 >= 0.0) || !isfinite(c->alpha2) || !isfinite(c->alpha3))
+        return false;
     return true;
 }
 
@@ -293,6 +296,9 @@ void hydro_config_default(hydro_config *c) {
     c->max_newton = 100;
     c->search_margin = 1.15;
     c->graph = 1;
+    c->entropy_switch = 0;
+    c->alpha2 = 1e-3;
+    c->alpha3 = 1e-3;
 }
 
 int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
@@ -454,7 +460,7 @@ static int stage_state(hydro_ctx *c, const hydro_particles *p, cudaStream_t st) 
 
 int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *grad,
                     double *alpha, double *ncond, hydro_stream stream) {
-    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
+    if (c) c->grav_live = c->ent_live = false;   // (gravity and entropy: hydro_step only)
     if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -476,7 +482,7 @@ int hydro_gradients(hydro_ctx *c, const hydro_particles *p, double *B, double *g
 
 int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const double *grad,
                  const double *alpha, double dt, double *dQ, hydro_stream stream) {
-    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
+    if (c) c->grav_live = c->ent_live = false;   // (gravity and entropy: hydro_step only)
     if (!c || !c->have_lists) return c ? HYDRO_ESTATE : HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
     if (!valid_particles(c, p, true) || !B || !grad || !alpha || !dQ || !(dt > 0.0))
@@ -508,6 +514,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;
+    if (c->cfg.entropy_switch && !c->entA) return HYDRO_ESTATE;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = p->n;
     const bool timing = stats != nullptr && c->have_events;
@@ -529,6 +536,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
     if (rc) return rc;
     API_CUDA(gather_gravity(c, st));
+    API_CUDA(gather_entropy(c, st));
     if (timing) API_CUDA(record_event(c->ev[1], st));
     API_CUDA(reset_guard(c, st));
     int rebuilds = 0, rounds = 0, ncond_fail = 0;
@@ -775,6 +783,12 @@ int hydro_set_gravity(hydro_ctx *c, const double *acc) {
     return HYDRO_OK;
 }
 
+int hydro_set_entropy(hydro_ctx *c, double *A) {
+    if (!c) return HYDRO_EINVAL;
+    c->entA = A;
+    return HYDRO_OK;
+}
+
 int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (!c || !t) return HYDRO_EINVAL;
     if (!(t->search_margin >= 1.0) || t->nbr_slots < 32 || t->nbr_slots > 256) return HYDRO_EINVAL;
@@ -788,7 +802,7 @@ int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
 }
 
 int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_stream stream) {
-    if (c) c->grav_live = false;   // (gravity enters hydro_step only)
+    if (c) c->grav_live = c->ent_live = false;   // (gravity and entropy: hydro_step only)
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true)) return HYDRO_EINVAL;
     if (c->cfg.learned_guess && !c->have_mlp) return HYDRO_ESTATE;

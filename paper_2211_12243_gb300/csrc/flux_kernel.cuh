@@ -65,6 +65,10 @@ struct FluxArgs {
     // records, for the hard-face kernel's separations
     double *dM;
     const float *recf;
+    // entropy switch (§2.3.7), MFV: sum_j c_m,ij A_upwind, n sorted (NULL:
+    // off); A is the records' R_PAD slot.  A face whose mass flux c_m
+    // leaves the owner carries c_m A_owner, else c_m A_partner
+    double *dS;
 };
 
 template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
@@ -558,6 +562,12 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                                 atomicAdd(&a.dM[q * a.n + j], cm * (double)d[q]);
                             }
                         }
+                        if (a.dS && c[0] != R(0)) {
+                            const double cm = widen(c[0]);
+                            const double sf = cm * widen(c[0] > R(0) ? ri[R_PAD] : rj[R_PAD]);
+                            atomicAdd(&a.dS[f + ol], -sf);
+                            atomicAdd(&a.dS[j], sf);
+                        }
                     }
                 }
                 fs.pairs++;
@@ -719,6 +729,13 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
                     atomicAdd(&a.dM[q * a.n + s], cm * (double)d[q]);
                     atomicAdd(&a.dM[q * a.n + j], cm * (double)d[q]);
                 }
+            }
+            if (a.dS && c[0] != 0.f) {
+                const double cm = widen(c[0]);
+                const double sf =
+                    cm * (double)a.recf[(int64_t)(c[0] > 0.f ? s : j) * REC + R_PAD];
+                atomicAdd(&a.dS[s], -sf);
+                atomicAdd(&a.dS[j], sf);
             }
         }
     }

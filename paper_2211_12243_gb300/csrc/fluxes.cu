@@ -128,9 +128,12 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_dQ.ensure((size_t)5 * n));
     if (c->grav_live) HYD_CUDA(c->d_dM.ensure((size_t)3 * n));
+    // the entropy flux only matters where mass moves (MFV)
+    const bool ent_flux = c->ent_live && c->cfg.scheme == HYDRO_MFV;
     auto clear = [&]() -> cudaError_t {
         HYD_CUDA(cudaMemsetAsync(c->d_dQ.get(), 0, sizeof(double) * 5 * n, st));
         if (c->grav_live) HYD_CUDA(cudaMemsetAsync(c->d_dM.get(), 0, sizeof(double) * 3 * n, st));
+        if (ent_flux) HYD_CUDA(cudaMemsetAsync(c->d_dS.get(), 0, sizeof(double) * n, st));
         // flux_pairs, newton_iters, guess_fallbacks, vacuum, first_order,
         // learned_faces, hard_faces, hard_ovf
         return cudaMemsetAsync(&c->d_cnt->flux_pairs, 0, 8 * sizeof(unsigned long long), st);
@@ -207,6 +210,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.node_cnt = c->d_node_cnt.get();
     a.recf = c->d_recf.get();
     a.dM = c->grav_live ? c->d_dM.get() : nullptr;
+    a.dS = ent_flux ? c->d_dS.get() : nullptr;
     // the adaptive learned path times its probes with the same events
     const bool adapt = c->cfg.learned_guess == 1 && c->cfg.precision == HYDRO_MIXED &&
                        c->cfg.riemann == HYDRO_RIEMANN_EXACT && c->have_mlp;

@@ -143,6 +143,7 @@ cudaError_t enqueue_step(hydro_ctx *c, hydro_particles *p, double dt, bool sums,
     HYD_CUDA(sort_particles(c, p, st));
     HYD_CUDA(gather_state(c, p, p->h, nullptr, c->cfg.search_margin, true, st));
     HYD_CUDA(gather_gravity(c, st));
+    HYD_CUDA(gather_entropy(c, st));
     HYD_CUDA(build_tree(c, st));
     HYD_CUDA(build_lists(c, c->nbr_per_particle, st));
     k_note_ovf<<<1, 1, 0, st>>>(c->d_cnt);
@@ -207,6 +208,10 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
     put(c->grav);
     put(c->d_agrav.get());
     put(c->d_dM.get());
+    put(c->entA);
+    for (const void *q : {(const void *)c->d_A0.get(), (const void *)c->d_A1.get(),
+                          (const void *)c->d_ekmax.get(), (const void *)c->d_dS.get()})
+        put(q);
     k.push_back((unsigned long long)c->rec_cap);
     k.push_back((unsigned long long)c->rec_keep | ((unsigned long long)c->rec_hard_only << 32));
     for (const void *q :

@@ -187,6 +187,14 @@ struct hydro_ctx {
     hyd::DevBuf<double> d_agrav;      // 3 n
     hyd::DevBuf<double> d_dM;         // 3 n
 
+    // entropy switch (§2.3.7): the caller's entropic function A (caller
+    // order, rewritten by each step) or NULL; its sorted copy at the start
+    // of the step; the value the step uses (re-set where the energies gave
+    // the pressure); E_kin^max; sum_j c_m,ij A_upwind
+    double *entA = nullptr;
+    bool ent_live = false;            // d_A0 holds this step's sorted copy (hydro_step only)
+    hyd::DevBuf<double> d_A0, d_A1, d_ekmax, d_dS;   // n each
+
     // reductions
     hyd::DevBuf<double> d_partials;
 
@@ -318,6 +326,8 @@ cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
 cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard = false);
 // the caller's acceleration into sorted order (no-op without one)
 cudaError_t gather_gravity(hydro_ctx *c, stream_t st);
+// the caller's entropic function into sorted order (no-op with the switch off)
+cudaError_t gather_entropy(hydro_ctx *c, stream_t st);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,

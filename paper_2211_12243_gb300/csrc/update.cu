@@ -25,6 +25,11 @@ struct UpdArgs {
     bool abort_check;
     const double *agrav;   // sorted SoA 3 n (NULL: no gravity)
     const double *dM;      // sum_j dm_ij r_ij, sorted SoA 3 n
+    // entropy switch (§2.3.7): the value of A the step used (sorted; NULL:
+    // off), MFV's sum_j c_m,ij A_upwind (NULL for MFM) and the caller's array
+    const double *A1;
+    const double *dS;
+    double *A_out;
 };
 
 __global__ void k_update(UpdArgs a) {
@@ -82,6 +87,9 @@ __global__ void k_update(UpdArgs a) {
     a.p.etot[o] = E1; a.p.eint[o] = U1;
     a.p.h[o] = a.h[s];
     a.p.omega[o] = a.om[s];
+    // the entropic function: constant along an MFM particle; MFV carries
+    // m A with the mass fluxes
+    if (a.A1) a.A_out[o] = a.dS ? (m0 * a.A1[s] + a.dS[s]) / m1 : a.A1[s];
 }
 
 // totals before / after the update, reduced per warp and added to the
@@ -191,6 +199,9 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.abort_check = abort_check;
     a.agrav = c->grav_live ? c->d_agrav.get() : nullptr;
     a.dM = c->grav_live ? c->d_dM.get() : nullptr;
+    a.A1 = c->ent_live ? c->d_A1.get() : nullptr;
+    a.dS = c->ent_live && c->cfg.scheme == HYDRO_MFV ? c->d_dS.get() : nullptr;
+    a.A_out = c->entA;
     k_update<<<grid_for(a.n, 256), 256, 0, st>>>(a);
     return launch_check();
 }

@@ -46,6 +46,7 @@ class Config(C.Structure):
         ("beta_max", C.c_double), ("c_cfl", C.c_double), ("alpha1", C.c_double),
         ("h_tol", C.c_double), ("p_tol", C.c_double), ("max_h_iter", C.c_int),
         ("max_newton", C.c_int), ("search_margin", C.c_double), ("graph", C.c_int),
+        ("entropy_switch", C.c_int), ("alpha2", C.c_double), ("alpha3", C.c_double),
     ]
 
 
@@ -105,7 +106,8 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_get_stats", "hydro_mlp_load", "hydro_mlp_get", "hydro_mlp_predict",
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
-           "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity"]
+           "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity",
+           "hydro_set_entropy"]
 
 
 def _load():
@@ -143,6 +145,7 @@ def _load():
         L.hydro_autotune.argtypes = [vp, P(Particles), P(Tuning), vp]
         L.hydro_set_tuning.argtypes = [vp, P(Tuning)]
         L.hydro_set_gravity.argtypes = [vp, vp]
+        L.hydro_set_entropy.argtypes = [vp, vp]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
@@ -350,6 +353,15 @@ class Hydro:
         rc = self.lib.hydro_set_gravity(self.h, _ptr(acc) if acc is not None else None)
         if rc:
             raise HydroError(rc, "hydro_set_gravity")
+
+    def set_entropy(self, A):
+        """A: CUDA float64 tensor [n] (caller order), the entropic function
+        that hydro_step reads and rewrites with cfg.entropy_switch = 1; kept
+        alive by the caller, or None (hydro_set_entropy)."""
+        self._entA = A
+        rc = self.lib.hydro_set_entropy(self.h, _ptr(A) if A is not None else None)
+        if rc:
+            raise HydroError(rc, "hydro_set_entropy")
 
     def set_tuning(self, d):
         t = Tuning()

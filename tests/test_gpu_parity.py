@@ -297,3 +297,75 @@ def test_gravity_step_matches_oracle(orc, hyd, scheme, precision, tol):
             scale = np.abs(d_o).max() + 1e-300
             assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, (graph, k)
     H.set_gravity(None)
+
+
+def _entropy_mix(n=10, seed=5):
+    """Cold streams colliding along x (|v| = 2, U/m = 2.5e-3) with a hot
+    slab (U/m = 2.5, z < 0.3) and a little transverse noise: the hot slab
+    takes the total-energy route, stream particles near the two interfaces
+    the entropy route (E_kin^max ~ 8 m >> U / alpha2) where A > 0, the
+    interiors the internal-energy route (§2.3.7).  A: random, a fifth unset
+    (zero)."""
+    rng = np.random.default_rng(seed)
+    w = dict(W.lattice_wave(n, jitter=0.0))
+    N = w["x"].size
+    m = np.full(N, 1.0 / n ** 3)
+    vx = np.where(w["x"] < 0.5, 2.0, -2.0)
+    vy = rng.normal(0.0, 1e-3, N)
+    w["m"] = m
+    w["px"], w["py"], w["pz"] = m * vx, m * vy, 0.0 * m
+    u = np.where(w["z"] < 0.3, 2.5, 2.5e-3)
+    w["U"] = m * u
+    w["E"] = w["U"] + 0.5 * m * (vx * vx + vy * vy)
+    w["A"] = np.where(rng.random(N) < 0.2, 0.0, rng.uniform(5e-3, 2e-2, N))
+    return w
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_entropy_switch_step_matches_oracle(orc, hyd, scheme, precision, tol):
+    """hydro_set_entropy with cfg.entropy_switch (§2.3.7): the pressure
+    routes, the re-set of A where the energies gave the pressure, the MFV
+    entropy flux and the MFM constant A; the host-driven and the graph step
+    end where the oracle's step ends."""
+    import torch
+    w = _entropy_mix()
+    co = orc.config(gamma=w["gamma"], scheme=scheme, entropy=True)
+    so, _, info_o = orc.step(co, w, -1.0)
+    assert info_o["status"] == 0
+    # every route is taken
+    ek = orc.ekin_max(w["x"], w["y"], w["z"], w["L"], so["h"], w["m"], w["px"], w["py"], w["pz"])
+    _, _, _, _, _, src = orc.primitives(co, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"],
+                                        so["omega"], h=so["h"], A=w["A"], ekmax=ek, want_src=True)
+    assert all((src == r).sum() > 0 for r in (0, 1, 2)), np.bincount(src)
+    cg = hyd.default_config(gamma=w["gamma"], precision=precision, scheme=scheme,
+                            entropy_switch=1)
+    H = hyd.Hydro(cg)
+    H.set_boxes(*hyd.single_box(w))
+    st = hyd.to_device(w)
+    with pytest.raises(hyd.HydroError):
+        H.step(st, -1.0)             # the switch is on and no A is held
+    init = {k: v.clone() for k, v in st.items()}
+    A0 = torch.as_tensor(w["A"], device="cuda").clone()
+    A = A0.clone()
+    H.set_entropy(A)
+    for graph in (0, 1):
+        for k, v in init.items():
+            st[k].copy_(v)
+        A.copy_(A0)
+        stats = H.step(st, -1.0)
+        torch.cuda.synchronize()
+        assert stats["status"] == 0 and stats["graph"] == graph, stats
+        assert stats["dt"] == pytest.approx(info_o["dt"], rel=tol)
+        sg = {k: v.cpu().numpy() for k, v in st.items()}
+        for k in ("h", "omega"):
+            assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol, (graph, k)
+        for k in ("m", "px", "py", "pz", "E", "U"):
+            d_o = so[k] - w[k]
+            d_g = sg[k] - w[k]
+            scale = np.abs(d_o).max() + 1e-300
+            assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, (graph, k)
+        Ag = A.cpu().numpy()
+        assert np.all(Ag > 0)
+        assert np.max(np.abs(Ag - so["A"]) / so["A"]) < tol * 10, (graph, scheme)
+    H.set_entropy(None)
