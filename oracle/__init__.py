@@ -60,6 +60,12 @@ class StepInfo(C.Structure):
                 ("ncond_fail", C.c_int64), ("grad_pairs", C.c_int64), ("flux", FluxStats)]
 
 
+class RungInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("rung_max", C.c_int), ("substeps", C.c_int64),
+                ("active_steps", C.c_int64), ("faces", C.c_int64), ("capped", C.c_int64),
+                ("limiter_sweeps", C.c_int)]
+
+
 def config(gamma=5.0 / 3.0, kernel="wendland", n_ngb=32.0, scheme="mfv", riemann="exact",
            limiter=True, time_extrap=True, ncond_crit=100.0, ngb_grow=1.2, max_ngb_grow=5,
            psi1=0.5, psi2=0.25, beta_min=1.0, beta_max=2.0, c_cfl=0.2, alpha1=0.01,
@@ -111,6 +117,13 @@ def lib():
         L.orc_step.restype = i32
         L.orc_step.argtypes = ([P(Config), i64] + [vp] * 14 + [d] + [vp] * 5 + [P(StepInfo)])
         L.orc_ekin_max.restype = None
+        L.orc_rung_select.restype = i32
+        L.orc_rung_select.argtypes = [d, d, d, i32, P(i32)]
+        L.orc_rung_limit.restype = i32
+        L.orc_rung_limit.argtypes = [i64, vp, vp]
+        L.orc_step_rungs.restype = i32
+        L.orc_step_rungs.argtypes = ([P(Config), i64] + [vp] * 12 + [d, d, i32, vp, vp, vp,
+                                                                    P(RungInfo)])
         L.orc_ekin_max.argtypes = [i64] + [vp] * 10
         L.orc_num_threads.restype = i32
         L.orc_set_num_threads.argtypes = [i32]
@@ -328,3 +341,43 @@ def step(cfg, state, dt=-1.0, acc=None):
     s["L"] = L
     s["gamma"] = state.get("gamma", cfg.gamma)
     return s, out, inf
+
+
+def rung_select(dt_cfl, dt_acc, dt0, max_rung=12):
+    """Rung of one particle (§2.3.10): (r, capped)."""
+    cap = C.c_int32(0)
+    r = lib().orc_rung_select(float(dt_cfl), float(dt_acc), float(dt0), int(max_rung),
+                              C.byref(cap))
+    return r, bool(cap.value)
+
+
+def rung_limit(pairs, rung):
+    """Neighbour limiter |r_i - r_j| <= 2 over the pairs [k, 2] (§2.3.10);
+    returns (rungs, sweeps)."""
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    r = np.ascontiguousarray(rung, dtype=np.int32).copy()
+    sweeps = lib().orc_rung_limit(pr.shape[0], _p(pr), _p(r))
+    return r, sweeps
+
+
+def step_rungs(cfg, state, dt0, c_acc=0.2, max_rung=12):
+    """One base step dt0 with individual timesteps (§2.3.4, §2.3.10) on a
+    copy of ``state``.  Returns (new_state, rung, info); info["dt_cfl"],
+    info["dt_acc"]: the two timestep criteria of every particle at the start."""
+    s = {k: _f64(state[k]).copy() for k in ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")}
+    L = _f64(state["L"])
+    n = s["x"].size
+    s["omega"] = np.zeros(n)
+    rung = np.zeros(n, dtype=np.int32)
+    dtc, dta = np.zeros(n), np.zeros(n)
+    info = RungInfo()
+    st = lib().orc_step_rungs(C.byref(cfg), n, _p(s["x"]), _p(s["y"]), _p(s["z"]), _p(L),
+                              _p(s["m"]), _p(s["px"]), _p(s["py"]), _p(s["pz"]), _p(s["E"]),
+                              _p(s["U"]), _p(s["h"]), _p(s["omega"]), float(dt0), float(c_acc),
+                              int(max_rung), _p(rung), _p(dtc), _p(dta), C.byref(info))
+    inf = {k: getattr(info, k) for k, _ in RungInfo._fields_}
+    inf["dt_cfl"], inf["dt_acc"] = dtc, dta
+    inf["status"] = st
+    s["L"] = L
+    s["gamma"] = state.get("gamma", cfg.gamma)
+    return s, rung, inf

@@ -966,12 +966,15 @@ static void ks_add(orc_ksum *k, double v)
 
 /* Per-face computation for the unordered pair (i, j), oriented i -> j.
  * Returns c = dt |A_ij| F (mass, momentum 3, energy) in the lab frame:
- * particle i loses c, particle j gains c. */
+ * particle i loses c, particle j gains c.  tl, tr: the times over which the
+ * predictor advances the i and j states (dt/2 for a global step; under
+ * individual timesteps the time since the particle's state was taken plus
+ * half the face's step). */
 static void orc_face(const orc_config *c, int64_t i, int64_t j, const double d[3], double r,
                      const double *h, const double *omega, const double *B6,
                      const double *Wp[5], const double *grad, const double *alpha, double dt,
-                     const double *pguess, double cflux[5], orc_flux_stats *st,
-                     double *face_out)
+                     double tl, double tr, const double *pguess, double cflux[5],
+                     orc_flux_stats *st, double *face_out)
 {
     double g = c->gamma;
     /* face vector A_ij = omega_i omega_j [B_i dx W(r,h_i) + B_j dx W(r,h_j)] */
@@ -1017,14 +1020,14 @@ static void orc_face(const orc_config *c, int64_t i, int64_t j, const double d[3
     if (c->time_extrap) {
         double divi = Gi[1][0] + Gi[2][1] + Gi[3][2];
         double divj = Gj[1][0] + Gj[2][1] + Gj[3][2];
-        L_[0] -= 0.5 * dt * Wi[0] * divi;
-        R_[0] -= 0.5 * dt * Wj[0] * divj;
+        L_[0] -= tl * Wi[0] * divi;
+        R_[0] -= tr * Wj[0] * divj;
         for (int a = 0; a < 3; a++) {
-            L_[1 + a] -= 0.5 * dt * Gi[4][a] / Wi[0];
-            R_[1 + a] -= 0.5 * dt * Gj[4][a] / Wj[0];
+            L_[1 + a] -= tl * Gi[4][a] / Wi[0];
+            R_[1 + a] -= tr * Gj[4][a] / Wj[0];
         }
-        L_[4] -= 0.5 * dt * g * Wi[4] * divi;
-        R_[4] -= 0.5 * dt * g * Wj[4] * divj;
+        L_[4] -= tl * g * Wi[4] * divi;
+        R_[4] -= tr * g * Wj[4] * divj;
     }
     if (!(L_[0] > 0.0 && L_[4] > 0.0 && R_[0] > 0.0 && R_[4] > 0.0)) {
         for (int f = 0; f < 5; f++) { L_[f] = Wi[f]; R_[f] = Wj[f]; }
@@ -1150,6 +1153,16 @@ int64_t orc_flux_pairs(int64_t n, const double *x, const double *y, const double
  * pair_guess (optional, one per pair) overrides the Riemann initial guess.
  * face_out (optional, 9 per pair): rho_L, u_L, p_L, rho_R, u_R, p_R, p*, u*,
  * Newton iterations. */
+static void orc_fluxes_impl(const orc_config *c, int64_t n, const double *x, const double *y,
+                            const double *z, const double *L, const double *h,
+                            const double *omega, const double *B6, const double *rho,
+                            const double *vx, const double *vy, const double *vz,
+                            const double *p, const double *grad, const double *alpha, double dt,
+                            const double *dtp, const double *toff, int64_t npairs,
+                            const int64_t *pairs, const double *pair_guess, double *dQ,
+                            orc_flux_stats *st, double *face_out, double *dQabs, double *dM,
+                            const double *A, double *dS);
+
 void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y,
                 const double *z, const double *L, const double *h, const double *omega,
                 const double *B6, const double *rho, const double *vx, const double *vy,
@@ -1157,6 +1170,24 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
                 double dt, int64_t npairs, const int64_t *pairs, const double *pair_guess,
                 double *dQ, orc_flux_stats *st, double *face_out, double *dQabs, double *dM,
                 const double *A, double *dS)
+{
+    orc_fluxes_impl(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, dt, NULL,
+                    NULL, npairs, pairs, pair_guess, dQ, st, face_out, dQabs, dM, A, dS);
+}
+
+/* orc_fluxes with individual timesteps (dtp non-NULL): the face (i, j)
+ * takes dt_ij = min(dtp_i, dtp_j) (§2.3.4, the rule of Springel 2010 §7.2),
+ * and its predictor advances each side over toff + dt_ij / 2, toff the time
+ * since that particle's state was taken.  dt is unused then. */
+static void orc_fluxes_impl(const orc_config *c, int64_t n, const double *x, const double *y,
+                            const double *z, const double *L, const double *h,
+                            const double *omega, const double *B6, const double *rho,
+                            const double *vx, const double *vy, const double *vz,
+                            const double *p, const double *grad, const double *alpha, double dt,
+                            const double *dtp, const double *toff, int64_t npairs,
+                            const int64_t *pairs, const double *pair_guess, double *dQ,
+                            orc_flux_stats *st, double *face_out, double *dQabs, double *dM,
+                            const double *A, double *dS)
 {
     const double *Wp[5] = {rho, vx, vy, vz, p};
     double *cf = (double *)malloc((size_t)(npairs > 0 ? npairs : 1) * 5 * sizeof(double));
@@ -1171,7 +1202,13 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
             int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
             double d[3];
             double r = sqrt(orc_sep(x, y, z, L, i, j, d));
-            orc_face(c, i, j, d, r, h, omega, B6, Wp, grad, alpha, dt,
+            double dtf = dt, tl = 0.5 * dt, tr = 0.5 * dt;
+            if (dtp) {
+                dtf = dtp[i] < dtp[j] ? dtp[i] : dtp[j];
+                tl = toff[i] + 0.5 * dtf;
+                tr = toff[j] + 0.5 * dtf;
+            }
+            orc_face(c, i, j, d, r, h, omega, B6, Wp, grad, alpha, dtf, tl, tr,
                      pair_guess ? pair_guess + k : NULL, cf + 5 * k, &loc,
                      face_out ? face_out + 9 * k : NULL);
         }
@@ -1420,6 +1457,261 @@ int orc_step(const orc_config *c, int64_t n, double *x, double *y, double *z,
     }
     free(nngb); free(act); free(B6); free(nc); free(rho); free(vx); free(vy); free(vz);
     free(p); free(grad); free(alpha); free(vsig); free(dQ);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Individual timesteps (§2.3.4 power-of-two hierarchy, §2.3.10 criteria)    */
+/* ------------------------------------------------------------------------ */
+
+/* The rung of one particle (§2.3.10): the smallest integer r >= 0 with
+ * min(dt_cfl, dt_acc) > 2^-r dt0, at most max_rung (*capped set when even
+ * max_rung does not satisfy the criterion). */
+int orc_rung_select(double dt_cfl, double dt_acc, double dt0, int max_rung, int *capped)
+{
+    const double t = dt_cfl < dt_acc ? dt_cfl : dt_acc;
+    int r = 0;
+    while (r < max_rung && !(t > ldexp(dt0, -r))) r++;
+    if (capped) *capped = !(t > ldexp(dt0, -r));
+    return r;
+}
+
+/* The neighbour limiter of §2.3.10 (Saitoh & Makino 2009): interacting
+ * particles (the unordered flux pairs) differ by at most two rungs.  Rungs
+ * only rise: r_i <- max(r_i, r_j - 2) over the pairs, swept until nothing
+ * changes (the least such assignment above the input).  Returns the sweeps. */
+int orc_rung_limit(int64_t npairs, const int64_t *pairs, int32_t *rung)
+{
+    int sweeps = 0, changed = 1;
+    while (changed) {
+        changed = 0;
+        sweeps++;
+        for (int64_t k = 0; k < npairs; k++) {
+            const int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+            if (rung[i] < rung[j] - 2) { rung[i] = rung[j] - 2; changed = 1; }
+            if (rung[j] < rung[i] - 2) { rung[j] = rung[i] - 2; changed = 1; }
+        }
+    }
+    return sweeps;
+}
+
+typedef struct {
+    int status;
+    int rung_max;            /* deepest rung of the base step */
+    int64_t substeps;        /* 2^rung_max */
+    int64_t active_steps;    /* particle steps taken over the base step */
+    int64_t faces;           /* faces solved over the base step */
+    int64_t capped;          /* particles the criteria wanted beyond max_rung */
+    int limiter_sweeps;
+} orc_rung_info;
+
+/* density + N_cond guard (§2.3.5) for the particles with ract set (all when
+ * ract is NULL): N_NGB restarts from n_ngb; h and omega of the others stay.
+ * B6 and nc receive the matrices of every particle (the caller keeps the
+ * rows it needs). */
+static int orc_density_guard(const orc_config *c, int64_t n, const double *x, const double *y,
+                             const double *z, const double *L, const int32_t *ract, double *h,
+                             double *omega, double *B6, double *nc, int *rounds_out,
+                             int64_t *fail_out)
+{
+    int status = ORC_OK;
+    double *nngb = (double *)malloc((size_t)n * sizeof(double));
+    int32_t *act = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    for (int64_t i = 0; i < n; i++) { nngb[i] = c->n_ngb; act[i] = ract ? ract[i] : 1; }
+    int rounds = 0;
+    int64_t fail = 0;
+    for (;;) {
+        int s = orc_density(c, n, x, y, z, L, nngb, act, h, omega, NULL);
+        if (s != ORC_OK) status = s;
+        orc_matrices(c, n, x, y, z, L, h, omega, B6, NULL, nc);
+        fail = 0;
+        for (int64_t i = 0; i < n; i++) {
+            act[i] = (ract ? ract[i] : 1) && nc[i] > c->ncond_crit;
+            fail += act[i];
+        }
+        if (fail == 0 || rounds == c->max_ngb_grow) break;
+        for (int64_t i = 0; i < n; i++) if (act[i]) nngb[i] *= c->ngb_grow;
+        rounds++;
+    }
+    if (fail && status == ORC_OK) status = ORC_ENCOND;
+    free(nngb);
+    free(act);
+    if (rounds_out) *rounds_out = rounds;
+    if (fail_out) *fail_out = fail;
+    return status;
+}
+
+/* unordered flux pairs r_ij < max(h_i, h_j) at the current positions;
+ * *np receives the count; the caller frees the array */
+static int64_t *orc_pairs_alloc(int64_t n, const double *x, const double *y, const double *z,
+                                const double *L, const double *h, int64_t *np)
+{
+    int64_t cap = n * 64 + 64;
+    int64_t *pairs = (int64_t *)malloc((size_t)cap * 2 * sizeof(int64_t));
+    int64_t k = orc_flux_pairs(n, x, y, z, L, h, cap, pairs);
+    if (k > cap) {
+        free(pairs);
+        cap = k;
+        pairs = (int64_t *)malloc((size_t)cap * 2 * sizeof(int64_t));
+        k = orc_flux_pairs(n, x, y, z, L, h, cap, pairs);
+    }
+    *np = k;
+    return pairs;
+}
+
+/* One base step dt0 > 0 with individual timesteps (§2.3.4, §2.3.10).
+ * Sub-step 0 synchronises every particle: density, guard, primitives and
+ * gradients as in orc_step; then each particle's rung from the CFL
+ * timestep (Eq. 31) and the acceleration criterion
+ * dt_acc = c_acc sqrt(h / |a|), a = -grad p / rho (the limited pressure
+ * gradient of the face reconstruction; no external acceleration), the
+ * rung selection and the neighbour limiter above.  The base step then
+ * runs 2^rmax sub-steps of dt0 2^-rmax; at sub-step k the particles with
+ * k divisible by 2^(rmax - r_i) start a step of dt0 2^-r_i: their density,
+ * guard, primitives and gradients are recomputed at the current positions
+ * (the others keep those of their last start, used as they are).  Every
+ * unordered flux pair with an active particle exchanges, with
+ * dt_ij = min(dt_i, dt_j), c = dt_ij |A_ij| F, subtracted from i and added
+ * to j (so the exchange is symmetric), each side predicted over the time
+ * since its start plus dt_ij / 2.  Every particle then takes its received
+ * change (U by Eq. 24 with its current velocity) and drifts by the
+ * sub-step with the mean of its velocities before and after.  Rungs are
+ * fixed over the base step.  rung (out): the rungs used; dt_cfl, dt_acc
+ * (optional outputs): the two criteria at sub-step 0. */
+int orc_step_rungs(const orc_config *c, int64_t n, double *x, double *y, double *z,
+                   const double *L, double *m, double *px, double *py, double *pz, double *E,
+                   double *U, double *h, double *omega, double dt0, double c_acc, int max_rung,
+                   int32_t *rung, double *dt_cfl, double *dt_acc, orc_rung_info *info)
+{
+    int status = ORC_OK;
+    double *B6 = (double *)malloc((size_t)n * 6 * sizeof(double));
+    double *B6t = (double *)malloc((size_t)n * 6 * sizeof(double));
+    double *nc = (double *)malloc((size_t)n * sizeof(double));
+    double *prim[5], *primt[5];
+    for (int f = 0; f < 5; f++) {
+        prim[f] = (double *)malloc((size_t)n * sizeof(double));
+        primt[f] = (double *)malloc((size_t)n * sizeof(double));
+    }
+    double *grad = (double *)malloc((size_t)n * 15 * sizeof(double));
+    double *alpha = (double *)malloc((size_t)n * 5 * sizeof(double));
+    double *gradt = (double *)malloc((size_t)n * 15 * sizeof(double));
+    double *alphat = (double *)malloc((size_t)n * 5 * sizeof(double));
+    double *vsig = (double *)malloc((size_t)n * sizeof(double));
+    double *dQ = (double *)malloc((size_t)n * 6 * sizeof(double));
+    double *dtp = (double *)malloc((size_t)n * sizeof(double));
+    double *toff = (double *)malloc((size_t)n * sizeof(double));
+    int32_t *ract = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *kstart = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    orc_rung_info inf;
+    memset(&inf, 0, sizeof inf);
+
+    /* sub-step 0: everything, as in orc_step */
+    int s = orc_density_guard(c, n, x, y, z, L, NULL, h, omega, B6, nc, NULL, NULL);
+    if (s != ORC_OK) status = s;
+    orc_primitives(c, n, m, px, py, pz, E, U, omega, NULL, NULL, NULL, NULL, NULL, prim[0],
+                   prim[1], prim[2], prim[3], prim[4]);
+    orc_gradients(c, n, x, y, z, L, h, omega, prim[0], prim[1], prim[2], prim[3], prim[4], B6,
+                  nc, grad, alpha, vsig);
+    /* rungs (§2.3.10) */
+    for (int64_t i = 0; i < n; i++) {
+        const double dtc = c->c_cfl * h[i] / vsig[i];
+        const double gx = alpha[5 * i + 4] * grad[15 * i + 12];
+        const double gy = alpha[5 * i + 4] * grad[15 * i + 13];
+        const double gz = alpha[5 * i + 4] * grad[15 * i + 14];
+        const double acc = sqrt(gx * gx + gy * gy + gz * gz) / prim[0][i];
+        const double dta = acc > 0.0 ? c_acc * sqrt(h[i] / acc) : INFINITY;
+        if (dt_cfl) dt_cfl[i] = dtc;
+        if (dt_acc) dt_acc[i] = dta;
+        int cap = 0;
+        rung[i] = orc_rung_select(dtc, dta, dt0, max_rung, &cap);
+        inf.capped += cap;
+    }
+    {
+        int64_t np;
+        int64_t *pairs = orc_pairs_alloc(n, x, y, z, L, h, &np);
+        inf.limiter_sweeps = orc_rung_limit(np, pairs, rung);
+        free(pairs);
+    }
+    int rmax = 0;
+    for (int64_t i = 0; i < n; i++) if (rung[i] > rmax) rmax = rung[i];
+    const int64_t K = (int64_t)1 << rmax;
+    const double dtmin = ldexp(dt0, -rmax);
+    for (int64_t i = 0; i < n; i++) {
+        dtp[i] = ldexp(dt0, -rung[i]);
+        kstart[i] = 0;
+    }
+    for (int64_t k = 0; k < K; k++) {
+        for (int64_t i = 0; i < n; i++) {
+            ract[i] = k % ((int64_t)1 << (rmax - rung[i])) == 0;
+            inf.active_steps += ract[i];
+        }
+        if (k > 0) {
+            s = orc_density_guard(c, n, x, y, z, L, ract, h, omega, B6t, nc, NULL, NULL);
+            if (s != ORC_OK && status == ORC_OK) status = s;
+            for (int64_t i = 0; i < n; i++)
+                if (ract[i]) memcpy(B6 + 6 * i, B6t + 6 * i, 6 * sizeof(double));
+            orc_primitives(c, n, m, px, py, pz, E, U, omega, NULL, NULL, NULL, NULL, NULL,
+                           primt[0], primt[1], primt[2], primt[3], primt[4]);
+            for (int f = 0; f < 5; f++)
+                for (int64_t i = 0; i < n; i++)
+                    if (ract[i]) prim[f][i] = primt[f][i];
+            orc_gradients(c, n, x, y, z, L, h, omega, prim[0], prim[1], prim[2], prim[3],
+                          prim[4], B6, nc, gradt, alphat, vsig);
+            for (int64_t i = 0; i < n; i++)
+                if (ract[i]) {
+                    memcpy(grad + 15 * i, gradt + 15 * i, 15 * sizeof(double));
+                    memcpy(alpha + 5 * i, alphat + 5 * i, 5 * sizeof(double));
+                }
+        }
+        for (int64_t i = 0; i < n; i++) {
+            if (ract[i]) kstart[i] = k;
+            toff[i] = (double)(k - kstart[i]) * dtmin;
+        }
+        /* the faces with an active particle */
+        int64_t np;
+        int64_t *pairs = orc_pairs_alloc(n, x, y, z, L, h, &np);
+        int64_t w = 0;
+        for (int64_t q = 0; q < np; q++) {
+            const int64_t i = pairs[2 * q], j = pairs[2 * q + 1];
+            if (ract[i] || ract[j]) { pairs[2 * w] = i; pairs[2 * w + 1] = j; w++; }
+        }
+        orc_flux_stats fst;
+        orc_fluxes_impl(c, n, x, y, z, L, h, omega, B6, prim[0], prim[1], prim[2], prim[3],
+                        prim[4], grad, alpha, dtmin, dtp, toff, w, pairs, NULL, dQ, &fst, NULL,
+                        NULL, NULL, NULL, NULL);
+        free(pairs);
+        inf.faces += w;
+        /* every particle takes what it received and drifts */
+        for (int64_t i = 0; i < n; i++) {
+            const double vox = px[i] / m[i], voy = py[i] / m[i], voz = pz[i] / m[i];
+            const double dm = dQ[6 * i + 0], dpx = dQ[6 * i + 1], dpy = dQ[6 * i + 2];
+            const double dpz = dQ[6 * i + 3], dE = dQ[6 * i + 4];
+            const double v2 = vox * vox + voy * voy + voz * voz;
+            const double dU = dE - (vox * dpx + voy * dpy + voz * dpz) + 0.5 * v2 * dm;
+            m[i] += dm;
+            px[i] += dpx;
+            py[i] += dpy;
+            pz[i] += dpz;
+            E[i] += dE;
+            U[i] += dU;
+            const double nx = px[i] / m[i], ny = py[i] / m[i], nz = pz[i] / m[i];
+            double xs[3] = {x[i] + dtmin * 0.5 * (vox + nx), y[i] + dtmin * 0.5 * (voy + ny),
+                            z[i] + dtmin * 0.5 * (voz + nz)};
+            for (int a = 0; a < 3; a++) {
+                if (xs[a] >= L[a]) xs[a] -= L[a];
+                if (xs[a] < 0.0) xs[a] += L[a];
+            }
+            x[i] = xs[0]; y[i] = xs[1]; z[i] = xs[2];
+        }
+    }
+    inf.status = status;
+    inf.rung_max = rmax;
+    inf.substeps = K;
+    if (info) *info = inf;
+    free(B6); free(B6t); free(nc);
+    for (int f = 0; f < 5; f++) { free(prim[f]); free(primt[f]); }
+    free(grad); free(alpha); free(gradt); free(alphat); free(vsig); free(dQ); free(dtp);
+    free(toff); free(ract); free(kstart);
     return status;
 }
 

@@ -722,3 +722,181 @@ def test_entropy_constant_in_mfm_and_carried_in_mfv(orc, scheme):
         before = math.fsum(s1["m"] * A_used)
         after = math.fsum(s2["m"] * s2["A"])
         assert abs(after - before) < 1e-13 * math.fsum(np.abs(s1["m"] * A_used))
+
+
+# --------------------------------------------------------------------------
+# individual timesteps (§2.3.4 hierarchy, §2.3.10 criteria)
+# --------------------------------------------------------------------------
+
+def test_rung_select_closed_form(orc):
+    """The smallest r >= 0 with min(dt_cfl, dt_acc) > 2^-r dt0: 0 above dt0,
+    floor(log2(dt0 / t)) + 1 below it (strict at the powers of two), capped."""
+    dt0 = 0.37
+    cases = [(2 * dt0, np.inf, 0), (dt0, np.inf, 1), (dt0 * (1 + 1e-12), np.inf, 0),
+             (dt0 / 2, np.inf, 2), (np.inf, dt0 / 4, 3), (dt0 / 3, dt0, 2), (dt0, dt0 / 3, 2),
+             (np.inf, np.inf, 0)]
+    for dtc, dta, want in cases:
+        assert orc.rung_select(dtc, dta, dt0, 12) == (want, False), (dtc, dta)
+    assert orc.rung_select(dt0 * 2.0 ** -13, np.inf, dt0, 12) == (12, True)
+    assert orc.rung_select(dt0 * 2.0 ** -12 * 1.5, np.inf, dt0, 12) == (12, False)
+    rng = np.random.default_rng(11)
+    for t in dt0 * np.exp(rng.uniform(-8.0, 1.0, 400)):
+        e = math.log2(dt0 / t)
+        if abs(e - round(e)) < 1e-9:
+            continue
+        want = 0 if t > dt0 else math.floor(e) + 1
+        assert orc.rung_select(t, np.inf, dt0, 20)[0] == want, t
+
+
+def test_rung_limiter_is_graph_distance_bound(orc):
+    """Limited rungs r_i = max_j (r0_j - 2 d(i, j)), d the hop distance in
+    the interaction graph (breadth-first search from every particle)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import shortest_path
+    rng = np.random.default_rng(12)
+    n = 300
+    pairs = set()
+    while len(pairs) < 500:
+        i, j = rng.integers(0, n, 2)
+        if i != j:
+            pairs.add((min(i, j), max(i, j)))
+    pairs = np.array(sorted(pairs), dtype=np.int64)
+    r0 = rng.integers(0, 12, n).astype(np.int32)
+    r0[rng.random(n) < 0.7] = 0
+    got, sweeps = orc.rung_limit(pairs, r0)
+    g = coo_matrix((np.ones(len(pairs)), (pairs[:, 0], pairs[:, 1])), shape=(n, n))
+    d = shortest_path(g, directed=False, unweighted=True)
+    want = np.max(np.where(np.isfinite(d), r0[None, :] - 2 * d, -np.inf), axis=1)
+    assert np.array_equal(got, want.astype(np.int32))
+    assert sweeps >= 2
+    for i, j in pairs:
+        assert abs(int(got[i]) - int(got[j])) <= 2
+
+
+def test_rungs_reduce_to_the_global_step(orc):
+    """A base step no particle's criteria subdivide (every rung 0) is the
+    global step with dt = dt0, to the last bit."""
+    w = W.sod(8)
+    co = orc.config(gamma=w["gamma"])
+    _, _, i0 = orc.step(co, w, -1.0)
+    dt0 = 0.5 * i0["dt"]
+    sr, rung, ir = orc.step_rungs(co, w, dt0, c_acc=1e9)
+    sg, _, _ = orc.step(co, w, dt0)
+    assert ir["status"] == 0 and ir["rung_max"] == 0 and not rung.any()
+    for k in ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h", "omega"):
+        assert np.array_equal(sr[k], sg[k]), k
+
+
+def test_rung_criteria_and_assignment(orc):
+    """At the start: dt_cfl is the global step's per-particle CFL value (its
+    minimum is the global CFL dt, Eq. 31); dt_acc = c_acc sqrt(h rho / |grad
+    p|) for a linear pressure field (exact gradients away from the periodic
+    seam, limiter off); the rungs are rung_select of the two, limited."""
+    n = 12
+    w = dict(W.lattice_wave(n, jitter=0.0))
+    eps = 0.3
+    x = w["x"]
+    p = 1.0 + eps * x
+    N = x.size
+    m = np.full(N, 1.0 / n ** 3)
+    w["m"] = m
+    w["px"], w["py"], w["pz"] = 0.0 * m, 0.0 * m, 0.0 * m
+    w["U"] = p * m / (w["gamma"] - 1.0)   # volume = 1 / n^3 = m at rho = 1
+    w["E"] = w["U"].copy()
+    co = orc.config(gamma=w["gamma"], limiter=False)
+    _, _, i0 = orc.step(co, w, -1.0)
+    c_acc = 0.2
+    sr, rung, ir = orc.step_rungs(co, w, 4.0 * i0["dt"], c_acc=c_acc)
+    assert ir["status"] == 0
+    assert ir["dt_cfl"].min() == pytest.approx(i0["dt"], rel=1e-14)
+    # interior: every neighbour within h on the same side of the seam
+    h0 = orc.step(co, w, -1.0)[0]["h"]   # (the step's solved h at the start)
+    inner = (x > 1.5 * h0.max()) & (x < 1.0 - 1.5 * h0.max())
+    assert inner.sum() > N // 3
+    # p_i = U_i (gamma - 1) / omega_i and rho_i = m_i / omega_i with the
+    # lattice's uniform omega, so |grad p| / rho = eps exactly
+    want = c_acc * np.sqrt(h0 / eps)
+    assert np.allclose(ir["dt_acc"][inner], want[inner], rtol=1e-9, atol=0)
+    r0 = np.array([orc.rung_select(a, b, 4.0 * i0["dt"], 12)[0]
+                   for a, b in zip(ir["dt_cfl"], ir["dt_acc"])], dtype=np.int32)
+    pairs = []
+    L = w["L"]
+    for i in range(N):
+        d = np.stack([x - x[i], w["y"] - w["y"][i], w["z"] - w["z"][i]], 1)
+        d -= np.round(d / L) * L
+        r2 = (d[:, 0] ** 2 + d[:, 1] ** 2) + d[:, 2] ** 2
+        hm = np.maximum(h0, h0[i])
+        for j in np.nonzero((r2 < hm * hm) & (np.arange(N) > i))[0]:
+            pairs.append((i, j))
+    limited, _ = orc.rung_limit(np.array(pairs), r0)
+    assert np.array_equal(rung, limited)
+    assert len(set(rung.tolist())) >= 2
+
+
+def test_rung_step_conserves_and_counts(orc):
+    """Several rungs (Sod tube, dt0 = 8 CFL steps): mass, momentum and energy
+    are conserved to rounding (every face applies min(dt_i, dt_j) to both
+    sides); each particle takes 2^r_i steps."""
+    w = W.sod(8)
+    co = orc.config(gamma=w["gamma"])
+    _, _, i0 = orc.step(co, w, -1.0)
+    sr, rung, ir = orc.step_rungs(co, w, 8.0 * i0["dt"], c_acc=0.2)
+    assert ir["status"] == 0
+    assert len(set(rung.tolist())) >= 2 and ir["substeps"] == 2 ** ir["rung_max"]
+    assert ir["active_steps"] == int(np.sum(2 ** rung.astype(np.int64)))
+    for k in ("m", "E"):
+        assert abs(math.fsum(sr[k]) - math.fsum(w[k])) < 1e-13 * math.fsum(np.abs(w[k]))
+    scale = math.fsum(w["m"] * (np.abs(w["px"] / w["m"]) + np.sqrt(w["gamma"] * (w["gamma"] - 1)
+                                                                   * w["U"] / w["m"])))
+    for k in ("px", "py", "pz"):
+        assert abs(math.fsum(sr[k]) - math.fsum(w[k])) < 1e-13 * scale, k
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_rung_steps_follow_the_sod_solution(orc, scheme):
+    """A gamma = 1.4 Sod tube run with individual timesteps (base steps of
+    four CFL steps) stays as close to the exact solution as the global
+    CFL-stepped run over the same time."""
+    gamma, t_end = 1.4, 0.1
+    n = 24
+    a = 1.0 / n
+    i, j, k = np.meshgrid(np.arange(2 * n), np.arange(4), np.arange(4), indexing="ij")
+    x, y, z = (i.ravel() + 0.5) * a, (j.ravel() + 0.5) * a, (k.ravel() + 0.5) * a
+    left = x < 1.0
+    rho = np.where(left, 1.0, 0.25)
+    p = np.where(left, 1.0, 0.1795)
+    m = rho * a ** 3
+    U = p * a ** 3 / (gamma - 1.0)
+    zero = 0.0 * m
+    w = dict(x=x, y=y, z=z, m=m, px=zero, py=zero, pz=zero, E=U.copy(), U=U,
+             h=np.full(x.size, 2.0 * a), L=np.array([2.0, 4 * a, 4 * a]), gamma=gamma)
+    co = orc.config(gamma=gamma, scheme=scheme)
+    r = orc.riemann_star(1.0, 0.0, 1.0, 0.25, 0.0, 0.1795, gamma)
+
+    def l1(s, t):
+        sel = (s["x"] > 0.6) & (s["x"] < 1.4)
+        ex = np.array([orc.riemann_sample(1.0, -(xi - 1.0) / t, 1.0, 0.25, -(xi - 1.0) / t,
+                                          0.1795, gamma, r["p"], r["u"] - (xi - 1.0) / t)[0]
+                       for xi in s["x"][sel]])
+        return float(np.mean(np.abs(s["m"][sel] / s["omega"][sel] - ex)))
+
+    errs, rungs = {}, set()
+    for mode in ("global", "rungs"):
+        s, t = dict(w), 0.0
+        while t < t_end * (1 - 1e-12):
+            _, _, i0 = orc.step(co, s, -1.0)
+            if mode == "global":
+                dt = min(i0["dt"], t_end - t)
+                s, _, info = orc.step(co, s, dt)
+            else:
+                dt = min(4.0 * i0["dt"], t_end - t)
+                s, rung, info = orc.step_rungs(co, s, dt, c_acc=0.2)
+                rungs |= set(rung.tolist())
+            assert info["status"] == 0
+            t += dt
+        # volumes at the final positions
+        s["omega"] = orc.step(co, s, 1e-300)[0]["omega"]
+        errs[mode] = l1(s, t)
+    assert len(rungs) >= 2, rungs
+    assert errs["rungs"] < 1.3 * errs["global"] + 2e-3, errs
+    assert errs["rungs"] < 0.06, errs
