@@ -109,6 +109,9 @@ typedef struct {
                             to its kinetic or gravitational energy (0: off) */
     double alpha2;       /* entropy route when U < alpha2 (E_kin^max + U) (1/1000) */
     double alpha3;       /* ... or when U < alpha3 E_grav (1/1000) */
+    double c_acc;        /* hydro_step_rungs: acceleration timestep factor,
+                            dt_acc = c_acc sqrt(h / |a|) (§2.3.10; 0.2) */
+    int max_rung;        /* hydro_step_rungs: deepest rung (12, at most 20) */
 } hydro_config;
 
 /* Caller-owned particle state, caller order, all device pointers, n each.
@@ -166,6 +169,11 @@ typedef struct {
                                  failed, this context runs host-driven from now on */
     float learned_probe_ms[2];/* learned_guess = 1: flux-stage times of the last plain
                                  and learned probe calls (CUDA events; 0 before) */
+    /* hydro_step_rungs (0 after hydro_step): */
+    int rung_max;             /* the deepest rung of the base step */
+    int64_t substeps;         /* 2^rung_max */
+    int64_t active_steps;     /* particle steps taken, sum_i 2^rung_i */
+    int64_t rung_capped;      /* particles whose criteria asked for more than max_rung */
 } hydro_stats;
 
 /* Defaults described above.  Always succeeds. */
@@ -240,6 +248,37 @@ int hydro_fluxes(hydro_ctx *ctx, const hydro_particles *p, const double *B,
  * stats (host, optional): filled after a stream synchronisation. */
 int hydro_step(hydro_ctx *ctx, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream);
+
+/* One base step dt0 > 0 with individual timesteps (§2.3.4 power-of-two
+ * hierarchy, §2.3.10 criteria).  At its start every particle is
+ * synchronised: neighbours, density, guard, primitives and gradients as in
+ * hydro_step; then its rung r_i, the smallest r >= 0 (at most max_rung)
+ * with min(dt_CFL,i, dt_acc,i) > 2^-r dt0, where dt_CFL is Eq. 31's
+ * per-particle value and dt_acc = c_acc sqrt(h_i / |a_i|) with
+ * a_i = -grad p_i / rho_i (the limited pressure gradient of the face
+ * reconstruction); then the neighbour limiter |r_i - r_j| <= 2 over the
+ * flux pairs (rungs only rise, to the least such assignment).  Rungs stay
+ * fixed over the base step, which runs 2^rmax sub-steps of dt0 2^-rmax.
+ * At sub-step k the particles with k divisible by 2^(rmax - r_i) start a
+ * step of dt_i = dt0 2^-r_i: their neighbours, density, guard,
+ * primitives and gradients are recomputed at the current positions; the
+ * others keep those of their last start (h, omega, primitives, B and
+ * gradients as they were).  Every flux pair with an active particle
+ * exchanges c = dt_ij |A_ij| F with dt_ij = min(dt_i, dt_j), subtracted
+ * from one particle and added to the other (Springel 2010 §7.2); each
+ * side's state is predicted (Eq. 16's half step) over the time since its
+ * start plus dt_ij / 2.  Every particle then takes what it received (U by
+ * Eq. 24 with its current velocity) and drifts by the sub-step with the mean
+ * of its velocities before and after.  rung (device, n int32, caller order,
+ * out): the rungs used.  Host-driven (not a captured graph); plain Riemann
+ * guess (learned_guess is not used); an external acceleration
+ * (hydro_set_gravity) or the entropy switch give HYDRO_ESTATE.  On an error
+ * the state holds the sub-steps completed before it.  stats (host,
+ * optional): counters summed over the sub-steps, totals before the first
+ * and after the last, dt = dt0, dt_next = the smallest CFL dt at the start,
+ * rung_max, substeps, active_steps, rung_capped. */
+int hydro_step_rungs(hydro_ctx *ctx, hydro_particles *p, double dt0, int32_t *rung,
+                     hydro_stats *stats, hydro_stream stream);
 
 /* Read (synchronising the stream) and clear the device status word:
  * returns the first error recorded by any kernel since the last read. */

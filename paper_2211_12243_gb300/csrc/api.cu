@@ -48,6 +48,7 @@ bool valid_config(const hydro_config *c) {
     if (c->entropy_switch != 0 && c->entropy_switch != 1) return false;
     if (!(c->alpha2 >= 0.0) || !(c->alpha3 >= 0.0) || !isfinite(c->alpha2) || !isfinite(c->alpha3))
         return false;
+    if (!(c->c_acc > 0.0) || c->max_rung < 0 || c->max_rung > 20) return false;
     return true;
 }
 
@@ -299,6 +300,8 @@ void hydro_config_default(hydro_config *c) {
     c->entropy_switch = 0;
     c->alpha2 = 1e-3;
     c->alpha3 = 1e-3;
+    c->c_acc = 0.2;
+    c->max_rung = 12;
 }
 
 int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
@@ -505,6 +508,137 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     if (stats) memset(stats, 0, sizeof(*stats));
     const int rc = step_impl(c, p, dt, stats, stream);
     // a step that stopped early reports its error in the statistics too
+    if (stats && rc != HYDRO_OK && stats->status == HYDRO_OK) stats->status = rc;
+    return rc;
+}
+
+// individual timesteps: the base step of 2^rmax sub-steps (see hydro.h)
+static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *rung,
+                      hydro_stats *stats, cudaStream_t st) {
+    if (!c || !c->have_plan) return HYDRO_EINVAL;
+    if (!valid_particles(c, p, true) || !rung || !(dt0 > 0.0) || !isfinite(dt0))
+        return HYDRO_EINVAL;
+    if (c->grav || c->cfg.entropy_switch) return HYDRO_ESTATE;
+    const int64_t n = p->n;
+    API_CUDA(ensure_state(c, n));
+    API_CUDA(c->d_rung_c.ensure(n));
+    API_CUDA(c->d_kstart_c.ensure(n));
+    API_CUDA(c->d_rung_s.ensure(n));
+    API_CUDA(c->d_ract.ensure(n));
+    API_CUDA(c->d_toff.ensure(n));
+    API_CUDA(c->d_rec_store.ensure((size_t)n * REC));
+    API_CUDA(cudaMemsetAsync(c->d_rung_c.get(), 0, n * sizeof(int32_t), st));
+    API_CUDA(cudaMemsetAsync(c->d_kstart_c.get(), 0, n * sizeof(int32_t), st));
+    c->rung_live = true;
+    c->rung_dt0 = dt0;
+    c->learned_decision = 0;   // plain Riemann guess
+    c->grav_live = c->ent_live = false;
+    hydro_stats S;
+    memset(&S, 0, sizeof(S));
+    S.dt = dt0;
+    int rmax = 0, status = HYDRO_OK;
+    int64_t K = 1;
+    double dtmin = dt0;
+    for (int64_t k = 0; k < K; k++) {
+        API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
+        int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
+        if (rc) return rc;
+        // omega of the particles that do not start (the others' is solved)
+        API_CUDA(gather_from_caller(c->d_perm.get(), p->omega, n, 1, c->d_omsorted.get(), n, st));
+        API_CUDA(rung_prep(c, k, rmax, dtmin, st));
+        if (k > 0) {
+            API_CUDA(rung_records(c, false, st));
+            API_CUDA(rung_fill(c, st));
+        } else {
+            API_CUDA(reset_guard(c, st));
+        }
+        int rebuilds = 0, rounds = 0, ncond_fail = 0;
+        bool first = true;
+        for (;;) {
+            rc = density_all(c, p, !first || k > 0, rebuilds, st);
+            if (rc) return rc;
+            API_CUDA(run_primitives(c, st, !first));
+            API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
+            API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+            API_CUDA(cudaStreamSynchronize(st));
+            first = false;
+            if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
+            API_CUDA(guard_grow(c, st));
+            rounds++;
+        }
+        if (k == 0) {
+            // rungs (§2.3.10): criteria, then the limiter to its fixed point
+            API_CUDA(rung_assign(c, dt0, st));
+            for (int sweep = 0;; sweep++) {
+                // each sweep carries a raise at least one hop further and a
+                // raise travels at most max_rung / 2 + 1 hops
+                if (sweep > 2 * c->cfg.max_rung + 8) return HYDRO_ESTATE;
+                API_CUDA(rung_limit_sweep(c, st));
+                int changed = 0;
+                API_CUDA(cudaMemcpyAsync(&changed, &c->d_cnt->rung_changed, sizeof(int),
+                                         cudaMemcpyDeviceToHost, st));
+                API_CUDA(cudaStreamSynchronize(st));
+                if (!changed) break;
+            }
+            API_CUDA(rung_scatter(c, st));
+            int rinfo[2] = {0, 0};
+            API_CUDA(cudaMemcpyAsync(rinfo, &c->d_cnt->rung_max, 2 * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+            API_CUDA(cudaStreamSynchronize(st));
+            rmax = rinfo[0];
+            S.rung_capped = rinfo[1];
+            K = (int64_t)1 << rmax;
+            dtmin = ldexp(dt0, -rmax);
+            // every particle starts at sub-step 0 (counted once)
+            API_CUDA(cudaMemsetAsync(&c->d_cnt->rung_active, 0, sizeof(unsigned long long), st));
+            API_CUDA(rung_prep(c, 0, rmax, dtmin, st));
+        }
+        API_CUDA(rung_records(c, true, st));
+        API_CUDA(run_fluxes(c, dtmin, nullptr, st));
+        API_CUDA(run_update(c, p, dtmin, nullptr, false, st));
+        if (stats) API_CUDA(run_update_sums(c, st));
+        API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        const DevCounters &H = *c->h_cnt;
+        if (k == 0) {
+            double dtc;
+            memcpy(&dtc, &H.dt_min_bits, sizeof(double));
+            S.dt_next = dtc;
+            for (int q = 0; q < 5; q++) (q == 0 ? S.mass[0] : q < 4 ? S.mom[0][q - 1] : S.energy[0]) = H.sums[0][q];
+        }
+        for (int q = 0; q < 5; q++) (q == 0 ? S.mass[1] : q < 4 ? S.mom[1][q - 1] : S.energy[1]) = H.sums[1][q];
+        S.grad_pairs += (int64_t)H.grad_pairs;
+        S.flux_pairs += (int64_t)H.flux_pairs;
+        S.newton_iters += (int64_t)H.newton_iters;
+        S.vacuum_faces += (int64_t)H.vacuum;
+        S.first_order_faces += (int64_t)H.first_order;
+        S.active_steps += (int64_t)H.rung_active;
+        S.ngb_rounds = std::max(S.ngb_rounds, rounds);
+        S.ncond_fail += ncond_fail;
+        S.list_rebuilds += rebuilds;
+        int sk = flags_to_status(H.flags);
+        if (ncond_fail && sk == HYDRO_OK) sk = HYDRO_ENCOND;
+        if (status == HYDRO_OK) status = sk;
+        if (sk != HYDRO_OK && sk != HYDRO_ENCOND && sk != HYDRO_ENOCONV_H) break;
+    }
+    API_CUDA(cudaMemcpyAsync(rung, c->d_rung_c.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    S.status = status;
+    S.rung_max = rmax;
+    S.substeps = K;
+    if (stats) *stats = S;
+    return status;
+}
+
+int hydro_step_rungs(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *rung,
+                     hydro_stats *stats, hydro_stream stream) {
+    if (stats) memset(stats, 0, sizeof(*stats));
+    const int rc = rungs_impl(c, p, dt0, rung, stats, (cudaStream_t)stream);
+    if (c) {
+        c->rung_live = false;
+        c->learned_decision = -1;
+    }
     if (stats && rc != HYDRO_OK && stats->status == HYDRO_OK) stats->status = rc;
     return rc;
 }

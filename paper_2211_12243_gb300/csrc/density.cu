@@ -447,10 +447,11 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
     if (c->cfg.precision == HYDRO_MIXED) {
         // 64-bit fixed-point copies for the refinement step (xs.. are sorted)
         // (positions are fixed within a step: the solves of selected
-        // particles reuse the copies of the step's first, full solve)
+        // particles reuse the copies of the step's first, full solve; the
+        // sub-steps of individual timesteps move every particle)
         HYD_CUDA(c->d_q64.ensure((size_t)3 * n));
         uint64_t *q64 = c->d_q64.get();
-        if (!only_active) {
+        if (!only_active || c->rung_live) {
             k_fixed64<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_xs.get(), c->d_ys.get(),
                                                          c->d_zs.get(), c->d_pbox.get(),
                                                          c->d_boxes.get(), q64, q64 + n, q64 + 2 * n);

@@ -69,6 +69,15 @@ struct FluxArgs {
     // off); A is the records' R_PAD slot.  A face whose mass flux c_m
     // leaves the owner carries c_m A_owner, else c_m A_partner
     double *dS;
+    // individual timesteps (§2.3.4; NULL: one global dt): per sorted
+    // particle its rung, the time since its state was taken and whether it
+    // starts a step now.  A face with an active particle exchanges over
+    // dt_ij = dt0 2^-max(r_i, r_j) = min(dt_i, dt_j), each side predicted
+    // over toff + dt_ij / 2; faces of two inactive particles are skipped
+    const int32_t *rung;
+    const double *toff;
+    const uint8_t *ract;
+    double dt0;
 };
 
 template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
@@ -164,9 +173,11 @@ struct FaceState {
 };
 
 // face vector, extrapolated and limited states; false when A_ij = 0 (no flux)
+// hl, hr: the times the predictor advances the owner and partner states
+// over (dt / 2 for one global dt)
 template <typename R>
 __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, const R *ri,
-                                           const R *rj, const R d[3], R r, R dt,
+                                           const R *rj, const R d[3], R r, R dt, R hl, R hr,
                                            FaceState<R> &st, FaceStats &fs) {
     const R pi = R(3.14159265358979323846);
     const R hi_ = ri[R_H], hj = rj[R_H];
@@ -211,19 +222,18 @@ __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, 
     }
     const R g = K.g;
     if (a.time_extrap) {
-        const R hdt = R(0.5) * dt;
         R divi = Gi[3] + Gi[7] + Gi[11];
         R divj = Gj[3] + Gj[7] + Gj[11];
-        Lf[0] -= hdt * ri[R_RHO] * divi;
-        Rf[0] -= hdt * rj[R_RHO] * divj;
-        const R iri = div_(hdt, ri[R_RHO]), irj = div_(hdt, rj[R_RHO]);
+        Lf[0] -= hl * ri[R_RHO] * divi;
+        Rf[0] -= hr * rj[R_RHO] * divj;
+        const R iri = div_(hl, ri[R_RHO]), irj = div_(hr, rj[R_RHO]);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             Lf[1 + q] -= Gi[12 + q] * iri;
             Rf[1 + q] -= Gj[12 + q] * irj;
         }
-        Lf[4] -= hdt * g * ri[R_P] * divi;
-        Rf[4] -= hdt * g * rj[R_P] * divj;
+        Lf[4] -= hl * g * ri[R_P] * divi;
+        Rf[4] -= hr * g * rj[R_P] * divj;
     }
     if (!(Lf[0] > R(0) && Lf[4] > R(0) && Rf[0] > R(0) && Rf[4] > R(0))) {
 #pragma unroll
@@ -530,7 +540,15 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 R d[3], r2;
                 rec_sep(ri, rj, bx, d, r2);
                 FaceState<R> st;
-                if (face_state<R>(a, K, ri, rj, d, sqrt_(r2), dt, st, fs)) {
+                R dtf = dt, hl = R(0.5) * dt, hr = hl;
+                if (a.rung) {
+                    const int64_t so = f + ol;
+                    const double dtd = ldexp(a.dt0, -max(a.rung[so], a.rung[j]));
+                    dtf = (R)dtd;
+                    hl = (R)(a.toff[so] + 0.5 * dtd);
+                    hr = (R)(a.toff[j] + 0.5 * dtd);
+                }
+                if (face_state<R>(a, K, ri, rj, d, sqrt_(r2), dtf, hl, hr, st, fs)) {
                     bool deferred = false;
                     if constexpr (DEFER) {
                         // hard faces are queued for the learned-guess pass,
@@ -609,6 +627,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 R d[3], r2;
                 rec_sep(own4, rc4, bx, d, r2);
                 if (mem(r2, j)) has = (j > s) || !member_j(r2, rc4[R_H], a, s, j, bx);
+                if (has && a.ract && !a.ract[s] && !a.ract[j]) has = false;
             }
             jc = jn;
             jn = jnn;

@@ -211,6 +211,10 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.recf = c->d_recf.get();
     a.dM = c->grav_live ? c->d_dM.get() : nullptr;
     a.dS = ent_flux ? c->d_dS.get() : nullptr;
+    a.rung = c->rung_live ? c->d_rung_s.get() : nullptr;
+    a.toff = c->rung_live ? c->d_toff.get() : nullptr;
+    a.ract = c->rung_live ? c->d_ract.get() : nullptr;
+    a.dt0 = c->rung_dt0;
     // the adaptive learned path times its probes with the same events
     const bool adapt = c->cfg.learned_guess == 1 && c->cfg.precision == HYDRO_MIXED &&
                        c->cfg.riemann == HYDRO_RIEMANN_EXACT && c->have_mlp;

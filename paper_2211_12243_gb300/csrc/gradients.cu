@@ -36,6 +36,7 @@ struct GradArgs {
     double *dt_part;                     // per-particle CFL dt (+inf: no signal)
     int32_t *npair;                      // per-particle gradient pairs
     DevCounters *cnt;
+    const uint8_t *ract;                 // individual timesteps: only these (NULL: all)
 };
 
 template <typename R>
@@ -67,7 +68,7 @@ template <typename R, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int mypairs = 0;
-    if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO))) {
+    if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO)) && (!a.ract || a.ract[s])) {
         const Box bx = a.boxes[a.pbox[s]];
         R ri[10];
         load10<R>(rec + s * REC, ri);
@@ -251,6 +252,10 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
             a.active[s] |= ACT_NCOND;
             atomicAdd(&a.cnt->ncond_fail, 1);
         }
+    } else if (s < a.n && a.ract && !a.ract[s]) {
+        // not starting a step: no pairs, no CFL limit in this sub-step
+        a.dt_part[s] = INFINITY;
+        a.npair[s] = 0;
     }
 }
 
@@ -300,10 +305,11 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
                              const double *__restrict__ om, const double *__restrict__ h,
                              double gm1, double alpha1, const uint8_t *__restrict__ active,
                              bool only_guard, const double *__restrict__ agrav, EntArgs ent,
-                             R *__restrict__ rec) {
+                             const uint8_t *__restrict__ ract, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     if (only_guard && !(active[s] & ACT_GUARD)) return;
+    if (ract && !ract[s]) return;   // (individual timesteps: its record is kept)
     double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
     double E = Q[4 * n + s], U = Q[5 * n + s];
     double w = om[s];
@@ -446,6 +452,7 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
     const uint8_t *act = c->d_active.get();
     const double *ag = c->grav_live ? c->d_agrav.get() : nullptr;
     const bool mixed = c->cfg.precision == HYDRO_MIXED;
+    const uint8_t *ract = c->rung_live ? c->d_ract.get() : nullptr;
     EntArgs ent = {};
     if (c->ent_live) {
         ent.A0 = c->d_A0.get();
@@ -472,12 +479,12 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
         k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                               c->d_hsorted.get(), gm1,
                                                               c->cfg.alpha1, act, only_guard, ag,
-                                                              ent, c->d_recf.get());
+                                                              ent, ract, c->d_recf.get());
     else
         k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
                                                                c->cfg.alpha1, act, only_guard, ag,
-                                                               ent, c->d_recd.get());
+                                                               ent, ract, c->d_recd.get());
     return launch_check();
 }
 
@@ -528,6 +535,7 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.dt_part = c->d_vsig_dt.get();
     a.npair = c->d_gpairs.get();
     a.cnt = c->d_cnt;
+    a.ract = c->rung_live ? c->d_ract.get() : nullptr;
     if (only_redo) HYD_CUDA(mark_reverse(c, st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));

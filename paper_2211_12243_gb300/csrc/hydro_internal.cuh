@@ -92,6 +92,11 @@ struct DevCounters {
     int abort;                        // the step cannot finish on the device: no update
     int ovf_first;                    // buckets of the first list pass with long lists
     int nguard;                       // particles whose N_NGB grew in this guard round
+    // rung assignment (hydro_step_rungs)
+    int rung_changed;                 // the limiter raised a rung in this sweep
+    int rung_max;                     // the deepest rung
+    int rung_capped;                  // particles the criteria wanted beyond max_rung
+    unsigned long long rung_active;   // particles starting a step in this sub-step
 };
 
 // bucket tree topology (host plan, mirrored on the device)
@@ -194,6 +199,18 @@ struct hydro_ctx {
     double *entA = nullptr;
     bool ent_live = false;            // d_A0 holds this step's sorted copy (hydro_step only)
     hyd::DevBuf<double> d_A0, d_A1, d_ekmax, d_dS;   // n each
+
+    // individual timesteps (hydro_step_rungs): rungs and the sub-step at
+    // which each particle's current step started (caller order); per sorted
+    // particle its rung, whether it starts a step at this sub-step and the
+    // time since its state was taken; the records of every particle at its
+    // last start (caller order, REC scalars of the precision's type)
+    bool rung_live = false;
+    double rung_dt0 = 0.0;
+    hyd::DevBuf<int32_t> d_rung_c, d_kstart_c, d_rung_s;
+    hyd::DevBuf<uint8_t> d_ract;
+    hyd::DevBuf<double> d_toff;
+    hyd::DevBuf<double> d_rec_store;  // n REC doubles (float records use half)
 
     // reductions
     hyd::DevBuf<double> d_partials;
@@ -328,6 +345,21 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard = false);
 cudaError_t gather_gravity(hydro_ctx *c, stream_t st);
 // the caller's entropic function into sorted order (no-op with the switch off)
 cudaError_t gather_entropy(hydro_ctx *c, stream_t st);
+
+// rungs.cu (individual timesteps)
+// sorted rung, "starts a step now" and time since the state was taken at
+// sub-step k of 2^rmax (the starting particles' start moves to k)
+cudaError_t rung_prep(hydro_ctx *c, int64_t k, int rmax, double dtmin, stream_t st);
+// N_NGB restarted and the density solve flag for the starting particles
+cudaError_t rung_fill(hydro_ctx *c, stream_t st);
+// save: the starting particles' records to the caller-order store; load:
+// the others' records (all but the positions) from it
+cudaError_t rung_records(hydro_ctx *c, bool save, stream_t st);
+// rung from the two criteria (gradient stage outputs), then limiter sweeps
+cudaError_t rung_assign(hydro_ctx *c, double dt0, stream_t st);
+cudaError_t rung_limit_sweep(hydro_ctx *c, stream_t st);
+// sorted rungs to the caller-order master copy (and the deepest rung)
+cudaError_t rung_scatter(hydro_ctx *c, stream_t st);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,

@@ -47,6 +47,7 @@ class Config(C.Structure):
         ("h_tol", C.c_double), ("p_tol", C.c_double), ("max_h_iter", C.c_int),
         ("max_newton", C.c_int), ("search_margin", C.c_double), ("graph", C.c_int),
         ("entropy_switch", C.c_int), ("alpha2", C.c_double), ("alpha3", C.c_double),
+        ("c_acc", C.c_double), ("max_rung", C.c_int),
     ]
 
 
@@ -72,6 +73,8 @@ class Stats(C.Structure):
         ("ms_density", C.c_float), ("ms_gradients", C.c_float), ("ms_fluxes", C.c_float),
         ("ms_update", C.c_float), ("ms_flux_kernel", C.c_float), ("ms_hard_faces", C.c_float),
         ("graph", C.c_int), ("learned_probe_ms", C.c_float * 2),
+        ("rung_max", C.c_int), ("substeps", C.c_int64), ("active_steps", C.c_int64),
+        ("rung_capped", C.c_int64),
     ]
 
     def as_dict(self):
@@ -107,7 +110,7 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
            "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity",
-           "hydro_set_entropy"]
+           "hydro_set_entropy", "hydro_step_rungs"]
 
 
 def _load():
@@ -131,6 +134,7 @@ def _load():
         L.hydro_gradients.argtypes = [vp, P(Particles), vp, vp, vp, vp, vp]
         L.hydro_fluxes.argtypes = [vp, P(Particles), vp, vp, vp, C.c_double, vp, vp]
         L.hydro_step.argtypes = [vp, P(Particles), C.c_double, P(Stats), vp]
+        L.hydro_step_rungs.argtypes = [vp, P(Particles), C.c_double, vp, P(Stats), vp]
         L.hydro_sync_status.argtypes = [vp, vp]
         L.hydro_get_stats.argtypes = [vp, P(Stats), vp]
         L.hydro_mlp_load.argtypes = [vp, vp, C.c_size_t]
@@ -334,6 +338,17 @@ class Hydro:
                                  _stream(stream))
         if rc and check:
             raise HydroError(rc, "hydro_step")
+        return s.as_dict() if stats else rc
+
+    def step_rungs(self, st, dt0, rung, stats=True, stream=None, check=True):
+        """One base step dt0 with individual timesteps (hydro_step_rungs);
+        rung: CUDA int32 tensor [n] receiving the rungs used."""
+        p = particles_struct(st)
+        s = Stats() if stats else None
+        rc = self.lib.hydro_step_rungs(self.h, C.byref(p), float(dt0), _ptr(rung),
+                                       C.byref(s) if stats else None, _stream(stream))
+        if rc and check:
+            raise HydroError(rc, "hydro_step_rungs")
         return s.as_dict() if stats else rc
 
     def autotune(self, st, stream=None):
