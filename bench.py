@@ -77,6 +77,14 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=None,
                     help="size of the CPU sample (Sod 40, Sedov 32, log-normal 2^15)")
     ap.add_argument("--cpu-reps", type=int, default=6)
+    ap.add_argument("--gravity", action="store_true",
+                    help="step with a seeded external acceleration field (hydro_set_gravity)")
+    ap.add_argument("--entropy", action="store_true",
+                    help="step with the entropy switch on (hydro_set_entropy)")
+    ap.add_argument("--rungs", type=float, default=None, metavar="K",
+                    help="time base steps of individual timesteps (hydro_step_rungs) with "
+                         "dt0 = K times the CFL dt of the initial state; value = pairs over "
+                         "the whole base step")
     return ap.parse_args()
 
 
@@ -304,6 +312,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.rungs is not None:
+        return bench_rungs(args)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -337,6 +347,16 @@ def main():
     H.set_boxes(*boxes_of(hydro, w))
     H.reserve(n, 96)
     st = hydro.to_device(w)
+    acc = None
+    if args.gravity:
+        # a seeded acceleration field of order the sound speed squared over the box
+        g = np.random.default_rng(20221122 + 7).normal(0.0, 0.1, (n, 3))
+        acc = torch.as_tensor(g, device="cuda").contiguous()
+        H.set_gravity(acc)
+    if args.entropy:
+        H.set_config(entropy_switch=1)
+        st["A"] = torch.zeros(n, dtype=torch.float64, device="cuda")   # unset: set by the first step
+        H.set_entropy(st["A"])
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
@@ -534,7 +554,8 @@ def main():
                    "pairs_per_step": r["pairs"] / args.steps,
                    "grad_pairs": last["grad_pairs"], "flux_pairs": last["flux_pairs"],
                    "newton_iters_per_face": iters / max(faces, 1),
-                   "learned_guess": learned},
+                   "learned_guess": learned,
+                   "gravity": bool(args.gravity), "entropy_switch": bool(args.entropy)},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
         "clocks": clocks, "plain_fp64": fp64, "mixed_plain_guess": plain_guess,
         "stage_ms": {k: last[k] for k in ("ms_neighbours", "ms_density", "ms_gradients",
@@ -557,6 +578,97 @@ def main():
     return 0
 
 
+def bench_rungs(args):
+    """Individual timesteps: base steps of hydro_step_rungs, each from the
+    initial state (dt0 = K CFL steps of it), L2 flushed before each."""
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2211_12243_gb300 import build, hydro
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    kind = args.workload
+    w, wname = make_workload(kind, args.n, seed=rank)
+    n = w["x"].size
+    riemann = args.riemann or ("hllc" if kind == "wave" else "exact")
+    cfg = hydro.default_config(gamma=w["gamma"], scheme=args.scheme, riemann=riemann,
+                               precision=args.precision, search_margin=1.15)
+    H = hydro.Hydro(cfg)
+    H.set_boxes(*boxes_of(hydro, w))
+    H.reserve(n, 96)
+    st = hydro.to_device(w)
+    # the initial state's converged h and its CFL dt (one untimed step on a copy)
+    tmp = {k: v.clone() for k, v in st.items()}
+    s0 = H.step(tmp, -1.0, check=False)
+    assert s0["status"] in (0, -5), s0
+    st["h"].copy_(tmp["h"])
+    del tmp
+    dt0 = args.rungs * s0["dt"]
+    saved = {k: v.clone() for k, v in st.items()}
+    rung = torch.zeros(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for k, v in saved.items():
+            st[k].copy_(v)
+        s = H.step_rungs(st, dt0, rung, check=False)
+        assert s["status"] in (0, -5), s
+    clk = ClockSampler(local)
+    clk.start()
+    ms, pairs, psteps, stats = 0.0, 0, 0, None
+    launches0 = hydro.kernel_launches()
+    for _ in range(args.steps):
+        for k, v in saved.items():
+            st[k].copy_(v)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = H.step_rungs(st, dt0, rung, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert stats["status"] in (0, -5), stats
+        ms += e0.elapsed_time(e1)
+        pairs += stats["grad_pairs"] + stats["flux_pairs"]
+        psteps += stats["active_steps"]
+    launches = hydro.kernel_launches() - launches0
+    clocks = clk.stop()
+    pairs_all, ms_max, _ = aggregate(world, pairs, ms, ms, "cuda")
+    hist = np.bincount(rung.cpu().numpy(), minlength=stats["rung_max"] + 1).tolist()
+    line = {
+        "metric": METRIC + " [individual timesteps: pairs over the whole base step]",
+        "value": pairs_all / (ms_max / 1000.0), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": wname, "particles": n, "variant": "hydro_step_rungs",
+                   "dt0_cfl_steps": args.rungs, "rung_histogram": hist,
+                   "rung_max": stats["rung_max"], "substeps": stats["substeps"],
+                   "particle_steps_per_base_step": psteps / args.steps,
+                   "pairs_per_base_step": pairs / args.steps,
+                   "precision": args.precision, "scheme": args.scheme, "riemann": riemann,
+                   "timed_steps": "each from the initial state",
+                   "l2": "flushed before every timed base step (256 MB write)"},
+        "particle_steps_per_s": psteps * world / (ms_max / 1000.0),
+        "gpu_launches": launches, "clocks": clocks, "roofline": None, "cpu_baseline": None,
+        "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 # Algorithmic arithmetic of one float face (counted from the face routine;
 # FMA = 2, each compare/min/max/select 1, sqrt/div/pow 1 each):
 # kernel weights 22, face vector 53, extrapolation 80, pairwise limiter 180,
@@ -568,10 +680,10 @@ FLOPS_PER_NEWTON = 38.0
 # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
-# of the current kernel on the Sod tube at n = 60 (181.9 MB for 6,385,500
+# of the current kernel on the Sod tube at n = 60 (182.2 MB for 6,385,500
 # faces, lists compacted by the density stage); a launch's traffic scales
 # with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = 28.49
+FLUX_TRAFFIC_BYTES_PER_FACE = 28.53
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -617,34 +617,40 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         int jn = 1 < cnt ? a.nbr_idx[o + 1] : 0;
         R rc4[4] = {R(0), R(0), R(0), R(0)};
         if (0 < cnt) load4<R>(rec + (int64_t)jc * REC, rc4);
-        for (int k = 0; k < maxc; k++) {
-            R rn4[4] = {R(0), R(0), R(0), R(0)};
-            if (k + 1 < cnt) load4<R>(rec + (int64_t)jn * REC, rn4);
-            const int jnn = k + 2 < cnt ? a.nbr_idx[o + k + 2] : 0;
-            bool has = false;
-            const int j = jc;
-            if (k < cnt && j != s) {
-                R d[3], r2;
-                rec_sep(own4, rc4, bx, d, r2);
-                if (mem(r2, j)) has = (j > s) || !member_j(r2, rc4[R_H], a, s, j, bx);
-                if (has && a.ract && !a.ract[s] && !a.ract[j]) has = false;
-            }
-            jc = jn;
-            jn = jnn;
+        // (one call site of solve: the face code is instantiated once, which
+        // keeps the kernel's instruction footprint small; the last pass
+        // drains the queue)
+        for (int k = 0; k < maxc || qn > 0; k++) {
+            if (k < maxc) {
+                R rn4[4] = {R(0), R(0), R(0), R(0)};
+                if (k + 1 < cnt) load4<R>(rec + (int64_t)jn * REC, rn4);
+                const int jnn = k + 2 < cnt ? a.nbr_idx[o + k + 2] : 0;
+                bool has = false;
+                const int j = jc;
+                if (k < cnt && j != s) {
+                    R d[3], r2;
+                    rec_sep(own4, rc4, bx, d, r2);
+                    if (mem(r2, j)) has = (j > s) || !member_j(r2, rc4[R_H], a, s, j, bx);
+                    if (has && a.ract && !a.ract[s] && !a.ract[j]) has = false;
+                }
+                jc = jn;
+                jn = jnn;
 #pragma unroll
-            for (int q = 0; q < 4; q++) rc4[q] = rn4[q];
-            unsigned m = __ballot_sync(0xffffffffu, has);
-            if (has) {
-                int pos = qn + __popc(m & lt);
-                sm.qj[pos] = j;
-                sm.qo[pos] = (uint8_t)lane;
+                for (int q = 0; q < 4; q++) rc4[q] = rn4[q];
+                unsigned m = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    int pos = qn + __popc(m & lt);
+                    sm.qj[pos] = j;
+                    sm.qo[pos] = (uint8_t)lane;
+                }
+                qn += __popc(m);
+                __syncwarp();
             }
-            qn += __popc(m);
-            __syncwarp();
-            if (qn >= 32) {
-                solve(32);
+            if (qn >= 32 || (k >= maxc && qn > 0)) {
+                const int nb = qn < 32 ? qn : 32;
+                solve(nb);
                 // move the remainder to the front
-                int rest = qn - 32;
+                int rest = qn - nb;
                 int tj = 0;
                 uint8_t to = 0;
                 if (lane < rest) { tj = sm.qj[32 + lane]; to = sm.qo[32 + lane]; }
@@ -654,7 +660,6 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 __syncwarp();
             }
         }
-        if (qn > 0) solve(qn);
         if constexpr (DEFER) {
             const int rest = hq.cnt;
             if (rest > 0) flush_hard(rest);

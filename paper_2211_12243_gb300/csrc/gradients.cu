@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) k_grad_reduce(int64_t n, const double *__
 struct EntArgs {
     const double *A0;      // entropic function at the start of the step (sorted)
     double *A1;            // the value the step uses (sorted out)
-    const double *ekmax;   // E_kin^max (sorted)
+    uint8_t *cand;         // 1: the energies did not give the pressure (sorted)
     double gamma, alpha2, alpha3;
 };
 
@@ -320,14 +320,11 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
         egrav = m * sqrt(ax * ax + ay * ay + az * az) * h[s];
     }
     R *r = rec + s * REC;
-    // the pressure route of §2.3.7: 0 total energy, 1 entropic function
-    // (p = A rho^gamma), 2 internal energy
+    // the pressure route of §2.3.7: 0 total energy, 2 internal energy; the
+    // entropy route (1) is taken over by k_entropy_route, which needs the
+    // neighbours' velocities this kernel writes
     auto route = [&](double ekin) -> int {
         if (U > alpha1 * (egrav + ekin) && E - ekin > 0.0) return 0;
-        if (ent.A0) {
-            const double A = ent.A0[s];
-            if (A > 0.0 && (U < ent.alpha2 * (ent.ekmax[s] + U) || U < ent.alpha3 * egrav)) return 1;
-        }
         return 2;
     };
     double pd = 0.0;   // the pressure in double (entropy switch only)
@@ -337,7 +334,7 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
         from = route(ekin);
         const double therm = from == 0 ? E - ekin : U;
         const double rho = m / w;
-        pd = from == 1 ? ent.A0[s] * pow(rho, ent.gamma) : therm * gm1 / w;
+        pd = therm * gm1 / w;
         r[R_H] = (R)h[s];
         r[R_RHO] = (R)rho;
         r[R_VX] = (R)(px / m);
@@ -358,58 +355,75 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
         r[R_VY] = (R)((float)py * imf);
         r[R_VZ] = (R)((float)pz * imf);
         r[R_OM] = (R)wf;
-        if (from == 1) {
-            pd = ent.A0[s] * pow(m / w, ent.gamma);
-            r[R_P] = (R)pd;
-        } else {
-            r[R_P] = (R)((float)therm * (float)gm1 / wf);
-            if (ent.A1) pd = therm * gm1 / w;
-        }
+        r[R_P] = (R)((float)therm * (float)gm1 / wf);
+        if (ent.A1) pd = therm * gm1 / w;
     }
     if (ent.A1) {
-        // A follows the pressure actually used: re-set where the energies gave it
-        const double A = from == 1 ? ent.A0[s] : pd / pow(m / w, ent.gamma);
+        // A follows the pressure the energies gave (k_entropy_route keeps A
+        // where it takes the entropy route instead)
+        const double A = pd / pow(m / w, ent.gamma);
         ent.A1[s] = A;
         r[R_PAD] = (R)A;
+        ent.cand[s] = from != 0;
     }
 }
 
-// E_kin^max,i = max_j (1/2) m_i |v_j - v_i|^2 over j != i with r_ij < h_i
-// (§2.3.7), over the particle's list at the solved h; velocities from the
-// conserved state in double
+// The entropy route of §2.3.7 for the particles the energies did not
+// claim (U <= alpha1 (E_grav + E_kin) or E - E_kin <= 0) and whose A is
+// set: p = A rho^gamma when U < alpha3 E_grav or U < alpha2 (E_kin^max + U),
+// E_kin^max = max_j (1/2) m_i |v_j - v_i|^2 over j != i with r_ij < h_i.
+// alpha2 (e + U) grows with e, so the walk of the particle's list stops at
+// the first neighbour whose e satisfies the test (then E_kin^max does);
+// velocities are the records' (written by k_primitives for every particle).
 template <typename R>
-__global__ void k_ekin_max(int64_t n, const int64_t *__restrict__ nbr_off,
-                           const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
-                           const double *__restrict__ xs, const double *__restrict__ ys,
-                           const double *__restrict__ zs, const double *__restrict__ h,
-                           const int32_t *__restrict__ pbox, const Box *__restrict__ boxes,
-                           const double *__restrict__ Q, const R *__restrict__ rec,
-                           const uint8_t *__restrict__ active, bool only_guard,
-                           double *__restrict__ out) {
+__global__ void k_entropy_route(int64_t n, const int64_t *__restrict__ nbr_off,
+                                const int32_t *__restrict__ nbr_cnt,
+                                const int32_t *__restrict__ nbr_idx, const double *__restrict__ xs,
+                                const double *__restrict__ ys, const double *__restrict__ zs,
+                                const double *__restrict__ h, const int32_t *__restrict__ pbox,
+                                const Box *__restrict__ boxes, const double *__restrict__ Q,
+                                const double *__restrict__ om, const double *__restrict__ agrav,
+                                const uint8_t *__restrict__ active, bool only_guard, EntArgs ent,
+                                R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     if (only_guard && !(active[s] & ACT_GUARD)) return;
-    const Box bx = boxes[pbox[s]];
-    Member mem;
-    mem.init(xs, ys, zs, s, h[s], bx);
-    const double mi = Q[s];
-    const double vx = Q[n + s] / mi, vy = Q[2 * n + s] / mi, vz = Q[3 * n + s] / mi;
-    const R *ri = rec + s * REC;
-    double best = 0.0;
-    const int64_t o = nbr_off[s];
-    const int c = nbr_cnt[s];
-    for (int k = 0; k < c; k++) {
-        const int j = nbr_idx[o + k];
-        if (j == s) continue;
-        R d[3], r2;
-        rec_sep(ri, rec + (int64_t)j * REC, bx, d, r2);
-        if (!mem(r2, j)) continue;
-        const double mj = Q[j];
-        const double dx = Q[n + j] / mj - vx, dy = Q[2 * n + j] / mj - vy, dz = Q[3 * n + j] / mj - vz;
-        const double e = 0.5 * mi * ((dx * dx + dy * dy) + dz * dz);
-        best = e > best ? e : best;
+    if (!ent.cand[s]) return;   // (k_primitives: the energies gave the pressure)
+    const double A = ent.A0[s];
+    if (!(A > 0.0)) return;
+    const double m = Q[s], U = Q[5 * n + s];
+    double egrav = 0.0;
+    if (agrav) {
+        const double ax = agrav[s], ay = agrav[n + s], az = agrav[2 * n + s];
+        egrav = m * sqrt(ax * ax + ay * ay + az * az) * h[s];
     }
-    out[s] = best;
+    R *ri = rec + s * REC;
+    bool cold = U < ent.alpha3 * egrav;
+    if (!cold) {
+        const Box bx = boxes[pbox[s]];
+        Member mem;
+        mem.init(xs, ys, zs, s, h[s], bx);
+        const double vx = (double)ri[R_VX], vy = (double)ri[R_VY], vz = (double)ri[R_VZ];
+        const int64_t o = nbr_off[s];
+        const int c = nbr_cnt[s];
+        for (int k = 0; k < c && !cold; k++) {
+            const int j = nbr_idx[o + k];
+            if (j == s) continue;
+            const R *rj = rec + (int64_t)j * REC;
+            R d[3], r2;
+            rec_sep(ri, rj, bx, d, r2);
+            if (!mem(r2, j)) continue;
+            const double dx = (double)rj[R_VX] - vx, dy = (double)rj[R_VY] - vy,
+                         dz = (double)rj[R_VZ] - vz;
+            const double e = 0.5 * m * ((dx * dx + dy * dy) + dz * dz);
+            cold = U < ent.alpha2 * (e + U);
+        }
+    }
+    if (cold) {
+        ri[R_P] = (R)(A * pow(m / om[s], ent.gamma));
+        ent.A1[s] = A;
+        ri[R_PAD] = (R)A;
+    }
 }
 
 // N_NGB *= grow for particles that failed the N_cond check; they (only)
@@ -457,23 +471,10 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
     if (c->ent_live) {
         ent.A0 = c->d_A0.get();
         ent.A1 = c->d_A1.get();
-        ent.ekmax = c->d_ekmax.get();
+        ent.cand = c->d_ecand.get();
         ent.gamma = c->cfg.gamma;
         ent.alpha2 = c->cfg.alpha2;
         ent.alpha3 = c->cfg.alpha3;
-        // E_kin^max over the lists at the solved h (velocities do not change
-        // in a guard round: only the re-solved particles' sets do)
-        if (mixed)
-            k_ekin_max<float><<<grid_for(n, 128), 128, 0, st>>>(
-                n, c->d_nbr_off.get(), c->d_nbr_cnt.get(), c->d_nbr_idx.get(), c->d_xs.get(),
-                c->d_ys.get(), c->d_zs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(),
-                c->d_Q.get(), c->d_recf.get(), act, only_guard, c->d_ekmax.get());
-        else
-            k_ekin_max<double><<<grid_for(n, 128), 128, 0, st>>>(
-                n, c->d_nbr_off.get(), c->d_nbr_cnt.get(), c->d_nbr_idx.get(), c->d_xs.get(),
-                c->d_ys.get(), c->d_zs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(),
-                c->d_Q.get(), c->d_recd.get(), act, only_guard, c->d_ekmax.get());
-        HYD_CUDA(launch_check());
     }
     if (mixed)
         k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
@@ -485,7 +486,23 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
                                                                c->d_hsorted.get(), gm1,
                                                                c->cfg.alpha1, act, only_guard, ag,
                                                                ent, ract, c->d_recd.get());
-    return launch_check();
+    HYD_CUDA(launch_check());
+    if (c->ent_live) {
+        // the entropy route for the particles the energies did not claim
+        // (in a guard round, of the re-solved particles: only their h moved)
+        if (mixed)
+            k_entropy_route<float><<<grid_for(n, 128), 128, 0, st>>>(
+                n, c->d_nbr_off.get(), c->d_nbr_cnt.get(), c->d_nbr_idx.get(), c->d_xs.get(),
+                c->d_ys.get(), c->d_zs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(),
+                c->d_Q.get(), c->d_omsorted.get(), ag, act, only_guard, ent, c->d_recf.get());
+        else
+            k_entropy_route<double><<<grid_for(n, 128), 128, 0, st>>>(
+                n, c->d_nbr_off.get(), c->d_nbr_cnt.get(), c->d_nbr_idx.get(), c->d_xs.get(),
+                c->d_ys.get(), c->d_zs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(),
+                c->d_Q.get(), c->d_omsorted.get(), ag, act, only_guard, ent, c->d_recd.get());
+        HYD_CUDA(launch_check());
+    }
+    return cudaSuccess;
 }
 
 cudaError_t gather_entropy(hydro_ctx *c, stream_t st) {
@@ -494,7 +511,7 @@ cudaError_t gather_entropy(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_A0.ensure(n));
     HYD_CUDA(c->d_A1.ensure(n));
-    HYD_CUDA(c->d_ekmax.ensure(n));
+    HYD_CUDA(c->d_ecand.ensure(n));
     HYD_CUDA(c->d_dS.ensure(n));
     return gather_from_caller(c->d_perm.get(), c->entA, n, 1, c->d_A0.get(), n, st);
 }

@@ -210,7 +210,7 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
     put(c->d_dM.get());
     put(c->entA);
     for (const void *q : {(const void *)c->d_A0.get(), (const void *)c->d_A1.get(),
-                          (const void *)c->d_ekmax.get(), (const void *)c->d_dS.get()})
+                          (const void *)c->d_ecand.get(), (const void *)c->d_dS.get()})
         put(q);
     k.push_back((unsigned long long)c->rec_cap);
     k.push_back((unsigned long long)c->rec_keep | ((unsigned long long)c->rec_hard_only << 32));

@@ -195,10 +195,12 @@ struct hydro_ctx {
     // entropy switch (§2.3.7): the caller's entropic function A (caller
     // order, rewritten by each step) or NULL; its sorted copy at the start
     // of the step; the value the step uses (re-set where the energies gave
-    // the pressure); E_kin^max; sum_j c_m,ij A_upwind
+    // the pressure); sum_j c_m,ij A_upwind; the particles the energies did
+    // not claim
     double *entA = nullptr;
     bool ent_live = false;            // d_A0 holds this step's sorted copy (hydro_step only)
-    hyd::DevBuf<double> d_A0, d_A1, d_ekmax, d_dS;   // n each
+    hyd::DevBuf<double> d_A0, d_A1, d_dS;   // n each
+    hyd::DevBuf<uint8_t> d_ecand;
 
     // individual timesteps (hydro_step_rungs): rungs and the sub-step at
     // which each particle's current step started (caller order); per sorted
