@@ -369,3 +369,46 @@ def test_entropy_switch_step_matches_oracle(orc, hyd, scheme, precision, tol):
         assert np.all(Ag > 0)
         assert np.max(np.abs(Ag - so["A"]) / so["A"]) < tol * 10, (graph, scheme)
     H.set_entropy(None)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_entropy_switch_with_guard_rounds(orc, hyd, precision, tol):
+    """The entropy route of re-solved particles in the N_cond guard rounds
+    (§2.3.5, §2.3.7): a log-normal box with a low threshold (all five growth
+    rounds) and cold random velocities, the switch on, A set for most
+    particles; the step ends where the oracle's ends."""
+    import torch
+    w = dict(W.lognormal(4096, seed=2, grid=16))
+    n = w["x"].size
+    rng = np.random.default_rng(9)
+    v = rng.normal(0.0, 3.0, (n, 3))
+    w["px"], w["py"], w["pz"] = w["m"] * v[:, 0], w["m"] * v[:, 1], w["m"] * v[:, 2]
+    w["U"] = 1e-4 * w["U"]
+    w["E"] = w["U"] + 0.5 * w["m"] * np.sum(v * v, 1)
+    w["A"] = np.where(rng.random(n) < 0.1, 0.0, rng.uniform(0.5, 2.0, n))
+    co = orc.config(gamma=w["gamma"], ncond_crit=4.0, entropy=True)
+    so, _, info_o = orc.step(co, w, 1e-4)
+    assert info_o["ngb_rounds"] == 5 and info_o["status"] == 0
+    ek = orc.ekin_max(w["x"], w["y"], w["z"], w["L"], so["h"], w["m"], w["px"], w["py"], w["pz"])
+    _, _, _, _, _, src = orc.primitives(co, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"],
+                                        so["omega"], h=so["h"], A=w["A"], ekmax=ek, want_src=True)
+    assert (src == 1).sum() > n // 2 and (src == 2).sum() > 0, np.bincount(src)
+    H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision=precision, ncond_crit=4.0,
+                                     entropy_switch=1))
+    H.set_boxes(*hyd.single_box(w))
+    st = hyd.to_device(w)
+    A = torch.as_tensor(w["A"], device="cuda").clone()
+    H.set_entropy(A)
+    stats = H.step(st, 1e-4, check=False)
+    torch.cuda.synchronize()
+    assert stats["status"] == 0 and stats["ngb_rounds"] == 5, stats
+    sg = {k: v.cpu().numpy() for k, v in st.items()}
+    for k in ("h", "omega"):
+        assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol, k
+    for k in ("m", "px", "py", "pz", "E", "U"):
+        d_o = so[k] - w[k]
+        d_g = sg[k] - w[k]
+        scale = np.abs(d_o).max() + 1e-300
+        assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, k
+    Ag = A.cpu().numpy()
+    assert np.max(np.abs(Ag - so["A"]) / so["A"]) < tol * 10

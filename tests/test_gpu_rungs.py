@@ -146,3 +146,30 @@ def test_rung_step_rejects_what_it_does_not_combine(hyd):
     s = H.step_rungs(st, 1e-3, rung)
     assert s["status"] == 0
     H.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_rung_step_with_guard_rounds(orc, hyd, precision, tol):
+    """N_cond guard rounds inside the sub-steps (a log-normal box at a low
+    threshold, MFM): only the particles starting a step grow their N_NGB,
+    and the base step ends where the oracle's ends."""
+    w = W.lognormal(4096, seed=2, grid=16, contrast=100.0)
+    co = orc.config(gamma=w["gamma"], scheme="mfm", ncond_crit=4.0)
+    _, _, i0 = orc.step(co, w, -1.0)
+    assert i0["ngb_rounds"] >= 1
+    dt0 = 5.0 * i0["dt"]
+    so, rung_o, io = orc.step_rungs(co, w, dt0)
+    assert io["status"] == 0 and len(set(rung_o.tolist())) >= 3
+    assert _margin(dt0, io["dt_cfl"], io["dt_acc"]) > (1e-4 if precision == "mixed" else 1e-9)
+    cg = hyd.default_config(gamma=w["gamma"], precision=precision, scheme="mfm", ncond_crit=4.0)
+    sg, rung_g, stats = _run_gpu(hyd, w, cg, dt0)
+    assert stats["status"] == 0, stats
+    assert stats["ngb_rounds"] >= 1
+    assert np.array_equal(rung_g, rung_o)
+    for k in ("h", "omega"):
+        assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol * 10, k
+    for k in ("px", "py", "pz", "E", "U"):
+        d_o = so[k] - w[k]
+        d_g = sg[k] - w[k]
+        scale = np.abs(d_o).max() + 1e-300
+        assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, k
