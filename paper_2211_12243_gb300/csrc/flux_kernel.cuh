@@ -99,8 +99,8 @@ __device__ __forceinline__ R pair_limit(R e, R a, R b, R psi1, R psi2, bool posi
     R lo = a < b ? a : b, hi = a > b ? a : b;
     R lox = lo - d1, hix = hi + d1;
     if (positive) {
-        if (sgn_(lox) != sgn_(lo)) lox = lo == R(0) ? R(0) : lo / (R(1) + d1 / fabs(lo));
-        if (sgn_(hix) != sgn_(hi)) hix = hi == R(0) ? R(0) : hi / (R(1) + d1 / fabs(hi));
+        if (sgn_(lox) != sgn_(lo)) lox = lo == R(0) ? R(0) : div_(lo, R(1) + div_(d1, fabs(lo)));
+        if (sgn_(hix) != sgn_(hi)) hix = hi == R(0) ? R(0) : div_(hi, R(1) + div_(d1, fabs(hi)));
     }
     if (a < b) {
         R t = e < mean + d2 ? e : mean + d2;

@@ -72,8 +72,6 @@ cudaError_t launch_hard_faces(const FluxArgs &a, int scheme, stream_t st) {
     return launch_check();
 }
 
-inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
 }  // namespace
 
 void read_learn_probe(hydro_ctx *c) {
