@@ -541,7 +541,14 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
     double dtmin = dt0;
     for (int64_t k = 0; k < K; k++) {
         API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
-        int rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
+        // the order of sub-step 0 is kept: the sub-steps drift the particles
+        // by a fraction of h, so only the boxes and lists are rebuilt
+        int rc = k == 0 ? build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st)
+                        : HYDRO_OK;
+        if (k > 0) {
+            API_CUDA(gather_state(c, p, p->h, nullptr, c->cfg.search_margin, true, st));
+            rc = lists_all(c, st);
+        }
         if (rc) return rc;
         // omega of the particles that do not start (the others' is solved)
         API_CUDA(gather_from_caller(c->d_perm.get(), p->omega, n, 1, c->d_omsorted.get(), n, st));
