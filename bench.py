@@ -174,10 +174,10 @@ def make_workload(kind, n, seed=0):
     return W.sod(n or 78), name
 
 
-def oracle_sample_rate(kind, n, reps):
+def oracle_sample_rate(kind, n, reps, threads=None):
     """The oracle's gradient + flux stages on a small case of the same
     generator (density solved first, untimed); pairs counted like the GPU
-    metric."""
+    metric.  threads: OpenMP threads of the timed passes (default: all)."""
     import oracle
     if n is None:
         n = {"sod": 40, "sedov": 32, "lognormal": 1 << 15, "batch": 6, "wave": 32}[kind]
@@ -201,6 +201,9 @@ def oracle_sample_rate(kind, n, reps):
         prep.append((x, y, z, L, h, om, prims))
     t = 0.0
     fpairs = 0
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
     for _ in range(reps):
         fpairs = 0
         for x, y, z, L, h, om, prims in prep:
@@ -213,7 +216,9 @@ def oracle_sample_rate(kind, n, reps):
             fpairs += len(pairs)
     total = reps * (gpairs + fpairs)
     npart = sum(len(p[0]) for p in prep)
-    return dict(value=total / t, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+    cores = oracle.num_threads()
+    oracle.set_num_threads(all_threads)
+    return dict(value=total / t, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"{kind} generator at n={n} ({npart} particles), oracle gradient+flux stages "
                        f"(E/B/N_cond, gradients+limiter, pair enumeration, fluxes), {reps} passes, "
                        f"{total} pair-interactions in {t:.2f} s"), t
@@ -536,6 +541,9 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu, _ = oracle_sample_rate(args.workload, args.cpu_n, args.cpu_reps)
+        # the same sample on one core (one pass)
+        one, _ = oracle_sample_rate(args.workload, args.cpu_n, 1, threads=1)
+        cpu["single_core"] = {"value": one["value"], "cores": one["cores"], "sample": one["sample"]}
 
     last = r["last"]
     line = {
