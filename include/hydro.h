@@ -174,6 +174,8 @@ typedef struct {
     int64_t substeps;         /* 2^rung_max */
     int64_t active_steps;     /* particle steps taken, sum_i 2^rung_i */
     int64_t rung_capped;      /* particles whose criteria asked for more than max_rung */
+    int64_t rung_sparse;      /* sub-steps that rebuilt and walked only the lists of the
+                                 buckets within reach of the starting particles */
 } hydro_stats;
 
 /* Defaults described above.  Always succeeds. */

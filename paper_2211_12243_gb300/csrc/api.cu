@@ -512,6 +512,46 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     return rc;
 }
 
+// Lists for a sub-step of individual timesteps.  The faces with a particle
+// a that starts a step are found from the lists of a and of the particles j
+// with r_aj < h_j (the flux kernel's owner of a face is one of its two
+// particles, seeing the other within its own h).  So only the buckets
+// holding such particles need fresh lists and a flux walk: a reverse walk
+// of the tree from every starting particle flags them (ACT_REDO), and when
+// they are few their lists are rebuilt into the overflow region and the
+// flux kernel walks only them; the other lists are stale and unused.  Too
+// many, or no room: every list, every bucket.
+static int rung_lists(hydro_ctx *c, cudaStream_t st) {
+    const int64_t n = c->plan.n, nb = c->plan.nbucket;
+    c->rung_touch_n = -1;
+    API_CUDA(build_tree(c, st));
+    API_CUDA(mark_reverse(c, st));
+    API_CUDA(queue_flagged(c, ACT_REDO, st));
+    int nq = 0;
+    API_CUDA(cudaMemcpyAsync(&nq, &c->d_cnt->ovf_buckets, sizeof(int), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    if (nq > 0 && nq <= nb / 4 && c->have_lists && c->list_cap > 0) {
+        API_CUDA(c->d_touch.ensure(nb));
+        API_CUDA(cudaMemcpyAsync(c->d_touch.get(), c->d_ovf.get(), (size_t)nq * sizeof(int32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+        API_CUDA(set_u64(&c->d_cnt->list_cursor, (unsigned long long)n * c->list_cap, st));
+        API_CUDA(build_lists_queued(c, nq, st));
+        int fl = 0;
+        unsigned long long cursor = 0;
+        API_CUDA(cudaMemcpyAsync(&fl, &c->d_cnt->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaMemcpyAsync(&cursor, &c->d_cnt->list_cursor, sizeof(cursor),
+                                 cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+        if (!(fl & (ST_LIST_CAPACITY | ST_STACK))) {
+            c->rung_touch_n = nq;
+            return HYDRO_OK;
+        }
+        if (fl & ST_LIST_CAPACITY) grow_overflow(c, cursor);
+        API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
+    }
+    return lists_all(c, st);
+}
+
 // individual timesteps: the base step of 2^rmax sub-steps (see hydro.h)
 static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *rung,
                       hydro_stats *stats, cudaStream_t st) {
@@ -543,11 +583,12 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         API_CUDA(cudaMemsetAsync(c->d_cnt, 0, sizeof(DevCounters), st));
         // the order of sub-step 0 is kept: the sub-steps drift the particles
         // by a fraction of h, so only the boxes and lists are rebuilt
-        int rc = k == 0 ? build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st)
-                        : HYDRO_OK;
-        if (k > 0) {
+        int rc = HYDRO_OK;
+        if (k == 0) {
+            c->rung_touch_n = -1;
+            rc = build_all(c, p, p->h, nullptr, c->cfg.search_margin, true, st);
+        } else {
             API_CUDA(gather_state(c, p, p->h, nullptr, c->cfg.search_margin, true, st));
-            rc = lists_all(c, st);
         }
         if (rc) return rc;
         // omega of the particles that do not start (the others' is solved)
@@ -556,6 +597,9 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         if (k > 0) {
             API_CUDA(rung_records(c, false, st));
             API_CUDA(rung_fill(c, st));
+            rc = rung_lists(c, st);
+            if (rc) return rc;
+            if (c->rung_touch_n >= 0) S.rung_sparse++;
         } else {
             API_CUDA(reset_guard(c, st));
         }
@@ -604,7 +648,8 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         API_CUDA(rung_records(c, true, st));
         API_CUDA(run_fluxes(c, dtmin, nullptr, st));
         API_CUDA(run_update(c, p, dtmin, nullptr, false, st));
-        if (stats) API_CUDA(run_update_sums(c, st));
+        // totals before the first sub-step and after the last
+        if (stats && (k == 0 || k == K - 1)) API_CUDA(run_update_sums(c, st));
         API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
         const DevCounters &H = *c->h_cnt;

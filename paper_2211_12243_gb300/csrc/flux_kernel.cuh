@@ -78,6 +78,10 @@ struct FluxArgs {
     const double *toff;
     const uint8_t *ract;
     double dt0;
+    // the buckets to walk (NULL: all nbucket; else nbucket of these ids):
+    // the sub-steps of individual timesteps walk only the buckets whose
+    // particles can reach a particle starting a step
+    const int32_t *bucket_ids;
 };
 
 template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
@@ -472,10 +476,11 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     int hh = 0;   // the oldest entry of the warp's hard queue (a ring of HQ)
     if (DEFER && lane == 0) hq.cnt = 0;
     __syncwarp();
-    const int64_t b = blockIdx.x * (int64_t)FLUX_WARPS + warp;
+    const int64_t bi = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
     unsigned long long n_hard = 0;
-    if (b < a.nbucket) {
+    if (bi < a.nbucket) {
+        const int64_t b = a.bucket_ids ? (int64_t)a.bucket_ids[bi] : bi;
         const int f = a.node_first[b], nown = a.node_cnt[b];
         const bool own = lane < nown;
         const int s = f + (own ? lane : 0);

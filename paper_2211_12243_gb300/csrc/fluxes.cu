@@ -213,6 +213,11 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.toff = c->rung_live ? c->d_toff.get() : nullptr;
     a.ract = c->rung_live ? c->d_ract.get() : nullptr;
     a.dt0 = c->rung_dt0;
+    a.bucket_ids = nullptr;
+    if (c->rung_live && c->rung_touch_n >= 0) {
+        a.bucket_ids = c->d_touch.get();
+        a.nbucket = c->rung_touch_n;
+    }
     // the adaptive learned path times its probes with the same events
     const bool adapt = c->cfg.learned_guess == 1 && c->cfg.precision == HYDRO_MIXED &&
                        c->cfg.riemann == HYDRO_RIEMANN_EXACT && c->have_mlp;

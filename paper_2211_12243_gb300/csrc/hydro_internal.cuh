@@ -213,6 +213,10 @@ struct hydro_ctx {
     hyd::DevBuf<uint8_t> d_ract;
     hyd::DevBuf<double> d_toff;
     hyd::DevBuf<double> d_rec_store;  // n REC doubles (float records use half)
+    // the buckets whose particles can reach a particle starting a step (the
+    // only lists a sparse sub-step rebuilds and walks); -1: all buckets
+    hyd::DevBuf<int32_t> d_touch;
+    int64_t rung_touch_n = -1;
 
     // reductions
     hyd::DevBuf<double> d_partials;
@@ -362,6 +366,9 @@ cudaError_t rung_assign(hydro_ctx *c, double dt0, stream_t st);
 cudaError_t rung_limit_sweep(hydro_ctx *c, stream_t st);
 // sorted rungs to the caller-order master copy (and the deepest rung)
 cudaError_t rung_scatter(hydro_ctx *c, stream_t st);
+// the buckets holding a particle flagged ACT_REDO into d_ovf (count in
+// ovf_buckets)
+cudaError_t queue_flagged(hydro_ctx *c, uint8_t bits, stream_t st);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,

@@ -479,17 +479,18 @@ __global__ void k_export_fill(int64_t n, const int32_t *__restrict__ perm,
     }
 }
 
-// queue the buckets holding a particle to search again (active bit 0), and
-// clear the search-failure flag that the rebuild answers
+// queue the buckets holding a particle with one of the bits set (bit 0: to
+// search again, and then clear the search-failure flag that the rebuild
+// answers)
 __global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ first,
                                const int32_t *__restrict__ cnt, const uint8_t *__restrict__ active,
                                int32_t *__restrict__ queue, int *__restrict__ nqueue,
-                               DevCounters *counters) {
+                               DevCounters *counters, uint8_t bits = 1) {
     int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
-    if (b == 0 && lane == 0) atomicAnd(&counters->flags, ~ST_SEARCH);
+    if (bits == 1 && b == 0 && lane == 0) atomicAnd(&counters->flags, ~ST_SEARCH);
     if (b >= nbucket) return;
-    bool act = lane < cnt[b] && (active[first[b] + lane] & 1);
+    bool act = lane < cnt[b] && (active[first[b] + lane] & bits);
     if (__any_sync(0xffffffffu, act) && lane == 0) queue[atomicAdd(nqueue, 1)] = (int32_t)b;
 }
 
@@ -700,6 +701,16 @@ cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st) {
     if (*nq == 0) return cudaSuccess;
     HYD_CUDA(build_tree(c, st));   // the buckets' search radii changed
     return build_lists_queued(c, *nq, st);
+}
+
+cudaError_t queue_flagged(hydro_ctx *c, uint8_t bits, stream_t st) {
+    const Plan &P = c->plan;
+    HYD_CUDA(c->d_ovf.ensure(P.nbucket));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
+    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+        P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
+        &c->d_cnt->ovf_buckets, c->d_cnt, bits);
+    return launch_check();
 }
 
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st) {

@@ -2,10 +2,12 @@
 // the per-particle bookkeeping of hydro_step_rungs.  The base step dt0 runs
 // 2^rmax sub-steps; at sub-step k a particle of rung r starts a step when k
 // is a multiple of 2^(rmax - r).  The master copies of the rungs and of the
-// sub-step at which each particle's step started are kept in caller order
-// (the particles are re-sorted every sub-step); each sub-step gathers them
-// into sorted order with the flag "starts now" and the time since the
-// particle's state was taken.  A particle that does not start keeps the
+// sub-step at which each particle's step started are kept in caller order;
+// each sub-step gathers them into sorted order (the order of sub-step 0)
+// with the flag "starts now" and the time since the particle's state was
+// taken, and lists the starting particles for the reverse tree walk that
+// finds the buckets whose lists the sub-step needs (the driver,
+// rung_lists in api.cu).  A particle that does not start keeps the
 // record (h, rho, v, p, omega, B, limited gradients) of its last start: the
 // records of the starting particles are saved in caller order after their
 // gradients, and the others' are loaded back over the freshly gathered
@@ -23,7 +25,7 @@ __global__ void k_rung_prep(int64_t n, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ rung_c, int32_t *__restrict__ kstart_c,
                             int64_t k, int rmax, double dtmin, int32_t *__restrict__ rung_s,
                             uint8_t *__restrict__ ract, double *__restrict__ toff,
-                            DevCounters *cnt) {
+                            int32_t *__restrict__ act_idx, DevCounters *cnt) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool act = false;
     if (s < n) {
@@ -41,7 +43,15 @@ __global__ void k_rung_prep(int64_t n, const int32_t *__restrict__ perm,
         toff[s] = (double)(k - ks) * dtmin;
     }
     const unsigned m = __ballot_sync(0xffffffffu, act);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->rung_active, (unsigned long long)__popc(m));
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) {
+        atomicAdd(&cnt->rung_active, (unsigned long long)__popc(m));
+        base = atomicAdd(&cnt->nguard, __popc(m));
+    }
+    // the starting particles also form the list the reverse walk reads
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (act) act_idx[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)s;
 }
 
 // the particles starting a step solve their density with N_NGB restarted
@@ -162,10 +172,12 @@ __global__ void k_rung_scatter(int64_t n, const int32_t *__restrict__ perm,
 
 cudaError_t rung_prep(hydro_ctx *c, int64_t k, int rmax, double dtmin, stream_t st) {
     const int64_t n = c->plan.n;
+    HYD_CUDA(c->d_guard_idx.ensure(n));
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nguard, 0, sizeof(int), st));
     k_rung_prep<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_perm.get(), c->d_rung_c.get(),
                                                    c->d_kstart_c.get(), k, rmax, dtmin,
                                                    c->d_rung_s.get(), c->d_ract.get(),
-                                                   c->d_toff.get(), c->d_cnt);
+                                                   c->d_toff.get(), c->d_guard_idx.get(), c->d_cnt);
     return launch_check();
 }
 

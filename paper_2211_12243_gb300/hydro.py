@@ -74,7 +74,7 @@ class Stats(C.Structure):
         ("ms_update", C.c_float), ("ms_flux_kernel", C.c_float), ("ms_hard_faces", C.c_float),
         ("graph", C.c_int), ("learned_probe_ms", C.c_float * 2),
         ("rung_max", C.c_int), ("substeps", C.c_int64), ("active_steps", C.c_int64),
-        ("rung_capped", C.c_int64),
+        ("rung_capped", C.c_int64), ("rung_sparse", C.c_int64),
     ]
 
     def as_dict(self):
