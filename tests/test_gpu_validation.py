@@ -215,3 +215,57 @@ def test_gresho_vortex_keeps_its_profile(hyd, scheme):
     assert abs(lz1 - lz0) < 0.06 * abs(lz0), (lz0, lz1)
     # linear momentum is conserved by construction
     assert abs(np.sum(out["px"])) < 1e-12 * np.sum(np.abs(w["px"])) + 1e-15
+
+
+def _evolve_rungs(hyd, w, cfg, t_end, mult=4.0):
+    """Base steps of hydro_step_rungs of mult CFL steps each (the CFL dt of
+    the base step's start, from a global step on a copy), the last cut to
+    land on t_end."""
+    import torch
+    H = hyd.Hydro(cfg)
+    H.set_boxes(*hyd.single_box(w))
+    st = hyd.to_device(w)
+    rung = torch.zeros(w["x"].size, dtype=torch.int32, device="cuda")
+    t, rungs = 0.0, set()
+    while t < t_end * (1.0 - 1e-12):
+        probe = {k: v.clone() for k, v in st.items()}
+        dt_cfl = H.step(probe, -1.0)["dt"]
+        dt0 = min(mult * dt_cfl, t_end - t)
+        s = H.step_rungs(st, dt0, rung)
+        assert s["status"] == 0, s
+        rungs |= set(np.unique(rung.cpu().numpy()).tolist())
+        t += dt0
+    torch.cuda.synchronize()
+    H.build_neighbours(st, st["h"] * 1.3, export=False)
+    H.density(st)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in st.items()}
+    H.close()
+    return out, t, rungs
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_sod_with_individual_timesteps_follows_exact_solution(orc, hyd, scheme):
+    """The gamma = 1.4 tube at n = 100 run with individual timesteps (base
+    steps of four CFL steps, §2.3.4, §2.3.10) stays as close to the exact
+    solution as the global CFL-stepped run."""
+    gamma, t_end = 1.4, 0.13
+    r = orc.riemann_star(1.0, 0.0, 1.0, 0.25, 0.0, 0.1795, gamma)
+    w = _sod(100, gamma=gamma)
+    cfg = hyd.default_config(gamma=gamma, precision="mixed", scheme=scheme, kernel="cubic",
+                             n_ngb=64.0)
+    errs = {}
+    outs = {"global": _evolve(hyd, w, cfg, t_end)[:2]}
+    o, t, rungs = _evolve_rungs(hyd, w, cfg, t_end)
+    outs["rungs"] = (o, t)
+    assert len(rungs) >= 2, rungs
+    for mode, (out, t) in outs.items():
+        x = out["x"]
+        sel = (x > 0.6) & (x < 1.4)
+        ex = np.array([orc.riemann_sample(1.0, -(xi - 1.0) / t, 1.0, 0.25, -(xi - 1.0) / t, 0.1795,
+                                          gamma, r["p"], r["u"] - (xi - 1.0) / t)[0]
+                       for xi in x[sel]])
+        errs[mode] = float(np.mean(np.abs(out["m"][sel] / out["omega"][sel] - ex)))
+    print(f"sod rungs {scheme}: L1(rho) {errs}, rungs {sorted(rungs)}")
+    assert errs["rungs"] < 1.3 * errs["global"] + 2e-3, errs
+    assert errs["rungs"] < 0.03, errs
