@@ -16,8 +16,7 @@
  * Layout of every array: structure of arrays, particle index = the caller's
  * order.  Periodic box [0,Lx) x [0,Ly) x [0,Lz).
  *
- * Readings of the paper taken here where it is silent (each listed in the
- * design notes of the repository):
+ * Readings of the paper taken here where it is silent:
  *   - Kernel: Wendland C2 (default) or cubic spline, compact radius H = h.
  *   - W(r_ij) in E_i and grad_i uses the evaluating particle's own h_i; the
  *     j-term of A_ij uses h_j.

@@ -6,8 +6,8 @@
 // each sub-step gathers them into sorted order (the order of sub-step 0)
 // with the flag "starts now" and the time since the particle's state was
 // taken, and lists the starting particles for the reverse tree walk that
-// finds the buckets whose lists the sub-step needs (the driver,
-// rung_lists in api.cu).  A particle that does not start keeps the
+// finds the buckets whose lists the sub-step needs (rung_lists in api.cu).
+// A particle that does not start keeps the
 // record (h, rho, v, p, omega, B, limited gradients) of its last start: the
 // records of the starting particles are saved in caller order after their
 // gradients, and the others' are loaded back over the freshly gathered

@@ -13,9 +13,9 @@ simulations on the GPU through the C ABI:
   rho = 1, gamma = 1.4, p(0) = 5, 64^2 particles per plane of side 2 on a
   Cartesian lattice, to t = 3: the profile is kept up to a small decay.
 
-Densities are set through the particle masses on a uniform lattice (the
-paper sets them through the number density for the tube; §9 of the design
-notes records this reading).  Printed figures: pytest -s."""
+Densities are set through the particle masses on a uniform lattice (a
+reading: the paper sets them through the number density for the tube).
+Printed figures: pytest -s."""
 import math
 
 import numpy as np
@@ -110,7 +110,8 @@ def test_soundwave_converges_at_second_order(hyd, scheme):
     # near second order (measured: MFM 1.9, MFV 1.6 at C_CFL = 0.1); errors
     # well below the amplitude.  Longer runs (N = 128: 1300 steps) meet a
     # transverse instability that the wave drives in the lattice (the FP64
-    # oracle shows it too; see the design notes), so the series stops at 64.
+    # oracle shows it too, with and without limiters, predictor, MFM or HLLC;
+    # it needs the particles to move), so the series stops at 64.
     assert l1[16] > l1[32] > l1[64], l1
     assert slope > 1.45, (l1, slope)
     assert l1[64] < 0.02 * A, l1
