@@ -465,7 +465,11 @@ struct HardQ {
 
 // MINB: resident CTAs per SM the register allocation must allow (the
 // launch-bounds variants the autotuner chooses from; 4 by default in float)
-template <typename R, int RIEM, int SCHEME, bool DEFER, int MINB = (sizeof(R) == 4 ? 4 : 2)>
+// LEAN: compiled without the optional per-face work (individual timesteps,
+// face recording, the gravity and entropy sums); the launchers take it
+// when none is on, which keeps the kernel's code small
+template <typename R, int RIEM, int SCHEME, bool DEFER, int MINB = (sizeof(R) == 4 ? 4 : 2),
+          bool LEAN = false>
 __global__ void __launch_bounds__(FLUX_WARPS * 32, MINB)
 k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     __shared__ FluxSmem<R> sm_all[FLUX_WARPS];
@@ -546,7 +550,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                 rec_sep(ri, rj, bx, d, r2);
                 FaceState<R> st;
                 R dtf = dt, hl = R(0.5) * dt, hr = hl;
-                if (a.rung) {
+                if (!LEAN && a.rung) {
                     const int64_t so = f + ol;
                     const double dtd = ldexp(a.dt0, -max(a.rung[so], a.rung[j]));
                     dtf = (R)dtd;
@@ -575,17 +579,18 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                     if (!deferred) {
                         R ps;
                         face_finish<R, RIEM, SCHEME>(a, K, st, R(-1), c, fs, ps);
-                        if (RIEM == HYDRO_RIEMANN_EXACT && a.rec_faces) record_face<R>(a, K, st, ps, f + ol, j);
+                        if (!LEAN && RIEM == HYDRO_RIEMANN_EXACT && a.rec_faces)
+                            record_face<R>(a, K, st, ps, f + ol, j);
 #pragma unroll
                         for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + j], widen(c[q]));
-                        if (a.dM && c[0] != R(0)) {
+                        if (!LEAN && a.dM && c[0] != R(0)) {
                             const double cm = widen(c[0]);
                             for (int q = 0; q < 3; q++) {
                                 atomicAdd(&a.dM[q * a.n + f + ol], cm * (double)d[q]);
                                 atomicAdd(&a.dM[q * a.n + j], cm * (double)d[q]);
                             }
                         }
-                        if (a.dS && c[0] != R(0)) {
+                        if (!LEAN && a.dS && c[0] != R(0)) {
                             const double cm = widen(c[0]);
                             const double sf = cm * widen(c[0] > R(0) ? ri[R_PAD] : rj[R_PAD]);
                             atomicAdd(&a.dS[f + ol], -sf);
@@ -636,7 +641,7 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                     R d[3], r2;
                     rec_sep(own4, rc4, bx, d, r2);
                     if (mem(r2, j)) has = (j > s) || !member_j(r2, rc4[R_H], a, s, j, bx);
-                    if (has && a.ract && !a.ract[s] && !a.ract[j]) has = false;
+                    if (!LEAN && has && a.ract && !a.ract[s] && !a.ract[j]) has = false;
                 }
                 jc = jn;
                 jn = jnn;
@@ -778,6 +783,20 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
     }
     if (!ok && tid == 0) atomicOr(&a.cnt->flags, ST_MLP);
     mlp_tile_teardown(T);
+}
+
+// one flux launch, in the lean variant when no optional per-face work is on
+template <typename R, int RIEM, int SCHEME, bool DEFER, int MINB>
+cudaError_t launch_k_fluxes(const FluxArgs &a, const R *rec, stream_t st) {
+    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if constexpr (!DEFER) {
+        if (!a.rung && !a.rec_faces && !a.dM && !a.dS && !a.ract) {
+            k_fluxes<R, RIEM, SCHEME, DEFER, MINB, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+            return launch_check();
+        }
+    }
+    k_fluxes<R, RIEM, SCHEME, DEFER, MINB, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+    return launch_check();
 }
 
 }  // namespace

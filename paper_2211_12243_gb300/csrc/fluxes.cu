@@ -17,7 +17,8 @@ namespace {
 template <typename R>
 cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme, int minb,
                           stream_t st, cudaEvent_t *ev) {
-    unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    constexpr int MB = sizeof(R) == 4 ? 4 : 2;
+    constexpr int E = HYDRO_RIEMANN_EXACT, H = HYDRO_RIEMANN_HLLC;
     if (ev) HYD_CUDA(record_event(ev[0], st));
     bool done = false;
     if constexpr (sizeof(R) == 4) {
@@ -27,14 +28,13 @@ cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme,
         }
     }
     if (!done) {
-        if (riem == HYDRO_RIEMANN_HLLC) {
-            if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-            else k_fluxes<R, HYDRO_RIEMANN_HLLC, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        if (riem == H) {
+            if (scheme == HYDRO_MFM) HYD_CUDA((launch_k_fluxes<R, H, HYDRO_MFM, false, MB>(a, rec, st)));
+            else HYD_CUDA((launch_k_fluxes<R, H, HYDRO_MFV, false, MB>(a, rec, st)));
         } else {
-            if (scheme == HYDRO_MFM) k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFM, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-            else k_fluxes<R, HYDRO_RIEMANN_EXACT, HYDRO_MFV, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+            if (scheme == HYDRO_MFM) HYD_CUDA((launch_k_fluxes<R, E, HYDRO_MFM, false, MB>(a, rec, st)));
+            else HYD_CUDA((launch_k_fluxes<R, E, HYDRO_MFV, false, MB>(a, rec, st)));
         }
-        HYD_CUDA(launch_check());
     }
     if (ev) HYD_CUDA(record_event(ev[1], st));
     return cudaSuccess;

@@ -12,19 +12,17 @@ namespace {
 template <int MINB>
 cudaError_t launch_minb(const FluxArgs &a, const float *rec, int riem, int scheme, bool defer,
                         stream_t st) {
-    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
     constexpr int E = HYDRO_RIEMANN_EXACT, H = HYDRO_RIEMANN_HLLC;
     if (defer) {
-        if (scheme == HYDRO_MFM) k_fluxes<float, E, HYDRO_MFM, true, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-        else k_fluxes<float, E, HYDRO_MFV, true, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-    } else if (riem == H) {
-        if (scheme == HYDRO_MFM) k_fluxes<float, H, HYDRO_MFM, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-        else k_fluxes<float, H, HYDRO_MFV, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-    } else {
-        if (scheme == HYDRO_MFM) k_fluxes<float, E, HYDRO_MFM, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-        else k_fluxes<float, E, HYDRO_MFV, false, MINB><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        if (scheme == HYDRO_MFM) return launch_k_fluxes<float, E, HYDRO_MFM, true, MINB>(a, rec, st);
+        return launch_k_fluxes<float, E, HYDRO_MFV, true, MINB>(a, rec, st);
     }
-    return launch_check();
+    if (riem == H) {
+        if (scheme == HYDRO_MFM) return launch_k_fluxes<float, H, HYDRO_MFM, false, MINB>(a, rec, st);
+        return launch_k_fluxes<float, H, HYDRO_MFV, false, MINB>(a, rec, st);
+    }
+    if (scheme == HYDRO_MFM) return launch_k_fluxes<float, E, HYDRO_MFM, false, MINB>(a, rec, st);
+    return launch_k_fluxes<float, E, HYDRO_MFV, false, MINB>(a, rec, st);
 }
 
 }  // namespace

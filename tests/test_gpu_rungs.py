@@ -104,10 +104,13 @@ def test_rung_step_matches_oracle(orc, hyd, name, scheme, precision, tol):
         assert np.array_equal(sg["m"], w["m"])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_rungs_reduce_to_hydro_step(orc, hyd, precision):
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_rungs_reduce_to_hydro_step(orc, hyd, precision, tol):
     """A base step below every particle's criteria (all rungs 0) is
-    hydro_step with dt = dt0 (to the rounding of the atomic flux sums)."""
+    hydro_step with dt = dt0: in FP64 to the rounding of the atomic flux
+    sums; in the mixed path to float rounding (hydro_step runs the flux
+    kernel compiled without the optional per-face work, whose float
+    arithmetic the compiler may round differently)."""
     import torch
     w = _moving(W.lattice_wave(10, jitter=0.05))
     co = orc.config(gamma=w["gamma"])
@@ -123,11 +126,14 @@ def test_rungs_reduce_to_hydro_step(orc, hyd, precision):
     torch.cuda.synchronize()
     sg = {k: v.cpu().numpy() for k, v in st.items()}
     H.close()
-    for k in ("h", "omega", "x", "y", "z"):
+    for k in ("h", "omega"):
         assert np.max(np.abs(sr[k] - sg[k])) <= 1e-14 * np.max(np.abs(sg[k])), k
+    for k in ("x", "y", "z"):
+        moved = np.max(np.abs(sg[k] - w[k])) + 1e-300
+        assert np.max(np.abs(sr[k] - sg[k])) <= tol * moved + 1e-14 * np.max(np.abs(sg[k])), k
     for k in ("m", "px", "py", "pz", "E", "U"):
         d = np.max(np.abs((sr[k] - w[k]) - (sg[k] - w[k])))
-        assert d <= 1e-12 * (np.abs(sg[k] - w[k]).max() + 1e-300), k
+        assert d <= tol * (np.abs(sg[k] - w[k]).max() + 1e-300), k
 
 
 def test_rung_step_rejects_what_it_does_not_combine(hyd):
