@@ -64,11 +64,13 @@ __device__ __forceinline__ void load10<double>(const double *p, double v[10]) {
 
 // MINB: resident CTAs per SM the register allocation must allow (1: no
 // bound; 5, 6: the variants hydro_autotune times)
-template <typename R, int MINB>
+// LEAN: compiled without the staged outputs (outB, outG, outA, outN) and
+// the individual-timestep mask, which hydro_step does not use
+template <typename R, int MINB, bool LEAN = false>
 __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int mypairs = 0;
-    if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO)) && (!a.ract || a.ract[s])) {
+    if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO)) && (LEAN || !a.ract || a.ract[s])) {
         const Box bx = a.boxes[a.pbox[s]];
         R ri[10];
         load10<R>(rec + s * REC, ri);
@@ -228,17 +230,17 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
         for (int f = 0; f < 5; f++)
 #pragma unroll
             for (int q = 0; q < 3; q++) rs[R_G + 3 * f + q] = alpha[f] * G[f][q];
-        if (a.outB) {
+        if (!LEAN && a.outB) {
             for (int k = 0; k < 6; k++) a.outB[k * a.n + s] = Bd[k];
         }
-        if (a.outG) {
+        if (!LEAN && a.outG) {
             for (int f = 0; f < 5; f++)
                 for (int q = 0; q < 3; q++) a.outG[(3 * f + q) * a.n + s] = (double)G[f][q];
         }
-        if (a.outA) {
+        if (!LEAN && a.outA) {
             for (int f = 0; f < 5; f++) a.outA[f * a.n + s] = (double)alpha[f];
         }
-        if (a.outN) a.outN[s] = ncond;
+        if (!LEAN && a.outN) a.outN[s] = ncond;
         // CFL timestep of Eq. 31 with the signal velocity of Eq. 32 (the
         // minimum over particles is taken by k_grad_reduce)
         double dti = INFINITY;
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
             a.active[s] |= ACT_NCOND;
             atomicAdd(&a.cnt->ncond_fail, 1);
         }
-    } else if (s < a.n && a.ract && !a.ract[s]) {
+    } else if (!LEAN && s < a.n && a.ract && !a.ract[s]) {
         // not starting a step: no pairs, no CFL limit in this sub-step
         a.dt_part[s] = INFINITY;
         a.npair[s] = 0;
@@ -558,16 +560,29 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
     HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
     const unsigned grid = grid_for(n, 128);
+    const bool lean = !a.outB && !a.outG && !a.outA && !a.outN && !a.ract;
     if (c->cfg.precision == HYDRO_MIXED) {
         float *r = c->d_recf.get();
-        if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, 0, st>>>(a, r);
-        else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, 0, st>>>(a, r);
-        else k_gradients<float, 1><<<grid, 128, 0, st>>>(a, r);
+        if (lean) {
+            if (c->grad_minb == 5) k_gradients<float, 5, true><<<grid, 128, 0, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<float, 6, true><<<grid, 128, 0, st>>>(a, r);
+            else k_gradients<float, 1, true><<<grid, 128, 0, st>>>(a, r);
+        } else {
+            if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, 0, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, 0, st>>>(a, r);
+            else k_gradients<float, 1><<<grid, 128, 0, st>>>(a, r);
+        }
     } else {
         double *r = c->d_recd.get();
-        if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, 0, st>>>(a, r);
-        else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, 0, st>>>(a, r);
-        else k_gradients<double, 1><<<grid, 128, 0, st>>>(a, r);
+        if (lean) {
+            if (c->grad_minb == 5) k_gradients<double, 5, true><<<grid, 128, 0, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<double, 6, true><<<grid, 128, 0, st>>>(a, r);
+            else k_gradients<double, 1, true><<<grid, 128, 0, st>>>(a, r);
+        } else {
+            if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, 0, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, 0, st>>>(a, r);
+            else k_gradients<double, 1><<<grid, 128, 0, st>>>(a, r);
+        }
     }
     HYD_CUDA(launch_check());
     k_grad_reduce<<<152 * 2, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
