@@ -688,10 +688,10 @@ FLOPS_PER_NEWTON = 38.0
 # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
-# of the current kernel on the Sod tube at n = 60 (182.2 MB for 6,385,500
+# of the current kernel on the Sod tube at n = 60 (182.3 MB for 6,385,500
 # faces, lists compacted by the density stage); a launch's traffic scales
 # with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = 28.53
+FLUX_TRAFFIC_BYTES_PER_FACE = 28.54
 
 if __name__ == "__main__":
     sys.exit(main())
