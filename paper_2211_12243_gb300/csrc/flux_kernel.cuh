@@ -789,11 +789,9 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
 template <typename R, int RIEM, int SCHEME, bool DEFER, int MINB>
 cudaError_t launch_k_fluxes(const FluxArgs &a, const R *rec, stream_t st) {
     const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
-    if constexpr (!DEFER) {
-        if (!a.rung && !a.rec_faces && !a.dM && !a.dS && !a.ract) {
-            k_fluxes<R, RIEM, SCHEME, DEFER, MINB, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-            return launch_check();
-        }
+    if (!a.rung && !a.rec_faces && !a.dM && !a.dS && !a.ract) {
+        k_fluxes<R, RIEM, SCHEME, DEFER, MINB, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
+        return launch_check();
     }
     k_fluxes<R, RIEM, SCHEME, DEFER, MINB, false><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
     return launch_check();

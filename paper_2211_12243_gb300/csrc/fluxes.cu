@@ -46,12 +46,8 @@ cudaError_t launch_fluxes_defer(const FluxArgs &a, const float *rec, int scheme,
                                 stream_t st) {
     if (minb == 5 || minb == 6)
         return launch_fluxes_occ(minb, a, rec, HYDRO_RIEMANN_EXACT, scheme, true, st);
-    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
-    if (scheme == HYDRO_MFM)
-        k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFM, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-    else
-        k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFV, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
-    return launch_check();
+    if (scheme == HYDRO_MFM) return launch_k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFM, true, 4>(a, rec, st);
+    return launch_k_fluxes<float, HYDRO_RIEMANN_EXACT, HYDRO_MFV, true, 4>(a, rec, st);
 }
 
 // ... then the hard-face kernel solves them from the network (pass 2)
