@@ -537,6 +537,13 @@ def main():
                                                        tuning["flux_min_ctas"] == 4) else None),
             "kernel": f"k_fluxes<float,{riemann},{args.scheme}>", "kernel_ms": kern_ms,
             "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # the other bound checked: the kernel's DRAM bytes against the measured
+    # copy bandwidth (far below it: the kernel is not bandwidth bound)
+    hbm_peak = measured_hbm_gbs()
+    if roof["traffic"] and hbm_peak and kern_ms > 0:
+        ach = roof["traffic"] / (kern_ms / 1000.0) / 1e9
+        roof["secondary"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "peak_note": "measured copy bandwidth"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -584,6 +591,15 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of this machine's GPUs (GB/s), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
 
 
 def bench_rungs(args):
