@@ -512,6 +512,22 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     return rc;
 }
 
+// The lists of the buckets holding a particle of the guard round (their
+// search radii grew in guard_grow), rebuilt before the re-solve; a full
+// rebuild when the overflow region is too small.
+static int guard_lists(hydro_ctx *c, cudaStream_t st) {
+    int nq = 0;
+    API_CUDA(rebuild_active_lists(c, &nq, st));
+    API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    const int fl = c->h_cnt->flags;
+    if (fl & (ST_LIST_CAPACITY | ST_STACK)) {
+        if (fl & ST_LIST_CAPACITY) grow_overflow(c, c->h_cnt->list_cursor);
+        return lists_all(c, st);
+    }
+    return HYDRO_OK;
+}
+
 // Lists for a sub-step of individual timesteps.  The faces with a particle
 // a that starts a step are found from the lists of a and of the particles j
 // with r_aj < h_j (the flux kernel's owner of a face is one of its two
@@ -616,6 +632,8 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
             first = false;
             if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
             API_CUDA(guard_grow(c, st));
+            rc = guard_lists(c, st);
+            if (rc) return rc;
             rounds++;
         }
         if (k == 0) {
@@ -741,6 +759,8 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
         first = false;
         if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
         API_CUDA(guard_grow(c, st));
+        rc = guard_lists(c, st);
+        if (rc) return rc;
         rounds++;
     }
     if (timing) API_CUDA(record_event(c->ev[3], st));

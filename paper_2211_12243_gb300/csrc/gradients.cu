@@ -428,15 +428,26 @@ __global__ void k_entropy_route(int64_t n, const int64_t *__restrict__ nbr_off,
     }
 }
 
+constexpr double GUARD_SEARCH = 1.5;
+
 // N_NGB *= grow for particles that failed the N_cond check; they (only)
 // get their density solved again
 __global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__restrict__ nngb,
-                             double grow, int32_t *__restrict__ guard_idx, int *__restrict__ nguard) {
+                             double grow, int32_t *__restrict__ guard_idx, int *__restrict__ nguard,
+                             double *__restrict__ hs, const double *__restrict__ h,
+                             const int32_t *__restrict__ pbox, const Box *__restrict__ boxes) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint8_t a = active[s];
     if (a & ACT_NCOND) {
         nngb[s] *= grow;
+        // the root moves out with N_NGB, and further than the cube root of
+        // the growth where the particle's surroundings are sparse: its list
+        // is rebuilt at GUARD_SEARCH h (at most half the shortest box side)
+        // before the re-solve, rather than after a failed one
+        const Box bx = boxes[pbox[s]];
+        const double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+        hs[s] = fmin(fmax(hs[s], h[s] * GUARD_SEARCH), half);
         active[s] = ACT_SOLVE | ACT_GUARD;
         guard_idx[atomicAdd(nguard, 1)] = (int32_t)s;
     } else {
@@ -595,7 +606,9 @@ cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nguard, 0, sizeof(int), st));
     k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_nngb.get(),
                                                    c->cfg.ngb_grow, c->d_guard_idx.get(),
-                                                   &c->d_cnt->nguard);
+                                                   &c->d_cnt->nguard, c->d_hs.get(),
+                                                   c->d_hsorted.get(), c->d_pbox.get(),
+                                                   c->d_boxes.get());
     return launch_check();
 }
 

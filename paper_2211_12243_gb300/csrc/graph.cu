@@ -127,6 +127,7 @@ cudaError_t cond_guard(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
 cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const long long k0 = launch_count();
     HYD_CUDA(guard_grow(c, s));
+    HYD_CUDA(rebuild_active_lists_dev(c, s));   // the grown search radii
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(search_loop(c, 2, s));
     HYD_CUDA(run_primitives(c, s, true));

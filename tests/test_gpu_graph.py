@@ -80,11 +80,14 @@ def test_graph_steps_match_host_steps(hyd, name, precision, tol, restart):
     runs = {}
     for graph in (1, 0):
         cfg = hyd.default_config(gamma=w["gamma"], precision=precision, graph=graph, **opts)
-        runs[graph] = _run(hyd, w, cfg, 4, restart, dt)
+        runs[graph] = _run(hyd, w, cfg, 6, restart, dt)
     how = [s["graph"] for s, _ in runs[1]]
-    # graph steps from the second on; a step may hand over once to the host
-    # path to grow a buffer (2), after which the graph runs again
+    # graph steps from the second on; a step may hand over to the host path
+    # to grow a buffer (2: the overflow region of the lists, which the guard
+    # rounds' rebuilt lists fill, or the fixed list slots), after which the
+    # graph runs again
     assert how[0] == 0 and how[-1] == 1 and all(g in (1, 2) for g in how[1:]), how
+    assert how.count(2) <= 2, how
     for k, ((sg, xg), (sh, xh)) in enumerate(zip(runs[1], runs[0])):
         assert sh["graph"] == 0
         for key in ("status", "grad_pairs", "flux_pairs", "ngb_rounds", "ncond_fail",
