@@ -428,7 +428,7 @@ __global__ void k_entropy_route(int64_t n, const int64_t *__restrict__ nbr_off,
     }
 }
 
-constexpr double GUARD_SEARCH = 1.5;
+constexpr double GUARD_SEARCH = 2.0;
 
 // N_NGB *= grow for particles that failed the N_cond check; they (only)
 // get their density solved again
