@@ -900,3 +900,43 @@ def test_rung_steps_follow_the_sod_solution(orc, scheme):
     assert len(rungs) >= 2, rungs
     assert errs["rungs"] < 1.3 * errs["global"] + 2e-3, errs
     assert errs["rungs"] < 0.06, errs
+
+
+def test_entropy_is_carried_upwind_by_mfv(orc):
+    """A cold, nearly pressureless lattice with random velocities and a step
+    in A (1e-8 on [0, 1/2), 2e-8 on [1/2, 1)).  The MFV mass fluxes (relative
+    to the faces, which move with the particles' mean velocity) run both ways
+    across the step; with the donor's A each particle's new A is a weighted
+    mean of its own and its donors' values, so A stays within [1e-8, 2e-8]
+    and particles farther than h from the step keep theirs (§2.3.7, the MFV
+    transport of m A).  A receiver's or a central A would leave that range."""
+    n = 16
+    w = dict(W.lattice_wave(n, jitter=0.0))
+    N = w["x"].size
+    rng = np.random.default_rng(21)
+    m = np.full(N, 1.0 / n ** 3)
+    v = rng.normal(0.0, 0.3, (N, 3))
+    w["m"] = m
+    w["px"], w["py"], w["pz"] = m * v[:, 0], m * v[:, 1], m * v[:, 2]
+    w["U"] = 1e-7 * m
+    w["E"] = w["U"] + 0.5 * m * np.sum(v * v, 1)
+    x = w["x"]
+    w["A"] = np.where(x < 0.5, 1e-8, 2e-8)
+    co = orc.config(gamma=w["gamma"], scheme="mfv", entropy=True)
+    s1, _, info = orc.step(co, w, 0.01)
+    assert info["status"] == 0
+    # every particle took the entropy route (cold, E_kin^max >> U / alpha2)
+    ek = orc.ekin_max(w["x"], w["y"], w["z"], w["L"], s1["h"], m, w["px"], w["py"], w["pz"])
+    src = orc.primitives(co, m, w["px"], w["py"], w["pz"], w["E"], w["U"], s1["omega"],
+                         h=s1["h"], A=w["A"], ekmax=ek, want_src=True)[-1]
+    assert np.all(src == 1), np.bincount(src)
+    A = s1["A"]
+    assert A.min() >= 1e-8 * (1 - 1e-12) and A.max() <= 2e-8 * (1 + 1e-12), (A.min(), A.max())
+    # mixing happened at both steps (x = 1/2 and the periodic x = 0)
+    mixed = (A > 1e-8 * (1 + 1e-6)) & (A < 2e-8 * (1 - 1e-6))
+    assert mixed.sum() > N // 20, mixed.sum()
+    h = float(np.max(s1["h"]))
+    d = np.minimum(np.abs(x - 0.5), np.minimum(x, 1.0 - x))   # distance to a step
+    far = d > 1.5 * h
+    assert far.sum() > N // 10
+    assert np.allclose(A[far], w["A"][far], rtol=1e-12, atol=0)
