@@ -1,0 +1,39 @@
+"""The bench's reference arm (the FP64 oracle on the host cores) runs
+without a GPU: its JSON line carries the contract's keys, and the oracle
+sampler's pair count and rate are consistent.  CPU only."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--cpu-n", "12"],
+                       capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["config"]["workload"] == "sod3d_1067742_mfv_exact"
+
+
+def test_oracle_sampler_counts_pairs_like_the_metric():
+    sys.path.insert(0, ROOT)
+    import bench
+    r1, t1 = bench.oracle_sample_rate("wave", 10, 1)
+    r2, t2 = bench.oracle_sample_rate("wave", 10, 1, threads=1)
+    assert r1["cores"] >= 1 and r2["cores"] == 1
+    assert r1["value"] > 0 and r2["value"] > 0
+    # the same sample: the same pair count in the description
+    count = lambda r: int(r["sample"].split(" pair-interactions")[0].split()[-1])
+    assert count(r1) == count(r2) > 0
