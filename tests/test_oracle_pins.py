@@ -542,6 +542,140 @@ def test_sod_tube_follows_exact_solution(orc, scheme):
 
 
 # --------------------------------------------------------------------------
+# half-step predictor (§2.3.4, Eq. 16: face states advanced by dt/2)
+# --------------------------------------------------------------------------
+def _lattice_faces(orc, cfg, w, rho, v, p, dt):
+    """Face states (rho, u, p on both sides, normal velocities in the frame
+    of the pair's mean velocity) of every flux pair, from the oracle's full
+    pipeline: density, E and B, limited gradients, face reconstruction."""
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, rho, v, p)
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, _ = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    pairs = orc.flux_pairs(w["x"], w["y"], w["z"], w["L"], h)
+    _, _, faces = orc.fluxes(cfg, w["x"], w["y"], w["z"], w["L"], h, om, B6, prims, grad,
+                             alpha, dt, pairs=pairs, want_faces=True)
+    return h, alpha, pairs, faces
+
+
+def test_predictor_accelerates_by_the_pressure_gradient(orc):
+    """Perfect lattice at rest, linear density and pressure fields: Euler's
+    momentum equation gives each side's velocity after half a step as
+    -dt/2 grad p / rho (the particle's own rho), so in the frame of the
+    pair (at rest) the face's normal velocities are -dt/2 (grad p . n) /
+    rho_i and -dt/2 (grad p . n) / rho_j; with div v = 0 density and
+    pressure only take their midpoint values.  On a cubic lattice B is
+    isotropic, so the face normal is the separation's direction."""
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1) - 0.5
+    g_p = np.array([0.3, -0.2, 0.15])
+    g_rho = np.array([0.4, 0.1, -0.3])
+    rho, p = 2.5 + x @ g_rho, 3.0 + x @ g_p
+    dt = 0.01
+    h, alpha, pairs, F = _lattice_faces(orc, cfg, w, rho, np.zeros_like(x), p, dt)
+    inner = np.all(np.abs(x) < 0.5 - h.max() - 1e-3, axis=1)   # away from the periodic seam
+    assert np.all(alpha[inner] == 1.0)
+    sel = inner[pairs[:, 0]] & inner[pairs[:, 1]]
+    assert sel.sum() > 1000
+    i, j = pairs[sel, 0], pairs[sel, 1]
+    F = F[sel]
+    d = x[j] - x[i]
+    nh = d / np.linalg.norm(d, axis=1)[:, None]
+    xm = x[i] + 0.5 * d
+    scale = 0.5 * dt * np.linalg.norm(g_p) / rho.min()
+    assert np.abs(F[:, 1] - (-0.5 * dt * (nh @ g_p) / rho[i])).max() < 1e-12 * scale
+    assert np.abs(F[:, 4] - (-0.5 * dt * (nh @ g_p) / rho[j])).max() < 1e-12 * scale
+    for k in (0, 3):
+        assert np.abs(F[:, k] - (2.5 + xm @ g_rho)).max() < 1e-13 * 2.5
+    for k in (2, 5):
+        assert np.abs(F[:, k] - (3.0 + xm @ g_p)).max() < 1e-13 * 3.0
+
+
+def test_predictor_compresses_with_the_velocity_divergence(orc):
+    """Uniform density and pressure, linear velocity v = K x: continuity and
+    the adiabatic pressure equation give the face states after half a step
+    as rho (1 - dt/2 tr K) and p (1 - dt/2 gamma tr K) on both sides, and
+    the extrapolated velocities equal the pair's mean velocity at the
+    midpoint (zero normal velocity in its frame)."""
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1) - 0.5
+    K = np.array([[0.3, 0.1, -0.05], [0.02, -0.1, 0.04], [0.0, 0.07, 0.2]])
+    v = x @ K.T
+    N = x.shape[0]
+    dt = 0.01
+    h, alpha, pairs, F = _lattice_faces(orc, cfg, w, np.full(N, 2.5), v, np.full(N, 3.0), dt)
+    inner = np.all(np.abs(x) < 0.5 - h.max() - 1e-3, axis=1)
+    sel = inner[pairs[:, 0]] & inner[pairs[:, 1]]
+    assert sel.sum() > 1000
+    F = F[sel]
+    tr = np.trace(K)
+    for k in (0, 3):
+        assert np.abs(F[:, k] - 2.5 * (1.0 - 0.5 * dt * tr)).max() < 1e-13 * 2.5
+    for k in (2, 5):
+        assert np.abs(F[:, k] - 3.0 * (1.0 - 0.5 * dt * cfg.gamma * tr)).max() < 1e-13 * 3.0
+    vscale = np.abs(v).max()
+    assert np.abs(F[:, 1]).max() < 1e-13 * vscale and np.abs(F[:, 4]).max() < 1e-13 * vscale
+
+
+# --------------------------------------------------------------------------
+# Sedov-Taylor blast (§3.1): shock radius of the self-similar solution
+# --------------------------------------------------------------------------
+def test_sedov_similarity_constant():
+    """The similarity integration (tests/sedov_similarity.py) reproduces the
+    textbook shock constants of the 3D blast, xi0 = 1.1517 at gamma = 5/3
+    and 1.0328 at gamma = 1.4, independently of its grid."""
+    import sedov_similarity as S
+    assert S.xi0(5.0 / 3.0) == pytest.approx(1.1517, abs=2e-4)
+    assert S.xi0(1.4) == pytest.approx(1.0328, abs=2e-4)
+    assert abs(S.xi0(5.0 / 3.0, n=4000) - S.xi0(5.0 / 3.0)) < 2e-5
+    # the profile starts from the strong-shock jump: rho = (g+1)/(g-1) rho1
+    pr = S.profile(5.0 / 3.0, n=2000)
+    assert pr[0, 1] == 4.0 and np.all(np.diff(pr[:, 1]) < 0)
+
+
+def _sedov_run(orc, n, t_end):
+    w = W.sedov(n)
+    cfg = orc.config(gamma=w["gamma"])
+    s, t = dict(w), 0.0
+    while t < t_end:
+        s, _, info = orc.step(cfg, s, -1.0)
+        assert info["status"] == 0
+        t += info["dt"]
+    return w, s, t
+
+
+def test_oracle_sedov_blast_follows_similarity_solution(orc):
+    """Sedov blast (the config-3 generator: energy 1 on the central 32
+    particles of a unit lattice, rho = 1) run by the oracle to t ~ 0.018:
+    the density-weighted radius of the shell (particles denser than halfway
+    between the ambient and the peak density) lies within 4 % of
+    R = xi0 (E t^2 / rho)^(1/5); total energy is conserved to 1e-13 (the
+    paper reports machine precision); the peak density rises with
+    resolution and stays below the strong-shock limit 4."""
+    import sedov_similarity as S
+    peaks = []
+    for n in (24, 32):
+        w, s, t = _sedov_run(orc, n, 0.0184)
+        R = S.shock_radius(1.0, t)
+        r = np.sqrt((s["x"] - 0.5) ** 2 + (s["y"] - 0.5) ** 2 + (s["z"] - 0.5) ** 2)
+        rho = s["m"] / s["omega"]
+        shell = rho > 0.5 * (1.0 + rho.max())
+        r_shell = np.average(r[shell], weights=rho[shell])
+        assert abs(r_shell / R - 1.0) < 0.04, (n, r_shell, R)
+        e0, e1 = math.fsum(w["E"]), math.fsum(s["E"])
+        assert abs(e1 - e0) < 1e-13 * e0
+        assert abs(math.fsum(s["m"]) - math.fsum(w["m"])) < 1e-13 * math.fsum(w["m"])
+        for k in ("px", "py", "pz"):
+            assert abs(math.fsum(s[k])) < 1e-13 * math.fsum(np.abs(s[k]))
+        peaks.append(rho.max())
+    assert 1.5 < peaks[0] < peaks[1] < 4.0, peaks
+
+
+# --------------------------------------------------------------------------
 # external acceleration (§2.3.8) integrated by the rule of §2.3.4
 # --------------------------------------------------------------------------
 def _uniform_moving(v0, n=8):
