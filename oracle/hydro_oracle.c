@@ -1032,8 +1032,21 @@ static void orc_face(const orc_config *c, int64_t i, int64_t j, const double d[3
         for (int f = 0; f < 5; f++) { L_[f] = Wi[f]; R_[f] = Wj[f]; }
         st->first_order++;
     }
-    /* boost to the frame moving with (v_i + v_j)/2, project on n */
-    double vf[3] = {0.5 * (Wi[1] + Wj[1]), 0.5 * (Wi[2] + Wj[2]), 0.5 * (Wi[3] + Wj[3])};
+    /* boost to the frame of the face, project on n.  The fluxes are those of
+     * the half step (Eq. 16), so the face moves with the mean of the two
+     * particles' velocities at the half step: each velocity advanced by the
+     * predictor's acceleration -grad p / rho over tl (resp. tr), the same
+     * times as the face states (with the predictor off: the velocities at
+     * the step's start). */
+    double vf[3];
+    for (int a = 0; a < 3; a++) {
+        double vi = Wi[1 + a], vj = Wj[1 + a];
+        if (c->time_extrap) {
+            vi -= tl * Gi[4][a] / Wi[0];
+            vj -= tr * Gj[4][a] / Wj[0];
+        }
+        vf[a] = 0.5 * (vi + vj);
+    }
     double vl[3], vr[3];
     for (int a = 0; a < 3; a++) { vl[a] = L_[1 + a] - vf[a]; vr[a] = R_[1 + a] - vf[a]; }
     double ul = vl[0] * nh[0] + vl[1] * nh[1] + vl[2] * nh[2];

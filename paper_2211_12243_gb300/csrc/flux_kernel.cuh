@@ -46,6 +46,8 @@ struct FluxArgs {
     double *dQ;              // 5 n, sorted SoA
     DevCounters *cnt;
     const unsigned char *mlp_blob;   // packed network (hard-face kernel)
+    int mlp_stall;                   // error-path test hook (hydro_test_mlp_stall)
+    int riemann_polish;              // float path: FP64 Newton step after convergence
     float *hard;             // deferred hard faces: FaceState fields [HF_N][hard_cap]
     int32_t *hard_idx;       // their owner and partner (sorted indices) [2][hard_cap]
     unsigned long long *hard_cursor;   // faces taken in each of the HARD_SUB sub-buffers
@@ -225,6 +227,10 @@ __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, 
         }
     }
     const R g = K.g;
+    // the face moves with the mean of the particles' velocities at the half
+    // step (the predictor's acceleration over hl, hr; Eq. 16's fluxes are
+    // those of the half step)
+    R av[3] = {R(0), R(0), R(0)};
     if (a.time_extrap) {
         R divi = Gi[3] + Gi[7] + Gi[11];
         R divj = Gj[3] + Gj[7] + Gj[11];
@@ -233,8 +239,10 @@ __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, 
         const R iri = div_(hl, ri[R_RHO]), irj = div_(hr, rj[R_RHO]);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            Lf[1 + q] -= Gi[12 + q] * iri;
-            Rf[1 + q] -= Gj[12 + q] * irj;
+            const R ai = Gi[12 + q] * iri, aj = Gj[12 + q] * irj;
+            Lf[1 + q] -= ai;
+            Rf[1 + q] -= aj;
+            av[q] = ai + aj;
         }
         Lf[4] -= hl * g * ri[R_P] * divi;
         Rf[4] -= hr * g * rj[R_P] * divj;
@@ -244,9 +252,9 @@ __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, 
         for (int f = 0; f < 5; f++) { Lf[f] = ri[R_RHO + f]; Rf[f] = rj[R_RHO + f]; }
         fs.first_order++;
     }
-    st.vf[0] = R(0.5) * (ri[R_VX] + rj[R_VX]);
-    st.vf[1] = R(0.5) * (ri[R_VY] + rj[R_VY]);
-    st.vf[2] = R(0.5) * (ri[R_VZ] + rj[R_VZ]);
+    st.vf[0] = R(0.5) * ((ri[R_VX] + rj[R_VX]) - av[0]);
+    st.vf[1] = R(0.5) * ((ri[R_VY] + rj[R_VY]) - av[1]);
+    st.vf[2] = R(0.5) * ((ri[R_VZ] + rj[R_VZ]) - av[2]);
     R vl[3], vr[3];
 #pragma unroll
     for (int q = 0; q < 3; q++) { vl[q] = Lf[1 + q] - st.vf[q]; vr[q] = Rf[1 + q] - st.vf[q]; }
@@ -297,7 +305,8 @@ __device__ __forceinline__ void face_finish(const FluxArgs &a, const GasK<R> &K,
     } else {
         R ps, us;
         R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)a.ptolf;
-        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, p0, tol, a.max_newton, ps, us);
+        const GasK<double> *kd = sizeof(R) == 4 && a.riemann_polish ? &a.Kd : nullptr;
+        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, p0, tol, a.max_newton, ps, us, kd);
         fs.iters += so.iters;
         if (so.vacuum) { fs.vacuum++; return; }
         ps_out = ps;
@@ -703,7 +712,7 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
     MlpTile &T = *reinterpret_cast<MlpTile *>(
         (reinterpret_cast<uintptr_t>(dyn_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, lane = tid & 31;
-    bool ok = mlp_tile_setup(T, a.mlp_blob);
+    bool ok = mlp_tile_setup(T, a.mlp_blob, a.mlp_stall != 0);
     uint32_t phase = 0;
     const GasK<float> &K = a.Kf;
     // tiles of 128 slots never straddle sub-buffers (their size is a

@@ -561,11 +561,12 @@ def _lattice_faces(orc, cfg, w, rho, v, p, dt):
 def test_predictor_accelerates_by_the_pressure_gradient(orc):
     """Perfect lattice at rest, linear density and pressure fields: Euler's
     momentum equation gives each side's velocity after half a step as
-    -dt/2 grad p / rho (the particle's own rho), so in the frame of the
-    pair (at rest) the face's normal velocities are -dt/2 (grad p . n) /
-    rho_i and -dt/2 (grad p . n) / rho_j; with div v = 0 density and
-    pressure only take their midpoint values.  On a cubic lattice B is
-    isotropic, so the face normal is the separation's direction."""
+    -dt/2 grad p / rho (the particle's own rho).  The face moves with the
+    mean of the two half-step velocities, so in its frame the normal
+    velocities are equal and opposite, u_L - u_R = -dt/2 (grad p . n)
+    (1/rho_i - 1/rho_j); with div v = 0 density and pressure only take
+    their midpoint values.  On a cubic lattice B is isotropic, so the face
+    normal is the separation's direction."""
     n = 12
     w = W.lattice_wave(n, jitter=0.0)
     cfg = orc.config()
@@ -585,8 +586,10 @@ def test_predictor_accelerates_by_the_pressure_gradient(orc):
     nh = d / np.linalg.norm(d, axis=1)[:, None]
     xm = x[i] + 0.5 * d
     scale = 0.5 * dt * np.linalg.norm(g_p) / rho.min()
-    assert np.abs(F[:, 1] - (-0.5 * dt * (nh @ g_p) / rho[i])).max() < 1e-12 * scale
-    assert np.abs(F[:, 4] - (-0.5 * dt * (nh @ g_p) / rho[j])).max() < 1e-12 * scale
+    rel = -0.5 * dt * (nh @ g_p) * (1.0 / rho[i] - 1.0 / rho[j])
+    assert np.abs(rel).max() > 1e-3 * scale
+    assert np.abs((F[:, 1] - F[:, 4]) - rel).max() < 1e-12 * scale
+    assert np.abs(F[:, 1] + F[:, 4]).max() < 1e-12 * scale
     for k in (0, 3):
         assert np.abs(F[:, k] - (2.5 + xm @ g_rho)).max() < 1e-13 * 2.5
     for k in (2, 5):
@@ -673,6 +676,64 @@ def test_oracle_sedov_blast_follows_similarity_solution(orc):
             assert abs(math.fsum(s[k])) < 1e-13 * math.fsum(np.abs(s[k]))
         peaks.append(rho.max())
     assert 1.5 < peaks[0] < peaks[1] < 4.0, peaks
+
+
+# --------------------------------------------------------------------------
+# sound wave (§3.1): second-order convergence of the linear solution
+# --------------------------------------------------------------------------
+def _soundwave(n, A, gamma=1.4, planes=8, n_ngb=32.0):
+    """One wavelength along x of a unit box, `planes` lattice planes across;
+    rho = 1 + A cos(2 pi x), p = 1 + gamma A cos(2 pi x), v_x = A c_s cos(2 pi x)
+    (through the masses and energies of a uniform lattice)."""
+    a = 1.0 / n
+    i, j, k = np.meshgrid(np.arange(n), np.arange(planes), np.arange(planes), indexing="ij")
+    x, y, z = (i.ravel() + 0.5) * a, (j.ravel() + 0.5) * a, (k.ravel() + 0.5) * a
+    cs = math.sqrt(gamma)
+    ph = np.cos(2.0 * math.pi * x)
+    rho, p, vx = 1.0 + A * ph, 1.0 + gamma * A * ph, A * cs * ph
+    m = rho * a ** 3
+    U = p * a ** 3 / (gamma - 1.0)
+    h = np.full(x.size, (3.0 * n_ngb / (4.0 * math.pi)) ** (1.0 / 3.0) * a)
+    return dict(x=x, y=y, z=z, m=m, px=m * vx, py=0.0 * x, pz=0.0 * x, E=U + 0.5 * m * vx * vx,
+                U=U, h=h, L=np.array([1.0, planes * a, planes * a]), gamma=gamma), cs
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_oracle_soundwave_converges_at_second_order(orc, scheme):
+    """The paper's sound-wave test (§3.1: gamma = 1.4, c_s = sqrt(gamma),
+    N_NGB = 32, cubic spline, limiter off) run by the oracle for one
+    crossing time at N = 16, 32, 64 particles per wavelength: the L1 error of
+    the density against the linear solution falls at second order (the paper
+    finds both schemes second order).  The amplitude is 1e-5, not the
+    paper's 1e-3: at 1e-3 the wave's own nonlinear steepening over one
+    crossing (an O(A^2) departure from the linear solution) is reached by
+    N = 64, which the paper notes as the floor of the L1 norm.  Transverse
+    velocities stay at rounding level."""
+    A, gamma = 1e-5, 1.4
+    l1 = {}
+    for n in (16, 32, 64):
+        w, cs = _soundwave(n, A, gamma)
+        cfg = orc.config(gamma=gamma, kernel="cubic", scheme=scheme, limiter=False, c_cfl=0.1)
+        t_end = 1.0 / cs
+        s, t, dt_next = w, 0.0, None
+        while t < t_end * (1.0 - 1e-12):
+            dt = -1.0 if dt_next is None or t + dt_next < t_end else t_end - t
+            s, _, info = orc.step(cfg, s, dt)
+            assert info["status"] == 0
+            t += info["dt"]
+            dt_next = info["dt_next"]
+        _, om, _, _ = orc.density(cfg, s["x"], s["y"], s["z"], s["L"], s["h"])
+        rho = s["m"] / om
+        # the kernel estimate of a lattice's density is uniformly biased by a
+        # few per cent: the perturbation is measured against its mean
+        delta = rho / rho.mean() - 1.0
+        exact = A * np.cos(2.0 * math.pi * s["x"] - 2.0 * math.pi * cs * t)
+        l1[n] = float(np.mean(np.abs(delta - exact)))
+        vt = np.sqrt(np.mean((s["py"] / s["m"]) ** 2 + (s["pz"] / s["m"]) ** 2))
+        assert vt < 1e-12, (n, vt)
+    assert math.log2(l1[16] / l1[32]) > 1.7, l1
+    assert math.log2(l1[32] / l1[64]) > 1.9, l1
+    assert l1[64] < 1e-2 * A, l1
 
 
 # --------------------------------------------------------------------------
