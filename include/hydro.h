@@ -112,6 +112,13 @@ typedef struct {
     double c_acc;        /* hydro_step_rungs: acceleration timestep factor,
                             dt_acc = c_acc sqrt(h / |a|) (§2.3.10; 0.2) */
     int max_rung;        /* hydro_step_rungs: deepest rung (12, at most 20) */
+    int riemann_polish;  /* mixed precision, exact solver: 1 takes one more
+                            Newton step of Toro's pressure function in FP64
+                            once the float iteration has converged, so p* and
+                            u* are the roots of the (float) face states to
+                            double precision before they are rounded to float
+                            for the flux; 0 (default): the float iteration
+                            alone (its root is within a few float ulps) */
 } hydro_config;
 
 /* Caller-owned particle state, caller order, all device pointers, n each.
@@ -158,7 +165,10 @@ typedef struct {
     int ngb_rounds;           /* N_cond growth rounds taken */
     int64_t ncond_fail;       /* particles above the threshold at the end */
     int list_rebuilds;        /* neighbour-list rebuilds for h beyond the radius */
-    double mass[2], mom[2][3], energy[2];   /* totals before / after the step */
+    double mass[2], mom[2][3], energy[2];   /* totals of the state before / after the
+                                 step: compensated sums in a fixed order over
+                                 the particles, so any difference is the
+                                 step's (fluxes and external sources) */
     float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
     float ms_flux_kernel;     /* the pair-flux kernel alone (CUDA events on the stream) */
     float ms_hard_faces;      /* the learned-guess hard-face kernel (0 when off) */
@@ -247,7 +257,13 @@ int hydro_fluxes(hydro_ctx *ctx, const hydro_particles *p, const double *B,
  * given dt (dt <= 0: CFL dt = min_i c_cfl h_i / v_sig,i, Eqs. 31-32),
  * conserved update (Eq. 16), internal energy (Eq. 24) and drift
  * x += dt (v^n + v^{n+1}) / 2 wrapped into the box.  Updates p in place.
- * stats (host, optional): filled after a stream synchronisation. */
+ * stats (host, optional): filled after a stream synchronisation.
+ * Errors that leave p exactly as it was: a non-finite value anywhere in
+ * the caller's state (HYDRO_ENONFINITE, found by a check before any other
+ * work), an h iteration that did not converge within max_h_iter
+ * (HYDRO_ENOCONV_H), a tensor-core wait of the learned guess that gave up
+ * (HYDRO_EMLP).  HYDRO_ENCOND (particles still ill-conditioned after all
+ * N_NGB growths) completes the step and reports them. */
 int hydro_step(hydro_ctx *ctx, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream);
 
@@ -381,6 +397,17 @@ int hydro_record_faces(hydro_ctx *ctx, float *buf, int64_t capacity, double keep
  * capacity were not stored).  Synchronising. */
 int hydro_recorded_faces(hydro_ctx *ctx, int64_t *count, hydro_stream stream);
 
+/* Test hook of the learned guess's error path (no counterpart in the
+ * paper).  With on = 1 the network's kernels of this context (the
+ * hard-face pass of hydro_step and hydro_mlp_predict) do not issue the copy
+ * of the weights into shared memory, so the wait on its barrier can never
+ * finish: it gives up after a short poll limit (about 0.3 ms), the kernel
+ * records HYDRO_EMLP, releases its tensor memory (nothing is in flight) and
+ * every face keeps the plain guess.  hydro_step then returns HYDRO_EMLP and
+ * leaves the state untouched; hydro_sync_status reports it after
+ * hydro_mlp_predict.  on = 0 restores the normal path.  EINVAL otherwise. */
+int hydro_test_mlp_stall(hydro_ctx *ctx, int on);
+
 /* Totals over the n particles of mass, px, py, pz and etot (compensated
  * sums), written to totals[0..4] (device), computed without allocating
  * anything and without a context.  For callers that cannot call cudaMalloc
@@ -393,7 +420,10 @@ int hydro_recorded_faces(hydro_ctx *ctx, int64_t *count, hydro_stream stream);
  * Scratch: a fixed 640 KiB array in the library's static device memory,
  * held by every GPU that loads the library until the process exits.  The
  * first call on a device looks up that array's device address (once per
- * device, with the device current); later calls reuse it.  All calls share
+ * device, with the device current) and later calls reuse it, so make that
+ * first call before capturing any stream, and do not call the entry point
+ * again after cudaDeviceReset in the same process (the reset unloads the
+ * array; the remembered address would be stale).  All calls share
  * the array: each overwrites the part it uses, so nothing needs clearing,
  * but calls that overlap on the GPU race on it.  Asynchronous on stream. */
 int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const double *py,
@@ -410,8 +440,9 @@ int hydro_totals_noalloc(int64_t n, const double *mass, const double *px, const 
  * the work on the exchanged mass, (1/2) a . sum_j dm_ij r_ij (dm_ij the mass
  * i gains from j through their face, r_ij = x_i - x_j; zero for MFM).  The
  * internal energy takes no source.  E_grav = m |a| h enters the
- * total-energy pressure switch (§2.3.7).  The totals in hydro_stats then
- * include the work of the external force.  Always HYDRO_OK for a context. */
+ * total-energy pressure switch (§2.3.7).  The totals in hydro_stats are
+ * taken before and after the step, so their difference is the external
+ * impulse and work (the fluxes conserve their part).  Always HYDRO_OK for a context. */
 int hydro_set_gravity(hydro_ctx *ctx, const double *acc);
 
 /* The entropic function A of the entropy switch (§2.3.7) for the following

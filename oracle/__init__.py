@@ -21,15 +21,30 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
+_CNT_SRC = os.path.join(_HERE, "flopcount.cpp")
+_CNT_LIB = os.path.join(_HERE, "libflopcount.so")
+_cnt = None
+
+
+def _fresh(lib, *srcs):
+    return os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(s) for s in srcs)
+
+
 def build(force=False):
-    """Compile the oracle shared library (seconds)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    """Compile the oracle shared library and its operation-counting build
+    (seconds)."""
+    if force or not _fresh(_LIB, _SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    if force or not _fresh(_CNT_LIB, _SRC, _CNT_SRC):
+        tmp = _CNT_LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-w", "-o", tmp, _CNT_SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _CNT_LIB)
     return _LIB
 
 
@@ -279,6 +294,31 @@ def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
                      _p(dM), _p(AA), _p(dS))
     out = (dQ, st.as_dict(), faces) + ((dQabs,) if want_abs else ()) + ((dM,) if want_dM else ())
     return out + ((dS,) if A is not None else ())
+
+
+OP_KEYS = ("add", "mul", "div", "sqrt", "pow", "cmp", "fabs", "faces", "newton_iters")
+
+
+def count_face_ops(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs):
+    """Operations of the oracle's per-face arithmetic over the given pairs
+    (flopcount.cpp: the oracle compiled with a counting scalar type), as a
+    dict of OP_KEYS totals.  Single-threaded."""
+    global _cnt
+    if _cnt is None:
+        build()
+        _cnt = C.CDLL(_CNT_LIB)
+        _cnt.orc_count_faces.restype = None
+        _cnt.orc_count_faces.argtypes = [C.POINTER(Config), C.c_int64] + [C.c_void_p] * 14 + [
+            C.c_double, C.c_int64, C.c_void_p, C.c_void_p]
+    x, y, z, L, h, omega, B6 = map(_f64, (x, y, z, L, h, omega, B6))
+    grad, alpha = _f64(grad), _f64(alpha)
+    rho, vx, vy, vz, p = map(_f64, prims)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int64)
+    out = np.zeros(9, dtype=np.int64)
+    _cnt.orc_count_faces(C.byref(cfg), x.size, _p(x), _p(y), _p(z), _p(L), _p(h), _p(omega),
+                         _p(B6), _p(rho), _p(vx), _p(vy), _p(vz), _p(p), _p(grad), _p(alpha),
+                         float(dt), pairs.shape[0], _p(pairs), _p(out))
+    return {k: int(v) for k, v in zip(OP_KEYS, out)}
 
 
 def riemann_guess(rl, ul, pl, rr, ur, pr, g):

@@ -49,6 +49,7 @@ bool valid_config(const hydro_config *c) {
     if (!(c->alpha2 >= 0.0) || !(c->alpha3 >= 0.0) || !isfinite(c->alpha2) || !isfinite(c->alpha3))
         return false;
     if (!(c->c_acc > 0.0) || c->max_rung < 0 || c->max_rung > 20) return false;
+    if (c->riemann_polish != 0 && c->riemann_polish != 1) return false;
     return true;
 }
 
@@ -302,6 +303,7 @@ void hydro_config_default(hydro_config *c) {
     c->alpha3 = 1e-3;
     c->c_acc = 0.2;
     c->max_rung = 12;
+    c->riemann_polish = 0;
 }
 
 int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
@@ -316,6 +318,7 @@ int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_cnt, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_learn, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters));
+    if (e == cudaSuccess) e = ensure_sum_partials(c);
     if (e == cudaSuccess) {
         for (int k = 0; k < 10 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
         c->have_events = e == cudaSuccess;
@@ -503,6 +506,16 @@ int hydro_fluxes(hydro_ctx *c, const hydro_particles *p, const double *B, const 
 static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
                      hydro_stream stream);
 
+// every value of the caller's state finite, checked before anything runs
+// (a non-finite input returns HYDRO_ENONFINITE and changes nothing)
+static int check_inputs(hydro_ctx *c, const hydro_particles *p, cudaStream_t st) {
+    API_CUDA(run_check_inputs(c, p, st));
+    int bad = 0;
+    API_CUDA(cudaMemcpyAsync(&bad, &c->d_cnt->bad_input, sizeof(int), cudaMemcpyDeviceToHost, st));
+    API_CUDA(cudaStreamSynchronize(st));
+    return bad ? HYDRO_ENONFINITE : HYDRO_OK;
+}
+
 int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream) {
     if (stats) memset(stats, 0, sizeof(*stats));
@@ -576,6 +589,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         return HYDRO_EINVAL;
     if (c->grav || c->cfg.entropy_switch) return HYDRO_ESTATE;
     const int64_t n = p->n;
+    if (int rc0 = check_inputs(c, p, st)) return rc0;
     API_CUDA(ensure_state(c, n));
     API_CUDA(c->d_rung_c.ensure(n));
     API_CUDA(c->d_kstart_c.ensure(n));
@@ -665,9 +679,10 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         }
         API_CUDA(rung_records(c, true, st));
         API_CUDA(run_fluxes(c, dtmin, nullptr, st));
-        API_CUDA(run_update(c, p, dtmin, nullptr, false, st));
         // totals before the first sub-step and after the last
-        if (stats && (k == 0 || k == K - 1)) API_CUDA(run_update_sums(c, st));
+        if (stats && k == 0) API_CUDA(run_sums(c, 0, st));
+        API_CUDA(run_update(c, p, dtmin, nullptr, false, 0, st));
+        if (stats && k == K - 1) API_CUDA(run_sums(c, 1, st));
         API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
         const DevCounters &H = *c->h_cnt;
@@ -722,6 +737,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = p->n;
     const bool timing = stats != nullptr && c->have_events;
+    if (int rc0 = check_inputs(c, p, st)) return rc0;
     API_CUDA(ensure_state(c, n));
     // the first step of a context runs host-driven (it sizes every buffer);
     // later ones replay the captured graph unless it asks for the host path
@@ -770,8 +786,9 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     c->timing = false;
     API_CUDA((cudaError_t)rc);
     if (timing) API_CUDA(record_event(c->ev[4], st));
-    API_CUDA(run_update(c, p, dt, dt_dev, false, st));
-    if (stats) API_CUDA(run_update_sums(c, st));
+    if (stats) API_CUDA(run_sums(c, 0, st));
+    API_CUDA(run_update(c, p, dt, dt_dev, false, STEP_SKIP_FLAGS, st));
+    if (stats) API_CUDA(run_sums(c, 1, st));
     if (timing) API_CUDA(record_event(c->ev[5], st));
     c->last_stats.ngb_rounds = rounds;
     c->last_stats.list_rebuilds = rebuilds;
@@ -823,6 +840,12 @@ static const size_t kMlpParams = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 24 + 2 +
 static const size_t kMlpScale = 12 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 12;   // scale[12]
 static const size_t kMlpTScale = kMlpScale + 13;
 static const size_t kMlpXmin = kMlpTScale + 1;
+
+int hydro_test_mlp_stall(hydro_ctx *c, int on) {
+    if (!c || (on != 0 && on != 1)) return HYDRO_EINVAL;
+    c->mlp_stall = on;
+    return HYDRO_OK;
+}
 
 int hydro_mlp_load(hydro_ctx *c, const void *weights, size_t bytes) {
     if (!c || !weights) return HYDRO_EINVAL;

@@ -157,6 +157,8 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.dQ = c->d_dQ.get();
     a.cnt = c->d_cnt;
     a.mlp_blob = c->d_mlp_blob.get();
+    a.mlp_stall = c->mlp_stall;
+    a.riemann_polish = c->cfg.riemann_polish;
     a.hard = nullptr;
     a.hard_idx = nullptr;
     a.hard_cursor = nullptr;

@@ -168,8 +168,9 @@ cudaError_t enqueue_step(hydro_ctx *c, hydro_particles *p, double dt, bool sums,
     c->timing = false;
     HYD_CUDA(e);
     if (timing) HYD_CUDA(record_event(c->ev[4], st));
-    HYD_CUDA(run_update(c, p, dt, dt_dev, true, st));
-    if (sums) HYD_CUDA(run_update_sums(c, st));
+    if (sums) HYD_CUDA(run_sums(c, 0, st));
+    HYD_CUDA(run_update(c, p, dt, dt_dev, true, STEP_SKIP_FLAGS, st));
+    if (sums) HYD_CUDA(run_sums(c, 1, st));
     if (timing) HYD_CUDA(record_event(c->ev[5], st));
     return cudaSuccess;
 }
@@ -214,6 +215,7 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
                           (const void *)c->d_ecand.get(), (const void *)c->d_dS.get()})
         put(q);
     k.push_back((unsigned long long)c->rec_cap);
+    k.push_back((unsigned long long)c->mlp_stall);
     k.push_back((unsigned long long)c->rec_keep | ((unsigned long long)c->rec_hard_only << 32));
     for (const void *q :
          {(const void *)c->d_node_first.get(), (const void *)c->d_node_cnt.get(),

@@ -97,6 +97,7 @@ struct DevCounters {
     int rung_max;                     // the deepest rung
     int rung_capped;                  // particles the criteria wanted beyond max_rung
     unsigned long long rung_active;   // particles starting a step in this sub-step
+    int bad_input;                    // a non-finite value in the caller's state
 };
 
 // bucket tree topology (host plan, mirrored on the device)
@@ -229,6 +230,7 @@ struct hydro_ctx {
     hyd::DevBuf<double> d_mlp_acc;
     hyd::DevBuf<int> d_mlp_box;       // feature min / max as ordered integers
     bool have_mlp = false;
+    int mlp_stall = 0;                // error-path test hook (hydro_test_mlp_stall)
 
     // hard faces deferred to the learned-guess pass (FaceState fields, owner/partner)
     hyd::DevBuf<float> d_hard;
@@ -413,14 +415,18 @@ cudaError_t mlp_normalise(hydro_ctx *c, const float *x, const float *t, int64_t 
                           int *box, stream_t st);
 
 // update.cu (abort_check: skip the update when the device step set an abort
-// condition -- see graph.cu)
+// condition -- see graph.cu; skip_flags: status bits whose presence leaves
+// the caller's state untouched)
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
-                       bool abort_check, stream_t st);
+                       bool abort_check, int skip_flags, stream_t st);
+// status bits after which hydro_step leaves the caller's state as it was
+constexpr int STEP_SKIP_FLAGS = ST_NOCONV_H | ST_MLP;
 // *p = v on the stream (a kernel: no host memory is referenced, so the call
 // can be captured into a graph)
 cudaError_t set_u64(unsigned long long *p, unsigned long long v, stream_t st);
 cudaError_t run_sums(hydro_ctx *c, int which, stream_t st);
-cudaError_t run_update_sums(hydro_ctx *c, stream_t st);
+cudaError_t ensure_sum_partials(hydro_ctx *c);
+cudaError_t run_check_inputs(hydro_ctx *c, const hydro_particles *p, stream_t st);
 cudaError_t export_dQ(hydro_ctx *c, double *dQ, stream_t st);
 
 }  // namespace hyd

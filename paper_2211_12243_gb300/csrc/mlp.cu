@@ -65,11 +65,11 @@ __global__ void k_mlp_pack(const float *__restrict__ theta, unsigned char *__res
 __global__ void __launch_bounds__(128) k_mlp_predict(int64_t n, const float *__restrict__ faces,
                                                      const unsigned char *__restrict__ blob,
                                                      GasK<float> K, float *__restrict__ out,
-                                                     DevCounters *cnt) {
+                                                     DevCounters *cnt, int stall) {
     extern __shared__ unsigned char smem_raw[];
     MlpTile &t = tile_of(smem_raw);
     const int tid = threadIdx.x;
-    bool ok = mlp_tile_setup(t, blob);
+    bool ok = mlp_tile_setup(t, blob, stall != 0);
     uint32_t phase = 0;
     const int64_t ntile = (n + 127) / 128;
     for (int64_t tile = blockIdx.x; ok && tile < ntile; tile += gridDim.x) {
@@ -349,7 +349,8 @@ cudaError_t mlp_predict(hydro_ctx *c, const float *faces, int64_t n, float *out,
     const int64_t ntile = (n + 127) / 128;
     const unsigned grid = (unsigned)std::min<int64_t>(ntile > 0 ? ntile : 1, 152 * 4);
     k_mlp_predict<<<grid, 128, smem, st>>>(n, faces, c->d_mlp_blob.get(),
-                                           GasK<float>(c->cfg.gamma), out, c->d_cnt);
+                                           GasK<float>(c->cfg.gamma), out, c->d_cnt,
+                                           c->mlp_stall);
     return launch_check();
 }
 

@@ -140,6 +140,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int ma
     return false;
 }
 
+// non-blocking variant for the error-path test hook: test_wait never
+// suspends, so max_polls bounds the time (about 0.1 us per poll)
+__device__ __forceinline__ bool mbar_poll(uint32_t mbar, uint32_t parity, int max_polls) {
+    for (int i = 0; i < max_polls; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity));
+        if (done) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -223,6 +240,10 @@ constexpr int MLP_FB1 = 0, MLP_FB2 = 64, MLP_FW3 = 128, MLP_FMEAN = 192, MLP_FSC
               MLP_FXMAX = 231;
 constexpr uint32_t MLP_TMEM_COLS = 64;
 constexpr int MLP_WAIT_SPINS = 1 << 22;   // ~0.3 s of polling before giving up
+// the error-path test hook (hydro_test_mlp_stall): the weight copy is not
+// issued, so the set-up's wait can never finish and gives up after this
+// many polls (~0.3 ms); nothing is in flight when it does
+constexpr int MLP_STALL_POLLS = 4096;
 
 struct MlpTile {
     alignas(1024) unsigned char wb[MLP_BLOB];
@@ -237,8 +258,10 @@ __device__ __forceinline__ const float *mlp_f(const MlpTile &t) {
 }
 
 // all threads; returns false (and the tile is unusable) when the weight copy
-// did not arrive within the wait limit
-__device__ __forceinline__ bool mlp_tile_setup(MlpTile &t, const unsigned char *blob) {
+// did not arrive within the wait limit.  stall: the test hook -- no copy is
+// issued and the wait on its barrier runs out
+__device__ __forceinline__ bool mlp_tile_setup(MlpTile &t, const unsigned char *blob,
+                                               bool stall = false) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(smem_u32(&t.mbar_w), 1);
@@ -249,6 +272,10 @@ __device__ __forceinline__ bool mlp_tile_setup(MlpTile &t, const unsigned char *
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (stall) {
+        const bool none = mbar_poll(smem_u32(&t.mbar_w), 0, MLP_STALL_POLLS);
+        return !__syncthreads_or(!none);
+    }
     if (tid == 0) {
         mbar_expect_tx(smem_u32(&t.mbar_w), MLP_BLOB);
         bulk_g2s(smem_u32(t.wb), blob, MLP_BLOB, smem_u32(&t.mbar_w));

@@ -119,10 +119,13 @@ struct StarOut {
 
 // Newton iteration for p* from p0 (> 0, else the adaptive guess); stop when
 // the relative change falls below tol, then one more Newton step; bisection
-// on the bracket after max_newton iterations.
+// on the bracket after max_newton iterations.  kd (float path only, else
+// NULL): after the float iteration converged, one more Newton step with the
+// pressure function evaluated in FP64, and u* from it.
 template <typename R>
 __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
-                                              R p0, R tol, int max_newton, R &ps, R &us) {
+                                              R p0, R tol, int max_newton, R &ps, R &us,
+                                              const GasK<double> *kd = nullptr) {
     StarOut o{0, 0, 0};
     R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
     R du = ur - ul;
@@ -148,6 +151,24 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
         p = pn;
         o.iters = it;
         if (ch < tol) { conv = true; break; }
+    }
+    if (conv && sizeof(R) == 4 && kd) {
+        // the root of the float face states to double precision: one Newton
+        // step of f(p) = f_L(p) + f_R(p) + u_R - u_L evaluated in FP64 from
+        // the converged float root, then u* from the same evaluation
+        // corrected to first order for that step
+        const double pd = (double)p;
+        const double rld = rl, uld = ul, pld = pl, rrd = rr, urd = ur, prd = pr;
+        const double cld = sqrt(kd->g * pld / rld), crd = sqrt(kd->g * prd / rrd);
+        double fld, dfld, frd, dfrd;
+        side_f<double>(*kd, pd, rld, pld, cld, fld, dfld);
+        side_f<double>(*kd, pd, rrd, prd, crd, frd, dfrd);
+        const double dpd = -(fld + frd + (urd - uld)) / (dfld + dfrd);
+        if (pd + dpd > 0.0) {
+            ps = (R)(pd + dpd);
+            us = (R)(0.5 * (uld + urd) + 0.5 * (frd - fld) + 0.5 * (dfrd - dfld) * dpd);
+            return o;
+        }
     }
     if (conv && sizeof(R) == 4) {
         // float: the iteration has converged to rounding; u* from the last

@@ -100,7 +100,10 @@ extern "C" int hydro_totals_noalloc(int64_t n, const double *mass, const double 
     double *scratch = nullptr;
     {
         // set-up, once per device, with that device current: the device
-        // address of the scratch array (its host-side name is not one)
+        // address of the scratch array (its host-side name is not one).
+        // The first call on a device should precede any stream capture;
+        // a cudaDeviceReset unloads the array and leaves this address
+        // stale, so the entry point is not for use after a reset
         std::lock_guard<std::mutex> lock(g_tot_mutex);
         if (!g_tot_ptr[dev]) {
             void *p = nullptr;

@@ -1,6 +1,9 @@
 // End of the step (§2.3.4 Eq. 16, §2.3.7 Eq. 24): conserved update, the
 // separately integrated internal energy, the drift, and compensated
-// totals of mass, momentum and energy for the conservation diagnostics.
+// totals of mass, momentum and energy for the conservation diagnostics
+// (taken before the update and after it, so external sources count).
+#include <algorithm>
+
 #include "hydro_internal.cuh"
 
 namespace hyd {
@@ -23,6 +26,7 @@ struct UpdArgs {
     hydro_particles p;
     DevCounters *cnt;
     bool abort_check;
+    int skip_flags;        // status bits that leave the caller's state untouched
     const double *agrav;   // sorted SoA 3 n (NULL: no gravity)
     const double *dM;      // sum_j dm_ij r_ij, sorted SoA 3 n
     // entropy switch (§2.3.7): the value of A the step used (sorted; NULL:
@@ -41,6 +45,9 @@ __global__ void k_update(UpdArgs a) {
         const DevCounters &k = *a.cnt;
         if (k.abort || k.hard_ovf || (k.flags & (ST_LIST_CAPACITY | ST_STACK))) return;
     }
+    // an error the step reports (h not converged, the network's wait gave
+    // up): the caller's state stays as it was
+    if (a.skip_flags && (a.cnt->flags & a.skip_flags)) return;
     const int64_t n = a.n;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     double m0 = a.Q[s], px0 = a.Q[n + s], py0 = a.Q[2 * n + s], pz0 = a.Q[3 * n + s];
@@ -92,28 +99,17 @@ __global__ void k_update(UpdArgs a) {
     if (a.A1) a.A_out[o] = a.dS ? (m0 * a.A1[s] + a.dS[s]) / m1 : a.A1[s];
 }
 
-// totals before / after the update, reduced per warp and added to the
-// counters (diagnostics; the order of the block sums is not fixed)
-__global__ void k_update_sums(int64_t n, const double *__restrict__ Q, const double *__restrict__ dQ,
-                              double *__restrict__ out) {
-    double v[10];
+// every value of the caller's state finite (positions, conserved
+// quantities, smoothing lengths); a bad one sets bad_input
+__global__ void k_check_inputs(int64_t n, hydro_particles p, int *bad) {
+    const double *arr[10] = {p.x, p.y, p.z, p.mass, p.px, p.py, p.pz, p.etot, p.eint, p.h};
+    bool ok = true;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-    for (int q = 0; q < 10; q++) v[q] = 0.0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int q = 0; q < 5; q++) {
-            double now = Q[q * n + s];
-            v[5 + q] += now;
-            v[q] += now - dQ[q * n + s];
-        }
+        for (int q = 0; q < 10; q++) ok = ok && isfinite(arr[q][i]);
     }
-#pragma unroll
-    for (int q = 0; q < 10; q++)
-        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int q = 0; q < 10; q++) atomicAdd(&out[q], v[q]);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
 struct KS {
@@ -181,7 +177,7 @@ cudaError_t set_u64(unsigned long long *p, unsigned long long v, stream_t st) {
 }
 
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
-                       bool abort_check, stream_t st) {
+                       bool abort_check, int skip_flags, stream_t st) {
     UpdArgs a;
     a.n = c->plan.n;
     a.perm = c->d_perm.get();
@@ -197,6 +193,7 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.p = *p;
     a.cnt = c->d_cnt;
     a.abort_check = abort_check;
+    a.skip_flags = skip_flags;
     a.agrav = c->grav_live ? c->d_agrav.get() : nullptr;
     a.dM = c->grav_live ? c->d_dM.get() : nullptr;
     a.A1 = c->ent_live ? c->d_A1.get() : nullptr;
@@ -206,18 +203,27 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     return launch_check();
 }
 
-cudaError_t run_update_sums(hydro_ctx *c, stream_t st) {
-    k_update_sums<<<SUM_BLOCKS, SUM_THREADS, 0, st>>>(c->plan.n, c->d_Q.get(), c->d_dQ.get(),
-                                                      &c->d_cnt->sums[0][0]);
-    return launch_check();
+// totals of m, px, py, pz, E over the sorted conserved state, into
+// sums[which] of the counters: compensated (Kahan-Babuska) sums per thread,
+// per block and over the blocks in a fixed order, so the result does not
+// depend on scheduling.  The partials buffer is allocated with the state
+// (ensure_sum_partials), never here, so the step can be captured.
+cudaError_t ensure_sum_partials(hydro_ctx *c) {
+    return c->d_partials.ensure((size_t)SUM_BLOCKS * 5);
 }
 
 cudaError_t run_sums(hydro_ctx *c, int which, stream_t st) {
     const int64_t n = c->plan.n;
-    HYD_CUDA(c->d_partials.ensure((size_t)SUM_BLOCKS * 5));
     k_sums<<<SUM_BLOCKS, SUM_THREADS, 0, st>>>(n, c->d_Q.get(), c->d_partials.get());
     HYD_CUDA(launch_check());
     k_sums_final<<<1, 32, 0, st>>>(c->d_partials.get(), SUM_BLOCKS, c->d_cnt->sums[which]);
+    return launch_check();
+}
+
+cudaError_t run_check_inputs(hydro_ctx *c, const hydro_particles *p, stream_t st) {
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->bad_input, 0, sizeof(int), st));
+    const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>((p->n + 255) / 256, 1), SUM_BLOCKS);
+    k_check_inputs<<<grid, 256, 0, st>>>(p->n, *p, &c->d_cnt->bad_input);
     return launch_check();
 }
 

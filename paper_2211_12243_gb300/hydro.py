@@ -47,7 +47,7 @@ class Config(C.Structure):
         ("h_tol", C.c_double), ("p_tol", C.c_double), ("max_h_iter", C.c_int),
         ("max_newton", C.c_int), ("search_margin", C.c_double), ("graph", C.c_int),
         ("entropy_switch", C.c_int), ("alpha2", C.c_double), ("alpha3", C.c_double),
-        ("c_acc", C.c_double), ("max_rung", C.c_int),
+        ("c_acc", C.c_double), ("max_rung", C.c_int), ("riemann_polish", C.c_int),
     ]
 
 
@@ -110,7 +110,7 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
            "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity",
-           "hydro_set_entropy", "hydro_step_rungs"]
+           "hydro_set_entropy", "hydro_step_rungs", "hydro_test_mlp_stall"]
 
 
 def _load():
@@ -150,6 +150,7 @@ def _load():
         L.hydro_set_tuning.argtypes = [vp, P(Tuning)]
         L.hydro_set_gravity.argtypes = [vp, vp]
         L.hydro_set_entropy.argtypes = [vp, vp]
+        L.hydro_test_mlp_stall.argtypes = [vp, C.c_int]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
@@ -164,7 +165,7 @@ def totals_noalloc(st, out=None, stream=None):
     device tensor of 5 doubles."""
     import torch
     if out is None:
-        out = torch.empty(5, dtype=torch.float64, device=st["x"].device)
+        out = torch.empty(5, dtype=torch.float64, device=st["m"].device)
     n = st["m"].numel()
     rc = _load().hydro_totals_noalloc(n, _ptr(st["m"]), _ptr(st["px"]), _ptr(st["py"]),
                                       _ptr(st["pz"]), _ptr(st["E"]), _ptr(out), _stream(stream))
@@ -368,6 +369,13 @@ class Hydro:
         rc = self.lib.hydro_set_gravity(self.h, _ptr(acc) if acc is not None else None)
         if rc:
             raise HydroError(rc, "hydro_set_gravity")
+
+    def test_mlp_stall(self, on):
+        """Error-path test hook: the network's weight copy is not issued, so
+        its kernels' first wait runs out (hydro_test_mlp_stall)."""
+        rc = self.lib.hydro_test_mlp_stall(self.h, int(on))
+        if rc:
+            raise HydroError(rc, "hydro_test_mlp_stall")
 
     def set_entropy(self, A):
         """A: CUDA float64 tensor [n] (caller order), the entropic function
