@@ -8,16 +8,20 @@ recorded by the library around each stage, summed over the timed steps).
 The throughput over the whole step (neighbour search, density, gradients,
 fluxes, update) is reported beside it as `step_rate`.
 
-Default workload: the 3D Sod tube of 1,067,742 particles (4 x 1 x 1
-periodic box, left rho = 1, P = 1 at spacing 1/78, right rho = 0.125,
-P = 0.1 at spacing 2/78, gamma = 5/3, Wendland C2, N_NGB = 32, exact
-Riemann solver, MFV), mixed precision with the learned starting pressure.
+Default workload: one clustered log-normal box of 2^27 particles (density
+contrast 1e4 on a 256^3 Gaussian field, P ~ rho^gamma, Gaussian velocities
+of 0.1 c_s, gamma = 5/3, Wendland C2, N_NGB = 32, exact Riemann solver,
+MFV), mixed precision with the adaptive learned starting pressure.  Every
+step starts from the initial state with its converged smoothing lengths.
 Before the timed region (untimed) the network is trained on the GPU by the
-library's kernels on hard faces recorded from steps of the Sod tube, a
-log-normal field and a Sedov blast.  The mixed step with the plain guess
-and the plain FP64 step are timed on the same state for comparison.
+library's kernels on hard faces recorded from steps of the workload itself,
+a small log-normal field and a Sedov blast.  After it, on the same initial
+state: the mixed step with the plain guess, and the plain FP64 step, which
+also gives the mixed step's error at full size; the oracle times a sample of
+the same generator on the host cores and checks the GPU on that sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload lognormal|sod|sedov|batch|wave] [--n N]
 
 One JSON line on stdout (rank 0).  Under torchrun each rank steps its own
 independent box (weak scaling, no data-path collective).
@@ -40,7 +44,9 @@ if ROOT not in sys.path:
 
 METRIC = "hydro pair-interactions/s (grad+flux), mixed+learned vs plain FP64, 1 GB300"
 UNIT = "pair-interactions/s"
-WORKLOAD = "sod3d_1067742_mfv_exact"
+# default sizes: Sod resolution n (78: 1,067,742 particles), Sedov lattice
+# side, log-normal particles, number of boxes, wave lattice side
+DEFAULT_N = {"sod": 78, "sedov": 128, "lognormal": 1 << 27, "batch": 512, "wave": 32}
 
 
 def parse():
@@ -49,15 +55,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sod",
+    ap.add_argument("--workload", default="lognormal",
                     choices=["sod", "sedov", "lognormal", "batch", "wave"],
-                    help="sod: 3D Sod tube (default); sedov: Sedov-Taylor blast on an n^3 "
-                         "lattice; lognormal: clustered log-normal box of n particles; batch: n "
+                    help="lognormal: clustered log-normal box of n particles (default); sod: 3D "
+                         "Sod tube; sedov: Sedov-Taylor blast on an n^3 lattice; batch: n "
                          "independent periodic boxes of 4k-64k particles in one launch; wave: "
                          "n^3 jittered lattice with a density wave (HLLC)")
     ap.add_argument("--n", type=int, default=None,
-                    help="size: Sod resolution (78: 1,067,742), Sedov lattice side (128), "
-                         "log-normal particle count (2^24), number of boxes (512), wave "
+                    help="size: log-normal particle count (2^27), Sod resolution (78: "
+                         "1,067,742), Sedov lattice side (128), number of boxes (512), wave "
                          "lattice side (32)")
     ap.add_argument("--riemann", default=None, choices=["exact", "hllc"],
                     help="Riemann solver (default: exact; hllc for the wave)")
@@ -146,15 +152,16 @@ class ClockSampler:
 # CPU oracle baseline (test infrastructure, timed as it stands)
 # --------------------------------------------------------------------------
 def workload_name(kind, n):
+    n = n or DEFAULT_N[kind]
     if kind == "sedov":
-        return f"sedov3d_{n or 128}cubed_mfv_exact"
+        return f"sedov3d_{n}cubed_mfv_exact"
     if kind == "lognormal":
-        return f"lognormal3d_{n or (1 << 24)}_mfv_exact"
+        return f"lognormal3d_{n}_mfv_exact"
     if kind == "batch":
-        return f"batch_{n or 512}_boxes_4k_64k_mfv_exact"
+        return f"batch_{n}_boxes_4k_64k_mfv_exact"
     if kind == "wave":
-        return f"wave3d_{n or 32}cubed_mfv_hllc"
-    return WORKLOAD if (n or 78) == 78 else f"sod3d_n{n}"
+        return f"wave3d_{n}cubed_mfv_hllc"
+    return "sod3d_1067742_mfv_exact" if n == 78 else f"sod3d_n{n}"
 
 
 def make_workload(kind, n, seed=0):
@@ -163,15 +170,16 @@ def make_workload(kind, n, seed=0):
     on every rank."""
     from paper_2211_12243_gb300 import workloads as W
     name = workload_name(kind, n)
+    n = n or DEFAULT_N[kind]
     if kind == "sedov":
-        return W.sedov(n or 128), name
+        return W.sedov(n), name
     if kind == "lognormal":
-        return W.lognormal(n or (1 << 24), seed=seed), name
+        return W.lognormal(n, seed=seed), name
     if kind == "batch":
-        return W.batch(n or 512, seed=seed), name
+        return W.batch(n, seed=seed), name
     if kind == "wave":
-        return W.lattice_wave(n or 32), name
-    return W.sod(n or 78), name
+        return W.lattice_wave(n), name
+    return W.sod(n), name
 
 
 def oracle_sample_rate(kind, n, reps, threads=None):
@@ -279,15 +287,19 @@ def boxes_of(hydro, w):
     return hydro.single_box(w)
 
 
-def train_network(hydro, workloads, w, steps):
-    """Record the hard faces of a few mixed steps of the workload itself, a
-    log-normal field and a Sedov blast, and train the starting-pressure
-    network on them with the library's kernels (untimed)."""
+def train_network(hydro, workloads, w, kind, steps):
+    """Record the hard faces of a few mixed steps of the workload itself (a
+    2^21-particle sample of its generator when it is larger than 2^22), a
+    log-normal field, a Sod tube and a Sedov blast, and train the
+    starting-pressure network on them with the library's kernels
+    (untimed)."""
     import numpy as np
     import torch
     t0 = time.time()
-    sets = [(w, 2, 1.0), (workloads.lognormal(1 << 16, seed=5, grid=32), 2, 0.5),
-            (workloads.sedov(48), 8, 1.0)]
+    big = kind == "lognormal" and w["x"].size > (1 << 22)
+    own = make_workload(kind, 1 << 21, seed=9)[0] if big else w
+    sets = [(own, 2, 1.0), (workloads.lognormal(1 << 16, seed=5, grid=32), 2, 0.5),
+            (workloads.sod(24), 4, 1.0), (workloads.sedov(48), 8, 1.0)]
     bufs = []
     for wk, nstep, keep in sets:
         Hr = hydro.Hydro(hydro.default_config(gamma=wk["gamma"], precision="mixed",
@@ -313,6 +325,147 @@ def train_network(hydro, workloads, w, steps):
             "seconds": time.time() - t0}
 
 
+KEYS = ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")
+
+
+def timed_steps(hydro, Hc, state, k, warm, restart, ok_status, flush, stream, dt=-1.0):
+    """k timed steps (CUDA events on the stream, L2 flushed before each)
+    after `warm` untimed ones; with restart every step starts from the state
+    given.  Returns the summed stage times and counters."""
+    import torch
+    saved = {kk: v.clone() for kk, v in state.items()} if restart else None
+    for _ in range(warm):
+        if restart:
+            for kk, v in saved.items():
+                state[kk].copy_(v)
+        s = Hc.step(state, dt, check=False)
+        assert s["status"] in ok_status, s
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    acc = dict(pairs=0, flux_ms=0.0, grad_ms=0.0, kern_ms=0.0, hard_ms=0.0, flux_pairs=0,
+               iters=0, hard=0, learned=0, fallbacks=0, active=0, graph_steps=0)
+    launches0 = hydro.kernel_launches()
+    stats = None
+    for i in range(k):
+        if restart:
+            for kk, v in saved.items():
+                state[kk].copy_(v)
+        flush.zero_()
+        ev0[i].record(stream)
+        stats = Hc.step(state, dt, check=False)
+        ev1[i].record(stream)
+        assert stats["status"] in ok_status, stats
+        acc["pairs"] += stats["grad_pairs"] + stats["flux_pairs"]
+        acc["flux_ms"] += stats["ms_fluxes"]
+        acc["grad_ms"] += stats["ms_gradients"]
+        acc["kern_ms"] += stats["ms_flux_kernel"]
+        acc["hard_ms"] += stats["ms_hard_faces"]
+        acc["flux_pairs"] += stats["flux_pairs"]
+        acc["iters"] += stats["newton_iters"]
+        acc["hard"] += stats["hard_faces"]
+        acc["learned"] += stats["learned_faces"]
+        acc["fallbacks"] += stats["guess_fallbacks"]
+        acc["active"] += stats["learned_active"]
+        acc["graph_steps"] += stats["graph"] == 1
+    torch.cuda.synchronize()
+    acc["launches"] = hydro.kernel_launches() - launches0
+    acc["ms"] = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    acc["gf_ms"] = acc["grad_ms"] + acc["flux_ms"]
+    acc["last"] = stats
+    del saved
+    return acc
+
+
+def one_step_host(Hc, hydro, w, dt):
+    """One step of the workload's initial state with a fixed dt; the state
+    after it on the host (float64 numpy) and the step's statistics."""
+    import torch
+    st = hydro.to_device(w)
+    stats = Hc.step(st, dt, check=False)
+    torch.cuda.synchronize()
+    out = {k: st[k].cpu().numpy() for k in KEYS + ("omega",)}
+    del st
+    return out, stats
+
+
+def error_vs_fp64(w, mixed, fp64):
+    """The mixed step's error at full size against the plain FP64 step from
+    the same state with the same dt (the FP64 path itself matches the FP64
+    oracle to 1e-12 in the tests): per conserved component, the largest
+    difference of the step's change over the largest change; h relative."""
+    import numpy as np
+    out = {}
+    for k in ("m", "px", "py", "pz", "E"):
+        d_m = mixed[k] - w[k]
+        d_f = fp64[k] - w[k]
+        scale = float(np.abs(d_f).max()) + 1e-300
+        err = np.abs(d_m - d_f) / scale
+        out[k] = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999))}
+    out["h_max_rel"] = float(np.max(np.abs(mixed["h"] - fp64["h"]) / np.abs(fp64["h"])))
+    out["note"] = ("|dQ_mixed - dQ_fp64| / max|dQ_fp64| per component over all particles, one "
+                   "step from the initial state with the same dt")
+    return out
+
+
+def conservation_of(stats, w):
+    """Relative drift of the step's totals (compensated sums before and after
+    the update, from hydro_stats): mass and energy over sum |X|, momentum per
+    axis over sum m (|v| + c_s)."""
+    import numpy as np
+    m = w["m"]
+    v = np.stack([w["px"], w["py"], w["pz"]], 1) / m[:, None]
+    cs = np.sqrt(np.maximum(w["gamma"] * (w["gamma"] - 1) * w["U"] / m, 0))
+    ps = math.fsum(m * (np.linalg.norm(v, axis=1) + cs))
+    out = {"M": abs(stats["mass"][1] - stats["mass"][0]) / math.fsum(np.abs(m)),
+           "E": abs(stats["energy"][1] - stats["energy"][0]) / math.fsum(np.abs(w["E"]))}
+    for a, k in enumerate(("px", "py", "pz")):
+        out[k] = abs(stats["mom"][1][a] - stats["mom"][0][a]) / ps
+    return out
+
+
+def oracle_sample_parity(kind, hydro, n=None):
+    """The GPU's mixed step against the FP64 oracle's step on a sample of the
+    same generator: the per-particle flux error of each conserved component,
+    normalised by the particle's sum over its faces of |c| (the net can
+    cancel; a component that vanishes on every face takes the momentum
+    flux's scale through c_s), and the conservation drift of both."""
+    import numpy as np
+    import oracle
+    n = n or {"sod": 16, "sedov": 24, "lognormal": 1 << 14, "batch": 1 << 14, "wave": 16}[kind]
+    w, _ = make_workload("lognormal" if kind == "batch" else kind, n)
+    riemann = "hllc" if kind == "wave" else "exact"
+    cfg = oracle.config(gamma=w["gamma"], riemann=riemann)
+    so, out_o, info = oracle.step(cfg, w, -1.0)
+    Hs = hydro.Hydro(hydro.default_config(gamma=w["gamma"], precision="mixed", riemann=riemann))
+    Hs.set_boxes(*boxes_of(hydro, w))
+    sg, stats = one_step_host(Hs, hydro, w, info["dt"])
+    Hs.close()
+    prims = oracle.primitives(cfg, w["m"], w["px"], w["py"], w["pz"], w["E"], w["U"], so["omega"])
+    _, _, _, dQabs = oracle.fluxes(cfg, w["x"], w["y"], w["z"], w["L"], so["h"], so["omega"],
+                                   out_o["B6"], prims, out_o["grad"], out_o["alpha"], info["dt"],
+                                   want_abs=True)
+    rho, _, _, _, p = prims
+    cs = np.sqrt(w["gamma"] * p / rho)
+    pm = dQabs[:, 1] + dQabs[:, 2] + dQabs[:, 3]
+    sc = np.stack([np.maximum(dQabs[:, 0], pm / cs), pm, pm, pm,
+                   np.maximum(dQabs[:, 4], pm * cs)], 1) + 1e-300
+    keys = ("m", "px", "py", "pz", "E")
+    d = np.stack([(sg[k] - w[k]) - (so[k] - w[k]) for k in keys], 1)
+    err = np.abs(d) / sc
+    return {"particles": int(w["x"].size), "status_gpu": stats["status"],
+            "status_oracle": info["status"],
+            "flux_err_max": float(err.max()), "flux_err_p999": float(np.quantile(err, 0.999)),
+            "above_1e-5": int(np.sum(err.max(1) > 1e-5)),
+            "conservation_gpu": conservation_of(stats, w),
+            "note": "per-particle |dQ_gpu - dQ_oracle| / sum over faces |c|, one step, same dt"}
+
+
+def measured_peaks():
+    """This GPU's arithmetic throughput by the library's probes."""
+    from paper_2211_12243_gb300 import hydro
+    return {u: hydro.probe_peak(u) for u in ("fp32", "mufu", "fp64")}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -335,12 +488,14 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
+    t_setup = time.time()
     w, wname = make_workload(args.workload, args.n, seed=rank)
     n = w["x"].size
+    big = n > (1 << 25)
     learned = args.precision == "mixed" and not args.no_learned
-    training = train_network(hydro, workloads, w, args.train_steps) if learned else None
     riemann = args.riemann or ("hllc" if args.workload == "wave" else "exact")
     learned = learned and riemann == "exact"
+    training = train_network(hydro, workloads, w, args.workload, args.train_steps) if learned else None
     margin = 1.15
     graph = 0 if args.no_graph else 1
     common = dict(gamma=w["gamma"], scheme=args.scheme, riemann=riemann, search_margin=margin,
@@ -352,7 +507,6 @@ def main():
     H.set_boxes(*boxes_of(hydro, w))
     H.reserve(n, 96)
     st = hydro.to_device(w)
-    acc = None
     if args.gravity:
         # a seeded acceleration field of order the sound speed squared over the box
         g = np.random.default_rng(20221122 + 7).normal(0.0, 0.1, (n, 3))
@@ -370,73 +524,20 @@ def main():
     ok_status = (0, -5) if args.workload in ("lognormal", "batch") else (0,)
 
     restart = args.restart or args.workload in ("lognormal", "batch")
+    # the initial state's CFL dt (and, for restarted workloads, its
+    # converged smoothing lengths, which a running simulation carries: the
+    # generator's h are rough guesses from a coarse density grid)
+    tmp = {kk: v.clone() for kk, v in st.items()}
+    s0 = H.step(tmp, -1.0, check=False)
+    assert s0["status"] in ok_status, s0
+    dt_cmp = s0["dt"]
     if restart:
-        # every step restarts from the initial state, but with the smoothing
-        # lengths a running simulation carries: the generator's h are rough
-        # guesses from a coarse density grid, so one untimed step solves them
-        # and its h become the initial state's h
-        tmp = {kk: v.clone() for kk, v in st.items()}
-        s0 = H.step(tmp, -1.0, check=False)
-        assert s0["status"] in ok_status, s0
         st["h"].copy_(tmp["h"])
         w["h"] = tmp["h"].cpu().numpy()
-        del tmp
+    del tmp
 
-    def tune(Hc, state):
-        # launch parameters timed on this state (untimed; state untouched)
-        return None if args.no_autotune else Hc.autotune(state)
-
-    tuning = tune(H, st)
-
-    def timed_steps(Hc, state, k, warm):
-        saved = {kk: v.clone() for kk, v in state.items()} if restart else None
-        for _ in range(warm):
-            if restart:
-                for kk, v in saved.items():
-                    state[kk].copy_(v)
-            s = Hc.step(state, -1.0, check=False)
-            assert s["status"] in ok_status, s
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-        pairs = 0
-        flux_ms = 0.0
-        grad_ms = 0.0
-        kern_ms = 0.0
-        hard_ms = 0.0
-        flux_pairs = 0
-        iters = 0
-        hard = learned_faces = fallbacks = active = graph_steps = 0
-        launches0 = hydro.kernel_launches()
-        stats = None
-        for i in range(k):
-            if restart:
-                for kk, v in saved.items():
-                    state[kk].copy_(v)
-            flush.zero_()
-            ev0[i].record(stream)
-            stats = Hc.step(state, -1.0, check=False)
-            ev1[i].record(stream)
-            assert stats["status"] in ok_status, stats
-            pairs += stats["grad_pairs"] + stats["flux_pairs"]
-            flux_ms += stats["ms_fluxes"]
-            grad_ms += stats["ms_gradients"]
-            kern_ms += stats["ms_flux_kernel"]
-            hard_ms += stats["ms_hard_faces"]
-            flux_pairs += stats["flux_pairs"]
-            iters += stats["newton_iters"]
-            hard += stats["hard_faces"]
-            learned_faces += stats["learned_faces"]
-            fallbacks += stats["guess_fallbacks"]
-            active += stats["learned_active"]
-            graph_steps += stats["graph"] == 1
-        torch.cuda.synchronize()
-        launches = hydro.kernel_launches() - launches0 - 0
-        ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-        return dict(ms=ms, pairs=pairs, flux_ms=flux_ms, grad_ms=grad_ms, kern_ms=kern_ms,
-                    hard_ms=hard_ms, gf_ms=grad_ms + flux_ms,
-                    flux_pairs=flux_pairs, iters=iters, hard=hard, learned=learned_faces,
-                    fallbacks=fallbacks, active=active, launches=launches, last=stats,
-                    graph_steps=graph_steps)
+    tuning = None if args.no_autotune else H.autotune(st)
+    setup_s = time.time() - t_setup
 
     # ---- timed region: the mixed step
     if world > 1:
@@ -444,40 +545,51 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    r = timed_steps(H, st, args.steps, args.warmup)
+    r = timed_steps(hydro, H, st, args.steps, args.warmup, restart, ok_status, flush, stream)
     clocks = clk.stop()
     pairs_all, ms_max, gf_max = aggregate(world, r["pairs"], r["ms"], r["gf_ms"], "cuda")
     ms_per_step = ms_max / args.steps
     # the metric: pairs over the gradient + flux stage time; whole-step rate beside it
     value = pairs_all / (gf_max / 1000.0)
     step_rate = pairs_all / (ms_max / 1000.0)
+    last = r["last"]
+    conservation = conservation_of(last, w) if restart else None
 
     # ---- end to end through the public API with host buffers
-    keys = ("x", "y", "z", "m", "px", "py", "pz", "E", "U", "h")
-    host = {k: torch.as_tensor(w[k]).pin_memory() for k in keys}
-    host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in keys + ("omega",)}
+    host = {k: torch.as_tensor(w[k]).pin_memory() for k in KEYS}
+    host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in KEYS + ("omega",)}
     e2e_ms = 0.0
     e2e_pairs = 0
-    st2 = hydro.to_device(w)
-    for k in range(2 + args.steps):
+    e2e_steps = min(args.steps, 3) if big else args.steps
+    st2 = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
+    for k in range(1 + e2e_steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         flush.zero_()
         e0.record(stream)
-        for kk in keys:
+        for kk in KEYS:
             st2[kk].copy_(host[kk], non_blocking=True)
         s2 = H.step(st2, -1.0, check=False)
         assert s2["status"] in ok_status, s2
-        for kk in keys + ("omega",):
+        for kk in KEYS + ("omega",):
             host_out[kk].copy_(st2[kk], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        if k >= 2:
+        if k >= 1:
             e2e_ms += e0.elapsed_time(e1)
             e2e_pairs += s2["grad_pairs"] + s2["flux_pairs"]
-    e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT,
+    e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT, "steps": e2e_steps,
            "timed": "H2D copies of the inputs + hydro_step + D2H copies of the state",
-           "h2d_bytes_per_step": 8 * n * len(keys), "d2h_bytes_per_step": 8 * n * (len(keys) + 1)}
+           "h2d_bytes_per_step": 8 * n * len(KEYS), "d2h_bytes_per_step": 8 * n * (len(KEYS) + 1)}
+    del host, host_out, st2
+
+    # ---- the mixed step once more from the initial state, dt fixed (outside
+    # the timed region), for the comparison with the FP64 step
+    st.clear()
+    torch.cuda.empty_cache()
+    mixed_cmp, _ = one_step_host(H, hydro, w, dt_cmp)
+    H.close()
+    torch.cuda.empty_cache()
 
     # ---- the same mixed step with the plain (Toro) guess, same starting state
     plain_guess = None
@@ -487,63 +599,84 @@ def main():
         stp = hydro.to_device(w)
         if tuning:
             Hp.set_tuning(tuning)
-        kp = max(2, min(args.steps, 5))
-        rp = timed_steps(Hp, stp, kp, 1)
+        kp = 2 if big else max(2, min(args.steps, 5))
+        rp = timed_steps(hydro, Hp, stp, kp, 1, restart, ok_status, flush, stream)
         plain_guess = {"value": rp["pairs"] / (rp["gf_ms"] / 1000.0),
                        "step_rate": rp["pairs"] / (rp["ms"] / 1000.0), "ms_per_step": rp["ms"] / kp,
                        "flux_stage_ms": rp["flux_ms"] / kp, "flux_kernel_ms": rp["kern_ms"] / kp,
                        "newton_iters_per_face": rp["iters"] / max(rp["flux_pairs"], 1)}
         Hp.close()
+        del stp
+        torch.cuda.empty_cache()
 
-    # ---- plain FP64 step on the same starting state
+    # ---- plain FP64 step on the same starting state: its first (untimed)
+    # step from the initial state with the comparison dt gives the error of
+    # the mixed step at full size
     fp64 = None
+    err64 = None
     if not args.no_fp64:
         H64 = hydro.Hydro(hydro.default_config(precision="fp64", **common))
         H64.set_boxes(*boxes_of(hydro, w))
-        st64 = hydro.to_device(w)
         # the list radius and slots found for the mixed step; default kernels
         tuning64 = None if tuning is None else dict(tuning, grad_min_ctas=1, flux_min_ctas=4)
         if tuning64:
             H64.set_tuning(tuning64)
-        k64 = max(2, min(args.steps, 5))
-        r64 = timed_steps(H64, st64, k64, 1)
+        fp64_cmp, _ = one_step_host(H64, hydro, w, dt_cmp)
+        err64 = error_vs_fp64(w, mixed_cmp, fp64_cmp)
+        del fp64_cmp
+        st64 = hydro.to_device(w)
+        k64 = 1 if big else max(2, min(args.steps, 5))
+        r64 = timed_steps(hydro, H64, st64, k64, 0 if big else 1, restart, ok_status, flush,
+                          stream)
         fp64 = {"value": r64["pairs"] / (r64["gf_ms"] / 1000.0),
                 "step_rate": r64["pairs"] / (r64["ms"] / 1000.0), "ms_per_step": r64["ms"] / k64,
-                "flux_kernel_ms": r64["flux_ms"] / k64,
+                "flux_kernel_ms": r64["flux_ms"] / k64, "timed_steps": k64,
                 "tuning": None if tuning64 is None else {k: tuning64[k] for k in (
                     "search_margin", "nbr_slots", "grad_min_ctas")}}
         H64.close()
+        del st64
+        torch.cuda.empty_cache()
 
-    # ---- roofline of the dominant kernel (pair fluxes, float ALU bound):
-    # algorithmic flops of the faces it solves / its event-timed duration
+    # ---- roofline of the dominant kernel (pair fluxes): the oracle-counted
+    # work of the faces it solves over its event-timed duration, against this
+    # GPU's measured FP32 and special-function throughput
+    peaks = measured_peaks()
     faces = r["flux_pairs"] / args.steps
     hard = r["hard"] / args.steps
     iters = r["iters"] / args.steps
     kern_ms = r["kern_ms"] / args.steps
-    # hard faces are deferred to the hard-face kernel and solved there; the
+    # hard faces deferred to the hard-face kernel are solved there; the
     # Newton iterations are counted together, so the flux kernel is credited
     # with the share of its own faces
-    solved = faces - (hard if learned else 0.0)
+    solved = faces - (hard if r["active"] else 0.0)
     iters_own = iters * solved / max(faces, 1.0)
-    achieved = (solved * FLOPS_PER_FACE + iters_own * FLOPS_PER_NEWTON) / (kern_ms / 1000.0) / 1e12
-    peak = FP32_PEAK_TFLOPS
-    if riemann != "exact":
-        achieved = None   # the flop count below is the exact solver's
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": None if achieved is None else achieved / peak,
-            # measured for the default register bound (4 CTAs per SM) on the tube
-            "traffic": (FLUX_TRAFFIC_BYTES_PER_FACE * faces
-                        if args.workload == "sod" and (tuning is None or
-                                                       tuning["flux_min_ctas"] == 4) else None),
-            "kernel": f"k_fluxes<float,{riemann},{args.scheme}>", "kernel_ms": kern_ms,
-            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    # the other bound checked: the kernel's DRAM bytes against the measured
-    # copy bandwidth (far below it: the kernel is not bandwidth bound)
+    ops = FACE_OPS["lognormal" if args.workload == "batch" else args.workload]
+    flop = solved * ops["flop_base"] + iters_own * ops["flop_per_iter"]
+    mufu = solved * ops["mufu_base"] + iters_own * ops["mufu_per_iter"]
+    sec = kern_ms / 1000.0
+    comp = {"fp32": {"achieved": flop / sec / 1e12, "peak": peaks["fp32"], "unit": "TFLOP/s"},
+            "mufu": {"achieved": mufu / sec / 1e12, "peak": peaks["mufu"], "unit": "Tops/s"}}
+    for c in comp.values():
+        c["frac"] = c["achieved"] / c["peak"]
+    traffic_pf = FLUX_TRAFFIC_BYTES_PER_FACE.get(args.workload)
+    traffic = traffic_pf * faces if traffic_pf and (tuning is None or
+                                                    tuning["flux_min_ctas"] == 4) else None
     hbm_peak = measured_hbm_gbs()
-    if roof["traffic"] and hbm_peak and kern_ms > 0:
-        ach = roof["traffic"] / (kern_ms / 1000.0) / 1e9
-        roof["secondary"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach / hbm_peak, "peak_note": "measured copy bandwidth"}
+    if traffic and hbm_peak:
+        comp["hbm"] = {"achieved": traffic / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": traffic / sec / 1e9 / hbm_peak}
+    top = max(("fp32", "mufu"), key=lambda k: comp[k]["frac"])
+    roof = {"bound": "alu", "achieved": comp[top]["achieved"], "peak": comp[top]["peak"],
+            "unit": comp[top]["unit"] + (" (special-function unit)" if top == "mufu" else ""),
+            "frac": comp[top]["frac"], "traffic": traffic,
+            "kernel": f"k_fluxes<float,{riemann},{args.scheme}>", "kernel_ms": kern_ms,
+            "work_per_face": {k: ops[k] for k in ("flop_base", "flop_per_iter", "mufu_base",
+                                                 "mufu_per_iter")},
+            "work_note": "operations of the oracle's face routine counted by its counting build "
+                         "(oracle/face_work.py) on a sample of the same generator; each add, "
+                         "mul, div, sqrt, pow one flop; special-function ops: div 1, sqrt 1, pow 2",
+            "peak_note": "measured by hydro_probe_peak (burst, this GPU)", "components": comp,
+            "fp64_peak_tflops": peaks["fp64"]}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -551,8 +684,9 @@ def main():
         # the same sample on one core (one pass)
         one, _ = oracle_sample_rate(args.workload, args.cpu_n, 1, threads=1)
         cpu["single_core"] = {"value": one["value"], "cores": one["cores"], "sample": one["sample"]}
+        # on a sample of the same generator the oracle also checks the GPU step
+        cpu["gpu_parity_on_sample"] = oracle_sample_parity(args.workload, hydro)
 
-    last = r["last"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "step_rate": step_rate,
@@ -570,9 +704,11 @@ def main():
                    "grad_pairs": last["grad_pairs"], "flux_pairs": last["flux_pairs"],
                    "newton_iters_per_face": iters / max(faces, 1),
                    "learned_guess": learned,
-                   "gravity": bool(args.gravity), "entropy_switch": bool(args.entropy)},
+                   "gravity": bool(args.gravity), "entropy_switch": bool(args.entropy),
+                   "setup_s": setup_s},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
         "clocks": clocks, "plain_fp64": fp64, "mixed_plain_guess": plain_guess,
+        "error_vs_fp64": err64, "conservation": conservation,
         "stage_ms": {k: last[k] for k in ("ms_neighbours", "ms_density", "ms_gradients",
                                           "ms_fluxes", "ms_flux_kernel", "ms_hard_faces",
                                           "ms_update")},
@@ -693,21 +829,22 @@ def bench_rungs(args):
     return 0
 
 
-# Algorithmic arithmetic of one float face (counted from the face routine;
-# FMA = 2, each compare/min/max/select 1, sqrt/div/pow 1 each):
-# kernel weights 22, face vector 53, extrapolation 80, pairwise limiter 180,
-# half-step predictor 36, boost/projection 38, Riemann set-up + guess 30,
-# polish step + final evaluation 61, sampling 30, flux 35, de-boost and
-# scaling 24 -> 589 per face; each Newton iteration 38.
-FLOPS_PER_FACE = 589.0
-FLOPS_PER_NEWTON = 38.0
-# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic work of one face, counted by the oracle's counting build on a
+# sample of each generator (python -m oracle.face_work; tests check that
+# these equal a fresh count): flops per face and per Newton iteration (each
+# add, mul, div, sqrt, pow one flop) and special-function operations (div 1,
+# sqrt 1, pow 2).  The batch of boxes takes the log-normal counts.
+FACE_OPS = {
+    "sod": {"flop_base": 481.469, "flop_per_iter": 44.0, "mufu_base": 84.65, "mufu_per_iter": 16.0},
+    "sedov": {"flop_base": 504.363, "flop_per_iter": 44.0, "mufu_base": 77.628, "mufu_per_iter": 16.0},
+    "lognormal": {"flop_base": 577.432, "flop_per_iter": 44.101, "mufu_base": 84.84,
+                  "mufu_per_iter": 15.596},
+    "wave": {"flop_base": 466.427, "flop_per_iter": 0.0, "mufu_base": 34.0, "mufu_per_iter": 0.0},
+}
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
-# of the current kernel on the Sod tube at n = 60 (182.3 MB for 6,385,500
-# faces, lists compacted by the density stage); a launch's traffic scales
-# with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = 28.54
+# of the current kernel on a small case of the workload (profiles/); a
+# launch's traffic scales with its faces
+FLUX_TRAFFIC_BYTES_PER_FACE = {"sod": 28.54}
 
 if __name__ == "__main__":
     sys.exit(main())

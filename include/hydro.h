@@ -502,6 +502,17 @@ int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_
  * {4, 5, 6}; the time fields are ignored).  HYDRO_EINVAL otherwise. */
 int hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *t);
 
+/* Throughput of this GPU's arithmetic units, measured (no counterpart in the
+ * paper: the denominators of the benchmark's roofline).  unit:
+ * HYDRO_PROBE_FP32 float FMAs, HYDRO_PROBE_FP64 double FMAs (*value in
+ * TFLOP/s, two flops per FMA), HYDRO_PROBE_MUFU reciprocal square roots on
+ * the special-function unit (*value in T operations/s).  Independent FMA
+ * (or rsqrt) chains on 8 blocks of 256 threads per SM, the best of three
+ * timed launches (CUDA events on stream, synchronising).  Allocates and
+ * frees a small device buffer.  EINVAL for another unit. */
+enum { HYDRO_PROBE_FP32 = 0, HYDRO_PROBE_FP64 = 1, HYDRO_PROBE_MUFU = 2 };
+int hydro_probe_peak(int unit, double *value, hydro_stream stream);
+
 /* Number of kernels this library has launched in the process so far
  * (every entry point's launches, all contexts).  Diagnostics only. */
 int64_t hydro_kernel_launches(void);

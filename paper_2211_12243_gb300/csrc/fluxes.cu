@@ -165,7 +165,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.hard_cap = 0;
     const bool learned = c->learned_decision >= 0 ? c->learned_decision != 0 : decide_learned(c);
     c->learned_active = learned;
-    // room for 4 hard faces per particle to start with (sub-buffer sizes a
+    // room for 2 hard faces per particle to start with (sub-buffer sizes a
     // multiple of 128); a pass that fills a sub-buffer is redone with twice
     // the room
     const int64_t unit = (int64_t)HARD_SUB * 128;
@@ -184,7 +184,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
         a.hard_cap = c->hard_cap;
         return cudaSuccess;
     };
-    if (learned) HYD_CUDA(reserve_hard(4 * n + 65536));
+    if (learned) HYD_CUDA(reserve_hard(2 * n + 65536));
     a.rec_faces = c->rec_faces;
     a.rec_cursor = c->d_rec_cursor.get();
     a.rec_cap = c->rec_cap;

@@ -110,7 +110,8 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_mlp_features", "hydro_mlp_gradient", "hydro_mlp_train", "hydro_record_faces",
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
            "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity",
-           "hydro_set_entropy", "hydro_step_rungs", "hydro_test_mlp_stall"]
+           "hydro_set_entropy", "hydro_step_rungs", "hydro_test_mlp_stall",
+           "hydro_probe_peak"]
 
 
 def _load():
@@ -151,6 +152,7 @@ def _load():
         L.hydro_set_gravity.argtypes = [vp, vp]
         L.hydro_set_entropy.argtypes = [vp, vp]
         L.hydro_test_mlp_stall.argtypes = [vp, C.c_int]
+        L.hydro_probe_peak.argtypes = [C.c_int, C.POINTER(C.c_double), vp]
         L.hydro_kernel_launches.argtypes = []
         L.hydro_kernel_launches.restype = C.c_int64
         L.hydro_strerror.argtypes = [C.c_int]
@@ -172,6 +174,19 @@ def totals_noalloc(st, out=None, stream=None):
     if rc:
         raise HydroError(rc, "hydro_totals_noalloc")
     return out
+
+
+PROBES = {"fp32": 0, "fp64": 1, "mufu": 2}
+
+
+def probe_peak(unit, stream=None):
+    """Measured throughput of one arithmetic unit of the current GPU
+    (hydro_probe_peak): TFLOP/s for "fp32" and "fp64", Tops/s for "mufu"."""
+    v = C.c_double(0.0)
+    rc = _load().hydro_probe_peak(PROBES[unit], C.byref(v), _stream(stream))
+    if rc:
+        raise HydroError(rc, "hydro_probe_peak")
+    return v.value
 
 
 def kernel_launches():

@@ -1,6 +1,8 @@
 """The bench's reference arm (the FP64 oracle on the host cores) runs
 without a GPU: its JSON line carries the contract's keys, and the oracle
-sampler's pair count and rate are consistent.  CPU only."""
+sampler's pair count and rate are consistent; the per-face work the
+roofline uses equals a fresh count by the oracle's counting build.  CPU
+only."""
 import json
 import os
 import subprocess
@@ -11,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_the_contract_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-n", "12"],
+                        "--steps", "1", "--warmup", "0", "--cpu-n", "4096"],
                        capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
@@ -24,7 +26,7 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"]["value"] == line["value"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
-    assert line["config"]["workload"] == "sod3d_1067742_mfv_exact"
+    assert line["config"]["workload"] == "lognormal3d_134217728_mfv_exact"
 
 
 def test_oracle_sampler_counts_pairs_like_the_metric():
@@ -37,3 +39,17 @@ def test_oracle_sampler_counts_pairs_like_the_metric():
     # the same sample: the same pair count in the description
     count = lambda r: int(r["sample"].split(" pair-interactions")[0].split()[-1])
     assert count(r1) == count(r2) > 0
+
+
+def test_face_work_constants_match_a_fresh_count():
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import face_work
+    t = face_work.table()
+    assert set(t) == set(bench.FACE_OPS)
+    for kind, v in t.items():
+        for k, c in bench.FACE_OPS[kind].items():
+            assert abs(v[k] - c) <= 1e-3 * max(1.0, abs(c)), (kind, k, v[k], c)
+    # the counts measure real work: a Newton iteration evaluates both sides'
+    # pressure functions (two powers at least when a side rarefies)
+    assert 30 < t["sod"]["flop_per_iter"] < 80 and t["wave"]["flop_per_iter"] == 0.0
