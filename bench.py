@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="headline without the learned guess")
     ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--riemann-polish", action="store_true",
+                    help="mixed path: one FP64 Newton step after the float iteration "
+                         "(hydro_config.riemann_polish)")
     ap.add_argument("--restart", action="store_true",
                     help="start every step (warm-up and timed) from the initial state "
                          "(default for the log-normal box, whose state develops negative "
@@ -401,7 +404,15 @@ def error_vs_fp64(w, mixed, fp64):
         scale = float(np.abs(d_f).max()) + 1e-300
         err = np.abs(d_m - d_f) / scale
         out[k] = {"max": float(err.max()), "p999": float(np.quantile(err, 0.999))}
-    out["h_max_rel"] = float(np.max(np.abs(mixed["h"] - fp64["h"]) / np.abs(fp64["h"])))
+    dh = np.abs(mixed["h"] - fp64["h"]) / np.abs(fp64["h"])
+    out["h_max_rel"] = float(dh.max())
+    # particles whose h differs beyond the double-class refinement: N_cond
+    # guard decisions (a threshold on a float-accumulated E) that came out
+    # the other way, which move h by (1.2)^(1/3) per growth round
+    out["h_differs_1e-9"] = int(np.sum(dh > 1e-9))
+    errs = np.stack([np.abs((mixed[k] - w[k]) - (fp64[k] - w[k])) /
+                     (np.abs(fp64[k] - w[k]).max() + 1e-300) for k in ("m", "px", "py", "pz", "E")], 1)
+    out["particles_above_1e-5"] = int(np.sum(errs.max(1) > 1e-5))
     out["note"] = ("|dQ_mixed - dQ_fp64| / max|dQ_fp64| per component over all particles, one "
                    "step from the initial state with the same dt")
     return out
@@ -500,7 +511,8 @@ def main():
     graph = 0 if args.no_graph else 1
     common = dict(gamma=w["gamma"], scheme=args.scheme, riemann=riemann, search_margin=margin,
                   graph=graph)
-    cfg = hydro.default_config(precision=args.precision, learned_guess=int(learned), **common)
+    cfg = hydro.default_config(precision=args.precision, learned_guess=int(learned),
+                               riemann_polish=int(args.riemann_polish), **common)
     H = hydro.Hydro(cfg)
     if learned:
         H.mlp_load(training["theta"])
@@ -703,7 +715,7 @@ def main():
                    "pairs_per_step": r["pairs"] / args.steps,
                    "grad_pairs": last["grad_pairs"], "flux_pairs": last["flux_pairs"],
                    "newton_iters_per_face": iters / max(faces, 1),
-                   "learned_guess": learned,
+                   "learned_guess": learned, "riemann_polish": bool(args.riemann_polish),
                    "gravity": bool(args.gravity), "entropy_switch": bool(args.entropy),
                    "setup_s": setup_s},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],

@@ -166,8 +166,9 @@ typedef struct {
     int64_t ncond_fail;       /* particles above the threshold at the end */
     int list_rebuilds;        /* neighbour-list rebuilds for h beyond the radius */
     double mass[2], mom[2][3], energy[2];   /* totals of the state before / after the
-                                 step: compensated sums in a fixed order over
-                                 the particles, so any difference is the
+                                 step: double sums in a fixed order over the
+                                 particles (rounding below 1e-13 of sum |x| at
+                                 2^27 particles), so any difference is the
                                  step's (fluxes and external sources) */
     float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
     float ms_flux_kernel;     /* the pair-flux kernel alone (CUDA events on the stream) */
@@ -477,7 +478,11 @@ int hydro_set_entropy(hydro_ctx *ctx, double *A);
  *   grad_min_ctas: register bound of the gradient kernel (1: none; 5, 6
  *     resident 128-thread CTAs per SM), timed over the gradient stage;
  *   flux_min_ctas: register bound of the float flux kernel (4, 5, 6),
- *     timed over the plain-guess flux stage (mixed precision only).
+ *     timed over the plain-guess flux stage (mixed precision only);
+ *   flux_queue: the flux kernel's buckets one per warp by index (0) or
+ *     drawn by persistent warps from a global cursor (1, the default: a
+ *     warp done with a light bucket takes the next at once), timed over
+ *     the same stage with the chosen bound (mixed precision only).
  * The times (ms, best of two) are returned beside the choices. */
 typedef struct {
     double search_margin;
@@ -487,6 +492,8 @@ typedef struct {
     float front_ms[4][3];     /* [margin][slots] */
     float grad_ms[3];         /* [1, 5, 6] */
     float flux_ms[3];         /* [4, 5, 6]; 0 in FP64 */
+    int flux_queue;
+    float flux_queue_ms[2];   /* [by index, drawn]; 0 in FP64 */
 } hydro_tuning;
 
 /* Time the candidates above on the particles p (device, caller order; state
@@ -499,7 +506,8 @@ int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_
 
 /* Apply choices saved from an earlier hydro_autotune (search_margin >= 1,
  * nbr_slots in [32, 256], grad_min_ctas in {1, 5, 6}, flux_min_ctas in
- * {4, 5, 6}; the time fields are ignored).  HYDRO_EINVAL otherwise. */
+ * {4, 5, 6}, flux_queue in {0, 1}; the time fields are ignored).
+ * HYDRO_EINVAL otherwise. */
 int hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *t);
 
 /* Throughput of this GPU's arithmetic units, measured (no counterpart in the

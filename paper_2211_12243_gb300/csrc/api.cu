@@ -525,12 +525,13 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
     return rc;
 }
 
-// The lists of the buckets holding a particle of the guard round (their
-// search radii grew in guard_grow), rebuilt before the re-solve; a full
-// rebuild when the overflow region is too small.
+// New lists for the particles of the guard round (their search radii grew
+// in guard_grow), built one particle per warp before the re-solve; the tree
+// takes the grown radii first (the reverse walk of the gradient pass reads
+// them); a full rebuild when the overflow region is too small.
 static int guard_lists(hydro_ctx *c, cudaStream_t st) {
-    int nq = 0;
-    API_CUDA(rebuild_active_lists(c, &nq, st));
+    API_CUDA(build_tree(c, st));
+    API_CUDA(guard_particle_lists(c, st));
     API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaStreamSynchronize(st));
     const int fl = c->h_cnt->flags;
@@ -1023,7 +1024,9 @@ int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (!(t->search_margin >= 1.0) || t->nbr_slots < 32 || t->nbr_slots > 256) return HYDRO_EINVAL;
     if (t->grad_min_ctas != 1 && t->grad_min_ctas != 5 && t->grad_min_ctas != 6) return HYDRO_EINVAL;
     if (t->flux_min_ctas < 4 || t->flux_min_ctas > 6) return HYDRO_EINVAL;
+    if (t->flux_queue != 0 && t->flux_queue != 1) return HYDRO_EINVAL;
     c->cfg.search_margin = t->search_margin;
+    c->flux_queue = t->flux_queue;
     c->nbr_per_particle = t->nbr_slots;
     c->grad_minb = t->grad_min_ctas;
     c->flux_minb = t->flux_min_ctas;
@@ -1120,6 +1123,25 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
             T.flux_ms[k] = t;
             if (t < best) { best = t; bf = fminb[k]; }
         }
+        // buckets by index or drawn from the queue, with the chosen bound
+        c->flux_minb = bf;
+        best = 1e30f;
+        for (int q = 0; q < 2; q++) {
+            c->flux_queue = q;
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                API_CUDA(record_event(c->ev[0], st));
+                cudaError_t e = run_fluxes(c, -1.0, dt_dev, st);
+                if (e != cudaSuccess) { c->learned_decision = -1; return cuda_status(e); }
+                API_CUDA(record_event(c->ev[1], st));
+                API_CUDA(cudaEventSynchronize(c->ev[1]));
+                API_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+                t = std::min(t, ms);
+            }
+            T.flux_queue_ms[q] = t;
+            if (t < best) { best = t; T.flux_queue = q; }
+        }
+        c->flux_queue = T.flux_queue;
         c->learned_decision = -1;
     }
     c->flux_minb = bf;
@@ -1129,6 +1151,7 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
     T.nbr_slots = bs;
     T.grad_min_ctas = bg;
     T.flux_min_ctas = bf;
+    T.flux_queue = c->flux_queue;
     if (out) *out = T;
     return HYDRO_OK;
 }

@@ -84,6 +84,9 @@ struct FluxArgs {
     // the sub-steps of individual timesteps walk only the buckets whose
     // particles can reach a particle starting a step
     const int32_t *bucket_ids;
+    // persistent launch: the warps draw bucket indices from this cursor
+    // (zeroed before the launch); NULL: one bucket per warp
+    unsigned long long *queue;
 };
 
 template <typename R> __device__ __forceinline__ const GasK<R> &gas(const FluxArgs &a);
@@ -368,6 +371,10 @@ __device__ __forceinline__ void record_face(const FluxArgs &a, const GasK<R> &K,
 // HARD_SUB sub-buffers with a cursor each (CTA b writes sub-buffer b mod HARD_SUB)
 constexpr int HF_N = 19;
 constexpr int HARD_SUB = 256;
+// free slots a sub-buffer must keep before a warp defers more hard faces:
+// at most 16 warps (4 resident CTAs of 4 warps, 152 SMs x 6 CTAs / 256
+// sub-buffers rounded up) can fill one at once, each with up to HQ queued
+constexpr int64_t HARD_MARGIN = 2048;
 
 template <typename R>
 __device__ __forceinline__ void store_hard(const FluxArgs &a, const FaceState<R> &st, int64_t k,
@@ -489,10 +496,20 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
     int hh = 0;   // the oldest entry of the warp's hard queue (a ring of HQ)
     if (DEFER && lane == 0) hq.cnt = 0;
     __syncwarp();
-    const int64_t bi = blockIdx.x * (int64_t)FLUX_WARPS + warp;
     FaceStats fs{0, 0, 0, 0};
-    unsigned long long n_hard = 0;
-    if (bi < a.nbucket) {
+    unsigned long long n_hard = 0, n_noroom = 0;
+    // buckets: one per warp by its index, or (queue non-NULL) drawn by each
+    // warp from a global cursor until none is left -- a warp that finishes
+    // a light bucket takes the next one at once instead of idling until the
+    // heaviest bucket of its CTA is done
+    int64_t bi = blockIdx.x * (int64_t)FLUX_WARPS + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.queue, 1ull);
+            bi = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (bi >= a.nbucket) break;
         const int64_t b = a.bucket_ids ? (int64_t)a.bucket_ids[bi] : bi;
         const int f = a.node_first[b], nown = a.node_cnt[b];
         const bool own = lane < nown;
@@ -549,6 +566,19 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
         auto solve = [&](int nb) {
             R c[5] = {R(0), R(0), R(0), R(0), R(0)};
             int ol = 32 + lane;   // idle lanes: a key no owner has
+            // room left in the CTA's deferred-face sub-buffer (read once per
+            // batch): with less than HARD_MARGIN slots -- more than the warps
+            // that can share a sub-buffer at once hold in their rings -- the
+            // hard faces are solved here from the plain guess instead
+            bool room = true;
+            if constexpr (DEFER) {
+                unsigned long long used = 0;
+                if (lane == 0)
+                    used = *(volatile const unsigned long long *)&a.hard_cursor[blockIdx.x &
+                                                                               (HARD_SUB - 1)];
+                used = __shfl_sync(0xffffffffu, used, 0);
+                room = (int64_t)used + HARD_MARGIN < a.hard_cap / HARD_SUB;
+            }
             if (lane < nb) {
                 ol = sm.qo[lane];
                 const int j = sm.qj[lane];
@@ -571,8 +601,10 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
                     if constexpr (DEFER) {
                         // hard faces are queued for the learned-guess pass,
                         // which applies both sides of their flux
-                        if (two_shock_guess<R>(K, st)) {
-                            n_hard++;
+                        const bool hard = two_shock_guess<R>(K, st);
+                        n_hard += hard;
+                        n_noroom += hard && !room;
+                        if (hard && room) {
                             const int e = (hh + atomicAdd(&hq.cnt, 1)) & (HQ - 1);
                             const float v[HF_N] = {st.rl, st.ul, st.pl, st.rr, st.ur, st.pr,
                                                    st.wl[0], st.wl[1], st.wl[2], st.wr[0],
@@ -687,12 +719,16 @@ k_fluxes(FluxArgs a, const R *__restrict__ rec) {
 #pragma unroll
             for (int q = 0; q < 5; q++) atomicAdd(&a.dQ[q * a.n + s], acc.get(q));
         }
+        if (!a.queue) break;
+        __syncwarp();
     }
     unsigned long long p = wsum(fs.pairs), it = wsum(fs.iters), va = wsum(fs.vacuum),
-                       fo = wsum(fs.first_order), ha = DEFER ? wsum(n_hard) : 0ull;
+                       fo = wsum(fs.first_order), ha = DEFER ? wsum(n_hard) : 0ull,
+                       nr = DEFER ? wsum(n_noroom) : 0ull;
     if (lane == 0) {
         if (p) atomicAdd(&a.cnt->flux_pairs, p);
         if (ha) atomicAdd(&a.cnt->hard_faces, ha);
+        if (nr) atomicAdd(&a.cnt->guess_fallbacks, nr);
         if (it) atomicAdd(&a.cnt->newton_iters, it);
         if (va) atomicAdd(&a.cnt->vacuum, va);
         if (fo) atomicAdd(&a.cnt->first_order, fo);
@@ -797,7 +833,9 @@ __global__ void __launch_bounds__(128) k_hard_faces(FluxArgs a) {
 // one flux launch, in the lean variant when no optional per-face work is on
 template <typename R, int RIEM, int SCHEME, bool DEFER, int MINB>
 cudaError_t launch_k_fluxes(const FluxArgs &a, const R *rec, stream_t st) {
-    const unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    // persistent: as many CTAs as the register bound lets every SM hold
+    unsigned grid = (unsigned)((a.nbucket + FLUX_WARPS - 1) / FLUX_WARPS);
+    if (a.queue) grid = std::min<unsigned>(grid, 152u * MINB);
     if (!a.rung && !a.rec_faces && !a.dM && !a.dS && !a.ract) {
         k_fluxes<R, RIEM, SCHEME, DEFER, MINB, true><<<grid, FLUX_WARPS * 32, 0, st>>>(a, rec);
         return launch_check();

@@ -19,6 +19,7 @@ cudaError_t launch_fluxes(const FluxArgs &a, const R *rec, int riem, int scheme,
                           stream_t st, cudaEvent_t *ev) {
     constexpr int MB = sizeof(R) == 4 ? 4 : 2;
     constexpr int E = HYDRO_RIEMANN_EXACT, H = HYDRO_RIEMANN_HLLC;
+    if (a.queue) HYD_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st));
     if (ev) HYD_CUDA(record_event(ev[0], st));
     bool done = false;
     if constexpr (sizeof(R) == 4) {
@@ -165,9 +166,12 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.hard_cap = 0;
     const bool learned = c->learned_decision >= 0 ? c->learned_decision != 0 : decide_learned(c);
     c->learned_active = learned;
-    // room for 2 hard faces per particle to start with (sub-buffer sizes a
-    // multiple of 128); a pass that fills a sub-buffer is redone with twice
-    // the room
+    // room for 2 hard faces per particle, at least 4096 per sub-buffer (twice
+    // the margin the kernel keeps) and at most 2^26 faces in all (sub-buffer
+    // sizes a multiple of 128): a sub-buffer near full makes the flux kernel
+    // solve further hard faces itself from the plain guess, so the buffer
+    // does not grow with the problem; a pass that still fills one (a backstop)
+    // is redone with twice the room
     const int64_t unit = (int64_t)HARD_SUB * 128;
     auto reserve_hard = [&](int64_t want) -> cudaError_t {
         const int64_t cap = (want + unit - 1) / unit * unit;
@@ -184,7 +188,9 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
         a.hard_cap = c->hard_cap;
         return cudaSuccess;
     };
-    if (learned) HYD_CUDA(reserve_hard(2 * n + 65536));
+    if (learned)
+        HYD_CUDA(reserve_hard(std::min<int64_t>(std::max<int64_t>(2 * n + 65536, (int64_t)HARD_SUB * 4096),
+                                                (int64_t)1 << 26)));
     a.rec_faces = c->rec_faces;
     a.rec_cursor = c->d_rec_cursor.get();
     a.rec_cap = c->rec_cap;
@@ -212,6 +218,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     a.ract = c->rung_live ? c->d_ract.get() : nullptr;
     a.dt0 = c->rung_dt0;
     a.bucket_ids = nullptr;
+    a.queue = c->flux_queue ? &c->d_cnt->flux_cursor : nullptr;
     if (c->rung_live && c->rung_touch_n >= 0) {
         a.bucket_ids = c->d_touch.get();
         a.nbucket = c->rung_touch_n;
@@ -223,6 +230,7 @@ cudaError_t run_fluxes(hydro_ctx *c, double dt, const double *dt_dev, stream_t s
     if (learned) {
         for (int attempt = 0;; attempt++) {
             HYD_CUDA(cudaMemsetAsync(a.hard_cursor, 0, HARD_SUB * sizeof(unsigned long long), st));
+            if (a.queue) HYD_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st));
             if (ev) HYD_CUDA(record_event(ev[0], st));
             HYD_CUDA(launch_fluxes_defer(a, c->d_recf.get(), c->cfg.scheme, c->flux_minb, st));
             if (ev) HYD_CUDA(record_event(ev[1], st));

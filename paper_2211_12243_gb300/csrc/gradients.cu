@@ -37,6 +37,8 @@ struct GradArgs {
     int32_t *npair;                      // per-particle gradient pairs
     DevCounters *cnt;
     const uint8_t *ract;                 // individual timesteps: only these (NULL: all)
+    const int32_t *list;                 // only these particles (NULL: all n) ...
+    const int *nlist;                    // ... their count (device)
 };
 
 template <typename R>
@@ -66,9 +68,8 @@ __device__ __forceinline__ void load10<double>(const double *p, double v[10]) {
 // bound; 5, 6: the variants hydro_autotune times)
 // LEAN: compiled without the staged outputs (outB, outG, outA, outN) and
 // the individual-timestep mask, which hydro_step does not use
-template <typename R, int MINB, bool LEAN = false>
-__global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+template <typename R, bool LEAN>
+__device__ __forceinline__ void grad_one(const GradArgs &a, R *__restrict__ rec, int64_t s) {
     int mypairs = 0;
     if (s < a.n && (!a.only_redo || (a.active[s] & ACT_REDO)) && (LEAN || !a.ract || a.ract[s])) {
         const Box bx = a.boxes[a.pbox[s]];
@@ -259,6 +260,36 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
         a.dt_part[s] = INFINITY;
         a.npair[s] = 0;
     }
+}
+
+// one thread per particle: every particle (list NULL), or the *nlist
+// particles of list (a guard round's recomputed particles; the count is
+// read on the device, the threads stride over it)
+template <typename R, int MINB, bool LEAN = false>
+__global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
+    if (a.list) {
+        const int64_t nl = *a.nlist;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
+             t += (int64_t)gridDim.x * blockDim.x)
+            grad_one<R, LEAN>(a, rec, a.list[t]);
+        return;
+    }
+    grad_one<R, LEAN>(a, rec, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
+// the particles with one of `bits` set, appended to idx (count in *nidx;
+// the order of the warps' appends is not fixed)
+__global__ void k_compact_flags(int64_t n, const uint8_t *__restrict__ active, uint8_t bits,
+                                int32_t *__restrict__ idx, int *__restrict__ nidx) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool on = s < n && (active[s] & bits);
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (!m) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(nidx, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) idx[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)s;
 }
 
 // global CFL dt (minimum of the per-particle values, Eq. 31) and the count
@@ -566,11 +597,25 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.npair = c->d_gpairs.get();
     a.cnt = c->d_cnt;
     a.ract = c->rung_live ? c->d_ract.get() : nullptr;
-    if (only_redo) HYD_CUDA(mark_reverse(c, st));
+    a.list = nullptr;
+    a.nlist = nullptr;
+    unsigned grid = grid_for(n, 128);
+    if (only_redo) {
+        // the particles whose lists hold a re-solved one, compacted: a
+        // guard round recomputes few particles, spread over the whole set
+        HYD_CUDA(mark_reverse(c, st));
+        HYD_CUDA(c->d_redo_idx.ensure(n));
+        HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nredo, 0, sizeof(int), st));
+        k_compact_flags<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), ACT_REDO,
+                                                           c->d_redo_idx.get(), &c->d_cnt->nredo);
+        HYD_CUDA(launch_check());
+        a.list = c->d_redo_idx.get();
+        a.nlist = &c->d_cnt->nredo;
+        grid = 152 * 8;
+    }
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
     HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
-    const unsigned grid = grid_for(n, 128);
     const bool lean = !a.outB && !a.outG && !a.outA && !a.outN && !a.ract;
     if (c->cfg.precision == HYDRO_MIXED) {
         float *r = c->d_recf.get();

@@ -127,7 +127,8 @@ cudaError_t cond_guard(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
 cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const long long k0 = launch_count();
     HYD_CUDA(guard_grow(c, s));
-    HYD_CUDA(rebuild_active_lists_dev(c, s));   // the grown search radii
+    HYD_CUDA(build_tree(c, s));                 // the grown search radii
+    HYD_CUDA(guard_particle_lists(c, s));
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(search_loop(c, 2, s));
     HYD_CUDA(run_primitives(c, s, true));
@@ -238,7 +239,8 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
           (const void *)c->d_ovf.get(), (const void *)c->d_partials.get(),
           (const void *)c->d_mlp_blob.get(), (const void *)c->d_hard.get(),
           (const void *)c->d_hard_idx.get(), (const void *)c->d_hard_cursor.get(),
-          (const void *)c->d_rec_cursor.get()})
+          (const void *)c->d_rec_cursor.get(), (const void *)c->d_guard_idx.get(),
+          (const void *)c->d_redo_idx.get()})
         put(q);
     k.push_back((unsigned long long)c->d_nbr_idx.cap);
     return k;

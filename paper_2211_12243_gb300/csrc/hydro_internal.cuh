@@ -98,6 +98,8 @@ struct DevCounters {
     int rung_capped;                  // particles the criteria wanted beyond max_rung
     unsigned long long rung_active;   // particles starting a step in this sub-step
     int bad_input;                    // a non-finite value in the caller's state
+    int nredo;                        // particles a guard round recomputes the gradients of
+    unsigned long long flux_cursor;   // the flux kernel's bucket queue
 };
 
 // bucket tree topology (host plan, mirrored on the device)
@@ -179,6 +181,7 @@ struct hydro_ctx {
     hyd::DevBuf<double> d_vsig_dt;    // per-particle CFL dt
     hyd::DevBuf<int32_t> d_gpairs;    // per-particle gradient pairs
     hyd::DevBuf<int32_t> d_guard_idx; // the guard round's grown particles (nguard of them)
+    hyd::DevBuf<int32_t> d_redo_idx;  // the particles whose gradients it recomputes (nredo)
 
     // neighbour lists
     hyd::DevBuf<int32_t> d_nbr_idx;
@@ -287,6 +290,7 @@ struct hydro_ctx {
     // gradient kernel 1 (no bound), 5 or 6
     int flux_minb = 4;
     int grad_minb = 1;
+    int flux_queue = 1;               // flux kernel: buckets drawn from a cursor (0: by index)
     int64_t steps_done = 0;           // hydro_step calls completed
 };
 
@@ -339,6 +343,7 @@ cudaError_t mark_reverse(hydro_ctx *c, stream_t st);
 // wait): the queued overflow buckets, and the re-search rebuild
 cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);
 cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st);
+cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu

@@ -454,6 +454,149 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_build_lists(ListArgs a) 
     }
 }
 
+// Lists of single particles (the N_cond guard's grown particles, whose
+// search radii rose): one warp per particle walks the tree with that
+// particle's own sphere -- the lanes test a node's children at once, then a
+// bucket's particles at once -- instead of rebuilding the lists of the
+// particle's whole bucket at its largest radius.  The walk takes the
+// children in the order of k_build_lists's walk (internal nodes last pushed
+// first, buckets in ascending order), so a list holds the same entries in
+// the same order as a bucket rebuild would give it.  mode 1 counts and
+// reserves storage in the overflow region (flagging ST_LIST_CAPACITY when it
+// does not fit), mode 2 writes.  Warps stride over the *npidx particles of
+// pidx (the count is read on the device).
+struct PartListArgs {
+    const int32_t *pidx;
+    const int *npidx;
+    const int32_t *node_first, *node_cnt, *box_root, *pbox;
+    int64_t nbucket_total;
+    const uint4 *lo, *hi;
+    const uint32_t *qx, *qy, *qz;
+    const double *xs, *ys, *zs, *hs;
+    const Box *boxes;
+    int32_t *nbr_idx;
+    int64_t *nbr_off;
+    int32_t *nbr_cnt;
+    int64_t capacity;
+    DevCounters *cnt;
+    int mode;
+};
+
+constexpr int PL_WARPS = 4;
+
+__global__ void __launch_bounds__(PL_WARPS * 32) k_particle_lists(PartListArgs a) {
+    __shared__ int32_t stack_all[PL_WARPS][STACK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *stack = stack_all[warp];
+    const int np = *a.npidx;
+    const int nwarps = gridDim.x * PL_WARPS;
+    for (int g = blockIdx.x * PL_WARPS + warp; g < np; g += nwarps) {
+        const int s = a.pidx[g];
+        const Box bx = a.boxes[a.pbox[s]];
+        const uint32_t px = a.qx[s], py = a.qy[s], pz = a.qz[s];
+        const double x = a.xs[s], y = a.ys[s], z = a.zs[s], hs = a.hs[s];
+        const double h2 = __dmul_rn(hs, hs);
+        float lo2, hi2;
+        {
+            const float hf = (float)hs;
+            lo2 = hf * hf * (1.0f - 1e-4f);
+            hi2 = hf * hf * (1.0f + 1e-4f);
+            const double Lmin = fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+            if (hs < Lmin * (1.0 / 4096.0)) { lo2 = -1.0f; hi2 = 3.0e38f; }
+        }
+        int32_t *out = nullptr;
+        int64_t lim = 0;
+        if (a.mode == 2) {
+            const int64_t o = a.nbr_off[s];
+            out = a.nbr_idx + o;
+            lim = max((int64_t)0, a.capacity - o);
+        }
+        int count = 0;
+        // the particles of bucket b within the sphere, appended in order
+        auto scan_bucket = [&](int b) {
+            const int f = a.node_first[b], c = a.node_cnt[b];
+            bool in = false;
+            int j = f + lane;
+            if (lane < c) {
+                const float dx = qdiff(px, a.qx[j], bx.s[0]);
+                const float dy = qdiff(py, a.qy[j], bx.s[1]);
+                const float dz = qdiff(pz, a.qz[j], bx.s[2]);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                in = r2 < lo2;
+                if (!in && r2 <= hi2) {   // within the float band: decide in double
+                    const double ex = fold64(__dsub_rn(a.xs[j], x), bx.L[0]);
+                    const double ey = fold64(__dsub_rn(a.ys[j], y), bx.L[1]);
+                    const double ez = fold64(__dsub_rn(a.zs[j], z), bx.L[2]);
+                    in = r2_exact(ex, ey, ez) < h2;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in && a.mode == 2) {
+                const int pos = count + __popc(m & ((1u << lane) - 1u));
+                if (pos < lim) out[pos] = j;
+            }
+            count += __popc(m);
+        };
+        const int root = a.box_root[a.pbox[s]];
+        int sp = 0;
+        if (root < a.nbucket_total) {
+            scan_bucket(root);
+        } else {
+            if (lane == 0) stack[0] = root;
+            sp = 1;
+        }
+        __syncwarp();
+        bool stack_ovf = false;
+        while (sp > 0) {
+            sp--;
+            const int node = stack[sp];
+            __syncwarp();
+            const int nf = a.node_first[node], nc = a.node_cnt[node];
+            bool hit = false;
+            if (lane < nc) {
+                const uint4 l = a.lo[nf + lane], u = a.hi[nf + lane];
+                const float gx = u2f(point_gap(px, l.x, u.x)) * bx.s[0];
+                const float gy = u2f(point_gap(py, l.y, u.y)) * bx.s[1];
+                const float gz = u2f(point_gap(pz, l.z, u.z)) * bx.s[2];
+                hit = gx * gx + gy * gy + gz * gz <= hi2;
+            }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (nf < a.nbucket_total) {
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    scan_bucket(nf + k);
+                }
+                __syncwarp();
+            } else {
+                const int nh = __popc(m);
+                if (sp + nh > STACK) {   // (cannot happen for trees of MAX_LEVELS levels)
+                    stack_ovf = true;
+                    break;
+                }
+                if (hit) stack[sp + __popc(m & ((1u << lane) - 1u))] = nf + lane;
+                sp += nh;
+                __syncwarp();
+            }
+        }
+        if (stack_ovf) {
+            if (lane == 0) set_flag(a.cnt, ST_STACK);
+            continue;
+        }
+        if (a.mode == 1 && lane == 0) {
+            const unsigned long long base =
+                atomicAdd(&a.cnt->list_cursor, (unsigned long long)count);
+            a.nbr_off[s] = (int64_t)base;
+            a.nbr_cnt[s] = count;
+            if ((int64_t)base + count > a.capacity) {
+                set_flag(a.cnt, ST_LIST_CAPACITY);
+                a.nbr_cnt[s] = 0;   // nothing stored for this list
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_export_count(int64_t n, const int32_t *__restrict__ perm,
                                const int32_t *__restrict__ cnt, int64_t *__restrict__ rowlen) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -701,6 +844,39 @@ cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st) {
     if (*nq == 0) return cudaSuccess;
     HYD_CUDA(build_tree(c, st));   // the buckets' search radii changed
     return build_lists_queued(c, *nq, st);
+}
+
+// new lists, in the overflow region, for the particles of guard_idx (the
+// guard round's grown particles, count nguard on the device); the tree must
+// hold the current positions (its search radii are not used)
+cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st) {
+    const Plan &P = c->plan;
+    PartListArgs a;
+    a.pidx = c->d_guard_idx.get();
+    a.npidx = &c->d_cnt->nguard;
+    a.node_first = c->d_node_first.get();
+    a.node_cnt = c->d_node_cnt.get();
+    a.box_root = c->d_box_root.get();
+    a.pbox = c->d_pbox.get();
+    a.nbucket_total = P.nbucket;
+    a.lo = c->d_node_aabb.get();
+    a.hi = c->d_node_aabb_hi.get();
+    a.qx = c->d_qx.get(); a.qy = c->d_qy.get(); a.qz = c->d_qz.get();
+    a.xs = c->d_xs.get(); a.ys = c->d_ys.get(); a.zs = c->d_zs.get();
+    a.hs = c->d_hs.get();
+    a.boxes = c->d_boxes.get();
+    a.nbr_idx = c->d_nbr_idx.get();
+    a.nbr_off = c->d_nbr_off.get();
+    a.nbr_cnt = c->d_nbr_cnt.get();
+    a.capacity = (int64_t)c->d_nbr_idx.cap;
+    a.cnt = c->d_cnt;
+    const unsigned grid = 152 * 8;
+    for (int mode = 1; mode <= 2; mode++) {
+        a.mode = mode;
+        k_particle_lists<<<grid, PL_WARPS * 32, 0, st>>>(a);
+        HYD_CUDA(launch_check());
+    }
+    return cudaSuccess;
 }
 
 cudaError_t queue_flagged(hydro_ctx *c, uint8_t bits, stream_t st) {

@@ -75,6 +75,44 @@ __device__ __forceinline__ void side_f<float>(const GasK<float> &k, float p, flo
     df = shock ? dfs : dfr;
 }
 
+// float path inside the Newton loop: the per-face constants of one side
+// (the shock branch's A_K = 2/((g+1) rho_K) and B_K = (g-1)/(g+1) p_K, 1/p_K,
+// c_K/g) are formed once per face, and 1/p once per iteration for both
+// sides, which leaves two reciprocals, a square root and a power per side
+// and step on the special-function unit
+struct SideF {
+    float A, B, ipk, cg, pk, ck;
+};
+
+__device__ __forceinline__ SideF side_prep(const GasK<float> &k, float rk, float pk, float ck) {
+    SideF s;
+    s.A = __fdividef(k.g5, rk);
+    s.B = k.g6 * pk;
+    s.ipk = __fdividef(1.f, pk);
+    s.cg = ck * k.inv_g;
+    s.pk = pk;
+    s.ck = ck;
+    return s;
+}
+
+// f_K(p) and f_K'(p) with ip = 1/p: both branches evaluated and selected
+// (no divergence between shock and rarefaction sides); the rarefaction
+// derivative (1/(rho_K c_K)) (p/p_K)^(-(g+1)/(2g)) is written as
+// (p/p_K)^((g-1)/(2g)) c_K / (g p)
+__device__ __forceinline__ void side_eval(const GasK<float> &k, const SideF &s, float p, float ip,
+                                          float &f, float &df) {
+    const float ia = __fdividef(1.f, p + s.B);
+    const float q = sqrt_(s.A * ia);
+    const float fs = (p - s.pk) * q;
+    const float dfs = q * (1.f - 0.5f * (p - s.pk) * ia);
+    const float t = __powf(p * s.ipk, k.z);
+    const float fr = k.g4 * s.ck * (t - 1.f);
+    const float dfr = t * s.cg * ip;
+    const bool shock = p > s.pk;
+    f = shock ? fs : fr;
+    df = shock ? dfs : dfr;
+}
+
 template <typename R>
 __device__ __forceinline__ void side_f(const GasK<R> &k, R p, R rk, R pk, R ck, R &f, R &df) {
     if (p > pk) {
@@ -141,16 +179,34 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
     bool conv = false;
     R fl, dfl, fr, dfr;
     R dp_last = R(0);
-    for (int it = 1; it <= max_newton; it++) {
-        side_f(k, p, rl, pl, cl, fl, dfl);
-        side_f(k, p, rr, pr, cr, fr, dfr);
-        R pn = p - div_(fl + fr + du, dfl + dfr);
-        if (!(pn > pfloor)) pn = pfloor;
-        R ch = R(2) * div_(fabs(pn - p), pn + p);
-        dp_last = pn - p;
-        p = pn;
-        o.iters = it;
-        if (ch < tol) { conv = true; break; }
+    if constexpr (sizeof(R) == 4) {
+        const SideF sl = side_prep(k, rl, pl, cl), sr = side_prep(k, rr, pr, cr);
+        const float htol = 0.5f * tol;
+        for (int it = 1; it <= max_newton; it++) {
+            const float ip = __fdividef(1.f, p);
+            side_eval(k, sl, p, ip, fl, dfl);
+            side_eval(k, sr, p, ip, fr, dfr);
+            float pn = p - __fdividef(fl + fr + du, dfl + dfr);
+            if (!(pn > pfloor)) pn = pfloor;
+            // relative change 2 |pn - p| / (pn + p) < tol, without a division
+            const bool done = fabsf(pn - p) < htol * (pn + p);
+            dp_last = pn - p;
+            p = pn;
+            o.iters = it;
+            if (done) { conv = true; break; }
+        }
+    } else {
+        for (int it = 1; it <= max_newton; it++) {
+            side_f(k, p, rl, pl, cl, fl, dfl);
+            side_f(k, p, rr, pr, cr, fr, dfr);
+            R pn = p - div_(fl + fr + du, dfl + dfr);
+            if (!(pn > pfloor)) pn = pfloor;
+            R ch = R(2) * div_(fabs(pn - p), pn + p);
+            dp_last = pn - p;
+            p = pn;
+            o.iters = it;
+            if (ch < tol) { conv = true; break; }
+        }
     }
     if (conv && sizeof(R) == 4 && kd) {
         // the root of the float face states to double precision: one Newton
