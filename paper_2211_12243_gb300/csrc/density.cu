@@ -357,7 +357,9 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     double MQd = (double)MQ.hi + (double)MQ.lo;
     double hN = (double)h;
     double Kd = a.kernel == 0 ? 14.0 : 32.0 / 3.0;
-    double hnew = MQd > 0.0 ? hN - (Fd - (double)N / Kd) * hN / MQd : hN;
+    // (N_NGB in double: a guard round's grown 32 * 1.2^k is not a float)
+    const double Nd = a.nngb ? a.nngb[s] : a.n_ngb;
+    double hnew = MQd > 0.0 ? hN - (Fd - Nd / Kd) * hN / MQd : hN;
     if (fin || comp > 0.f) {
         // the compacted list is complete for r < crad
         const double crad = fin ? hN * (1.0 + 5e-5) : (double)comp;
