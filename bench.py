@@ -671,8 +671,9 @@ def main():
     for c in comp.values():
         c["frac"] = c["achieved"] / c["peak"]
     traffic_pf = FLUX_TRAFFIC_BYTES_PER_FACE.get(args.workload)
-    traffic = traffic_pf * faces if traffic_pf and (tuning is None or
-                                                    tuning["flux_min_ctas"] == 4) else None
+    # (measured for the register bound of 4 CTAs per SM with the bucket queue)
+    traffic = traffic_pf * faces if traffic_pf and (
+        tuning is None or (tuning["flux_min_ctas"] == 4 and tuning.get("flux_queue", 1) == 1)) else None
     hbm_peak = measured_hbm_gbs()
     if traffic and hbm_peak:
         comp["hbm"] = {"achieved": traffic / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -856,7 +857,7 @@ FACE_OPS = {
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
 # of the current kernel on a small case of the workload (profiles/); a
 # launch's traffic scales with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = {"sod": 28.54}
+FLUX_TRAFFIC_BYTES_PER_FACE = {"sod": 28.56, "lognormal": 32.60}
 
 if __name__ == "__main__":
     sys.exit(main())

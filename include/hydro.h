@@ -482,7 +482,11 @@ int hydro_set_entropy(hydro_ctx *ctx, double *A);
  *   flux_queue: the flux kernel's buckets one per warp by index (0) or
  *     drawn by persistent warps from a global cursor (1, the default: a
  *     warp done with a light bucket takes the next at once), timed over
- *     the same stage with the chosen bound (mixed precision only).
+ *     the same stage with the chosen bound (mixed precision only);
+ *   grad_rank: the gradient kernel's 128 particles of a CTA taken in
+ *     their order (0) or ranked by list length (1, the default: the lanes
+ *     of a warp walk lists of similar length), timed over the gradient
+ *     stage with the chosen bound.
  * The times (ms, best of two) are returned beside the choices. */
 typedef struct {
     double search_margin;
@@ -494,6 +498,8 @@ typedef struct {
     float flux_ms[3];         /* [4, 5, 6]; 0 in FP64 */
     int flux_queue;
     float flux_queue_ms[2];   /* [by index, drawn]; 0 in FP64 */
+    int grad_rank;
+    float grad_rank_ms[2];    /* [in order, ranked] */
 } hydro_tuning;
 
 /* Time the candidates above on the particles p (device, caller order; state
@@ -506,7 +512,8 @@ int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_
 
 /* Apply choices saved from an earlier hydro_autotune (search_margin >= 1,
  * nbr_slots in [32, 256], grad_min_ctas in {1, 5, 6}, flux_min_ctas in
- * {4, 5, 6}, flux_queue in {0, 1}; the time fields are ignored).
+ * {4, 5, 6}, flux_queue and grad_rank in {0, 1}; the time fields are
+ * ignored).
  * HYDRO_EINVAL otherwise. */
 int hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *t);
 

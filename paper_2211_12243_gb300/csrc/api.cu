@@ -1025,8 +1025,10 @@ int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (t->grad_min_ctas != 1 && t->grad_min_ctas != 5 && t->grad_min_ctas != 6) return HYDRO_EINVAL;
     if (t->flux_min_ctas < 4 || t->flux_min_ctas > 6) return HYDRO_EINVAL;
     if (t->flux_queue != 0 && t->flux_queue != 1) return HYDRO_EINVAL;
+    if (t->grad_rank != 0 && t->grad_rank != 1) return HYDRO_EINVAL;
     c->cfg.search_margin = t->search_margin;
     c->flux_queue = t->flux_queue;
+    c->grad_rank = t->grad_rank;
     c->nbr_per_particle = t->nbr_slots;
     c->grad_minb = t->grad_min_ctas;
     c->flux_minb = t->flux_min_ctas;
@@ -1101,6 +1103,23 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
         if (t < best) { best = t; bg = gminb[k]; }
     }
     c->grad_minb = bg;
+    // lanes in particle order or ranked by list length, with that bound
+    best = 1e30f;
+    for (int r = 0; r < 2; r++) {
+        c->grad_rank = r;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            API_CUDA(record_event(c->ev[0], st));
+            API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, false, st));
+            API_CUDA(record_event(c->ev[1], st));
+            API_CUDA(cudaEventSynchronize(c->ev[1]));
+            API_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            t = std::min(t, ms);
+        }
+        T.grad_rank_ms[r] = t;
+        if (t < best) { best = t; T.grad_rank = r; }
+    }
+    c->grad_rank = T.grad_rank;
     // flux stage, plain guess (the dt the gradients found)
     int bf = 4;
     if (c->cfg.precision == HYDRO_MIXED) {

@@ -50,6 +50,7 @@ struct DensArgs {
     double *h;                // sorted, in: guess, out: solution
     double *om;               // sorted out
     DevCounters *cnt;
+    bool rank;                // full solve: rank the CTA's particles by list length
 };
 
 // Growth of the search radius hs after a failed solve.  First failure
@@ -220,11 +221,32 @@ __device__ __forceinline__ df from_i64(long long v) {
 
 // ---------------------------------------------------------------- mixed path
 constexpr int DENS_THREADS = 128;
+static_assert(DENS_THREADS == 128, "the ranking keys hold a 7-bit lane index");
 
 __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
                                 const uint64_t *__restrict__ q64y,
                                 const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a.rank && !a.only_active) {
+        // the CTA's particles ranked by list length (as in the gradient
+        // kernel): the lanes of a warp walk lists of similar length
+        const int64_t base = blockIdx.x * (int64_t)blockDim.x;
+        __shared__ unsigned key[DENS_THREADS];
+        key[threadIdx.x] = ((s < a.n ? (unsigned)min(a.nbr_cnt[s], 0xFFFFFF) : 0u) << 7) |
+                           threadIdx.x;
+        __syncthreads();
+        for (int k = 2; k <= DENS_THREADS; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int t = threadIdx.x, u = t ^ j;
+                if (u > t) {
+                    const unsigned x = key[t], y = key[u];
+                    if ((x > y) == ((t & k) == 0)) { key[t] = y; key[u] = x; }
+                }
+                __syncthreads();
+            }
+        }
+        s = base + (key[threadIdx.x] & 127u);
+    }
     if (s >= a.n) return;
     if (a.only_active && !(a.active[s] & 1)) return;
     const Box bx = a.boxes[a.pbox[s]];
@@ -445,6 +467,7 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
     a.h = c->d_hsorted.get();
     a.om = c->d_omsorted.get();
     a.cnt = c->d_cnt;
+    a.rank = c->grad_rank != 0;   // (the gradient kernel's choice: the same divergence)
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_fail, 0, sizeof(int), st));
     if (c->cfg.precision == HYDRO_MIXED) {
         // 64-bit fixed-point copies for the refinement step (xs.. are sorted)

@@ -39,6 +39,7 @@ struct GradArgs {
     const uint8_t *ract;                 // individual timesteps: only these (NULL: all)
     const int32_t *list;                 // only these particles (NULL: all n) ...
     const int *nlist;                    // ... their count (device)
+    bool rank;                           // dense pass: rank the CTA's particles by list length
 };
 
 template <typename R>
@@ -274,7 +275,33 @@ __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restri
             grad_one<R, LEAN>(a, rec, a.list[t]);
         return;
     }
-    grad_one<R, LEAN>(a, rec, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    // the CTA's 128 consecutive particles, ranked by list length so that the
+    // lanes of a warp walk lists of similar length (one thread per particle:
+    // a warp runs until its longest list is done); the ranking stays inside
+    // the CTA, which keeps the Morton locality of the gathers
+    const int64_t base = blockIdx.x * (int64_t)blockDim.x;
+    const int64_t s0 = base + threadIdx.x;
+    if (!a.rank) {
+        grad_one<R, LEAN>(a, rec, s0);
+        return;
+    }
+    __shared__ unsigned key[128];
+    key[threadIdx.x] = ((s0 < a.n ? (unsigned)min(a.nbr_cnt[s0], 0xFFFFFF) : 0u) << 7) |
+                       threadIdx.x;
+    __syncthreads();
+    // bitonic sort of the 128 keys (ascending)
+    for (int k = 2; k <= 128; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int t = threadIdx.x, u = t ^ j;
+            if (u > t) {
+                const unsigned x = key[t], y = key[u];
+                const bool up = (t & k) == 0;
+                if ((x > y) == up) { key[t] = y; key[u] = x; }
+            }
+            __syncthreads();
+        }
+    }
+    grad_one<R, LEAN>(a, rec, base + (key[threadIdx.x] & 127u));
 }
 
 // the particles with one of `bits` set, appended to idx (count in *nidx;
@@ -599,11 +626,12 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.ract = c->rung_live ? c->d_ract.get() : nullptr;
     a.list = nullptr;
     a.nlist = nullptr;
+    a.rank = c->grad_rank != 0;
     unsigned grid = grid_for(n, 128);
     if (only_redo) {
         // the particles whose lists hold a re-solved one, compacted: a
         // guard round recomputes few particles, spread over the whole set
-        HYD_CUDA(mark_reverse(c, st));
+        HYD_CUDA(mark_reverse(c, st, true));
         HYD_CUDA(c->d_redo_idx.ensure(n));
         HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nredo, 0, sizeof(int), st));
         k_compact_flags<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), ACT_REDO,

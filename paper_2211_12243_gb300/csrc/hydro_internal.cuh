@@ -291,6 +291,7 @@ struct hydro_ctx {
     int flux_minb = 4;
     int grad_minb = 1;
     int flux_queue = 1;               // flux kernel: buckets drawn from a cursor (0: by index)
+    int grad_rank = 1;                // gradient kernel: lanes ranked by list length (0: not)
     int64_t steps_done = 0;           // hydro_step calls completed
 };
 
@@ -338,7 +339,7 @@ cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
 cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st);
 // ACT_REDO on the guard round's particles and on every particle i with one
 // of them in its list (r_ia < h_i), found by walks of the bucket tree
-cudaError_t mark_reverse(hydro_ctx *c, stream_t st);
+cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h = false);
 // the same two passes with the bucket count read on the device (no host
 // wait): the queued overflow buckets, and the re-search rebuild
 cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);

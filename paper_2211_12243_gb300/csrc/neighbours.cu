@@ -33,31 +33,34 @@ __device__ __forceinline__ float wmaxf(float v) {
     return v;
 }
 
-// level 0: bucket boxes from the particles
+// level 0: bucket boxes from the particles; lo.w the largest search
+// radius hs, hi.w the largest smoothing length h (both rounded up)
 __global__ void k_aabb_leaf(int64_t nbucket, const int32_t *__restrict__ first,
                             const int32_t *__restrict__ cnt, const uint32_t *__restrict__ qx,
                             const uint32_t *__restrict__ qy, const uint32_t *__restrict__ qz,
-                            const double *__restrict__ hs, uint4 *__restrict__ lo,
-                            uint4 *__restrict__ hi) {
+                            const double *__restrict__ hs, const double *__restrict__ hh,
+                            uint4 *__restrict__ lo, uint4 *__restrict__ hi) {
     int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (b >= nbucket) return;
     int f = first[b], c = cnt[b];
     uint32_t x0 = 0xffffffffu, y0 = 0xffffffffu, z0 = 0xffffffffu, x1 = 0, y1 = 0, z1 = 0;
-    float h = 0.f;
+    float h = 0.f, hm = 0.f;
     if (lane < c) {
         int s = f + lane;
         x0 = x1 = qx[s];
         y0 = y1 = qy[s];
         z0 = z1 = qz[s];
         h = __double2float_ru(hs[s]);
+        hm = __double2float_ru(hh[s]);
     }
     x0 = wmin(x0); y0 = wmin(y0); z0 = wmin(z0);
     x1 = wmax(x1); y1 = wmax(y1); z1 = wmax(z1);
     h = wmaxf(h);
+    hm = wmaxf(hm);
     if (lane == 0) {
         lo[b] = make_uint4(x0, y0, z0, __float_as_uint(h));
-        hi[b] = make_uint4(x1, y1, z1, 0u);
+        hi[b] = make_uint4(x1, y1, z1, __float_as_uint(hm));
     }
 }
 
@@ -71,18 +74,19 @@ __global__ void k_aabb_node(int64_t node0, int64_t nnode, const int32_t *__restr
     int64_t node = node0 + k;
     int f = first[node], c = cnt[node];
     uint32_t x0 = 0xffffffffu, y0 = 0xffffffffu, z0 = 0xffffffffu, x1 = 0, y1 = 0, z1 = 0;
-    float h = 0.f;
+    float h = 0.f, hm = 0.f;
     if (lane < c) {
         uint4 a = lo[f + lane], b = hi[f + lane];
         x0 = a.x; y0 = a.y; z0 = a.z; h = __uint_as_float(a.w);
-        x1 = b.x; y1 = b.y; z1 = b.z;
+        x1 = b.x; y1 = b.y; z1 = b.z; hm = __uint_as_float(b.w);
     }
     x0 = wmin(x0); y0 = wmin(y0); z0 = wmin(z0);
     x1 = wmax(x1); y1 = wmax(y1); z1 = wmax(z1);
     h = wmaxf(h);
+    hm = wmaxf(hm);
     if (lane == 0) {
         lo[node] = make_uint4(x0, y0, z0, __float_as_uint(h));
-        hi[node] = make_uint4(x1, y1, z1, 0u);
+        hi[node] = make_uint4(x1, y1, z1, __float_as_uint(hm));
     }
 }
 
@@ -642,10 +646,12 @@ __global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ firs
 // bucket tree per guard particle and warp.  The lanes test the children of
 // a node at once: a child is entered when the lower bound of its periodic
 // distance from a is within the largest search radius of its particles
-// (hs >= h); the particles of an entered bucket are tested exactly, one per
-// lane (the double-precision membership of the lists).  Marks ACT_REDO on
-// them and on a itself.  Warps stride over the guard particles, whose count
-// is read on the device.
+// (hs >= h), or (use_h) within their largest h when the tree was built --
+// the tighter bound for a guard round, where only the guard particles' h
+// moved since, and each of those marks itself; the particles of an entered
+// bucket are tested exactly, one per lane (the double-precision membership
+// of the lists).  Marks ACT_REDO on them and on a itself.  Warps stride
+// over the guard particles, whose count is read on the device.
 constexpr int RSTACK = 320;   // 32-ary tree of at most MAX_LEVELS levels
 constexpr int RWARPS = 4;
 
@@ -658,7 +664,8 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
                const uint32_t *__restrict__ qz, const double *__restrict__ xs,
                const double *__restrict__ ys, const double *__restrict__ zs,
                const double *__restrict__ h, const int32_t *__restrict__ pbox,
-               const Box *__restrict__ boxes, uint8_t *__restrict__ active, DevCounters *cnt) {
+               const Box *__restrict__ boxes, uint8_t *__restrict__ active, DevCounters *cnt,
+               bool use_h) {
     __shared__ int stack_all[RWARPS][RSTACK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *stack = stack_all[warp];
@@ -694,7 +701,7 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
             bool hit = false;
             if (lane < c) {
                 const uint4 l = lo[f + lane], u = hi[f + lane];
-                const float rmax = __uint_as_float(l.w) * 1.0001f;
+                const float rmax = __uint_as_float(use_h ? u.w : l.w) * 1.0001f;
                 const float gx = u2f(point_gap(pax, l.x, u.x)) * bx.s[0];
                 const float gy = u2f(point_gap(pay, l.y, u.y)) * bx.s[1];
                 const float gz = u2f(point_gap(paz, l.z, u.z)) * bx.s[2];
@@ -718,13 +725,14 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-cudaError_t mark_reverse(hydro_ctx *c, stream_t st) {
+cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h) {
     const Plan &P = c->plan;
     k_mark_reverse<<<152 * 4, RWARPS * 32, 0, st>>>(
         c->d_guard_idx.get(), &c->d_cnt->nguard, c->d_node_first.get(), c->d_node_cnt.get(),
         c->d_box_root.get(), P.nbucket, c->d_node_aabb.get(), c->d_node_aabb_hi.get(),
         c->d_qx.get(), c->d_qy.get(), c->d_qz.get(), c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
-        c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(), c->d_active.get(), c->d_cnt);
+        c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(), c->d_active.get(), c->d_cnt,
+        use_h);
     return launch_check();
 }
 
@@ -732,7 +740,8 @@ cudaError_t build_tree(hydro_ctx *c, stream_t st) {
     const Plan &P = c->plan;
     k_aabb_leaf<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_qx.get(), c->d_qy.get(),
-        c->d_qz.get(), c->d_hs.get(), c->d_node_aabb.get(), c->d_node_aabb_hi.get());
+        c->d_qz.get(), c->d_hs.get(), c->d_hsorted.get(), c->d_node_aabb.get(),
+        c->d_node_aabb_hi.get());
     HYD_CUDA(launch_check());
     for (int l = 1; l < P.nlevels; l++) {
         int64_t n0 = P.level_off[l], nn = P.level_off[l + 1] - P.level_off[l];

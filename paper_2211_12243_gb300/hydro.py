@@ -94,6 +94,7 @@ class Tuning(C.Structure):
         ("search_margin", C.c_double), ("nbr_slots", C.c_int), ("grad_min_ctas", C.c_int),
         ("flux_min_ctas", C.c_int), ("front_ms", (C.c_float * 3) * 4), ("grad_ms", C.c_float * 3),
         ("flux_ms", C.c_float * 3), ("flux_queue", C.c_int), ("flux_queue_ms", C.c_float * 2),
+        ("grad_rank", C.c_int), ("grad_rank_ms", C.c_float * 2),
     ]
 
     def as_dict(self):
@@ -101,7 +102,8 @@ class Tuning(C.Structure):
                 "grad_min_ctas": self.grad_min_ctas, "flux_min_ctas": self.flux_min_ctas,
                 "front_ms": [[self.front_ms[i][j] for j in range(3)] for i in range(4)],
                 "grad_ms": list(self.grad_ms), "flux_ms": list(self.flux_ms),
-                "flux_queue": self.flux_queue, "flux_queue_ms": list(self.flux_queue_ms)}
+                "flux_queue": self.flux_queue, "flux_queue_ms": list(self.flux_queue_ms),
+                "grad_rank": self.grad_rank, "grad_rank_ms": list(self.grad_rank_ms)}
 
 
 EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_config",
@@ -409,6 +411,7 @@ class Hydro:
         t.grad_min_ctas = d["grad_min_ctas"]
         t.flux_min_ctas = d["flux_min_ctas"]
         t.flux_queue = d.get("flux_queue", 1)
+        t.grad_rank = d.get("grad_rank", 1)
         rc = self.lib.hydro_set_tuning(self.h, C.byref(t))
         if rc:
             raise HydroError(rc, "hydro_set_tuning")
