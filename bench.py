@@ -94,6 +94,12 @@ def parse():
                     help="time base steps of individual timesteps (hydro_step_rungs) with "
                          "dt0 = K times the CFL dt of the initial state; value = pairs over "
                          "the whole base step")
+    ap.add_argument("--caller-order", action="store_true",
+                    help="keep the particles in the generator's order (sorted_output = 0): every "
+                         "step gathers them from and scatters them back to that order")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the short runs of the Sod tube, the Sedov blast and the batch of "
+                         "boxes that the default workload's line carries under other_workloads")
     return ap.parse_args()
 
 
@@ -471,6 +477,62 @@ def oracle_sample_parity(kind, hydro, n=None):
             "note": "per-particle |dQ_gpu - dQ_oracle| / sum over faces |c|, one step, same dt"}
 
 
+def other_workloads(hydro, flush, stream, steps=10, warm=3):
+    """Short runs of the other configurations at their full sizes -- the
+    1,067,742-particle Sod tube, the 128^3 Sedov blast and the 512 boxes of
+    4k-64k particles in one context -- each with its mixed step (plain guess,
+    autotuned, graph steps, L2 flushed before every step) against one plain
+    FP64 step of the same state: the metric, the whole-step rate and the
+    times of both; the state kept in the library's order (sorted_output)."""
+    import numpy as np
+    import torch
+    out = {}
+    for kind in ("sod", "sedov", "batch"):
+        w, name = make_workload(kind, DEFAULT_N[kind])
+        n = w["x"].size
+        restart = kind == "batch"
+        ok = (0, -5) if kind == "batch" else (0,)
+        common = dict(gamma=w["gamma"], riemann="exact", search_margin=1.15, graph=1,
+                      sorted_output=1)
+        H = hydro.Hydro(hydro.default_config(precision="mixed", **common))
+        H.set_boxes(*boxes_of(hydro, w))
+        H.reserve(n, 96)
+        st = hydro.to_device(w)
+        # one step on a copy: the library's order for the state (and, for the
+        # restarted batch, the converged h of the initial state)
+        tmp = {k: v.clone() for k, v in st.items()}
+        s0 = H.step(tmp, -1.0, check=False)
+        assert s0["status"] in ok, s0
+        perm = H.get_order().cpu().numpy()
+        for k in KEYS:
+            w[k] = tmp[k].cpu().numpy() if (restart and k == "h") else np.ascontiguousarray(w[k][perm])
+        del tmp
+        st = hydro.to_device(w)
+        tuning = H.autotune(st)
+        r = timed_steps(hydro, H, st, steps, warm, restart, ok, flush, stream)
+        H.close()
+        del st
+        torch.cuda.empty_cache()
+        H64 = hydro.Hydro(hydro.default_config(precision="fp64", **common))
+        H64.set_boxes(*boxes_of(hydro, w))
+        H64.set_tuning(dict(tuning, grad_min_ctas=1, flux_min_ctas=4))
+        st = hydro.to_device(w)
+        r64 = timed_steps(hydro, H64, st, 1, 1, restart, ok, flush, stream)
+        H64.close()
+        del st
+        torch.cuda.empty_cache()
+        out[name] = {
+            "particles": n, "value": r["pairs"] / (r["gf_ms"] / 1000.0),
+            "step_rate": r["pairs"] / (r["ms"] / 1000.0), "ms_per_step": r["ms"] / steps,
+            "grad_flux_ms_per_step": r["gf_ms"] / steps, "steps": steps,
+            "timed_steps": "each from the initial state" if restart else "consecutive",
+            "plain_fp64": {"value": r64["pairs"] / (r64["gf_ms"] / 1000.0),
+                           "ms_per_step": r64["ms"], "steps": 1},
+            "vs_plain_fp64": (r["pairs"] / r["gf_ms"]) / (r64["pairs"] / r64["gf_ms"]),
+            "note": "mixed step with the plain starting guess (no network trained for it)"}
+    return out
+
+
 def measured_peaks():
     """This GPU's arithmetic throughput by the library's probes."""
     from paper_2211_12243_gb300 import hydro
@@ -511,6 +573,8 @@ def main():
     graph = 0 if args.no_graph else 1
     common = dict(gamma=w["gamma"], scheme=args.scheme, riemann=riemann, search_margin=margin,
                   graph=graph)
+    sorted_out = not args.caller_order
+    common["sorted_output"] = int(sorted_out)
     cfg = hydro.default_config(precision=args.precision, learned_guess=int(learned),
                                riemann_polish=int(args.riemann_polish), **common)
     H = hydro.Hydro(cfg)
@@ -544,8 +608,24 @@ def main():
     assert s0["status"] in ok_status, s0
     dt_cmp = s0["dt"]
     if restart:
-        st["h"].copy_(tmp["h"])
         w["h"] = tmp["h"].cpu().numpy()
+    if sorted_out:
+        # the state kept in the library's own (Morton) order, as a simulation
+        # that keeps sorted_output on carries it from step to step (tmp, the
+        # step's output, is already in that order)
+        perm = H.get_order().cpu().numpy()
+        for kk in KEYS:
+            if not (restart and kk == "h"):
+                w[kk] = np.ascontiguousarray(w[kk][perm])
+        st = hydro.to_device(w)
+        if args.gravity:
+            acc = acc[torch.as_tensor(perm, device="cuda").long()].contiguous()
+            H.set_gravity(acc)
+        if args.entropy:
+            st["A"] = torch.zeros(n, dtype=torch.float64, device="cuda")
+            H.set_entropy(st["A"])
+    elif restart:
+        st["h"].copy_(tmp["h"])
     del tmp
 
     tuning = None if args.no_autotune else H.autotune(st)
@@ -574,25 +654,31 @@ def main():
     e2e_pairs = 0
     e2e_steps = min(args.steps, 3) if big else args.steps
     st2 = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
+    phase_ms = [0.0, 0.0, 0.0]   # H2D, step, D2H
     for k in range(1 + e2e_steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         flush.zero_()
-        e0.record(stream)
+        ev[0].record(stream)
         for kk in KEYS:
             st2[kk].copy_(host[kk], non_blocking=True)
+        ev[1].record(stream)
         s2 = H.step(st2, -1.0, check=False)
         assert s2["status"] in ok_status, s2
+        ev[2].record(stream)
         for kk in KEYS + ("omega",):
             host_out[kk].copy_(st2[kk], non_blocking=True)
-        e1.record(stream)
+        ev[3].record(stream)
         torch.cuda.synchronize()
         if k >= 1:
-            e2e_ms += e0.elapsed_time(e1)
+            e2e_ms += ev[0].elapsed_time(ev[3])
+            for q in range(3):
+                phase_ms[q] += ev[q].elapsed_time(ev[q + 1])
             e2e_pairs += s2["grad_pairs"] + s2["flux_pairs"]
     e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT, "steps": e2e_steps,
            "timed": "H2D copies of the inputs + hydro_step + D2H copies of the state",
-           "h2d_bytes_per_step": 8 * n * len(KEYS), "d2h_bytes_per_step": 8 * n * (len(KEYS) + 1)}
+           "h2d_bytes_per_step": 8 * n * len(KEYS), "d2h_bytes_per_step": 8 * n * (len(KEYS) + 1),
+           "ms_per_step": {"h2d": phase_ms[0] / e2e_steps, "step": phase_ms[1] / e2e_steps,
+                           "d2h": phase_ms[2] / e2e_steps}}
     del host, host_out, st2
 
     # ---- the mixed step once more from the initial state, dt fixed (outside
@@ -691,6 +777,12 @@ def main():
             "peak_note": "measured by hydro_probe_peak (burst, this GPU)", "components": comp,
             "fp64_peak_tflops": peaks["fp64"]}
 
+    # ---- the other configurations at their full sizes (default workload only)
+    others = None
+    if (world == 1 and not args.no_others and args.workload == "lognormal" and n == DEFAULT_N["lognormal"]
+            and args.precision == "mixed"):
+        others = other_workloads(hydro, flush, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu, _ = oracle_sample_rate(args.workload, args.cpu_n, args.cpu_reps)
@@ -713,6 +805,9 @@ def main():
                    "tuning": tuning,
                    "kernel": "wendland_c2", "n_ngb": 32,
                    "l2": "flushed before every timed step (256 MB write)",
+                   "particle_order": ("the library's Morton order, kept by sorted_output = 1 "
+                                      "(the generator's order applied the step's permutation "
+                                      "once, before timing)") if sorted_out else "the generator's",
                    "pairs_per_step": r["pairs"] / args.steps,
                    "grad_pairs": last["grad_pairs"], "flux_pairs": last["flux_pairs"],
                    "newton_iters_per_face": iters / max(faces, 1),
@@ -721,7 +816,7 @@ def main():
                    "setup_s": setup_s},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": r["launches"],
         "clocks": clocks, "plain_fp64": fp64, "mixed_plain_guess": plain_guess,
-        "error_vs_fp64": err64, "conservation": conservation,
+        "error_vs_fp64": err64, "conservation": conservation, "other_workloads": others,
         "stage_ms": {k: last[k] for k in ("ms_neighbours", "ms_density", "ms_gradients",
                                           "ms_fluxes", "ms_flux_kernel", "ms_hard_faces",
                                           "ms_update")},

@@ -119,6 +119,21 @@ typedef struct {
                             double precision before they are rounded to float
                             for the flux; 0 (default): the float iteration
                             alone (its root is within a few float ulps) */
+    int sorted_output;   /* hydro_step: 1 writes the particles back in the
+                            step's own (Morton) order instead of the caller's:
+                            after the step, index i of every array of
+                            hydro_particles (and the entropy array of
+                            hydro_set_entropy) holds the particle that was at
+                            index perm[i] of the input, perm from hydro_get_order.
+                            A state kept in that order is read and written
+                            by the next step with coalesced accesses (the
+                            caller's order is otherwise unrelated to the
+                            sort, and the gathers and the write-back scatter).
+                            The gravity array of hydro_set_gravity is input
+                            only: the caller reorders it.  hydro_step_rungs
+                            returns HYDRO_ESTATE while it is set.  A step
+                            that returns an error leaves the arrays in their
+                            input order.  0 (default): caller order. */
 } hydro_config;
 
 /* Caller-owned particle state, caller order, all device pointers, n each.
@@ -483,10 +498,13 @@ int hydro_set_entropy(hydro_ctx *ctx, double *A);
  *     drawn by persistent warps from a global cursor (1, the default: a
  *     warp done with a light bucket takes the next at once), timed over
  *     the same stage with the chosen bound (mixed precision only);
- *   grad_rank: the gradient kernel's 128 particles of a CTA taken in
- *     their order (0) or ranked by list length (1, the default: the lanes
- *     of a warp walk lists of similar length), timed over the gradient
- *     stage with the chosen bound.
+ *   grad_rank: the gradient kernel's particles taken in their order (0),
+ *     or ranked by list length within tiles of 128 consecutive particles
+ *     (1, the default: the lanes of a warp walk lists of similar length),
+ *     or within tiles of 128 R (2: R = 8, or fewer while that leaves fewer
+ *     than 8 CTAs per SM; the lengths even out further), timed over the
+ *     gradient stage with the chosen bound; the full density solve ranks
+ *     tiles of 128 when grad_rank is 1 or 2.
  * The times (ms, best of two) are returned beside the choices. */
 typedef struct {
     double search_margin;
@@ -499,7 +517,7 @@ typedef struct {
     int flux_queue;
     float flux_queue_ms[2];   /* [by index, drawn]; 0 in FP64 */
     int grad_rank;
-    float grad_rank_ms[2];    /* [in order, ranked] */
+    float grad_rank_ms[3];    /* [in order, tiles of 128, larger tiles] */
 } hydro_tuning;
 
 /* Time the candidates above on the particles p (device, caller order; state
@@ -512,10 +530,18 @@ int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_
 
 /* Apply choices saved from an earlier hydro_autotune (search_margin >= 1,
  * nbr_slots in [32, 256], grad_min_ctas in {1, 5, 6}, flux_min_ctas in
- * {4, 5, 6}, flux_queue and grad_rank in {0, 1}; the time fields are
+ * {4, 5, 6}, flux_queue in {0, 1}, grad_rank in {0, 1, 2}; the time fields are
  * ignored).
  * HYDRO_EINVAL otherwise. */
 int hydro_set_tuning(hydro_ctx *ctx, const hydro_tuning *t);
+
+/* The order of the last hydro_step (no counterpart in the paper: a property
+ * of the particle layout): perm[i] (device, n int32, caller-owned) receives
+ * the input index of the particle the step placed at sorted position i --
+ * with sorted_output, the index the particle had in the caller's arrays
+ * before the step.  Enqueued on `stream`.  HYDRO_EINVAL (NULL), HYDRO_ESTATE
+ * (no step taken yet). */
+int hydro_get_order(hydro_ctx *ctx, int32_t *perm, hydro_stream stream);
 
 /* Throughput of this GPU's arithmetic units, measured (no counterpart in the
  * paper: the denominators of the benchmark's roofline).  unit:

@@ -50,6 +50,7 @@ bool valid_config(const hydro_config *c) {
         return false;
     if (!(c->c_acc > 0.0) || c->max_rung < 0 || c->max_rung > 20) return false;
     if (c->riemann_polish != 0 && c->riemann_polish != 1) return false;
+    if (c->sorted_output != 0 && c->sorted_output != 1) return false;
     return true;
 }
 
@@ -164,7 +165,7 @@ int build_all(hydro_ctx *c, const hydro_particles *p, const double *h_in, const 
 // particles' radii grow and only their buckets get new lists (a full
 // rebuild when the overflow region is too small)
 int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &rebuilds,
-                cudaStream_t st) {
+                cudaStream_t st, bool guard = false) {
     API_CUDA(run_density(c, only_active, true, st));
     for (int round = 0;; round++) {
         int sf = 0;
@@ -175,7 +176,7 @@ int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &r
         rebuilds++;
         API_CUDA(grow_search_radius(c, st));
         int nq = 0;
-        API_CUDA(rebuild_active_lists(c, &nq, st));
+        API_CUDA(rebuild_active_lists(c, &nq, st, guard));
         API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
         const int fl = c->h_cnt->flags;
@@ -304,6 +305,7 @@ void hydro_config_default(hydro_config *c) {
     c->c_acc = 0.2;
     c->max_rung = 12;
     c->riemann_polish = 0;
+    c->sorted_output = 0;
 }
 
 int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
@@ -520,17 +522,19 @@ int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,
                hydro_stream stream) {
     if (stats) memset(stats, 0, sizeof(*stats));
     const int rc = step_impl(c, p, dt, stats, stream);
+    if (c && (rc == HYDRO_OK || rc == HYDRO_ENCOND)) c->have_order = true;
     // a step that stopped early reports its error in the statistics too
     if (stats && rc != HYDRO_OK && stats->status == HYDRO_OK) stats->status = rc;
     return rc;
 }
 
 // New lists for the particles of the guard round (their search radii grew
-// in guard_grow), built one particle per warp before the re-solve; the tree
-// takes the grown radii first (the reverse walk of the gradient pass reads
-// them); a full rebuild when the overflow region is too small.
-static int guard_lists(hydro_ctx *c, cudaStream_t st) {
-    API_CUDA(build_tree(c, st));
+// in guard_grow), built one particle per warp before the re-solve; a full
+// rebuild when the overflow region is too small.  first: the first round,
+// which builds the tree with the solved h and search radii (the later rounds
+// only raise its radius bounds for their particles).
+static int guard_lists(hydro_ctx *c, bool first, cudaStream_t st) {
+    if (first) API_CUDA(build_tree(c, st));
     API_CUDA(guard_particle_lists(c, st));
     API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaStreamSynchronize(st));
@@ -588,7 +592,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
     if (!c || !c->have_plan) return HYDRO_EINVAL;
     if (!valid_particles(c, p, true) || !rung || !(dt0 > 0.0) || !isfinite(dt0))
         return HYDRO_EINVAL;
-    if (c->grav || c->cfg.entropy_switch) return HYDRO_ESTATE;
+    if (c->grav || c->cfg.entropy_switch || c->cfg.sorted_output) return HYDRO_ESTATE;
     const int64_t n = p->n;
     if (int rc0 = check_inputs(c, p, st)) return rc0;
     API_CUDA(ensure_state(c, n));
@@ -637,7 +641,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
         int rebuilds = 0, rounds = 0, ncond_fail = 0;
         bool first = true;
         for (;;) {
-            rc = density_all(c, p, !first || k > 0, rebuilds, st);
+            rc = density_all(c, p, !first || k > 0, rebuilds, st, !first);
             if (rc) return rc;
             API_CUDA(run_primitives(c, st, !first));
             API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
@@ -647,7 +651,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
             first = false;
             if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
             API_CUDA(guard_grow(c, st));
-            rc = guard_lists(c, st);
+            rc = guard_lists(c, rounds == 0, st);
             if (rc) return rc;
             rounds++;
         }
@@ -763,7 +767,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
     int rebuilds = 0, rounds = 0, ncond_fail = 0;
     bool first = true;
     for (;;) {
-        rc = density_all(c, p, !first, rebuilds, st);
+        rc = density_all(c, p, !first, rebuilds, st, !first);
         if (rc) return rc;
         if (first && timing) API_CUDA(record_event(c->ev[2], st));
         // a guard round recomputes the primitives of its re-solved particles
@@ -776,7 +780,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
         first = false;
         if (ncond_fail == 0 || rounds >= c->cfg.max_ngb_grow) break;
         API_CUDA(guard_grow(c, st));
-        rc = guard_lists(c, st);
+        rc = guard_lists(c, rounds == 0, st);
         if (rc) return rc;
         rounds++;
     }
@@ -816,6 +820,14 @@ int hydro_sync_status(hydro_ctx *c, hydro_stream stream) {
     API_CUDA(cudaStreamSynchronize(st));
     API_CUDA(cudaMemsetAsync(&c->d_cnt->flags, 0, sizeof(int), st));
     return flags_to_status(f);
+}
+
+int hydro_get_order(hydro_ctx *c, int32_t *perm, hydro_stream stream) {
+    if (!c || !perm) return HYDRO_EINVAL;
+    if (!c->have_order) return HYDRO_ESTATE;
+    API_CUDA(cudaMemcpyAsync(perm, c->d_perm.get(), (size_t)c->plan.n * sizeof(int32_t),
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return HYDRO_OK;
 }
 
 int hydro_get_stats(hydro_ctx *c, hydro_stats *stats, hydro_stream stream) {
@@ -1025,7 +1037,7 @@ int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (t->grad_min_ctas != 1 && t->grad_min_ctas != 5 && t->grad_min_ctas != 6) return HYDRO_EINVAL;
     if (t->flux_min_ctas < 4 || t->flux_min_ctas > 6) return HYDRO_EINVAL;
     if (t->flux_queue != 0 && t->flux_queue != 1) return HYDRO_EINVAL;
-    if (t->grad_rank != 0 && t->grad_rank != 1) return HYDRO_EINVAL;
+    if (t->grad_rank < 0 || t->grad_rank > 2) return HYDRO_EINVAL;
     c->cfg.search_margin = t->search_margin;
     c->flux_queue = t->flux_queue;
     c->grad_rank = t->grad_rank;
@@ -1103,9 +1115,10 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
         if (t < best) { best = t; bg = gminb[k]; }
     }
     c->grad_minb = bg;
-    // lanes in particle order or ranked by list length, with that bound
+    // lanes in particle order, ranked by list length in tiles of 128, or in
+    // tiles of up to 1024, with that bound
     best = 1e30f;
-    for (int r = 0; r < 2; r++) {
+    for (int r = 0; r < 3; r++) {
         c->grad_rank = r;
         float t = 1e30f;
         for (int rep = 0; rep < 2; rep++) {

@@ -25,6 +25,7 @@
 // order of the entries, so the members are summed in the same order as in
 // the full list.
 #include "hydro_internal.cuh"
+#include "tile_rank.cuh"
 
 namespace hyd {
 
@@ -50,7 +51,7 @@ struct DensArgs {
     double *h;                // sorted, in: guess, out: solution
     double *om;               // sorted out
     DevCounters *cnt;
-    bool rank;                // full solve: rank the CTA's particles by list length
+    bool rank;                // full solve: rank the CTA's 128 particles by list length
 };
 
 // Growth of the search radius hs after a failed solve.  First failure
@@ -221,32 +222,13 @@ __device__ __forceinline__ df from_i64(long long v) {
 
 // ---------------------------------------------------------------- mixed path
 constexpr int DENS_THREADS = 128;
-static_assert(DENS_THREADS == 128, "the ranking keys hold a 7-bit lane index");
+static_assert(DENS_THREADS == RANK_THREADS, "the ranked tiles take 128 threads a round");
 
-__global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
-                                const uint64_t *__restrict__ q64y,
-                                const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a.rank && !a.only_active) {
-        // the CTA's particles ranked by list length (as in the gradient
-        // kernel): the lanes of a warp walk lists of similar length
-        const int64_t base = blockIdx.x * (int64_t)blockDim.x;
-        __shared__ unsigned key[DENS_THREADS];
-        key[threadIdx.x] = ((s < a.n ? (unsigned)min(a.nbr_cnt[s], 0xFFFFFF) : 0u) << 7) |
-                           threadIdx.x;
-        __syncthreads();
-        for (int k = 2; k <= DENS_THREADS; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                const int t = threadIdx.x, u = t ^ j;
-                if (u > t) {
-                    const unsigned x = key[t], y = key[u];
-                    if ((x > y) == ((t & k) == 0)) { key[t] = y; key[u] = x; }
-                }
-                __syncthreads();
-            }
-        }
-        s = base + (key[threadIdx.x] & 127u);
-    }
+// one particle's float Newton solve, then the double-float refinement
+__device__ __forceinline__ void dens_one(const DensArgs &a, const uint64_t *__restrict__ q64x,
+                                         const uint64_t *__restrict__ q64y,
+                                         const uint64_t *__restrict__ q64z,
+                                         float *__restrict__ rec, int64_t s) {
     if (s >= a.n) return;
     if (a.only_active && !(a.active[s] & 1)) return;
     const Box bx = a.boxes[a.pbox[s]];
@@ -408,6 +390,24 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
     rr[R_OM] = (float)om;
 }
 
+// one thread per particle, in the sorted order (a partial solve too: its
+// particles are often many and clustered, and a compacted list would scatter
+// each warp's gathers over the box); the full solve ranks the CTA's 128
+// particles by list length.  (Larger ranked tiles spread the repeated
+// gathers of the Newton iterations over more of the Morton curve: slower.)
+__global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
+                                const uint64_t *__restrict__ q64y,
+                                const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a.rank) {
+        __shared__ unsigned rank_key[RANK_THREADS];
+        const int64_t base = blockIdx.x * (int64_t)RANK_THREADS;
+        rank_tile(rank_key, 1, a.nbr_cnt, base, a.n);
+        s = base + rank_index(rank_key[threadIdx.x], 1);
+    }
+    dens_one(a, q64x, q64y, q64z, rec, s);
+}
+
 // the search radius of particles whose root lay beyond it, as the density
 // kernel grew it (not below margin h); never beyond half the shortest box
 // side (one periodic image)
@@ -467,7 +467,8 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
     a.h = c->d_hsorted.get();
     a.om = c->d_omsorted.get();
     a.cnt = c->d_cnt;
-    a.rank = c->grad_rank != 0;   // (the gradient kernel's choice: the same divergence)
+    // ranked when the gradient kernel ranks (the same divergence)
+    a.rank = c->grad_rank && !only_active;
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_fail, 0, sizeof(int), st));
     if (c->cfg.precision == HYDRO_MIXED) {
         // 64-bit fixed-point copies for the refinement step (xs.. are sorted)
@@ -482,9 +483,8 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
                                                          c->d_boxes.get(), q64, q64 + n, q64 + 2 * n);
             HYD_CUDA(launch_check());
         }
-        k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(a, q64, q64 + n,
-                                                                         q64 + 2 * n,
-                                                                         c->d_recf.get());
+        k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(
+            a, q64, q64 + n, q64 + 2 * n, c->d_recf.get());
     } else {
         k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
     }

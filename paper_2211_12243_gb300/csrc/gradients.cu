@@ -13,6 +13,7 @@
 // record array (the first 40 B of the line in float).
 #include "hydro_internal.cuh"
 #include "pairgeom.cuh"
+#include "tile_rank.cuh"
 
 namespace hyd {
 
@@ -38,8 +39,10 @@ struct GradArgs {
     DevCounters *cnt;
     const uint8_t *ract;                 // individual timesteps: only these (NULL: all)
     const int32_t *list;                 // only these particles (NULL: all n) ...
-    const int *nlist;                    // ... their count (device)
-    bool rank;                           // dense pass: rank the CTA's particles by list length
+    const int *nlist;                    // ... their count (device) ...
+    int *cursor;                         // ... taken by the warps 32 at a time
+    int rank_rounds;                     // dense pass: rank tiles of 128 x this many particles
+                                         // by list length (0: no ranking)
 };
 
 template <typename R>
@@ -265,58 +268,46 @@ __device__ __forceinline__ void grad_one(const GradArgs &a, R *__restrict__ rec,
 
 // one thread per particle: every particle (list NULL), or the *nlist
 // particles of list (a guard round's recomputed particles; the count is
-// read on the device, the threads stride over it)
+// read on the device, the warps take them 32 at a time)
 template <typename R, int MINB, bool LEAN = false>
 __global__ void __launch_bounds__(128, MINB) k_gradients(GradArgs a, R *__restrict__ rec) {
     if (a.list) {
-        const int64_t nl = *a.nlist;
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
-             t += (int64_t)gridDim.x * blockDim.x)
-            grad_one<R, LEAN>(a, rec, a.list[t]);
-        return;
-    }
-    // the CTA's 128 consecutive particles, ranked by list length so that the
-    // lanes of a warp walk lists of similar length (one thread per particle:
-    // a warp runs until its longest list is done); the ranking stays inside
-    // the CTA, which keeps the Morton locality of the gathers
-    const int64_t base = blockIdx.x * (int64_t)blockDim.x;
-    const int64_t s0 = base + threadIdx.x;
-    if (!a.rank) {
-        grad_one<R, LEAN>(a, rec, s0);
-        return;
-    }
-    __shared__ unsigned key[128];
-    key[threadIdx.x] = ((s0 < a.n ? (unsigned)min(a.nbr_cnt[s0], 0xFFFFFF) : 0u) << 7) |
-                       threadIdx.x;
-    __syncthreads();
-    // bitonic sort of the 128 keys (ascending)
-    for (int k = 2; k <= 128; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int t = threadIdx.x, u = t ^ j;
-            if (u > t) {
-                const unsigned x = key[t], y = key[u];
-                const bool up = (t & k) == 0;
-                if ((x > y) == up) { key[t] = y; key[u] = x; }
-            }
-            __syncthreads();
+        const int nl = *a.nlist;
+        for (int base = warp_chunk(a.cursor); base < nl; base = warp_chunk(a.cursor)) {
+            const int t = base + (threadIdx.x & 31);
+            if (t < nl) grad_one<R, LEAN>(a, rec, a.list[t]);
         }
+        return;
     }
-    grad_one<R, LEAN>(a, rec, base + (key[threadIdx.x] & 127u));
+    // tiles of 128 R consecutive particles ranked by list length (R rounds
+    // of 128 threads; one thread per particle, so a warp runs until its
+    // longest list is done), or the CTA's 128 in their order
+    const int rounds = a.rank_rounds > 0 ? a.rank_rounds : 1;
+    const int64_t tile = blockIdx.x * (int64_t)RANK_THREADS * rounds;
+    extern __shared__ unsigned rank_key[];
+    if (a.rank_rounds) rank_tile(rank_key, rounds, a.nbr_cnt, tile, a.n);
+    for (int r = 0; r < rounds; r++) {
+        const int t = r * RANK_THREADS + threadIdx.x;
+        grad_one<R, LEAN>(a, rec, tile + (a.rank_rounds ? rank_index(rank_key[t], rounds) : t));
+    }
 }
 
 // the particles with one of `bits` set, appended to idx (count in *nidx;
-// the order of the warps' appends is not fixed)
+// the order of the warps' appends is not fixed); warps stride over the
+// particles 32 at a time
 __global__ void k_compact_flags(int64_t n, const uint8_t *__restrict__ active, uint8_t bits,
                                 int32_t *__restrict__ idx, int *__restrict__ nidx) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const bool on = s < n && (active[s] & bits);
-    const unsigned m = __ballot_sync(0xffffffffu, on);
-    if (!m) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(nidx, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (on) idx[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s - lane < n; s += stride) {
+        const bool on = s < n && (active[s] & bits);
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(nidx, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (on) idx[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)s;
+    }
 }
 
 // global CFL dt (minimum of the per-particle values, Eq. 31) and the count
@@ -366,66 +357,69 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
                              double gm1, double alpha1, const uint8_t *__restrict__ active,
                              bool only_guard, const double *__restrict__ agrav, EntArgs ent,
                              const uint8_t *__restrict__ ract, R *__restrict__ rec) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    if (only_guard && !(active[s] & ACT_GUARD)) return;
-    if (ract && !ract[s]) return;   // (individual timesteps: its record is kept)
-    double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
-    double E = Q[4 * n + s], U = Q[5 * n + s];
-    double w = om[s];
-    // E_grav = m |a| h enters the total-energy switch (§2.3.7)
-    double egrav = 0.0;
-    if (agrav) {
-        const double ax = agrav[s], ay = agrav[n + s], az = agrav[2 * n + s];
-        egrav = m * sqrt(ax * ax + ay * ay + az * az) * h[s];
-    }
-    R *r = rec + s * REC;
-    // the pressure route of §2.3.7: 0 total energy, 2 internal energy; the
-    // entropy route (1) is taken over by k_entropy_route, which needs the
-    // neighbours' velocities this kernel writes
-    auto route = [&](double ekin) -> int {
-        if (U > alpha1 * (egrav + ekin) && E - ekin > 0.0) return 0;
-        return 2;
-    };
-    double pd = 0.0;   // the pressure in double (entropy switch only)
-    int from;
-    if (sizeof(R) == 8) {
-        double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
-        from = route(ekin);
-        const double therm = from == 0 ? E - ekin : U;
-        const double rho = m / w;
-        pd = therm * gm1 / w;
-        r[R_H] = (R)h[s];
-        r[R_RHO] = (R)rho;
-        r[R_VX] = (R)(px / m);
-        r[R_VY] = (R)(py / m);
-        r[R_VZ] = (R)(pz / m);
-        r[R_P] = (R)pd;
-        r[R_OM] = (R)w;
-    } else {
-        // float record: only E - E_kin needs double (cancellation)
-        double im = 1.0 / m;
-        double ekin = 0.5 * (px * px + py * py + pz * pz) * im;
-        from = route(ekin);
-        const double therm = from == 0 ? E - ekin : U;
-        float wf = (float)w, imf = (float)im;
-        r[R_H] = (R)h[s];
-        r[R_RHO] = (R)((float)m / wf);
-        r[R_VX] = (R)((float)px * imf);
-        r[R_VY] = (R)((float)py * imf);
-        r[R_VZ] = (R)((float)pz * imf);
-        r[R_OM] = (R)wf;
-        r[R_P] = (R)((float)therm * (float)gm1 / wf);
-        if (ent.A1) pd = therm * gm1 / w;
-    }
-    if (ent.A1) {
-        // A follows the pressure the energies gave (k_entropy_route keeps A
-        // where it takes the entropy route instead)
-        const double A = pd / pow(m / w, ent.gamma);
-        ent.A1[s] = A;
-        r[R_PAD] = (R)A;
-        ent.cand[s] = from != 0;
-    }
+    // (a grid-stride loop: a guard round's pass, which touches few
+    // particles, runs on a small grid instead of one thread per particle)
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) [&] {
+        if (only_guard && !(active[s] & ACT_GUARD)) return;
+        if (ract && !ract[s]) return;   // (individual timesteps: its record is kept)
+        double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
+        double E = Q[4 * n + s], U = Q[5 * n + s];
+        double w = om[s];
+        // E_grav = m |a| h enters the total-energy switch (§2.3.7)
+        double egrav = 0.0;
+        if (agrav) {
+            const double ax = agrav[s], ay = agrav[n + s], az = agrav[2 * n + s];
+            egrav = m * sqrt(ax * ax + ay * ay + az * az) * h[s];
+        }
+        R *r = rec + s * REC;
+        // the pressure route of §2.3.7: 0 total energy, 2 internal energy; the
+        // entropy route (1) is taken over by k_entropy_route, which needs the
+        // neighbours' velocities this kernel writes
+        auto route = [&](double ekin) -> int {
+            if (U > alpha1 * (egrav + ekin) && E - ekin > 0.0) return 0;
+            return 2;
+        };
+        double pd = 0.0;   // the pressure in double (entropy switch only)
+        int from;
+        if (sizeof(R) == 8) {
+            double ekin = (px * px + py * py + pz * pz) / (2.0 * m);
+            from = route(ekin);
+            const double therm = from == 0 ? E - ekin : U;
+            const double rho = m / w;
+            pd = therm * gm1 / w;
+            r[R_H] = (R)h[s];
+            r[R_RHO] = (R)rho;
+            r[R_VX] = (R)(px / m);
+            r[R_VY] = (R)(py / m);
+            r[R_VZ] = (R)(pz / m);
+            r[R_P] = (R)pd;
+            r[R_OM] = (R)w;
+        } else {
+            // float record: only E - E_kin needs double (cancellation)
+            double im = 1.0 / m;
+            double ekin = 0.5 * (px * px + py * py + pz * pz) * im;
+            from = route(ekin);
+            const double therm = from == 0 ? E - ekin : U;
+            float wf = (float)w, imf = (float)im;
+            r[R_H] = (R)h[s];
+            r[R_RHO] = (R)((float)m / wf);
+            r[R_VX] = (R)((float)px * imf);
+            r[R_VY] = (R)((float)py * imf);
+            r[R_VZ] = (R)((float)pz * imf);
+            r[R_OM] = (R)wf;
+            r[R_P] = (R)((float)therm * (float)gm1 / wf);
+            if (ent.A1) pd = therm * gm1 / w;
+        }
+        if (ent.A1) {
+            // A follows the pressure the energies gave (k_entropy_route keeps A
+            // where it takes the entropy route instead)
+            const double A = pd / pow(m / w, ent.gamma);
+            ent.A1[s] = A;
+            r[R_PAD] = (R)A;
+            ent.cand[s] = from != 0;
+        }
+    }();
 }
 
 // The entropy route of §2.3.7 for the particles the energies did not
@@ -531,6 +525,14 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
+cudaError_t compact_flags(int64_t n, const uint8_t *active, uint8_t bits, int32_t *idx, int *nidx,
+                          stream_t st) {
+    HYD_CUDA(cudaMemsetAsync(nidx, 0, sizeof(int), st));
+    k_compact_flags<<<std::min(grid_for(n, 256), SWEEP_GRID), 256, 0, st>>>(n, active, bits, idx,
+                                                                           nidx);
+    return launch_check();
+}
+
 cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
     const int64_t n = c->plan.n;
     double gm1 = c->cfg.gamma - 1.0;
@@ -547,13 +549,14 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
         ent.alpha2 = c->cfg.alpha2;
         ent.alpha3 = c->cfg.alpha3;
     }
+    const unsigned pgrid = only_guard ? std::min(grid_for(n, 256), SWEEP_GRID) : grid_for(n, 256);
     if (mixed)
-        k_primitives<float><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
+        k_primitives<float><<<pgrid, 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                               c->d_hsorted.get(), gm1,
                                                               c->cfg.alpha1, act, only_guard, ag,
                                                               ent, ract, c->d_recf.get());
     else
-        k_primitives<double><<<grid_for(n, 256), 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
+        k_primitives<double><<<pgrid, 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
                                                                c->cfg.alpha1, act, only_guard, ag,
                                                                ent, ract, c->d_recd.get());
@@ -626,20 +629,27 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     a.ract = c->rung_live ? c->d_ract.get() : nullptr;
     a.list = nullptr;
     a.nlist = nullptr;
-    a.rank = c->grad_rank != 0;
-    unsigned grid = grid_for(n, 128);
+    a.cursor = nullptr;
+    a.rank_rounds = c->grad_rank == 2 ? rank_rounds(n) : c->grad_rank;
+    unsigned grid = a.rank_rounds ? grid_for(n, RANK_THREADS * a.rank_rounds) : grid_for(n, 128);
+    size_t smem = a.rank_rounds ? sizeof(unsigned) * RANK_THREADS * a.rank_rounds : 0;
     if (only_redo) {
         // the particles whose lists hold a re-solved one, compacted: a
         // guard round recomputes few particles, spread over the whole set
+        // (the re-solved particles' radii into the tree first: the next
+        // round's reverse walk bounds by them)
+        HYD_CUDA(raise_tree(c, st));
         HYD_CUDA(mark_reverse(c, st, true));
         HYD_CUDA(c->d_redo_idx.ensure(n));
-        HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nredo, 0, sizeof(int), st));
-        k_compact_flags<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), ACT_REDO,
-                                                           c->d_redo_idx.get(), &c->d_cnt->nredo);
-        HYD_CUDA(launch_check());
+        HYD_CUDA(compact_flags(n, c->d_active.get(), ACT_REDO, c->d_redo_idx.get(),
+                               &c->d_cnt->nredo, st));
+        HYD_CUDA(cudaMemsetAsync(&c->d_cnt->redo_cursor, 0, sizeof(int), st));
         a.list = c->d_redo_idx.get();
         a.nlist = &c->d_cnt->nredo;
+        a.cursor = &c->d_cnt->redo_cursor;
+        a.rank_rounds = 0;
         grid = 152 * 8;
+        smem = 0;
     }
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
@@ -648,24 +658,24 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     if (c->cfg.precision == HYDRO_MIXED) {
         float *r = c->d_recf.get();
         if (lean) {
-            if (c->grad_minb == 5) k_gradients<float, 5, true><<<grid, 128, 0, st>>>(a, r);
-            else if (c->grad_minb == 6) k_gradients<float, 6, true><<<grid, 128, 0, st>>>(a, r);
-            else k_gradients<float, 1, true><<<grid, 128, 0, st>>>(a, r);
+            if (c->grad_minb == 5) k_gradients<float, 5, true><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<float, 6, true><<<grid, 128, smem, st>>>(a, r);
+            else k_gradients<float, 1, true><<<grid, 128, smem, st>>>(a, r);
         } else {
-            if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, 0, st>>>(a, r);
-            else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, 0, st>>>(a, r);
-            else k_gradients<float, 1><<<grid, 128, 0, st>>>(a, r);
+            if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, smem, st>>>(a, r);
+            else k_gradients<float, 1><<<grid, 128, smem, st>>>(a, r);
         }
     } else {
         double *r = c->d_recd.get();
         if (lean) {
-            if (c->grad_minb == 5) k_gradients<double, 5, true><<<grid, 128, 0, st>>>(a, r);
-            else if (c->grad_minb == 6) k_gradients<double, 6, true><<<grid, 128, 0, st>>>(a, r);
-            else k_gradients<double, 1, true><<<grid, 128, 0, st>>>(a, r);
+            if (c->grad_minb == 5) k_gradients<double, 5, true><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<double, 6, true><<<grid, 128, smem, st>>>(a, r);
+            else k_gradients<double, 1, true><<<grid, 128, smem, st>>>(a, r);
         } else {
-            if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, 0, st>>>(a, r);
-            else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, 0, st>>>(a, r);
-            else k_gradients<double, 1><<<grid, 128, 0, st>>>(a, r);
+            if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, smem, st>>>(a, r);
+            else k_gradients<double, 1><<<grid, 128, smem, st>>>(a, r);
         }
     }
     HYD_CUDA(launch_check());

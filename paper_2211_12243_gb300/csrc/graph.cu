@@ -101,10 +101,10 @@ cudaError_t cond_search(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle
 
 // one re-search round: radii of the failed particles grow, their buckets get
 // new lists, their density is solved again
-cudaError_t search_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
+cudaError_t search_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, bool guard) {
     const long long k0 = launch_count();
     HYD_CUDA(grow_search_radius(c, s));
-    HYD_CUDA(rebuild_active_lists_dev(c, s));
+    HYD_CUDA(rebuild_active_lists_dev(c, s, guard));
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(cond_search(c, s, h));
     c->cap_k_search = launch_count() - k0;
@@ -115,7 +115,7 @@ cudaError_t search_loop(hydro_ctx *c, int level, cudaStream_t st) {
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_round, 0, sizeof(int), st));
     return capture_while(
         c, level, st, [&](cudaStream_t s, cudaGraphConditionalHandle h) { return cond_search(c, s, h); },
-        [&](cudaStream_t s, cudaGraphConditionalHandle h) { return search_body(c, s, h); });
+        [&](cudaStream_t s, cudaGraphConditionalHandle h) { return search_body(c, s, h, level == 2); });
 }
 
 cudaError_t cond_guard(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
@@ -127,8 +127,7 @@ cudaError_t cond_guard(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
 cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const long long k0 = launch_count();
     HYD_CUDA(guard_grow(c, s));
-    HYD_CUDA(build_tree(c, s));                 // the grown search radii
-    HYD_CUDA(guard_particle_lists(c, s));
+    HYD_CUDA(guard_particle_lists(c, s));       // (the tree's radius bounds are not used)
     HYD_CUDA(run_density(c, true, true, s));
     HYD_CUDA(search_loop(c, 2, s));
     HYD_CUDA(run_primitives(c, s, true));
@@ -158,6 +157,9 @@ cudaError_t enqueue_step(hydro_ctx *c, hydro_particles *p, double dt, bool sums,
     if (timing) HYD_CUDA(record_event(c->ev[2], st));
     HYD_CUDA(run_primitives(c, st));
     HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, false, st));
+    // the tree with the solved h and search radii: the guard rounds only
+    // raise its radius bounds for their particles
+    HYD_CUDA(build_tree(c, st));
     HYD_CUDA(capture_while(
         c, 1, st, [&](cudaStream_t s, cudaGraphConditionalHandle h) { return cond_guard(c, s, h); },
         [&](cudaStream_t s, cudaGraphConditionalHandle h) { return guard_body(c, s, h); }));

@@ -19,6 +19,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "hydro.h"
@@ -99,6 +100,7 @@ struct DevCounters {
     unsigned long long rung_active;   // particles starting a step in this sub-step
     int bad_input;                    // a non-finite value in the caller's state
     int nredo;                        // particles a guard round recomputes the gradients of
+    int redo_cursor;                  // the guard round's gradient warps' place in theirs
     unsigned long long flux_cursor;   // the flux kernel's bucket queue
 };
 
@@ -266,6 +268,7 @@ struct hydro_ctx {
     int pending_status = 0;
 
     hydro_stats last_stats;
+    bool have_order = false;          // d_perm holds the order of a completed step
     cudaEvent_t ev[10];               // 0-5 stage boundaries, 6-8 around the flux kernels,
                                       // 9 after the learned-path counters' readback
     bool have_events = false;
@@ -334,16 +337,21 @@ cudaError_t gather_from_caller(const int32_t *perm, const double *src, int64_t n
 
 // neighbours.cu
 cudaError_t build_tree(hydro_ctx *c, stream_t st);
+cudaError_t raise_tree(hydro_ctx *c, stream_t st);
 cudaError_t build_lists(hydro_ctx *c, int cap, stream_t st);
 cudaError_t build_lists_queued(hydro_ctx *c, int nq, stream_t st);
-cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st);
+cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st, bool guard = false);
 // ACT_REDO on the guard round's particles and on every particle i with one
 // of them in its list (r_ia < h_i), found by walks of the bucket tree
 cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h = false);
+// gradients.cu: the particles with one of `bits` set in active, appended to
+// idx (count in *nidx, reset first; their order is not fixed)
+cudaError_t compact_flags(int64_t n, const uint8_t *active, uint8_t bits, int32_t *idx, int *nidx,
+                          stream_t st);
 // the same two passes with the bucket count read on the device (no host
 // wait): the queued overflow buckets, and the re-search rebuild
 cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);
-cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st);
+cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st, bool guard = false);
 cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
@@ -426,6 +434,22 @@ cudaError_t mlp_normalise(hydro_ctx *c, const float *x, const float *t, int64_t 
 cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double *dt_dev,
                        bool abort_check, int skip_flags, stream_t st);
 // status bits after which hydro_step leaves the caller's state as it was
+// A warp's next chunk of a device-sized list: 32 entries taken from a
+// global cursor (reset by the launcher), so the warps of a persistent grid
+// share the list as they come free -- the entries' costs vary (list lengths,
+// Newton iterations) and a fixed share per thread would leave the grid
+// waiting on its slowest threads.  Returns the chunk's first entry (>= nl:
+// the list is done); every lane of the warp calls it.
+__device__ __forceinline__ int warp_chunk(int *cursor) {
+    int base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, 32);
+    return __shfl_sync(0xffffffffu, base, 0);
+}
+
+// grid of the sweeps that touch few of the particles (the re-solves and
+// re-searches of a guard round): 16 CTAs per SM of the 152, the threads
+// striding over the particles, instead of a CTA per 128-256 particles
+constexpr unsigned SWEEP_GRID = 152 * 16;
 constexpr int STEP_SKIP_FLAGS = ST_NOCONV_H | ST_MLP;
 // *p = v on the stream (a kernel: no host memory is referenced, so the call
 // can be captured into a graph)

@@ -90,6 +90,32 @@ __global__ void k_aabb_node(int64_t node0, int64_t nnode, const int32_t *__restr
     }
 }
 
+// Raise the bounds of the buckets holding the particles idx[0 .. *nidx):
+// lo.w to at least their search radius hs, hi.w to at least their h.  In a
+// guard round only those particles' radii move, so the tree built before
+// the rounds stays exact in its boxes and an upper bound in .w (a bound
+// that stays above a radius that shrank only prunes less); the node levels
+// are then recomputed from the buckets.  Positive floats order like their
+// bit patterns, so the maximum is an integer atomic.  A particle's bucket is
+// the last one whose first particle is at or before it (buckets are
+// consecutive and non-empty).
+__global__ void k_aabb_raise(const int32_t *__restrict__ idx, const int *__restrict__ nidx,
+                             const int32_t *__restrict__ first, int64_t nbucket,
+                             const double *__restrict__ hs, const double *__restrict__ hh,
+                             uint4 *__restrict__ lo, uint4 *__restrict__ hi) {
+    const int ni = *nidx;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ni; t += gridDim.x * blockDim.x) {
+        const int s = idx[t];
+        int64_t a = 0, b = nbucket - 1;
+        while (a < b) {
+            const int64_t m = (a + b + 1) >> 1;
+            if (first[m] <= s) a = m; else b = m - 1;
+        }
+        atomicMax(&lo[a].w, __float_as_uint(__double2float_ru(hs[s])));
+        atomicMax(&hi[a].w, __float_as_uint(__double2float_ru(hh[s])));
+    }
+}
+
 // Lower bound of the periodic distance (fixed-point units) between the
 // intervals [a0,a1] and [b0,b1] on the circle of 2^32 units: the circular
 // distance of the centres minus both half-widths (rounded up), in 32-bit
@@ -633,12 +659,14 @@ __global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ firs
                                const int32_t *__restrict__ cnt, const uint8_t *__restrict__ active,
                                int32_t *__restrict__ queue, int *__restrict__ nqueue,
                                DevCounters *counters, uint8_t bits = 1) {
-    int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (bits == 1 && b == 0 && lane == 0) atomicAnd(&counters->flags, ~ST_SEARCH);
-    if (b >= nbucket) return;
-    bool act = lane < cnt[b] && (active[first[b] + lane] & bits);
-    if (__any_sync(0xffffffffu, act) && lane == 0) queue[atomicAdd(nqueue, 1)] = (int32_t)b;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (bits == 1 && w0 == 0 && lane == 0) atomicAnd(&counters->flags, ~ST_SEARCH);
+    // (warps stride over the buckets: a small grid covers every bucket)
+    for (int64_t b = w0; b < nbucket; b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        bool act = lane < cnt[b] && (active[first[b] + lane] & bits);
+        if (__any_sync(0xffffffffu, act) && lane == 0) queue[atomicAdd(nqueue, 1)] = (int32_t)b;
+    }
 }
 
 // The particles that hold a guard particle a in their list, i.e. r_ia < h_i
@@ -727,7 +755,9 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h) {
     const Plan &P = c->plan;
-    k_mark_reverse<<<152 * 4, RWARPS * 32, 0, st>>>(
+    // (a latency-bound walk per guard particle: as many resident warps as
+    // its 40 registers allow, 12 CTAs of 4 warps per SM)
+    k_mark_reverse<<<152 * 12, RWARPS * 32, 0, st>>>(
         c->d_guard_idx.get(), &c->d_cnt->nguard, c->d_node_first.get(), c->d_node_cnt.get(),
         c->d_box_root.get(), P.nbucket, c->d_node_aabb.get(), c->d_node_aabb_hi.get(),
         c->d_qx.get(), c->d_qy.get(), c->d_qz.get(), c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
@@ -742,6 +772,26 @@ cudaError_t build_tree(hydro_ctx *c, stream_t st) {
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_qx.get(), c->d_qy.get(),
         c->d_qz.get(), c->d_hs.get(), c->d_hsorted.get(), c->d_node_aabb.get(),
         c->d_node_aabb_hi.get());
+    HYD_CUDA(launch_check());
+    for (int l = 1; l < P.nlevels; l++) {
+        int64_t n0 = P.level_off[l], nn = P.level_off[l + 1] - P.level_off[l];
+        k_aabb_node<<<grid_for(nn * 32, 256), 256, 0, st>>>(n0, nn, c->d_node_first.get(),
+                                                            c->d_node_cnt.get(),
+                                                            c->d_node_aabb.get(),
+                                                            c->d_node_aabb_hi.get());
+        HYD_CUDA(launch_check());
+    }
+    return cudaSuccess;
+}
+
+// the tree's radius bounds raised for the guard round's particles
+// (guard_idx, count nguard on the device), the node levels recomputed
+cudaError_t raise_tree(hydro_ctx *c, stream_t st) {
+    const Plan &P = c->plan;
+    k_aabb_raise<<<152 * 4, 256, 0, st>>>(c->d_guard_idx.get(), &c->d_cnt->nguard,
+                                          c->d_node_first.get(), P.nbucket, c->d_hs.get(),
+                                          c->d_hsorted.get(), c->d_node_aabb.get(),
+                                          c->d_node_aabb_hi.get());
     HYD_CUDA(launch_check());
     for (int l = 1; l < P.nlevels; l++) {
         int64_t n0 = P.level_off[l], nn = P.level_off[l + 1] - P.level_off[l];
@@ -826,32 +876,34 @@ cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st) {
     return launch_lists(a, c->plan.nbucket, st);
 }
 
-cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st) {
+cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st, bool guard) {
     const Plan &P = c->plan;
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
-    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+    k_queue_active<<<std::min(grid_for(P.nbucket * 32, 256), SWEEP_GRID), 256, 0, st>>>(
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
         &c->d_cnt->ovf_buckets, c->d_cnt);
     HYD_CUDA(launch_check());
-    HYD_CUDA(build_tree(c, st));
+    // (in a guard round only the guard particles' radii grew)
+    HYD_CUDA(guard ? raise_tree(c, st) : build_tree(c, st));
     return build_lists_queued_dev(c, st);
 }
 
 // new lists (in the overflow region) for the buckets that hold a particle
 // whose search radius grew; every other list stays as it is.  *nq receives
 // the number of buckets rebuilt (the host waits for it).
-cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st) {
+cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st, bool guard) {
     const Plan &P = c->plan;
     HYD_CUDA(c->d_ovf.ensure(P.nbucket));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
-    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+    k_queue_active<<<std::min(grid_for(P.nbucket * 32, 256), SWEEP_GRID), 256, 0, st>>>(
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
         &c->d_cnt->ovf_buckets, c->d_cnt);
     HYD_CUDA(launch_check());
     HYD_CUDA(cudaMemcpyAsync(nq, &c->d_cnt->ovf_buckets, sizeof(int), cudaMemcpyDeviceToHost, st));
     HYD_CUDA(cudaStreamSynchronize(st));
     if (*nq == 0) return cudaSuccess;
-    HYD_CUDA(build_tree(c, st));   // the buckets' search radii changed
+    // the buckets' search radii changed (in a guard round: the guard particles')
+    HYD_CUDA(guard ? raise_tree(c, st) : build_tree(c, st));
     return build_lists_queued(c, *nq, st);
 }
 
@@ -892,7 +944,7 @@ cudaError_t queue_flagged(hydro_ctx *c, uint8_t bits, stream_t st) {
     const Plan &P = c->plan;
     HYD_CUDA(c->d_ovf.ensure(P.nbucket));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
-    k_queue_active<<<grid_for(P.nbucket * 32, 256), 256, 0, st>>>(
+    k_queue_active<<<std::min(grid_for(P.nbucket * 32, 256), SWEEP_GRID), 256, 0, st>>>(
         P.nbucket, c->d_node_first.get(), c->d_node_cnt.get(), c->d_active.get(), c->d_ovf.get(),
         &c->d_cnt->ovf_buckets, c->d_cnt, bits);
     return launch_check();

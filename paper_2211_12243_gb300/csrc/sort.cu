@@ -267,6 +267,7 @@ static int64_t scan_tmp_size(int64_t n) {
 
 cudaError_t sort_particles(hydro_ctx *c, const hydro_particles *p, stream_t st) {
     const int64_t n = p->n;
+    c->have_order = false;   // (hydro_step sets it once its step is done)
     HYD_CUDA(c->d_keys.ensure(n));
     HYD_CUDA(c->d_keys_alt.ensure(n));
     HYD_CUDA(c->d_perm.ensure(n));

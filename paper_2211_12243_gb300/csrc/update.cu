@@ -27,6 +27,7 @@ struct UpdArgs {
     DevCounters *cnt;
     bool abort_check;
     int skip_flags;        // status bits that leave the caller's state untouched
+    bool sorted_out;       // write the state back in the sorted order
     const double *agrav;   // sorted SoA 3 n (NULL: no gravity)
     const double *dM;      // sum_j dm_ij r_ij, sorted SoA 3 n
     // entropy switch (§2.3.7): the value of A the step used (sorted; NULL:
@@ -88,7 +89,7 @@ __global__ void k_update(UpdArgs a) {
         atomicOr(&a.cnt->flags, ST_NONFINITE);
     a.Q[s] = m1; a.Q[n + s] = px1; a.Q[2 * n + s] = py1; a.Q[3 * n + s] = pz1;
     a.Q[4 * n + s] = E1; a.Q[5 * n + s] = U1;
-    const int64_t o = a.perm[s];
+    const int64_t o = a.sorted_out ? s : a.perm[s];
     a.p.x[o] = x; a.p.y[o] = y; a.p.z[o] = z;
     a.p.mass[o] = m1; a.p.px[o] = px1; a.p.py[o] = py1; a.p.pz[o] = pz1;
     a.p.etot[o] = E1; a.p.eint[o] = U1;
@@ -204,6 +205,7 @@ cudaError_t run_update(hydro_ctx *c, hydro_particles *p, double dt, const double
     a.cnt = c->d_cnt;
     a.abort_check = abort_check;
     a.skip_flags = skip_flags;
+    a.sorted_out = c->cfg.sorted_output != 0 && !c->rung_live;
     a.agrav = c->grav_live ? c->d_agrav.get() : nullptr;
     a.dM = c->grav_live ? c->d_dM.get() : nullptr;
     a.A1 = c->ent_live ? c->d_A1.get() : nullptr;

@@ -48,6 +48,7 @@ class Config(C.Structure):
         ("max_newton", C.c_int), ("search_margin", C.c_double), ("graph", C.c_int),
         ("entropy_switch", C.c_int), ("alpha2", C.c_double), ("alpha3", C.c_double),
         ("c_acc", C.c_double), ("max_rung", C.c_int), ("riemann_polish", C.c_int),
+        ("sorted_output", C.c_int),
     ]
 
 
@@ -94,7 +95,7 @@ class Tuning(C.Structure):
         ("search_margin", C.c_double), ("nbr_slots", C.c_int), ("grad_min_ctas", C.c_int),
         ("flux_min_ctas", C.c_int), ("front_ms", (C.c_float * 3) * 4), ("grad_ms", C.c_float * 3),
         ("flux_ms", C.c_float * 3), ("flux_queue", C.c_int), ("flux_queue_ms", C.c_float * 2),
-        ("grad_rank", C.c_int), ("grad_rank_ms", C.c_float * 2),
+        ("grad_rank", C.c_int), ("grad_rank_ms", C.c_float * 3),
     ]
 
     def as_dict(self):
@@ -114,7 +115,7 @@ EXPORTS = ["hydro_config_default", "hydro_create", "hydro_destroy", "hydro_set_c
            "hydro_recorded_faces", "hydro_totals_noalloc", "hydro_kernel_launches",
            "hydro_strerror", "hydro_autotune", "hydro_set_tuning", "hydro_set_gravity",
            "hydro_set_entropy", "hydro_step_rungs", "hydro_test_mlp_stall",
-           "hydro_probe_peak"]
+           "hydro_probe_peak", "hydro_get_order"]
 
 
 def _load():
@@ -288,6 +289,7 @@ class Hydro:
                                       box_len.ctypes.data_as(C.c_void_p))
         if rc:
             raise HydroError(rc, "hydro_set_boxes")
+        self.n_particles = int(box_off[-1])
 
     def reserve(self, n, per_particle=0):
         rc = self.lib.hydro_reserve(self.h, int(n), int(per_particle))
@@ -387,6 +389,16 @@ class Hydro:
         rc = self.lib.hydro_set_gravity(self.h, _ptr(acc) if acc is not None else None)
         if rc:
             raise HydroError(rc, "hydro_set_gravity")
+
+    def get_order(self, stream=None):
+        """The last step's order (hydro_get_order): int32 CUDA tensor [n],
+        entry i the input index of the particle at sorted position i."""
+        import torch
+        perm = torch.empty(self.n_particles, dtype=torch.int32, device="cuda")
+        rc = self.lib.hydro_get_order(self.h, _ptr(perm), _stream(stream))
+        if rc:
+            raise HydroError(rc, "hydro_get_order")
+        return perm
 
     def test_mlp_stall(self, on):
         """Error-path test hook: the network's weight copy is not issued, so

@@ -87,3 +87,40 @@ def test_every_variant_computes_the_same_step(orc, hyd, variant, precision, tol,
             d_g = sg[k] - w[k]
             scale = np.abs(d_o).max() + 1e-300
             assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, (step, k)
+
+
+def test_ranked_tiles_reproduce_the_unranked_stages(hyd):
+    """The density and gradient kernels rank tiles of 128 consecutive
+    particles by list length (the gradient kernel also tiles of 128 R, R = 8
+    at 2^21 particles); each particle is still computed by one thread in one
+    order, so h, omega, B, the limited gradients and N_cond equal the
+    unranked kernels' bit for bit."""
+    import torch
+    w = W.lognormal(1 << 21, seed=3)
+    # converged smoothing lengths to start from (one short step solves them,
+    # with the re-searches the staged density call does not make)
+    H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision="mixed"))
+    H.set_boxes(*hyd.single_box(w))
+    st = hyd.to_device(w)
+    s = H.step(st, 1e-9, check=False)
+    assert s["status"] in (0, -5)   # (HYDRO_ENCOND: a few stay ill-conditioned)
+    torch.cuda.synchronize()
+    w = dict(w, **{k: st[k].cpu().numpy() for k in st})
+    H.close()
+    out = []
+    for rank in (0, 1, 2):
+        H = hyd.Hydro(hyd.default_config(gamma=w["gamma"], precision="mixed"))
+        H.set_tuning(dict(search_margin=1.1, nbr_slots=128, grad_min_ctas=1, flux_min_ctas=4,
+                          grad_rank=rank))
+        H.set_boxes(*hyd.single_box(w))
+        st = hyd.to_device(w)
+        H.build_neighbours(st, st["h"] * 1.3, export=False)
+        H.density(st)
+        B, G, A, N = H.gradients(st)
+        torch.cuda.synchronize()
+        c = lambda t: t.detach().cpu().numpy()
+        out.append(dict(h=c(st["h"]), omega=c(st["omega"]), B=c(B), G=c(G), A=c(A), N=c(N)))
+        H.close()
+    for r in (1, 2):
+        for k in out[0]:
+            assert np.array_equal(out[0][k], out[r][k], equal_nan=True), (r, k)
