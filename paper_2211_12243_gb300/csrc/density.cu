@@ -493,9 +493,9 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
 
 cudaError_t grow_search_radius(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
-    k_grow_search<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_hs.get(),
-                                                     c->d_hsorted.get(), c->cfg.search_margin,
-                                                     c->d_pbox.get(), c->d_boxes.get());
+    k_grow_search<<<grid_for(n, 256), 256, 0, st>>>(
+        n, c->d_active.get(), c->d_hs.get(), c->d_hsorted.get(), c->cfg.search_margin,
+        c->d_pbox.get(), c->d_boxes.get());
     return launch_check();
 }
 

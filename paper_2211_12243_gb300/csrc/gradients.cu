@@ -639,7 +639,7 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         // (the re-solved particles' radii into the tree first: the next
         // round's reverse walk bounds by them)
         HYD_CUDA(raise_tree(c, st));
-        HYD_CUDA(mark_reverse(c, st, true));
+        HYD_CUDA(mark_guard_reverse(c, st));
         HYD_CUDA(c->d_redo_idx.ensure(n));
         HYD_CUDA(compact_flags(n, c->d_active.get(), ACT_REDO, c->d_redo_idx.get(),
                                &c->d_cnt->nredo, st));
@@ -679,7 +679,7 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         }
     }
     HYD_CUDA(launch_check());
-    k_grad_reduce<<<152 * 2, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
+    k_grad_reduce<<<152 * 8, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
     return launch_check();
 }
 
@@ -687,11 +687,9 @@ cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_guard_idx.ensure(n));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nguard, 0, sizeof(int), st));
-    k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(n, c->d_active.get(), c->d_nngb.get(),
-                                                   c->cfg.ngb_grow, c->d_guard_idx.get(),
-                                                   &c->d_cnt->nguard, c->d_hs.get(),
-                                                   c->d_hsorted.get(), c->d_pbox.get(),
-                                                   c->d_boxes.get());
+    k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(
+        n, c->d_active.get(), c->d_nngb.get(), c->cfg.ngb_grow, c->d_guard_idx.get(),
+        &c->d_cnt->nguard, c->d_hs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get());
     return launch_check();
 }
 

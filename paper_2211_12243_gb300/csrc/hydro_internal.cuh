@@ -344,6 +344,10 @@ cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st, bool guard 
 // ACT_REDO on the guard round's particles and on every particle i with one
 // of them in its list (r_ia < h_i), found by walks of the bucket tree
 cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h = false);
+// the same marks for a guard round (bounded by the tree's largest h), by
+// tree walks from the grown particles or, when they are many, by a scan of
+// every particle's list (the choice made on the device)
+cudaError_t mark_guard_reverse(hydro_ctx *c, stream_t st);
 // gradients.cu: the particles with one of `bits` set in active, appended to
 // idx (count in *nidx, reset first; their order is not fixed)
 cudaError_t compact_flags(int64_t n, const uint8_t *active, uint8_t bits, int32_t *idx, int *nidx,
@@ -446,9 +450,11 @@ __device__ __forceinline__ int warp_chunk(int *cursor) {
     return __shfl_sync(0xffffffffu, base, 0);
 }
 
-// grid of the sweeps that touch few of the particles (the re-solves and
-// re-searches of a guard round): 16 CTAs per SM of the 152, the threads
-// striding over the particles, instead of a CTA per 128-256 particles
+// grid of the sweeps that test a flag of every particle and act on few of
+// them (the guard rounds' passes): 16 CTAs per SM of the 152, the threads
+// striding over the particles, instead of a CTA per 128-256 particles.
+// (Wider CTAs of 1024 threads were slower: a CTA holds its SM until its
+// slowest warp is done.)
 constexpr unsigned SWEEP_GRID = 152 * 16;
 constexpr int STEP_SKIP_FLAGS = ST_NOCONV_H | ST_MLP;
 // *p = v on the stream (a kernel: no host memory is referenced, so the call

@@ -680,6 +680,14 @@ __global__ void k_queue_active(int64_t nbucket, const int32_t *__restrict__ firs
 // bucket are tested exactly, one per lane (the double-precision membership
 // of the lists).  Marks ACT_REDO on them and on a itself.  Warps stride
 // over the guard particles, whose count is read on the device.
+// a guard round marks by scanning every list when it grew more than
+// n / MARK_SCAN_RATIO particles (k_mark_by_lists), else by tree walks
+constexpr int MARK_SCAN_RATIO = 1024;
+
+__device__ __forceinline__ bool mark_by_scan(int nguard, int64_t n) {
+    return (int64_t)nguard * MARK_SCAN_RATIO > n;
+}
+
 constexpr int RSTACK = 320;   // 32-ary tree of at most MAX_LEVELS levels
 constexpr int RWARPS = 4;
 
@@ -693,11 +701,13 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
                const double *__restrict__ ys, const double *__restrict__ zs,
                const double *__restrict__ h, const int32_t *__restrict__ pbox,
                const Box *__restrict__ boxes, uint8_t *__restrict__ active, DevCounters *cnt,
-               bool use_h) {
+               bool use_h, int64_t nparticles) {
     __shared__ int stack_all[RWARPS][RSTACK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *stack = stack_all[warp];
     const int ng = *nguard;
+    // (a guard round with many grown particles marks by the list scan below)
+    if (use_h && mark_by_scan(ng, nparticles)) return;
     const int nwarps = gridDim.x * RWARPS;
     for (int g = blockIdx.x * RWARPS + warp; g < ng; g += nwarps) {
         const int a = guard_idx[g];
@@ -749,9 +759,44 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
     }
 }
 
+// The same marks from the lists: particle i holds a guard particle a in its
+// list iff r_ia < h_i falls within the list's radius, and every list is
+// complete for r < h_i (after the density stage it holds its members and a
+// few entries just beyond), so scanning each particle's own list for a
+// guard flag marks every particle the walk would, plus a few whose
+// recomputation gives back their unchanged values.  One pass over all lists
+// costs about as much as the walks of n / MARK_SCAN_RATIO guard particles:
+// each kernel reads the round's guard count on the device and only one of
+// them works (the first round grows many particles, the later ones few).
+__global__ void __launch_bounds__(256)
+k_mark_by_lists(int64_t n, const int *__restrict__ nguard, const int64_t *__restrict__ nbr_off,
+                const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
+                uint8_t *__restrict__ active) {
+    if (!mark_by_scan(*nguard, n)) return;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t f = active[s];
+        bool hit = (f & ACT_GUARD) != 0;   // (a guard particle marks itself)
+        const int64_t o = nbr_off[s];
+        const int c = nbr_cnt[s];
+        for (int k = 0; k < c && !hit; k++) hit = (active[nbr_idx[o + k]] & ACT_GUARD) != 0;
+        // (only this thread writes active[s]; the others read its guard
+        // bit, which the write keeps)
+        if (hit) active[s] = f | ACT_REDO;
+    }
+}
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t mark_guard_reverse(hydro_ctx *c, stream_t st) {
+    HYD_CUDA(mark_reverse(c, st, true));
+    k_mark_by_lists<<<SWEEP_GRID, 256, 0, st>>>(c->plan.n, &c->d_cnt->nguard, c->d_nbr_off.get(),
+                                                c->d_nbr_cnt.get(), c->d_nbr_idx.get(),
+                                                c->d_active.get());
+    return launch_check();
+}
 
 cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h) {
     const Plan &P = c->plan;
@@ -762,7 +807,7 @@ cudaError_t mark_reverse(hydro_ctx *c, stream_t st, bool use_h) {
         c->d_box_root.get(), P.nbucket, c->d_node_aabb.get(), c->d_node_aabb_hi.get(),
         c->d_qx.get(), c->d_qy.get(), c->d_qz.get(), c->d_xs.get(), c->d_ys.get(), c->d_zs.get(),
         c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(), c->d_active.get(), c->d_cnt,
-        use_h);
+        use_h, P.n);
     return launch_check();
 }
 
