@@ -166,7 +166,7 @@ int build_all(hydro_ctx *c, const hydro_particles *p, const double *h_in, const 
 // rebuild when the overflow region is too small)
 int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &rebuilds,
                 cudaStream_t st, bool guard = false) {
-    API_CUDA(run_density(c, only_active, true, st));
+    API_CUDA(run_density(c, only_active, true, st, guard));
     for (int round = 0;; round++) {
         int sf = 0;
         API_CUDA(cudaMemcpyAsync(&sf, &c->d_cnt->search_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -174,7 +174,7 @@ int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &r
         if (sf == 0) return HYDRO_OK;
         if (round >= 8) return HYDRO_ESEARCH;
         rebuilds++;
-        API_CUDA(grow_search_radius(c, st));
+        API_CUDA(grow_search_radius(c, st, guard));
         int nq = 0;
         API_CUDA(rebuild_active_lists(c, &nq, st, guard));
         API_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -185,7 +185,7 @@ int density_all(hydro_ctx *c, const hydro_particles *p, bool only_active, int &r
             int rc = lists_all(c, st);
             if (rc) return rc;
         }
-        API_CUDA(run_density(c, true, true, st));
+        API_CUDA(run_density(c, true, true, st, guard));
     }
 }
 

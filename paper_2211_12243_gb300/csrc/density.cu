@@ -52,6 +52,9 @@ struct DensArgs {
     double *om;               // sorted out
     DevCounters *cnt;
     bool rank;                // full solve: rank the CTA's 128 particles by list length
+    const int32_t *list;      // a guard round: only these particles (the round's guard
+    const int *nlist;         // list, count on the device), taken by the warps 32 at a
+    int *cursor;              // time from a global cursor
 };
 
 // Growth of the search radius hs after a failed solve.  First failure
@@ -398,6 +401,14 @@ __device__ __forceinline__ void dens_one(const DensArgs &a, const uint64_t *__re
 __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
                                 const uint64_t *__restrict__ q64y,
                                 const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
+    if (a.list) {
+        const int nl = *a.nlist;
+        for (int b0 = warp_chunk(a.cursor); b0 < nl; b0 = warp_chunk(a.cursor)) {
+            const int t = b0 + (threadIdx.x & 31);
+            if (t < nl) dens_one(a, q64x, q64y, q64z, rec, a.list[t]);
+        }
+        return;
+    }
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a.rank) {
         __shared__ unsigned rank_key[RANK_THREADS];
@@ -411,19 +422,25 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
 // the search radius of particles whose root lay beyond it, as the density
 // kernel grew it (not below margin h); never beyond half the shortest box
 // side (one periodic image)
+// (list non-NULL: only its *nlist particles -- a guard round's, the only
+// ones it solves; every other particle's flags are clear then)
 __global__ void k_grow_search(int64_t n, uint8_t *__restrict__ active, double *__restrict__ hs,
                               const double *__restrict__ h, double margin,
-                              const int32_t *__restrict__ pbox, const Box *__restrict__ boxes) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    uint8_t a = active[s];
-    if (a & 2) {
-        const Box bx = boxes[pbox[s]];
-        double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
-        hs[s] = fmin(fmax(hs[s], h[s] * margin), half);   // (grown by the density kernel)
-        active[s] = (a & ACT_GUARD) | 1;
-    } else {
-        active[s] = a & ACT_GUARD;
+                              const int32_t *__restrict__ pbox, const Box *__restrict__ boxes,
+                              const int32_t *__restrict__ list, const int *__restrict__ nlist) {
+    const int64_t cnt = list ? (int64_t)*nlist : n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = list ? list[t] : t;
+        const uint8_t a = active[s];
+        if (a & 2) {
+            const Box bx = boxes[pbox[s]];
+            double half = 0.5 * fmin(bx.L[0], fmin(bx.L[1], bx.L[2]));
+            hs[s] = fmin(fmax(hs[s], h[s] * margin), half);   // (grown by the density kernel)
+            active[s] = (a & ACT_GUARD) | 1;
+        } else {
+            active[s] = a & ACT_GUARD;
+        }
     }
 }
 
@@ -445,7 +462,7 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st) {
+cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st, bool guard) {
     const int64_t n = c->plan.n;
     DensArgs a;
     a.n = n;
@@ -469,6 +486,9 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
     a.cnt = c->d_cnt;
     // ranked when the gradient kernel ranks (the same divergence)
     a.rank = c->grad_rank && !only_active;
+    a.list = nullptr;
+    a.nlist = nullptr;
+    a.cursor = nullptr;
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->search_fail, 0, sizeof(int), st));
     if (c->cfg.precision == HYDRO_MIXED) {
         // 64-bit fixed-point copies for the refinement step (xs.. are sorted)
@@ -483,19 +503,31 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
                                                          c->d_boxes.get(), q64, q64 + n, q64 + 2 * n);
             HYD_CUDA(launch_check());
         }
-        k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(
-            a, q64, q64 + n, q64 + 2 * n, c->d_recf.get());
+        unsigned grid = grid_for(n, DENS_THREADS);
+        if (guard && only_active) {
+            // the round's guard particles, few and scattered, each with a
+            // long list at its grown radius: one thread each, the warps
+            // drawing them from the guard list
+            HYD_CUDA(cudaMemsetAsync(&c->d_cnt->solve_cursor, 0, sizeof(int), st));
+            a.list = c->d_guard_idx.get();
+            a.nlist = &c->d_cnt->nguard;
+            a.cursor = &c->d_cnt->solve_cursor;
+            grid = 152 * 8;
+        }
+        k_density_mixed<<<grid, DENS_THREADS, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
+                                                       c->d_recf.get());
     } else {
         k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
     }
     return launch_check();
 }
 
-cudaError_t grow_search_radius(hydro_ctx *c, stream_t st) {
+cudaError_t grow_search_radius(hydro_ctx *c, stream_t st, bool guard) {
     const int64_t n = c->plan.n;
-    k_grow_search<<<grid_for(n, 256), 256, 0, st>>>(
+    k_grow_search<<<guard ? 152 * 4 : grid_for(n, 256), 256, 0, st>>>(
         n, c->d_active.get(), c->d_hs.get(), c->d_hsorted.get(), c->cfg.search_margin,
-        c->d_pbox.get(), c->d_boxes.get());
+        c->d_pbox.get(), c->d_boxes.get(), guard ? c->d_guard_idx.get() : nullptr,
+        &c->d_cnt->nguard);
     return launch_check();
 }
 

@@ -356,11 +356,14 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
                              const double *__restrict__ om, const double *__restrict__ h,
                              double gm1, double alpha1, const uint8_t *__restrict__ active,
                              bool only_guard, const double *__restrict__ agrav, EntArgs ent,
-                             const uint8_t *__restrict__ ract, R *__restrict__ rec) {
-    // (a grid-stride loop: a guard round's pass, which touches few
-    // particles, runs on a small grid instead of one thread per particle)
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) [&] {
+                             const uint8_t *__restrict__ ract, R *__restrict__ rec,
+                             const int32_t *__restrict__ list, const int *__restrict__ nlist) {
+    // (list non-NULL: a guard round's pass over its guard list, on a small
+    // grid, instead of one thread per particle)
+    const int64_t cnt = list ? (int64_t)*nlist : n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < cnt;
+         t += (int64_t)gridDim.x * blockDim.x) [&] {
+        const int64_t s = list ? list[t] : t;
         if (only_guard && !(active[s] & ACT_GUARD)) return;
         if (ract && !ract[s]) return;   // (individual timesteps: its record is kept)
         double m = Q[s], px = Q[n + s], py = Q[2 * n + s], pz = Q[3 * n + s];
@@ -549,17 +552,20 @@ cudaError_t run_primitives(hydro_ctx *c, stream_t st, bool only_guard) {
         ent.alpha2 = c->cfg.alpha2;
         ent.alpha3 = c->cfg.alpha3;
     }
-    const unsigned pgrid = only_guard ? std::min(grid_for(n, 256), SWEEP_GRID) : grid_for(n, 256);
+    const unsigned pgrid = only_guard ? 152 * 4 : grid_for(n, 256);
+    const int32_t *glist = only_guard ? c->d_guard_idx.get() : nullptr;
     if (mixed)
         k_primitives<float><<<pgrid, 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                               c->d_hsorted.get(), gm1,
                                                               c->cfg.alpha1, act, only_guard, ag,
-                                                              ent, ract, c->d_recf.get());
+                                                              ent, ract, c->d_recf.get(), glist,
+                                                              &c->d_cnt->nguard);
     else
         k_primitives<double><<<pgrid, 256, 0, st>>>(n, c->d_Q.get(), c->d_omsorted.get(),
                                                                c->d_hsorted.get(), gm1,
                                                                c->cfg.alpha1, act, only_guard, ag,
-                                                               ent, ract, c->d_recd.get());
+                                                               ent, ract, c->d_recd.get(), glist,
+                                                               &c->d_cnt->nguard);
     HYD_CUDA(launch_check());
     if (c->ent_live) {
         // the entropy route for the particles the energies did not claim

@@ -103,9 +103,9 @@ cudaError_t cond_search(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle
 // new lists, their density is solved again
 cudaError_t search_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, bool guard) {
     const long long k0 = launch_count();
-    HYD_CUDA(grow_search_radius(c, s));
+    HYD_CUDA(grow_search_radius(c, s, guard));
     HYD_CUDA(rebuild_active_lists_dev(c, s, guard));
-    HYD_CUDA(run_density(c, true, true, s));
+    HYD_CUDA(run_density(c, true, true, s, guard));
     HYD_CUDA(cond_search(c, s, h));
     c->cap_k_search = launch_count() - k0;
     return cudaSuccess;
@@ -128,7 +128,7 @@ cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
     const long long k0 = launch_count();
     HYD_CUDA(guard_grow(c, s));
     HYD_CUDA(guard_particle_lists(c, s));       // (the tree's radius bounds are not used)
-    HYD_CUDA(run_density(c, true, true, s));
+    HYD_CUDA(run_density(c, true, true, s, true));
     HYD_CUDA(search_loop(c, 2, s));
     HYD_CUDA(run_primitives(c, s, true));
     HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, true, s));

@@ -101,6 +101,7 @@ struct DevCounters {
     int bad_input;                    // a non-finite value in the caller's state
     int nredo;                        // particles a guard round recomputes the gradients of
     int redo_cursor;                  // the guard round's gradient warps' place in theirs
+    int solve_cursor;                 // the guard round's density warps' place in the guard list
     unsigned long long flux_cursor;   // the flux kernel's bucket queue
 };
 
@@ -361,8 +362,11 @@ cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu
 // compact: shrink each solved particle's list to its root (hydro_step only)
-cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st);
-cudaError_t grow_search_radius(hydro_ctx *c, stream_t st);
+// guard: a guard round's solve, whose particles are all in the round's
+// guard list (walked instead of every particle)
+cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t st,
+                        bool guard = false);
+cudaError_t grow_search_radius(hydro_ctx *c, stream_t st, bool guard = false);
 
 // gradients.cu
 // only_guard: the particles of the current guard round (their omega changed)
