@@ -490,7 +490,7 @@ int hydro_set_entropy(hydro_ctx *ctx, double *A);
  *     hydro_step {1.05, 1.1, 1.15, 1.25} and the fixed list slots per
  *     particle {64, 96, 128} (longer lists take two extra passes into an
  *     overflow region), timed over sort + lists + density;
- *   grad_min_ctas: register bound of the gradient kernel (1: none; 5, 6
+ *   grad_min_ctas: register bound of the gradient kernel (1: none; 4, 5, 6
  *     resident 128-thread CTAs per SM), timed over the gradient stage;
  *   flux_min_ctas: register bound of the float flux kernel (4, 5, 6),
  *     timed over the plain-guess flux stage (mixed precision only);
@@ -512,7 +512,7 @@ typedef struct {
     int grad_min_ctas;
     int flux_min_ctas;
     float front_ms[4][3];     /* [margin][slots] */
-    float grad_ms[3];         /* [1, 5, 6] */
+    float grad_ms[4];         /* [1, 4, 5, 6] */
     float flux_ms[3];         /* [4, 5, 6]; 0 in FP64 */
     int flux_queue;
     float flux_queue_ms[2];   /* [by index, drawn]; 0 in FP64 */
@@ -529,7 +529,7 @@ typedef struct {
 int hydro_autotune(hydro_ctx *ctx, hydro_particles *p, hydro_tuning *out, hydro_stream stream);
 
 /* Apply choices saved from an earlier hydro_autotune (search_margin >= 1,
- * nbr_slots in [32, 256], grad_min_ctas in {1, 5, 6}, flux_min_ctas in
+ * nbr_slots in [32, 256], grad_min_ctas in {1, 4, 5, 6}, flux_min_ctas in
  * {4, 5, 6}, flux_queue in {0, 1}, grad_rank in {0, 1, 2}; the time fields are
  * ignored).
  * HYDRO_EINVAL otherwise. */

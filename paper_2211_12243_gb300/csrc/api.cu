@@ -1034,7 +1034,7 @@ int hydro_set_entropy(hydro_ctx *c, double *A) {
 int hydro_set_tuning(hydro_ctx *c, const hydro_tuning *t) {
     if (!c || !t) return HYDRO_EINVAL;
     if (!(t->search_margin >= 1.0) || t->nbr_slots < 32 || t->nbr_slots > 256) return HYDRO_EINVAL;
-    if (t->grad_min_ctas != 1 && t->grad_min_ctas != 5 && t->grad_min_ctas != 6) return HYDRO_EINVAL;
+    if (t->grad_min_ctas != 1 && (t->grad_min_ctas < 4 || t->grad_min_ctas > 6)) return HYDRO_EINVAL;
     if (t->flux_min_ctas < 4 || t->flux_min_ctas > 6) return HYDRO_EINVAL;
     if (t->flux_queue != 0 && t->flux_queue != 1) return HYDRO_EINVAL;
     if (t->grad_rank < 0 || t->grad_rank > 2) return HYDRO_EINVAL;
@@ -1056,7 +1056,7 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
     API_CUDA(ensure_state(c, p->n));
     static const double margins[4] = {1.05, 1.1, 1.15, 1.25};
     static const int slots[3] = {64, 96, 128};
-    static const int gminb[3] = {1, 5, 6};
+    static const int gminb[4] = {1, 4, 5, 6};
     static const int fminb[3] = {4, 5, 6};
     hydro_tuning T;
     memset(&T, 0, sizeof(T));
@@ -1100,7 +1100,7 @@ int hydro_autotune(hydro_ctx *c, hydro_particles *p, hydro_tuning *out, hydro_st
     // gradient stage
     best = 1e30f;
     int bg = 1;
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 4; k++) {
         c->grad_minb = gminb[k];
         float t = 1e30f;
         for (int rep = 0; rep < 2; rep++) {

@@ -401,14 +401,6 @@ __device__ __forceinline__ void dens_one(const DensArgs &a, const uint64_t *__re
 __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
                                 const uint64_t *__restrict__ q64y,
                                 const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
-    if (a.list) {
-        const int nl = *a.nlist;
-        for (int b0 = warp_chunk(a.cursor); b0 < nl; b0 = warp_chunk(a.cursor)) {
-            const int t = b0 + (threadIdx.x & 31);
-            if (t < nl) dens_one(a, q64x, q64y, q64z, rec, a.list[t]);
-        }
-        return;
-    }
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a.rank) {
         __shared__ unsigned rank_key[RANK_THREADS];
@@ -417,6 +409,19 @@ __global__ void k_density_mixed(DensArgs a, const uint64_t *__restrict__ q64x,
         s = base + rank_index(rank_key[threadIdx.x], 1);
     }
     dens_one(a, q64x, q64y, q64z, rec, s);
+}
+
+// a guard round's re-solve: the warps take the particles of the round's
+// guard list 32 at a time (its own kernel: the branch would cost the full
+// solve's kernel ten registers)
+__global__ void k_density_mixed_list(DensArgs a, const uint64_t *__restrict__ q64x,
+                                     const uint64_t *__restrict__ q64y,
+                                     const uint64_t *__restrict__ q64z, float *__restrict__ rec) {
+    const int nl = *a.nlist;
+    for (int b0 = warp_chunk(a.cursor); b0 < nl; b0 = warp_chunk(a.cursor)) {
+        const int t = b0 + (threadIdx.x & 31);
+        if (t < nl) dens_one(a, q64x, q64y, q64z, rec, a.list[t]);
+    }
 }
 
 // the search radius of particles whose root lay beyond it, as the density
@@ -503,7 +508,6 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
                                                          c->d_boxes.get(), q64, q64 + n, q64 + 2 * n);
             HYD_CUDA(launch_check());
         }
-        unsigned grid = grid_for(n, DENS_THREADS);
         if (guard && only_active) {
             // the round's guard particles, few and scattered, each with a
             // long list at its grown radius: one thread each, the warps
@@ -512,10 +516,12 @@ cudaError_t run_density(hydro_ctx *c, bool only_active, bool compact, stream_t s
             a.list = c->d_guard_idx.get();
             a.nlist = &c->d_cnt->nguard;
             a.cursor = &c->d_cnt->solve_cursor;
-            grid = 152 * 8;
+            k_density_mixed_list<<<152 * 8, DENS_THREADS, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
+                                                                   c->d_recf.get());
+        } else {
+            k_density_mixed<<<grid_for(n, DENS_THREADS), DENS_THREADS, 0, st>>>(
+                a, q64, q64 + n, q64 + 2 * n, c->d_recf.get());
         }
-        k_density_mixed<<<grid, DENS_THREADS, 0, st>>>(a, q64, q64 + n, q64 + 2 * n,
-                                                       c->d_recf.get());
     } else {
         k_density_f64<<<grid_for(n, 128), 128, 0, st>>>(a, c->d_recd.get());
     }

@@ -664,22 +664,26 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
     if (c->cfg.precision == HYDRO_MIXED) {
         float *r = c->d_recf.get();
         if (lean) {
-            if (c->grad_minb == 5) k_gradients<float, 5, true><<<grid, 128, smem, st>>>(a, r);
+            if (c->grad_minb == 4) k_gradients<float, 4, true><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 5) k_gradients<float, 5, true><<<grid, 128, smem, st>>>(a, r);
             else if (c->grad_minb == 6) k_gradients<float, 6, true><<<grid, 128, smem, st>>>(a, r);
             else k_gradients<float, 1, true><<<grid, 128, smem, st>>>(a, r);
         } else {
-            if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, smem, st>>>(a, r);
+            if (c->grad_minb == 4) k_gradients<float, 4><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 5) k_gradients<float, 5><<<grid, 128, smem, st>>>(a, r);
             else if (c->grad_minb == 6) k_gradients<float, 6><<<grid, 128, smem, st>>>(a, r);
             else k_gradients<float, 1><<<grid, 128, smem, st>>>(a, r);
         }
     } else {
         double *r = c->d_recd.get();
         if (lean) {
-            if (c->grad_minb == 5) k_gradients<double, 5, true><<<grid, 128, smem, st>>>(a, r);
+            if (c->grad_minb == 4) k_gradients<double, 4, true><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 5) k_gradients<double, 5, true><<<grid, 128, smem, st>>>(a, r);
             else if (c->grad_minb == 6) k_gradients<double, 6, true><<<grid, 128, smem, st>>>(a, r);
             else k_gradients<double, 1, true><<<grid, 128, smem, st>>>(a, r);
         } else {
-            if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, smem, st>>>(a, r);
+            if (c->grad_minb == 4) k_gradients<double, 4><<<grid, 128, smem, st>>>(a, r);
+            else if (c->grad_minb == 5) k_gradients<double, 5><<<grid, 128, smem, st>>>(a, r);
             else if (c->grad_minb == 6) k_gradients<double, 6><<<grid, 128, smem, st>>>(a, r);
             else k_gradients<double, 1><<<grid, 128, smem, st>>>(a, r);
         }

@@ -93,7 +93,7 @@ class Stats(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [
         ("search_margin", C.c_double), ("nbr_slots", C.c_int), ("grad_min_ctas", C.c_int),
-        ("flux_min_ctas", C.c_int), ("front_ms", (C.c_float * 3) * 4), ("grad_ms", C.c_float * 3),
+        ("flux_min_ctas", C.c_int), ("front_ms", (C.c_float * 3) * 4), ("grad_ms", C.c_float * 4),
         ("flux_ms", C.c_float * 3), ("flux_queue", C.c_int), ("flux_queue_ms", C.c_float * 2),
         ("grad_rank", C.c_int), ("grad_rank_ms", C.c_float * 3),
     ]

@@ -193,6 +193,42 @@ def test_guard_rounds_match_oracle(orc, hyd, crit, precision, tol):
         assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, k
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_guard_rounds_2e16_match_oracle(orc, hyd, precision, tol, graph):
+    """The default threshold on 2^16 particles of the clustered generator:
+    the first growth round grows 249 particles, more than n / 1024, and the
+    recomputed particles are marked by a scan of every list; the second
+    grows 22 and the third 2, marked by tree walks from them (the counts are
+    the oracle's rounds at this seed).  Host-driven and graph steps."""
+    import torch
+    w = W.lognormal(1 << 16, seed=0)
+    co = orc.config(gamma=w["gamma"])
+    cg = hyd.default_config(gamma=w["gamma"], precision=precision, graph=graph)
+    so, _, info_o = orc.step(co, w, -1.0)
+    assert info_o["ngb_rounds"] == 3 and info_o["ncond_fail"] == 0
+    H = hyd.Hydro(cg)
+    H.set_boxes(*hyd.single_box(w))
+    for rep in range(2):            # the context's first step is host-driven, the second a graph
+        st = hyd.to_device(w)
+        stats = H.step(st, -1.0, check=False)
+        torch.cuda.synchronize()
+        sg = {k: v.cpu().numpy() for k, v in st.items()}
+        assert stats["status"] == info_o["status"]
+        assert stats["ngb_rounds"] == 3 and stats["ncond_fail"] == 0
+        assert stats["grad_pairs"] == info_o["grad_pairs"]
+        assert stats["flux_pairs"] == info_o["flux"]["pairs"]
+        for k in ("h", "omega"):
+            assert np.max(np.abs(sg[k] - so[k]) / np.abs(so[k])) < tol, k
+        for k in ("m", "px", "py", "pz", "E", "U"):
+            d_o = so[k] - w[k]
+            d_g = sg[k] - w[k]
+            scale = np.abs(d_o).max() + 1e-300
+            assert np.max(np.abs(d_g - d_o)) < max(tol, 1e-12) * scale * 10 + 1e-300, k
+        cons = conservation(w, sg, w["gamma"])
+        assert max(cons.values()) < 1e-12, cons
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_conserves_and_reports(hyd, precision):
     import torch
