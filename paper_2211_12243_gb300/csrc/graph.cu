@@ -203,7 +203,8 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
         }
     }
     k.push_back((unsigned long long)c->nbr_per_particle);
-    k.push_back((unsigned long long)c->flux_minb | ((unsigned long long)c->grad_minb << 8));
+    k.push_back((unsigned long long)c->flux_minb | ((unsigned long long)c->grad_minb << 8) |
+                ((unsigned long long)c->flux_queue << 16) | ((unsigned long long)c->grad_rank << 24));
     k.push_back((unsigned long long)c->ovf_reserve);
     k.push_back((unsigned long long)c->hard_cap);
     k.push_back((unsigned long long)c->plan.n);

@@ -55,13 +55,16 @@ def test_autotune_chooses_and_leaves_the_state(hyd, precision):
     dict(search_margin=1.05, nbr_slots=64, grad_min_ctas=5, flux_min_ctas=5),
     dict(search_margin=1.25, nbr_slots=128, grad_min_ctas=6, flux_min_ctas=6),
     dict(search_margin=1.1, nbr_slots=96, grad_min_ctas=1, flux_min_ctas=4),
+    dict(search_margin=1.05, nbr_slots=128, grad_min_ctas=4, flux_min_ctas=4, grad_rank=2),
 ])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
-@pytest.mark.parametrize("name", ["sod_exact", "lognormal_hllc"])
+@pytest.mark.parametrize("name", ["sod_exact", "lognormal_hllc", "lognormal_exact"])
 def test_every_variant_computes_the_same_step(orc, hyd, variant, precision, tol, name):
     import torch
     if name == "sod_exact":
         w, opts = W.sod(8), {}
+    elif name == "lognormal_exact":
+        w, opts = W.lognormal(4096, seed=2, grid=16), {}
     else:
         w, opts = W.lognormal(4096, seed=2, grid=16), dict(riemann="hllc")
     co = orc.config(gamma=w["gamma"], **opts)
