@@ -243,7 +243,7 @@ std::vector<unsigned long long> graph_key(const hydro_ctx *c, const hydro_partic
           (const void *)c->d_mlp_blob.get(), (const void *)c->d_hard.get(),
           (const void *)c->d_hard_idx.get(), (const void *)c->d_hard_cursor.get(),
           (const void *)c->d_rec_cursor.get(), (const void *)c->d_guard_idx.get(),
-          (const void *)c->d_redo_idx.get()})
+          (const void *)c->d_redo_idx.get(), (const void *)c->d_guard_bits.get()})
         put(q);
     k.push_back((unsigned long long)c->d_nbr_idx.cap);
     return k;

@@ -185,6 +185,7 @@ struct hydro_ctx {
     hyd::DevBuf<int32_t> d_gpairs;    // per-particle gradient pairs
     hyd::DevBuf<int32_t> d_guard_idx; // the guard round's grown particles (nguard of them)
     hyd::DevBuf<int32_t> d_redo_idx;  // the particles whose gradients it recomputes (nredo)
+    hyd::DevBuf<uint32_t> d_guard_bits; // the round's guard particles as a bitmap
 
     // neighbour lists
     hyd::DevBuf<int32_t> d_nbr_idx;

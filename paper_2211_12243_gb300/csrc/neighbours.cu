@@ -771,18 +771,29 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
 __global__ void __launch_bounds__(256)
 k_mark_by_lists(int64_t n, const int *__restrict__ nguard, const int64_t *__restrict__ nbr_off,
                 const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
-                uint8_t *__restrict__ active) {
+                const uint32_t *__restrict__ gbits, uint8_t *__restrict__ active) {
     if (!mark_by_scan(*nguard, n)) return;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
          s += (int64_t)gridDim.x * blockDim.x) {
-        const uint8_t f = active[s];
-        bool hit = (f & ACT_GUARD) != 0;   // (a guard particle marks itself)
         const int64_t o = nbr_off[s];
         const int c = nbr_cnt[s];
-        for (int k = 0; k < c && !hit; k++) hit = (active[nbr_idx[o + k]] & ACT_GUARD) != 0;
-        // (only this thread writes active[s]; the others read its guard
-        // bit, which the write keeps)
-        if (hit) active[s] = f | ACT_REDO;
+        bool hit = (gbits[s >> 5] >> (s & 31)) & 1u;   // (a guard particle marks itself)
+        for (int k = 0; k < c && !hit; k++) {
+            const int j = nbr_idx[o + k];
+            hit = (gbits[j >> 5] >> (j & 31)) & 1u;
+        }
+        if (hit) active[s] |= ACT_REDO;
+    }
+}
+
+// the guard round's particles as a bitmap (one bit per particle, a 32nd of
+// the flag bytes: the scan's lookups stay in L1 and L2)
+__global__ void k_guard_bits(const int32_t *__restrict__ guard_idx, const int *__restrict__ nguard,
+                             uint32_t *__restrict__ gbits) {
+    const int ng = *nguard;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ng; t += gridDim.x * blockDim.x) {
+        const int s = guard_idx[t];
+        atomicOr(&gbits[s >> 5], 1u << (s & 31));
     }
 }
 
@@ -792,9 +803,15 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 cudaError_t mark_guard_reverse(hydro_ctx *c, stream_t st) {
     HYD_CUDA(mark_reverse(c, st, true));
+    const int64_t nw = (c->plan.n + 31) / 32;
+    HYD_CUDA(c->d_guard_bits.ensure(nw));
+    HYD_CUDA(cudaMemsetAsync(c->d_guard_bits.get(), 0, nw * sizeof(uint32_t), st));
+    k_guard_bits<<<152 * 4, 256, 0, st>>>(c->d_guard_idx.get(), &c->d_cnt->nguard,
+                                          c->d_guard_bits.get());
+    HYD_CUDA(launch_check());
     k_mark_by_lists<<<SWEEP_GRID, 256, 0, st>>>(c->plan.n, &c->d_cnt->nguard, c->d_nbr_off.get(),
                                                 c->d_nbr_cnt.get(), c->d_nbr_idx.get(),
-                                                c->d_active.get());
+                                                c->d_guard_bits.get(), c->d_active.get());
     return launch_check();
 }
 
