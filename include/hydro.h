@@ -185,7 +185,11 @@ typedef struct {
                                  particles (rounding below 1e-13 of sum |x| at
                                  2^27 particles), so any difference is the
                                  step's (fluxes and external sources) */
-    float ms_sort, ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
+    float ms_sort;            /* 0: the sort is timed within ms_neighbours */
+    float ms_neighbours, ms_density, ms_gradients, ms_fluxes, ms_update;
+                              /* stage times (CUDA events on the stream; ms_neighbours:
+                                 the sort, gathers, tree and lists; ms_gradients:
+                                 primitives, gradients and the N_cond guard rounds) */
     float ms_flux_kernel;     /* the pair-flux kernel alone (CUDA events on the stream) */
     float ms_hard_faces;      /* the learned-guess hard-face kernel (0 when off) */
     int graph;                /* 1: the step ran as the captured graph; 0: host-driven
