@@ -537,6 +537,10 @@ def test_sod_tube_follows_exact_solution(orc, scheme):
         l1 = np.mean(np.abs(f - ex[:, k]))
         l1_frozen = np.mean(np.abs(frozen[:, k] - ex[:, k]))
         assert l1 < (0.6, 0.3, 0.5)[k] * l1_frozen, (k, l1, l1_frozen)
+        # and in absolute terms at this resolution (n = 16: 16 particles per unit
+        # length on the dense side; measured MFV 0.094 / 0.075 / 0.096, MFM 0.099 /
+        # 0.078 / 0.099 for rho / v / p over 1.3 < x < 3 at t = 0.4)
+        assert l1 < (0.11, 0.09, 0.11)[k], (k, l1)
     # transverse motion stays negligible (§3.1.2)
     assert np.abs(prims[2][sel]).max() < 1e-2 and np.abs(prims[3][sel]).max() < 1e-2
 
