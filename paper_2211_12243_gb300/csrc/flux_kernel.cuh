@@ -191,8 +191,9 @@ __device__ __forceinline__ bool face_state(const FluxArgs &a, const GasK<R> &K, 
     const R pi = R(3.14159265358979323846);
     const R hi_ = ri[R_H], hj = rj[R_H];
     const R kn = a.kernel == 0 ? R(21) / (R(2) * pi) : R(8) / pi;
-    const R wi = div_(kn, hi_ * hi_ * hi_) * kernel_shape<R>(a.kernel, div_(r, hi_));
-    const R wj = div_(kn, hj * hj * hj) * kernel_shape<R>(a.kernel, div_(r, hj));
+    const R ihi = div_(R(1), hi_), ihj = div_(R(1), hj);
+    const R wi = kn * ihi * ihi * ihi * kernel_shape<R>(a.kernel, r * ihi);
+    const R wj = kn * ihj * ihj * ihj * kernel_shape<R>(a.kernel, r * ihj);
     const R *Bi = ri + R_B, *Bj = rj + R_B;
     R A[3];
     {
@@ -309,7 +310,9 @@ __device__ __forceinline__ void face_finish(const FluxArgs &a, const GasK<R> &K,
         R ps, us;
         R tol = sizeof(R) == 8 ? (R)a.p_tol : (R)a.ptolf;
         const GasK<double> *kd = sizeof(R) == 4 && a.riemann_polish ? &a.Kd : nullptr;
-        StarOut so = star_solve<R>(K, rl, ul, pl, rr, ur, pr, p0, tol, a.max_newton, ps, us, kd);
+        const R cl = sqrt_(div_(K.g * pl, rl)), cr = sqrt_(div_(K.g * pr, rr));
+        StarOut so = star_solve<R>(K, rl, ul, pl, cl, rr, ur, pr, cr, p0, tol, a.max_newton, ps, us,
+                                   kd);
         fs.iters += so.iters;
         if (so.vacuum) { fs.vacuum++; return; }
         ps_out = ps;
@@ -320,12 +323,12 @@ __device__ __forceinline__ void face_finish(const FluxArgs &a, const GasK<R> &K,
         } else {
             R rs, uu, pp;
             int side;
-            star_sample<R>(K, rl, ul, pl, rr, ur, pr, ps, us, rs, uu, pp, side);
+            star_sample<R>(K, rl, ul, pl, cl, rr, ur, pr, cr, ps, us, rs, uu, pp, side);
             R w0 = side < 0 ? wl[0] : wr[0];
             R w1 = side < 0 ? wl[1] : wr[1];
             R w2 = side < 0 ? wl[2] : wr[2];
             R v2 = uu * uu + w0 * w0 + w1 * w1 + w2 * w2;
-            R et = R(0.5) * rs * v2 + div_(pp, K.gm1);
+            R et = R(0.5) * (rs * v2 + K.g4 * pp);   // (g4 = 2 / (gamma - 1))
             R m = rs * uu;
             F[0] = m;
             F[1] = m * (uu * nh[0] + w0) + pp * nh[0];

@@ -160,12 +160,13 @@ struct StarOut {
 // on the bracket after max_newton iterations.  kd (float path only, else
 // NULL): after the float iteration converged, one more Newton step with the
 // pressure function evaluated in FP64, and u* from it.
+// (cl, cr: the two sides' sound speeds, which the caller's sampling of
+// the solution needs as well)
 template <typename R>
-__device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
-                                              R p0, R tol, int max_newton, R &ps, R &us,
-                                              const GasK<double> *kd = nullptr) {
+__device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl, R cl, R rr, R ur,
+                                              R pr, R cr, R p0, R tol, int max_newton, R &ps,
+                                              R &us, const GasK<double> *kd = nullptr) {
     StarOut o{0, 0, 0};
-    R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
     R du = ur - ul;
     if (k.g4 * (cl + cr) <= du) {
         o.vacuum = 1;
@@ -267,9 +268,8 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
 
 // state at x/t = 0 of the exact solution; side = -1 left of the contact
 template <typename R>
-__device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, R rr, R ur, R pr,
-                                            R ps, R us, R &rho, R &u, R &p, int &side) {
-    R cl = sqrt_(div_(k.g * pl, rl)), cr = sqrt_(div_(k.g * pr, rr));
+__device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, R cl, R rr, R ur,
+                                            R pr, R cr, R ps, R us, R &rho, R &u, R &p, int &side) {
     if (R(0) <= us) {
         side = -1;
         if (ps > pl) {
