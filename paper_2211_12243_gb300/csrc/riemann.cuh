@@ -81,12 +81,13 @@ __device__ __forceinline__ void side_f<float>(const GasK<float> &k, float p, flo
 // sides, which leaves two reciprocals, a square root and a power per side
 // and step on the special-function unit
 struct SideF {
-    float A, B, ipk, cg, pk, ck;
+    float A, sA, B, ipk, cg, pk, ck;   // (sA = sqrt(A))
 };
 
 __device__ __forceinline__ SideF side_prep(const GasK<float> &k, float rk, float pk, float ck) {
     SideF s;
     s.A = __fdividef(k.g5, rk);
+    s.sA = sqrt_(s.A);
     s.B = k.g6 * pk;
     s.ipk = __fdividef(1.f, pk);
     s.cg = ck * k.inv_g;
@@ -98,11 +99,13 @@ __device__ __forceinline__ SideF side_prep(const GasK<float> &k, float rk, float
 // f_K(p) and f_K'(p) with ip = 1/p: both branches evaluated and selected
 // (no divergence between shock and rarefaction sides); the rarefaction
 // derivative (1/(rho_K c_K)) (p/p_K)^(-(g+1)/(2g)) is written as
-// (p/p_K)^((g-1)/(2g)) c_K / (g p)
+// (p/p_K)^((g-1)/(2g)) c_K / (g p); the shock branch's sqrt(A / (p + B)) and
+// 1 / (p + B) come from one reciprocal square root
 __device__ __forceinline__ void side_eval(const GasK<float> &k, const SideF &s, float p, float ip,
                                           float &f, float &df) {
-    const float ia = __fdividef(1.f, p + s.B);
-    const float q = sqrt_(s.A * ia);
+    const float rq = rsqrtf(p + s.B);
+    const float ia = rq * rq;
+    const float q = s.sA * rq;
     const float fs = (p - s.pk) * q;
     const float dfs = q * (1.f - 0.5f * (p - s.pk) * ia);
     const float t = __powf(p * s.ipk, k.z);
@@ -138,14 +141,15 @@ __device__ __forceinline__ R star_guess(const GasK<R> &k, R rl, R ul, R pl, R cl
     R pmin = pl < pr ? pl : pr, pmax = pl > pr ? pl : pr;
     if (pmax <= R(2) * pmin && ppv >= pmin && ppv <= pmax) return ppv;
     if (ppv < pmin) {
+        const R icl = div_(R(1), cl), icr = div_(R(1), cr);
         R pq = pow_(div_(pl, pr), k.z);
-        R um = div_(div_(pq * ul, cl) + div_(ur, cr) + k.g4 * (pq - R(1)), div_(pq, cl) + div_(R(1), cr));
-        R tl = R(1) + R(0.5) * k.gm1 * div_(ul - um, cl);
-        R tr = R(1) + R(0.5) * k.gm1 * div_(um - ur, cr);
+        R um = div_(pq * ul * icl + ur * icr + k.g4 * (pq - R(1)), pq * icl + icr);
+        R tl = R(1) + R(0.5) * k.gm1 * (ul - um) * icl;
+        R tr = R(1) + R(0.5) * k.gm1 * (um - ur) * icr;
         return R(0.5) * (pl * pow_(tl, k.zi) + pr * pow_(tr, k.zi));
     }
-    R gl = sqrt_(div_(div_(k.g5, rl), k.g6 * pl + ppv));
-    R gr = sqrt_(div_(div_(k.g5, rr), k.g6 * pr + ppv));
+    R gl = sqrt_(div_(k.g5, rl * (k.g6 * pl + ppv)));
+    R gr = sqrt_(div_(k.g5, rr * (k.g6 * pr + ppv)));
     return div_(gl * pl + gr * pr - (ur - ul), gl + gr);
 }
 
