@@ -650,110 +650,112 @@ def main():
 
     # ---- end to end through the public API with host buffers: every step
     # copies its inputs in (pinned host -> device), steps, and reads its state
-    # back (device -> pinned host).  The read-back goes through a device
-    # staging copy on a second stream, so it overlaps the next step; the
-    # last one ends inside the timed region.  One sequential step first
-    # (untimed) gives the three phases on their own.
-    host = {k: torch.as_tensor(w[k]).pin_memory() for k in KEYS}
-    host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in KEYS + ("omega",)}
-    e2e_steps = min(args.steps, 3) if big else args.steps
-    st2 = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
-    stage = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    flush.zero_()
-    ev[0].record(stream)
-    for kk in KEYS:
-        st2[kk].copy_(host[kk], non_blocking=True)
-    ev[1].record(stream)
-    s2 = H.step(st2, -1.0, check=False)
-    assert s2["status"] in ok_status, s2
-    ev[2].record(stream)
-    for kk in KEYS + ("omega",):
-        host_out[kk].copy_(st2[kk], non_blocking=True)
-    ev[3].record(stream)
-    torch.cuda.synchronize()
-    phases = {"h2d": ev[0].elapsed_time(ev[1]), "step": ev[1].elapsed_time(ev[2]),
-              "d2h": ev[2].elapsed_time(ev[3])}
-    # sequential: each step's read-back before the next step's copy-in
-    e_seq0 = torch.cuda.Event(enable_timing=True)
-    e_seq1 = torch.cuda.Event(enable_timing=True)
-    seq_pairs = 0
-    e_seq0.record(stream)
-    for k in range(e2e_steps):
+    # back (device -> pinned host), sequentially and then pipelined (below).
+    # One sequential step first (untimed) gives the three phases on their
+    # own.  Every step, copy and event runs on streams of its own: work on the
+    # legacy default stream would wait on the copy streams.
+    es = torch.cuda.Stream()
+    with torch.cuda.stream(es):
+        host = {k: torch.as_tensor(w[k]).pin_memory() for k in KEYS}
+        host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in KEYS + ("omega",)}
+        e2e_steps = min(args.steps, 3) if big else args.steps
+        st2 = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
+        stage = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         flush.zero_()
+        ev[0].record(es)
         for kk in KEYS:
             st2[kk].copy_(host[kk], non_blocking=True)
-        s2 = H.step(st2, -1.0, check=False)
+        ev[1].record(es)
+        s2 = H.step(st2, -1.0, check=False, stream=es)
         assert s2["status"] in ok_status, s2
-        seq_pairs += s2["grad_pairs"] + s2["flux_pairs"]
+        ev[2].record(es)
         for kk in KEYS + ("omega",):
             host_out[kk].copy_(st2[kk], non_blocking=True)
-    e_seq1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = e_seq0.elapsed_time(e_seq1)
-    # overlapped: each step's inputs arrive in a device staging copy on a
-    # copy stream while the previous step runs, and its state leaves from a
-    # staging copy on another while the next step runs (device-to-device
-    # copies into and out of the step's own arrays); the first H2D and the
-    # last D2H are inside the timed region
-    in_stage = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS}
-    cs_in = torch.cuda.Stream()
-    cs = torch.cuda.Stream()
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
-    d2h_done = None
-    e2e_pairs = 0
-    e_start.record(stream)
-    cs_in.wait_stream(stream)
-    with torch.cuda.stream(cs_in):
-        for kk in KEYS:
-            in_stage[kk].copy_(host[kk], non_blocking=True)
-    in_ready = torch.cuda.Event()
-    in_ready.record(cs_in)
-    for k in range(e2e_steps):
-        flush.zero_()
-        stream.wait_event(in_ready)
-        for kk in KEYS:
-            st2[kk].copy_(in_stage[kk], non_blocking=True)
-        if k + 1 < e2e_steps:
-            # the next step's inputs, once the staging copy is free again
-            in_free = torch.cuda.Event()
-            in_free.record(stream)
-            cs_in.wait_event(in_free)
-            with torch.cuda.stream(cs_in):
-                for kk in KEYS:
-                    in_stage[kk].copy_(host[kk], non_blocking=True)
-            in_ready = torch.cuda.Event()
-            in_ready.record(cs_in)
-        s2 = H.step(st2, -1.0, check=False)
-        assert s2["status"] in ok_status, s2
-        e2e_pairs += s2["grad_pairs"] + s2["flux_pairs"]
-        if d2h_done is not None:
-            stream.wait_event(d2h_done)   # (the staging buffers are free again)
-        for kk in KEYS + ("omega",):
-            stage[kk].copy_(st2[kk], non_blocking=True)
-        staged = torch.cuda.Event()
-        staged.record(stream)
-        cs.wait_event(staged)
-        with torch.cuda.stream(cs):
+        ev[3].record(es)
+        torch.cuda.synchronize()
+        phases = {"h2d": ev[0].elapsed_time(ev[1]), "step": ev[1].elapsed_time(ev[2]),
+                  "d2h": ev[2].elapsed_time(ev[3])}
+        # sequential: each step's read-back before the next step's copy-in
+        e_seq0 = torch.cuda.Event(enable_timing=True)
+        e_seq1 = torch.cuda.Event(enable_timing=True)
+        seq_pairs = 0
+        e_seq0.record(es)
+        for k in range(e2e_steps):
+            flush.zero_()
+            for kk in KEYS:
+                st2[kk].copy_(host[kk], non_blocking=True)
+            s2 = H.step(st2, -1.0, check=False, stream=es)
+            assert s2["status"] in ok_status, s2
+            seq_pairs += s2["grad_pairs"] + s2["flux_pairs"]
             for kk in KEYS + ("omega",):
-                host_out[kk].copy_(stage[kk], non_blocking=True)
-        d2h_done = torch.cuda.Event()
-        d2h_done.record(cs)
-    stream.wait_event(d2h_done)
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e_start.elapsed_time(e_end)
-    e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT, "steps": e2e_steps,
-           "timed": "per step: H2D copies of the inputs + hydro_step + D2H copies of the state, "
-                    "pipelined: the inputs arrive in a device staging copy on a copy stream "
-                    "during the previous step and the state leaves from one during the next "
-                    "(device-to-device copies into and out of the step's arrays); the first "
-                    "H2D and the last D2H inside the timed region",
-           "h2d_bytes_per_step": 8 * n * len(KEYS), "d2h_bytes_per_step": 8 * n * (len(KEYS) + 1),
-           "ms_per_step": e2e_ms / e2e_steps,
-           "sequential": {"value": seq_pairs / (seq_ms / 1000.0), "ms_per_step": seq_ms / e2e_steps},
-           "one_sequential_step_ms": phases}
+                host_out[kk].copy_(st2[kk], non_blocking=True)
+        e_seq1.record(es)
+        torch.cuda.synchronize()
+        seq_ms = e_seq0.elapsed_time(e_seq1)
+        # overlapped: each step's inputs arrive in a device staging copy on a
+        # copy stream while the previous step runs, and its state leaves from a
+        # staging copy on another while the next step runs (device-to-device
+        # copies into and out of the step's own arrays); the first H2D and the
+        # last D2H are inside the timed region
+        in_stage = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS}
+        cs_in = torch.cuda.Stream()
+        cs = torch.cuda.Stream()
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        d2h_done = None
+        e2e_pairs = 0
+        e_start.record(es)
+        cs_in.wait_stream(es)
+        with torch.cuda.stream(cs_in):
+            for kk in KEYS:
+                in_stage[kk].copy_(host[kk], non_blocking=True)
+        in_ready = torch.cuda.Event()
+        in_ready.record(cs_in)
+        for k in range(e2e_steps):
+            flush.zero_()
+            es.wait_event(in_ready)
+            for kk in KEYS:
+                st2[kk].copy_(in_stage[kk], non_blocking=True)
+            if k + 1 < e2e_steps:
+                # the next step's inputs, once the staging copy is free again
+                in_free = torch.cuda.Event()
+                in_free.record(es)
+                cs_in.wait_event(in_free)
+                with torch.cuda.stream(cs_in):
+                    for kk in KEYS:
+                        in_stage[kk].copy_(host[kk], non_blocking=True)
+                in_ready = torch.cuda.Event()
+                in_ready.record(cs_in)
+            s2 = H.step(st2, -1.0, check=False, stream=es)
+            assert s2["status"] in ok_status, s2
+            e2e_pairs += s2["grad_pairs"] + s2["flux_pairs"]
+            if d2h_done is not None:
+                es.wait_event(d2h_done)   # (the staging buffers are free again)
+            for kk in KEYS + ("omega",):
+                stage[kk].copy_(st2[kk], non_blocking=True)
+            staged = torch.cuda.Event()
+            staged.record(es)
+            cs.wait_event(staged)
+            with torch.cuda.stream(cs):
+                for kk in KEYS + ("omega",):
+                    host_out[kk].copy_(stage[kk], non_blocking=True)
+            d2h_done = torch.cuda.Event()
+            d2h_done.record(cs)
+        es.wait_event(d2h_done)
+        e_end.record(es)
+        torch.cuda.synchronize()
+        e2e_ms = e_start.elapsed_time(e_end)
+        e2e = {"value": e2e_pairs / (e2e_ms / 1000.0), "unit": UNIT, "steps": e2e_steps,
+               "timed": "per step: H2D copies of the inputs + hydro_step + D2H copies of the state, "
+                        "pipelined: the inputs arrive in a device staging copy on a copy es "
+                        "during the previous step and the state leaves from one during the next "
+                        "(device-to-device copies into and out of the step's arrays); the first "
+                        "H2D and the last D2H inside the timed region",
+               "h2d_bytes_per_step": 8 * n * len(KEYS), "d2h_bytes_per_step": 8 * n * (len(KEYS) + 1),
+               "ms_per_step": e2e_ms / e2e_steps,
+               "sequential": {"value": seq_pairs / (seq_ms / 1000.0), "ms_per_step": seq_ms / e2e_steps},
+               "one_sequential_step_ms": phases}
     del host, host_out, st2, stage, in_stage
 
     # ---- the mixed step once more from the initial state, dt fixed (outside
