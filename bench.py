@@ -658,7 +658,7 @@ def main():
     with torch.cuda.stream(es):
         host = {k: torch.as_tensor(w[k]).pin_memory() for k in KEYS}
         host_out = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in KEYS + ("omega",)}
-        e2e_steps = min(args.steps, 3) if big else args.steps
+        e2e_steps = args.steps
         st2 = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
         stage = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in KEYS + ("omega",)}
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]

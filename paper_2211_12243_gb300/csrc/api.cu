@@ -319,6 +319,8 @@ int hydro_create(hydro_ctx **out, const hydro_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_cnt, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_cnt, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_learn, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_bad, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&c->d_bad, c->h_bad, 0);
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, sizeof(DevCounters));
     if (e == cudaSuccess) e = ensure_sum_partials(c);
     if (e == cudaSuccess) {
@@ -340,6 +342,7 @@ void hydro_destroy(hydro_ctx *c) {
     if (c->d_cnt) cudaFree(c->d_cnt);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_learn) cudaFreeHost(c->h_learn);
+    if (c->h_bad) cudaFreeHost(c->h_bad);
     if (c->have_events)
         for (int k = 0; k < 10; k++) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -511,11 +514,10 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
 // every value of the caller's state finite, checked before anything runs
 // (a non-finite input returns HYDRO_ENONFINITE and changes nothing)
 static int check_inputs(hydro_ctx *c, const hydro_particles *p, cudaStream_t st) {
+    *(volatile int *)c->h_bad = 0;   // (no earlier check is in flight: each one was waited for)
     API_CUDA(run_check_inputs(c, p, st));
-    int bad = 0;
-    API_CUDA(cudaMemcpyAsync(&bad, &c->d_cnt->bad_input, sizeof(int), cudaMemcpyDeviceToHost, st));
     API_CUDA(cudaStreamSynchronize(st));
-    return bad ? HYDRO_ENONFINITE : HYDRO_OK;
+    return *(volatile int *)c->h_bad ? HYDRO_ENONFINITE : HYDRO_OK;
 }
 
 int hydro_step(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *stats,

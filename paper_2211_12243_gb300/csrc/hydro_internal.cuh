@@ -98,7 +98,6 @@ struct DevCounters {
     int rung_max;                     // the deepest rung
     int rung_capped;                  // particles the criteria wanted beyond max_rung
     unsigned long long rung_active;   // particles starting a step in this sub-step
-    int bad_input;                    // a non-finite value in the caller's state
     int nredo;                        // particles a guard round recomputes the gradients of
     int redo_cursor;                  // the guard round's gradient warps' place in theirs
     int solve_cursor;                 // the guard round's density warps' place in the guard list
@@ -267,6 +266,10 @@ struct hydro_ctx {
     // device counters + pinned host mirror
     hyd::DevCounters *d_cnt = nullptr;
     hyd::DevCounters *h_cnt = nullptr;
+    // the input check's flag in mapped host memory: the check kernel writes it
+    // and the host reads it after the kernel, with no copy (a copy would queue
+    // behind whatever the caller's copy streams are moving)
+    int *h_bad = nullptr, *d_bad = nullptr;
     int pending_status = 0;
 
     hydro_stats last_stats;

@@ -101,7 +101,9 @@ __global__ void k_update(UpdArgs a) {
 }
 
 // every value of the caller's state finite (positions, conserved
-// quantities, smoothing lengths); a bad one sets bad_input
+// quantities, smoothing lengths); a bad one sets *bad (a flag in mapped
+// host memory, cleared by the host before the launch: a plain store, the
+// same value from every block that finds one)
 __global__ void k_check_inputs(int64_t n, hydro_particles p, int *bad) {
     const double *arr[10] = {p.x, p.y, p.z, p.mass, p.px, p.py, p.pz, p.etot, p.eint, p.h};
     bool ok = true;
@@ -110,7 +112,7 @@ __global__ void k_check_inputs(int64_t n, hydro_particles p, int *bad) {
 #pragma unroll
         for (int q = 0; q < 10; q++) ok = ok && isfinite(arr[q][i]);
     }
-    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(bad, 1);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) *(volatile int *)bad = 1;
 }
 
 // totals in plain double with a fixed order (no atomics): each thread sums
@@ -233,9 +235,8 @@ cudaError_t run_sums(hydro_ctx *c, int which, stream_t st) {
 }
 
 cudaError_t run_check_inputs(hydro_ctx *c, const hydro_particles *p, stream_t st) {
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->bad_input, 0, sizeof(int), st));
     const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>((p->n + 255) / 256, 1), SUM_BLOCKS);
-    k_check_inputs<<<grid, 256, 0, st>>>(p->n, *p, &c->d_cnt->bad_input);
+    k_check_inputs<<<grid, 256, 0, st>>>(p->n, *p, c->d_bad);
     return launch_check();
 }
 
