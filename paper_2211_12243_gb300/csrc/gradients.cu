@@ -13,6 +13,7 @@
 // record array (the first 40 B of the line in float).
 #include "hydro_internal.cuh"
 #include "pairgeom.cuh"
+#include "riemann.cuh"
 #include "tile_rank.cuh"
 
 namespace hyd {
@@ -87,7 +88,7 @@ __device__ __forceinline__ void grad_one(const GradArgs &a, R *__restrict__ rec,
         const R norm = kernel_norm<R>(a.kernel, h);
         const R fi[5] = {ri[R_RHO], ri[R_VX], ri[R_VY], ri[R_VZ], ri[R_P]};
         const R g = (R)a.gamma;
-        const R ci = sqrt(g * ri[R_P] / ri[R_RHO]);
+        const R ci = sqrt_(div_(g * ri[R_P], ri[R_RHO]));
         R E[6] = {0, 0, 0, 0, 0, 0};
         R S[5][3];
         R fmx[5], fmn[5];
@@ -118,7 +119,7 @@ __device__ __forceinline__ void grad_one(const GradArgs &a, R *__restrict__ rec,
             rec_sep(ri, rj, bx, d, r2);
             if (!mem(r2, j)) continue;
             mypairs++;
-            R r = sqrt(r2);
+            R r = sqrt_(r2);
             R w = rj[R_OM] * norm * kernel_shape<R>(a.kernel, r * ih);
             E[0] += w * d[0] * d[0];
             E[1] += w * d[0] * d[1];
@@ -136,9 +137,9 @@ __device__ __forceinline__ void grad_one(const GradArgs &a, R *__restrict__ rec,
                 fmx[f] = fj[f] > fmx[f] ? fj[f] : fmx[f];
                 fmn[f] = fj[f] < fmn[f] ? fj[f] : fmn[f];
             }
-            R cj = sqrt(g * rj[R_P] / rj[R_RHO]);
-            R wdot = (d[0] * (rj[R_VX] - ri[R_VX]) + d[1] * (rj[R_VY] - ri[R_VY]) +
-                      d[2] * (rj[R_VZ] - ri[R_VZ])) / r;
+            R cj = sqrt_(div_(g * rj[R_P], rj[R_RHO]));
+            R wdot = div_(d[0] * (rj[R_VX] - ri[R_VX]) + d[1] * (rj[R_VY] - ri[R_VY]) +
+                          d[2] * (rj[R_VZ] - ri[R_VZ]), r);
             R sig = ci + cj - (wdot < R(0) ? wdot : R(0));
             vs = sig > vs ? sig : vs;
         }

@@ -361,7 +361,7 @@ cudaError_t compact_flags(int64_t n, const uint8_t *active, uint8_t bits, int32_
 // wait): the queued overflow buckets, and the re-search rebuild
 cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st);
 cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st, bool guard = false);
-cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st);
+cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st, bool only_search = false);
 cudaError_t export_lists(hydro_ctx *c, hydro_nbrlist *out, stream_t st);
 
 // density.cu

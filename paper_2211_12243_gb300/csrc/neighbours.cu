@@ -494,10 +494,14 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_build_lists(ListArgs a) 
 // the same order as a bucket rebuild would give it.  mode 1 counts and
 // reserves storage in the overflow region (flagging ST_LIST_CAPACITY when it
 // does not fit), mode 2 writes.  Warps stride over the *npidx particles of
-// pidx (the count is read on the device).
+// pidx (the count is read on the device); with `active` set, only those
+// with an ACT_SOLVE flag (a guard round's re-search: the guard particles
+// whose root left their radius), and mode 1 clears the search-failure flag
+// that the new lists answer.
 struct PartListArgs {
     const int32_t *pidx;
     const int *npidx;
+    const uint8_t *active;
     const int32_t *node_first, *node_cnt, *box_root, *pbox;
     int64_t nbucket_total;
     const uint4 *lo, *hi;
@@ -520,8 +524,11 @@ __global__ void __launch_bounds__(PL_WARPS * 32) k_particle_lists(PartListArgs a
     int32_t *stack = stack_all[warp];
     const int np = *a.npidx;
     const int nwarps = gridDim.x * PL_WARPS;
+    if (a.active && a.mode == 1 && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAnd(&a.cnt->flags, ~ST_SEARCH);
     for (int g = blockIdx.x * PL_WARPS + warp; g < np; g += nwarps) {
         const int s = a.pidx[g];
+        if (a.active && !(a.active[s] & ACT_SOLVE)) continue;   // (warp-uniform: one particle)
         const Box bx = a.boxes[a.pbox[s]];
         const uint32_t px = a.qx[s], py = a.qy[s], pz = a.qz[s];
         const double x = a.xs[s], y = a.ys[s], z = a.zs[s], hs = a.hs[s];
@@ -939,6 +946,8 @@ cudaError_t build_lists_queued_dev(hydro_ctx *c, stream_t st) {
 }
 
 cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st, bool guard) {
+    // (in a guard round only guard particles can have left their radius)
+    if (guard) return guard_particle_lists(c, st, true);
     const Plan &P = c->plan;
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
     k_queue_active<<<std::min(grid_for(P.nbucket * 32, 256), SWEEP_GRID), 256, 0, st>>>(
@@ -954,6 +963,10 @@ cudaError_t rebuild_active_lists_dev(hydro_ctx *c, stream_t st, bool guard) {
 // whose search radius grew; every other list stays as it is.  *nq receives
 // the number of buckets rebuilt (the host waits for it).
 cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st, bool guard) {
+    if (guard) {
+        *nq = 0;   // (no bucket rebuilt: the re-searched particles' own lists)
+        return guard_particle_lists(c, st, true);
+    }
     const Plan &P = c->plan;
     HYD_CUDA(c->d_ovf.ensure(P.nbucket));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ovf_buckets, 0, sizeof(int), st));
@@ -964,19 +977,23 @@ cudaError_t rebuild_active_lists(hydro_ctx *c, int *nq, stream_t st, bool guard)
     HYD_CUDA(cudaMemcpyAsync(nq, &c->d_cnt->ovf_buckets, sizeof(int), cudaMemcpyDeviceToHost, st));
     HYD_CUDA(cudaStreamSynchronize(st));
     if (*nq == 0) return cudaSuccess;
-    // the buckets' search radii changed (in a guard round: the guard particles')
-    HYD_CUDA(guard ? raise_tree(c, st) : build_tree(c, st));
+    // the buckets' search radii changed
+    HYD_CUDA(build_tree(c, st));
     return build_lists_queued(c, *nq, st);
 }
 
 // new lists, in the overflow region, for the particles of guard_idx (the
-// guard round's grown particles, count nguard on the device); the tree must
-// hold the current positions (its search radii are not used)
-cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st) {
+// guard round's grown particles, count nguard on the device; only_search:
+// only those flagged ACT_SOLVE by the re-search); the tree must hold the
+// current positions (its search radii are not used).  Every other list
+// stays as it is, compacted or not: a bucket rebuild would give the
+// re-searched particles the same lists.
+cudaError_t guard_particle_lists(hydro_ctx *c, stream_t st, bool only_search) {
     const Plan &P = c->plan;
     PartListArgs a;
     a.pidx = c->d_guard_idx.get();
     a.npidx = &c->d_cnt->nguard;
+    a.active = only_search ? c->d_active.get() : nullptr;
     a.node_first = c->d_node_first.get();
     a.node_cnt = c->d_node_cnt.get();
     a.box_root = c->d_box_root.get();
