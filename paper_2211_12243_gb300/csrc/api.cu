@@ -646,7 +646,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
             rc = density_all(c, p, !first || k > 0, rebuilds, st, !first);
             if (rc) return rc;
             API_CUDA(run_primitives(c, st, !first));
-            API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
+            API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st, false));
             API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
                                      cudaMemcpyDeviceToHost, st));
             API_CUDA(cudaStreamSynchronize(st));
@@ -657,6 +657,7 @@ static int rungs_impl(hydro_ctx *c, hydro_particles *p, double dt0, int32_t *run
             if (rc) return rc;
             rounds++;
         }
+        API_CUDA(grad_reduce(c, st));
         if (k == 0) {
             // rungs (§2.3.10): criteria, then the limiter to its fixed point
             API_CUDA(rung_assign(c, dt0, st));
@@ -775,7 +776,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
         // a guard round recomputes the primitives of its re-solved particles
         // and only the gradients their new densities change
         API_CUDA(run_primitives(c, st, !first));
-        API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st));
+        API_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, !first, st, false));
         API_CUDA(cudaMemcpyAsync(&ncond_fail, &c->d_cnt->ncond_fail, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
         API_CUDA(cudaStreamSynchronize(st));
@@ -786,6 +787,7 @@ static int step_impl(hydro_ctx *c, hydro_particles *p, double dt, hydro_stats *s
         if (rc) return rc;
         rounds++;
     }
+    API_CUDA(grad_reduce(c, st));
     if (timing) API_CUDA(record_event(c->ev[3], st));
     const double *dt_dev = dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);
     c->timing = timing;

@@ -486,14 +486,12 @@ __global__ void k_entropy_route(int64_t n, const int64_t *__restrict__ nbr_off,
 
 constexpr double GUARD_SEARCH = 2.0;
 
-// N_NGB *= grow for particles that failed the N_cond check; they (only)
-// get their density solved again
-__global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__restrict__ nngb,
-                             double grow, int32_t *__restrict__ guard_idx, int *__restrict__ nguard,
-                             double *__restrict__ hs, const double *__restrict__ h,
-                             const int32_t *__restrict__ pbox, const Box *__restrict__ boxes) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= n) return;
+__device__ __forceinline__ void grow_one(int64_t s, uint8_t *__restrict__ active,
+                                         double *__restrict__ nngb, double grow,
+                                         int32_t *__restrict__ guard_idx, int *__restrict__ nguard,
+                                         double *__restrict__ hs, const double *__restrict__ h,
+                                         const int32_t *__restrict__ pbox,
+                                         const Box *__restrict__ boxes) {
     uint8_t a = active[s];
     if (a & ACT_NCOND) {
         nngb[s] *= grow;
@@ -509,6 +507,24 @@ __global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__
     } else {
         active[s] = 0;
     }
+}
+
+// N_NGB *= grow for particles that failed the N_cond check; they (only)
+// get their density solved again.  After a guard round's gradient pass the
+// flags can be set only on the particles it recomputed (its redo list,
+// which holds the round's guard particles): then only those are visited;
+// after the full pass, every particle.
+__global__ void k_guard_grow(int64_t n, uint8_t *__restrict__ active, double *__restrict__ nngb,
+                             double grow, int32_t *__restrict__ guard_idx, int *__restrict__ nguard,
+                             double *__restrict__ hs, const double *__restrict__ h,
+                             const int32_t *__restrict__ pbox, const Box *__restrict__ boxes,
+                             const int32_t *__restrict__ redo_idx, const DevCounters *cnt) {
+    const bool redo = cnt->redo_pass;
+    const int64_t m = redo ? (int64_t)cnt->nredo : n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        grow_one(redo ? (int64_t)redo_idx[t] : t, active, nngb, grow, guard_idx, nguard, hs, h,
+                 pbox, boxes);
 }
 
 // caller's B, grad, alpha (already gathered to sorted SoA staging) into
@@ -606,8 +622,18 @@ cudaError_t gather_gravity(hydro_ctx *c, stream_t st) {
     return gather_from_caller(c->d_perm.get(), c->grav, n, 3, c->d_agrav.get(), n, st);
 }
 
+// the global CFL dt and the gradient pair count over every particle's
+// latest values (after the guard rounds, which only need N_cond)
+cudaError_t grad_reduce(hydro_ctx *c, stream_t st) {
+    const int64_t n = c->plan.n;
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
+    HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
+    k_grad_reduce<<<152 * 8, 256, 0, st>>>(n, c->d_vsig_dt.get(), c->d_gpairs.get(), c->d_cnt);
+    return launch_check();
+}
+
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
-                          double *ncond_out, bool only_redo, stream_t st) {
+                          double *ncond_out, bool only_redo, stream_t st, bool reduce) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_vsig_dt.ensure(n));
     HYD_CUDA(c->d_gpairs.ensure(n));
@@ -659,8 +685,8 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         smem = 0;
     }
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->ncond_fail, 0, sizeof(int), st));
-    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->grad_pairs, 0, sizeof(unsigned long long), st));
-    HYD_CUDA(set_u64(&c->d_cnt->dt_min_bits, 0x7FF0000000000000ull, st));   // +inf
+    // (non-zero bytes for a redo pass: the next guard growth reads the flag)
+    HYD_CUDA(cudaMemsetAsync(&c->d_cnt->redo_pass, only_redo ? 1 : 0, sizeof(int), st));
     const bool lean = !a.outB && !a.outG && !a.outA && !a.outN && !a.ract;
     if (c->cfg.precision == HYDRO_MIXED) {
         float *r = c->d_recf.get();
@@ -690,17 +716,18 @@ cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double 
         }
     }
     HYD_CUDA(launch_check());
-    k_grad_reduce<<<152 * 8, 256, 0, st>>>(n, a.dt_part, a.npair, c->d_cnt);
-    return launch_check();
+    return reduce ? grad_reduce(c, st) : cudaSuccess;
 }
 
 cudaError_t guard_grow(hydro_ctx *c, stream_t st) {
     const int64_t n = c->plan.n;
     HYD_CUDA(c->d_guard_idx.ensure(n));
     HYD_CUDA(cudaMemsetAsync(&c->d_cnt->nguard, 0, sizeof(int), st));
-    k_guard_grow<<<grid_for(n, 256), 256, 0, st>>>(
+    HYD_CUDA(c->d_redo_idx.ensure(n));
+    k_guard_grow<<<std::min(grid_for(n, 256), SWEEP_GRID), 256, 0, st>>>(
         n, c->d_active.get(), c->d_nngb.get(), c->cfg.ngb_grow, c->d_guard_idx.get(),
-        &c->d_cnt->nguard, c->d_hs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get());
+        &c->d_cnt->nguard, c->d_hs.get(), c->d_hsorted.get(), c->d_pbox.get(), c->d_boxes.get(),
+        c->d_redo_idx.get(), c->d_cnt);
     return launch_check();
 }
 

@@ -131,7 +131,7 @@ cudaError_t guard_body(hydro_ctx *c, cudaStream_t s, cudaGraphConditionalHandle 
     HYD_CUDA(run_density(c, true, true, s, true));
     HYD_CUDA(search_loop(c, 2, s));
     HYD_CUDA(run_primitives(c, s, true));
-    HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, true, s));
+    HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, true, s, false));
     HYD_CUDA(cond_guard(c, s, h));
     c->cap_k_guard = launch_count() - k0 - c->cap_k_search;   // its re-search body runs per round
     return cudaSuccess;
@@ -156,13 +156,14 @@ cudaError_t enqueue_step(hydro_ctx *c, hydro_particles *p, double dt, bool sums,
     HYD_CUDA(search_loop(c, 1, st));
     if (timing) HYD_CUDA(record_event(c->ev[2], st));
     HYD_CUDA(run_primitives(c, st));
-    HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, false, st));
+    HYD_CUDA(run_gradients(c, nullptr, nullptr, nullptr, nullptr, false, st, false));
     // the tree with the solved h and search radii: the guard rounds only
     // raise its radius bounds for their particles
     HYD_CUDA(build_tree(c, st));
     HYD_CUDA(capture_while(
         c, 1, st, [&](cudaStream_t s, cudaGraphConditionalHandle h) { return cond_guard(c, s, h); },
         [&](cudaStream_t s, cudaGraphConditionalHandle h) { return guard_body(c, s, h); }));
+    HYD_CUDA(grad_reduce(c, st));
     if (timing) HYD_CUDA(record_event(c->ev[3], st));
     const double *dt_dev =
         dt > 0.0 ? nullptr : reinterpret_cast<const double *>(&c->d_cnt->dt_min_bits);

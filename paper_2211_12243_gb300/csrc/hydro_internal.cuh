@@ -101,6 +101,8 @@ struct DevCounters {
     int nredo;                        // particles a guard round recomputes the gradients of
     int redo_cursor;                  // the guard round's gradient warps' place in theirs
     int solve_cursor;                 // the guard round's density warps' place in the guard list
+    int redo_pass;                    // the last gradient pass took only the redo list (1) or
+                                      // every particle (0): where flags can be set
     unsigned long long flux_cursor;   // the flux kernel's bucket queue
 };
 
@@ -399,8 +401,11 @@ cudaError_t rung_scatter(hydro_ctx *c, stream_t st);
 cudaError_t queue_flagged(hydro_ctx *c, uint8_t bits, stream_t st);
 // only_redo: recompute only the particles whose list holds a particle that
 // the guard re-solved (ACT_GUARD), keeping every other particle's results
+// reduce: also the global dt and pair count (grad_reduce); the step's
+// guard loops take them once, after their last round
 cudaError_t run_gradients(hydro_ctx *c, double *B_out, double *grad_out, double *alpha_out,
-                          double *ncond_out, bool only_redo, stream_t st);
+                          double *ncond_out, bool only_redo, stream_t st, bool reduce = true);
+cudaError_t grad_reduce(hydro_ctx *c, stream_t st);
 cudaError_t guard_grow(hydro_ctx *c, stream_t st);
 cudaError_t load_gradients(hydro_ctx *c, const double *B, const double *grad,
                            const double *alpha, stream_t st);

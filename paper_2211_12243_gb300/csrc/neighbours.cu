@@ -775,21 +775,42 @@ k_mark_reverse(const int32_t *__restrict__ guard_idx, const int *__restrict__ ng
 // costs about as much as the walks of n / MARK_SCAN_RATIO guard particles:
 // each kernel reads the round's guard count on the device and only one of
 // them works (the first round grows many particles, the later ones few).
+// Eight lanes read a list together, eight consecutive entries (one 32-byte
+// sector) at a time, so a warp scans four lists at once with whole-sector
+// reads rather than one scattered entry per lane.
+constexpr int MARK_GROUP = 8;
+
 __global__ void __launch_bounds__(256)
 k_mark_by_lists(int64_t n, const int *__restrict__ nguard, const int64_t *__restrict__ nbr_off,
                 const int32_t *__restrict__ nbr_cnt, const int32_t *__restrict__ nbr_idx,
                 const uint32_t *__restrict__ gbits, uint8_t *__restrict__ active) {
     if (!mark_by_scan(*nguard, n)) return;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = nbr_off[s];
-        const int c = nbr_cnt[s];
-        bool hit = (gbits[s >> 5] >> (s & 31)) & 1u;   // (a guard particle marks itself)
-        for (int k = 0; k < c && !hit; k++) {
-            const int j = nbr_idx[o + k];
-            hit = (gbits[j >> 5] >> (j & 31)) & 1u;
+    constexpr int PER_WARP = 32 / MARK_GROUP;
+    const int lane = threadIdx.x & 31, sub = lane & (MARK_GROUP - 1);
+    const unsigned gmask = ((1u << MARK_GROUP) - 1u) << (lane & ~(MARK_GROUP - 1));
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s0 = w * PER_WARP; s0 < n; s0 += nw * PER_WARP) {
+        const int64_t s = s0 + lane / MARK_GROUP;
+        int64_t o = 0;
+        int c = 0;
+        bool hit = false;
+        if (s < n) {
+            o = nbr_off[s];
+            c = nbr_cnt[s];
+            hit = (gbits[s >> 5] >> (s & 31)) & 1u;   // (a guard particle marks itself)
         }
-        if (hit) active[s] |= ACT_REDO;
+        const int cmax = __reduce_max_sync(0xffffffffu, hit ? 0 : c);
+        for (int k0 = 0; k0 < cmax; k0 += MARK_GROUP) {
+            bool h = false;
+            if (!hit && k0 + sub < c) {
+                const int j = nbr_idx[o + k0 + sub];
+                h = (gbits[j >> 5] >> (j & 31)) & 1u;
+            }
+            hit |= (__ballot_sync(0xffffffffu, h) & gmask) != 0u;
+            if (__all_sync(0xffffffffu, hit || k0 + MARK_GROUP >= c)) break;
+        }
+        if (hit && sub == 0) active[s] |= ACT_REDO;
     }
 }
 
