@@ -413,19 +413,6 @@ __device__ __forceinline__ void load_hard(const FluxArgs &a, int64_t k, FaceStat
     j = a.hard_idx[c + k];
 }
 
-// float -> double from the bit pattern with integer operations only (the
-// conversion instruction runs on the FP64 pipe): exact for normal floats,
-// infinities and NaNs; zeros and subnormals (below 1.2e-38) become signed 0
-__device__ __forceinline__ double widen(float f) {
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t ex = (u >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-    const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
-    const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);
-    const unsigned long long b = ex == 0u ? sign : (sign | (e64 << 52) | man);
-    return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ double widen(double f) { return f; }
 
 // owner accumulators: float-float (value = hi + lo) in the mixed path
 struct AccF {

@@ -400,19 +400,24 @@ __global__ void k_primitives(int64_t n, const double *__restrict__ Q,
             r[R_P] = (R)pd;
             r[R_OM] = (R)w;
         } else {
-            // float record: only E - E_kin needs double (cancellation)
-            double im = 1.0 / m;
+            // float record: only E - E_kin needs double (cancellation); 1/m
+            // from a float reciprocal and one Newton step in double (relative
+            // error ~1e-13) and the conversions to float by integer
+            // operations keep the work off the narrow FP64 pipe
+            const float mf = narrow(m);
+            double im = widen(__fdividef(1.f, mf));
+            im = fma(im, fma(-m, im, 1.0), im);
             double ekin = 0.5 * (px * px + py * py + pz * pz) * im;
             from = route(ekin);
             const double therm = from == 0 ? E - ekin : U;
-            float wf = (float)w, imf = (float)im;
-            r[R_H] = (R)h[s];
-            r[R_RHO] = (R)((float)m / wf);
-            r[R_VX] = (R)((float)px * imf);
-            r[R_VY] = (R)((float)py * imf);
-            r[R_VZ] = (R)((float)pz * imf);
+            const float wf = narrow(w), imf = narrow(im);
+            r[R_H] = (R)narrow(h[s]);
+            r[R_RHO] = (R)(mf / wf);
+            r[R_VX] = (R)(narrow(px) * imf);
+            r[R_VY] = (R)(narrow(py) * imf);
+            r[R_VZ] = (R)(narrow(pz) * imf);
             r[R_OM] = (R)wf;
-            r[R_P] = (R)((float)therm * (float)gm1 / wf);
+            r[R_P] = (R)(narrow(therm) * narrow(gm1) / wf);
             if (ent.A1) pd = therm * gm1 / w;
         }
         if (ent.A1) {

@@ -508,6 +508,36 @@ __device__ __forceinline__ float i2f_small(int32_t k) {
     return __int_as_float(0x4B400000 + k) - 12582912.0f;
 }
 
+// float -> double from the bit pattern with integer operations only (the
+// conversion instruction runs on the FP64 pipe): exact for normal floats,
+// infinities and NaNs; zeros and subnormals (below 1.2e-38) become signed 0
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long e64 = ex == 0xffu ? 0x7ffull : (unsigned long long)(ex + 896u);
+    const unsigned long long b = ex == 0u ? sign : (sign | (e64 << 52) | man);
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
+// double -> float rounded to nearest even with integer operations only
+// (the conversion instruction runs on the FP64 pipe); results outside the
+// normal float exponents 1..253 (zeros, subnormals, the largest floats,
+// infinities, NaNs) take the conversion instruction
+__device__ __forceinline__ float narrow(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex - 897u >= 253u) return (float)d;
+    const uint32_t keep = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the top 23 of 52 bits
+    const uint32_t rest = lo & 0x1fffffffu;                      // the 29 dropped
+    uint32_t b = ((ex - 896u) << 23) + keep;   // (a carry out of keep moves the exponent)
+    b += rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u));
+    return __uint_as_float(b | (hi & 0x80000000u));
+}
+
 // minimum-image separation b - a of two fixed-point coordinates, times the
 // unit s: the 32-bit difference split as hi * 2^11 + lo, each part exact
 __device__ __forceinline__ float qdiff(uint32_t a, uint32_t b, float s) {
