@@ -270,51 +270,49 @@ __device__ __forceinline__ StarOut star_solve(const GasK<R> &k, R rl, R ul, R pl
     return o;
 }
 
-// state at x/t = 0 of the exact solution; side = -1 left of the contact
+// state at x/t = 0 of the exact solution; side = -1 left of the contact.
+// The side the contact leaves at x/t = 0 is sampled as a left side: a right
+// side enters with its velocities negated (u -> -u, which maps the right
+// waves onto left ones exactly, since rounding to nearest is symmetric) and
+// the sampled velocity is negated back, so the lanes of a warp follow one
+// branch tree whichever side each face samples.
 template <typename R>
 __device__ __forceinline__ void star_sample(const GasK<R> &k, R rl, R ul, R pl, R cl, R rr, R ur,
                                             R pr, R cr, R ps, R us, R &rho, R &u, R &p, int &side) {
-    if (R(0) <= us) {
-        side = -1;
-        if (ps > pl) {
-            R sl = ul - cl * sqrt_(k.g2 * div_(ps, pl) + k.z);
-            if (R(0) <= sl) { rho = rl; u = ul; p = pl; }
-            else { R t = div_(ps, pl); rho = rl * div_(t + k.g6, k.g6 * t + R(1)); u = us; p = ps; }
-        } else {
-            if (R(0) <= ul - cl) { rho = rl; u = ul; p = pl; }
-            else {
-                R t = div_(ps, pl);
-                R cml = cl * pow_(t, k.z);
-                if (R(0) > us - cml) { rho = rl * pow_(t, k.inv_g); u = us; p = ps; }
-                else {
-                    R cc = k.g5 + div_(k.g6, cl) * ul;
-                    rho = rl * pow_(cc, k.g4);
-                    u = k.g5 * (cl + R(0.5) * k.gm1 * ul);
-                    p = pl * pow_(cc, k.zi);
-                }
-            }
+    const bool left = R(0) <= us;
+    side = left ? -1 : 1;
+    const R rK = left ? rl : rr, pK = left ? pl : pr, cK = left ? cl : cr;
+    const R uK = left ? ul : -ur, uS = left ? us : -us;
+    R rs, vs, qs;
+    if (ps > pK) {
+        // shock: the pre-shock state beyond it, else the star state
+        const R sK = uK - cK * sqrt_(k.g2 * div_(ps, pK) + k.z);
+        if (R(0) <= sK) { rs = rK; vs = uK; qs = pK; }
+        else {
+            const R t = div_(ps, pK);
+            rs = rK * div_(t + k.g6, k.g6 * t + R(1));
+            vs = uS;
+            qs = ps;
         }
+    } else if (R(0) <= uK - cK) {
+        rs = rK; vs = uK; qs = pK;   // beyond the rarefaction's head
     } else {
-        side = 1;
-        if (ps > pr) {
-            R sr = ur + cr * sqrt_(k.g2 * div_(ps, pr) + k.z);
-            if (R(0) >= sr) { rho = rr; u = ur; p = pr; }
-            else { R t = div_(ps, pr); rho = rr * div_(t + k.g6, k.g6 * t + R(1)); u = us; p = ps; }
-        } else {
-            if (R(0) >= ur + cr) { rho = rr; u = ur; p = pr; }
-            else {
-                R t = div_(ps, pr);
-                R cmr = cr * pow_(t, k.z);
-                if (R(0) <= us + cmr) { rho = rr * pow_(t, k.inv_g); u = us; p = ps; }
-                else {
-                    R cc = k.g5 - div_(k.g6, cr) * ur;
-                    rho = rr * pow_(cc, k.g4);
-                    u = k.g5 * (-cr + R(0.5) * k.gm1 * ur);
-                    p = pr * pow_(cc, k.zi);
-                }
-            }
+        const R t = div_(ps, pK);
+        const R cm = cK * pow_(t, k.z);
+        // (a right side keeps its tail point in the star region)
+        const bool star = left ? R(0) > uS - cm : R(0) >= uS - cm;
+        if (star) { rs = rK * pow_(t, k.inv_g); vs = uS; qs = ps; }
+        else {
+            // inside the fan
+            const R cc = k.g5 + div_(k.g6, cK) * uK;
+            rs = rK * pow_(cc, k.g4);
+            vs = k.g5 * (cK + R(0.5) * k.gm1 * uK);
+            qs = pK * pow_(cc, k.zi);
         }
     }
+    rho = rs;
+    u = left ? vs : -vs;
+    p = qs;
 }
 
 // HLLC flux along n (face frame) with the pressure-based wave speeds.
