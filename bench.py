@@ -1030,7 +1030,7 @@ FACE_OPS = {
 # DRAM bytes (read + write) per face of the flux kernel, from one ncu capture
 # of the current kernel on a small case of the workload (profiles/); a
 # launch's traffic scales with its faces
-FLUX_TRAFFIC_BYTES_PER_FACE = {"sod": 28.57, "lognormal": 32.59}
+FLUX_TRAFFIC_BYTES_PER_FACE = {"sod": 28.56, "lognormal": 32.59}
 
 if __name__ == "__main__":
     sys.exit(main())
