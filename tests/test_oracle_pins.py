@@ -355,6 +355,65 @@ def test_exact_riemann_special_cases(orc):
         assert c["p"] == pytest.approx(a["p"], rel=1e-14)
 
 
+_SAMPLE_CASES = [(1.0, 0.0, 1.0, 0.125, 0.0, 0.1),      # rarefaction | shock
+                 (1.0, -2.0, 0.4, 1.0, 2.0, 0.4),      # two rarefactions
+                 (1.0, 1.5, 1.0, 0.5, -1.0, 2.0),      # two shocks
+                 (0.3, 0.2, 5.0, 1.0, 0.1, 0.2),       # strong left rarefaction
+                 (1.0, 0.75, 1.0, 0.125, 0.0, 0.1)]    # sonic left rarefaction
+
+
+@pytest.mark.parametrize("d", _SAMPLE_CASES)
+@pytest.mark.parametrize("g", [1.4, 5.0 / 3.0])
+def test_exact_riemann_sampling_is_mirror_symmetric(orc, d, g):
+    """Euler's equations are invariant under x -> -x, u -> -u: the problem
+    with its sides swapped and its velocities negated has the mirrored
+    solution.  Sampled at x/t = 0 in frames moving with V across every wave
+    (head, fan, tail, star regions, shocks), the mirrored problem's state is
+    the original's with u negated, the side flag swapped, so the oracle's
+    right-side branches agree with its left-side ones, which the star-state
+    and jump-condition pins above fix."""
+    rl, ul, pl, rr, ur, pr = d
+    r = orc.riemann_star(*d, g)
+    assert r["vacuum"] == 0
+    ps, us = r["p"], r["u"]
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+    lo, hi = min(ul - cl, us) - 1.0, max(ur + cr, us) + 1.0
+    for V in np.linspace(lo, hi, 97) + 1e-7:
+        a = orc.riemann_sample(rl, ul - V, pl, rr, ur - V, pr, g, ps, us - V)
+        b = orc.riemann_sample(rr, -(ur - V), pr, rl, -(ul - V), pl, g, ps, -(us - V))
+        assert b[0] == pytest.approx(a[0], rel=1e-13)
+        assert b[1] == pytest.approx(-a[1], rel=1e-13, abs=1e-13)
+        assert b[2] == pytest.approx(a[2], rel=1e-13)
+        assert b[3] == -a[3]
+
+
+@pytest.mark.parametrize("g", [1.4, 5.0 / 3.0])
+def test_exact_riemann_fan_interior(orc, g):
+    """Inside a rarefaction fan the state at x/t = 0 is the sonic point of
+    the characteristic through the origin: u - c = 0 for a left fan (u + c
+    = 0 for a right one), with the entropy p / rho^g and the Riemann
+    invariant u + 2c/(g-1) (u - 2c/(g-1)) of the unperturbed side."""
+    rl, ul, pl, rr, ur, pr = 1.0, -2.0, 0.4, 1.0, 2.0, 0.4   # two rarefactions
+    r = orc.riemann_star(rl, ul, pl, rr, ur, pr, g)
+    ps, us = r["p"], r["u"]
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+    csl = cl * (ps / pl) ** ((g - 1) / (2 * g))
+    csr = cr * (ps / pr) ** ((g - 1) / (2 * g))
+    for sgn, (head, tail), (rk, uk, pk, ck) in (
+            (-1, (ul - cl, us - csl), (rl, ul, pl, cl)),
+            (1, (us + csr, ur + cr), (rr, ur, pr, cr))):
+        assert head < tail
+        for f in (0.2, 0.5, 0.8):
+            V = head + f * (tail - head)
+            rho, u, p, side = orc.riemann_sample(rl, ul - V, pl, rr, ur - V, pr, g, ps, us - V)
+            assert side == sgn
+            c = math.sqrt(g * p / rho)
+            assert u + sgn * c == pytest.approx(0.0, abs=1e-12)
+            assert p / rho ** g == pytest.approx(pk / rk ** g, rel=1e-12)
+            assert (u + V) - sgn * 2 * c / (g - 1) == pytest.approx(uk - sgn * 2 * ck / (g - 1),
+                                                                     rel=1e-12, abs=1e-12)
+
+
 def test_hllc_consistency(orc):
     g = 1.4
     n = np.array([0.6, 0.8, 0.0])
