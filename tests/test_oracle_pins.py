@@ -272,6 +272,44 @@ def test_limiter_bounds(orc):
             assert ext.min() >= 2.0 * (fmin - prims[f][i]) - 1e-12
 
 
+@pytest.mark.parametrize("frac,beta_max", [(0.9, 2.0), (-0.8, 2.0), (0.7, 1.0), (0.2, 2.0)])
+def test_limiter_closed_form_on_a_spike(orc, frac, beta_max):
+    """The conditioned Barth-Jespersen limiter (§2.3.6) in closed form: on a
+    perfect lattice (N_cond = 1, so beta = beta_max) a linear pressure
+    p = p0 + a x with a spike delta = frac M at one particle i (M = max_j a dx_j
+    over i's neighbours).  The neighbourhood is point-symmetric, so the
+    gradient at i is a exactly (the spike cancels), the midpoint
+    extrapolations reach +-M/2, and the neighbour extremes are +-M - delta:
+    alpha = min(1, beta min((M - delta) / (M/2), (M + delta) / (M/2)))."""
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config(beta_min=1.0, beta_max=beta_max)
+    x = np.stack([w["x"], w["y"], w["z"]], 1)
+    N = x.shape[0]
+    i = int(np.argmin(np.sum((x - 0.5 + 0.5 / n) ** 2, 1)))   # a central particle
+    a = 0.3
+    h0, _, _, _ = orc.density(cfg, w["x"], w["y"], w["z"], w["L"], w["h"])[:4]
+    d = x - x[i]
+    r = np.sqrt(np.sum(d * d, 1))
+    nb = (r < h0[i]) & (np.arange(N) != i)          # i's neighbours, by brute force
+    M = a * d[nb, 0].max()
+    assert M > 0 and np.isclose(d[nb, 0].min(), -d[nb, 0].max())
+    p = 3.0 + a * (x[:, 0] - x[i, 0])
+    p[i] += frac * M
+    rho = np.full(N, 1.5)
+    v = np.zeros((N, 3))
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, rho, v, p)
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    assert nc[i] == pytest.approx(1.0, rel=1e-12)
+    grad, alpha, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    assert np.abs(grad[i, 4] - np.array([a, 0.0, 0.0])).max() < 1e-10
+    delta = frac * M
+    expect = min(1.0, beta_max * min((M - delta) / (0.5 * M), (M + delta) / (0.5 * M)))
+    assert alpha[i, 4] == pytest.approx(expect, rel=1e-9)
+    assert np.all(alpha[i, :4] == 1.0)   # uniform density and velocity
+
+
 # --------------------------------------------------------------------------
 # Riemann solvers (§2.3.3): Toro's tables, jump conditions, invariants
 # --------------------------------------------------------------------------
