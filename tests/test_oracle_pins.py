@@ -272,18 +272,21 @@ def test_limiter_bounds(orc):
             assert ext.min() >= 2.0 * (fmin - prims[f][i]) - 1e-12
 
 
-@pytest.mark.parametrize("frac,beta_max", [(0.9, 2.0), (-0.8, 2.0), (0.7, 1.0), (0.2, 2.0)])
-def test_limiter_closed_form_on_a_spike(orc, frac, beta_max):
+@pytest.mark.parametrize("frac,beta_min,beta_max,ncrit",
+                         [(0.9, 1.0, 2.0, 100.0), (-0.8, 1.0, 2.0, 100.0), (0.7, 1.0, 1.0, 100.0),
+                          (0.2, 1.0, 2.0, 100.0), (0.9, 0.3, 2.0, 0.5), (0.9, 0.8, 2.0, 0.5)])
+def test_limiter_closed_form_on_a_spike(orc, frac, beta_min, beta_max, ncrit):
     """The conditioned Barth-Jespersen limiter (§2.3.6) in closed form: on a
-    perfect lattice (N_cond = 1, so beta = beta_max) a linear pressure
-    p = p0 + a x with a spike delta = frac M at one particle i (M = max_j a dx_j
-    over i's neighbours).  The neighbourhood is point-symmetric, so the
-    gradient at i is a exactly (the spike cancels), the midpoint
-    extrapolations reach +-M/2, and the neighbour extremes are +-M - delta:
+    perfect lattice (N_cond = 1, so beta = max(beta_min, beta_max
+    min(1, ncrit^2))) a linear pressure p = p0 + a x with a spike
+    delta = frac M at one particle i (M = max_j a dx_j over i's neighbours).
+    The neighbourhood is point-symmetric, so the gradient at i is a exactly
+    (the spike cancels), the midpoint extrapolations reach +-M/2, and the
+    neighbour extremes are +-M - delta:
     alpha = min(1, beta min((M - delta) / (M/2), (M + delta) / (M/2)))."""
     n = 12
     w = W.lattice_wave(n, jitter=0.0)
-    cfg = orc.config(beta_min=1.0, beta_max=beta_max)
+    cfg = orc.config(beta_min=beta_min, beta_max=beta_max, ncond_crit=ncrit)
     x = np.stack([w["x"], w["y"], w["z"]], 1)
     N = x.shape[0]
     i = int(np.argmin(np.sum((x - 0.5 + 0.5 / n) ** 2, 1)))   # a central particle
@@ -305,7 +308,8 @@ def test_limiter_closed_form_on_a_spike(orc, frac, beta_max):
     grad, alpha, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
     assert np.abs(grad[i, 4] - np.array([a, 0.0, 0.0])).max() < 1e-10
     delta = frac * M
-    expect = min(1.0, beta_max * min((M - delta) / (0.5 * M), (M + delta) / (0.5 * M)))
+    beta = max(beta_min, beta_max * min(1.0, ncrit ** 2))
+    expect = min(1.0, beta * min((M - delta) / (0.5 * M), (M + delta) / (0.5 * M)))
     assert alpha[i, 4] == pytest.approx(expect, rel=1e-9)
     assert np.all(alpha[i, :4] == 1.0)   # uniform density and velocity
 
