@@ -491,6 +491,22 @@ def test_pair_limiter_bounds(orc):
         # values inside [own, mean] are untouched
         if min(a, 0.5 * (a + b)) <= e <= max(a, 0.5 * (a + b)):
             assert out == e
+    # the ends of the allowed range are reached: an extrapolation far past the
+    # neighbour stops at mean + psi2 d (mean - psi2 d), one far behind the own
+    # value at own - psi1 d (own + psi1 d); in between the result does not
+    # decrease with the extrapolation
+    for _ in range(500):
+        a, b = rng.uniform(-2, 2, 2)
+        d = abs(a - b)
+        if d < 1e-6:
+            continue
+        s = 1.0 if a < b else -1.0
+        mean = 0.5 * (a + b)
+        assert orc.pair_limit(b + s * 10 * d, a, b) == pytest.approx(mean + s * 0.25 * d, rel=1e-14, abs=1e-14)
+        assert orc.pair_limit(a - s * 10 * d, a, b) == pytest.approx(a - s * 0.5 * d, rel=1e-14, abs=1e-14)
+        es = np.sort(rng.uniform(-4, 4, 64))
+        outs = np.array([orc.pair_limit(e, a, b) for e in es])
+        assert np.all(np.diff(outs) >= -1e-15)
     # positive quantities stay positive
     assert orc.pair_limit(-1.0, 0.1, 5.0, positive=True) > 0.0
     for _ in range(500):
