@@ -119,6 +119,9 @@ def lib():
         L.orc_fluxes.restype = None
         L.orc_fluxes.argtypes = ([P(Config), i64] + [vp] * 14 + [d, i64, vp, vp, vp,
                                  P(FluxStats), vp, vp, vp, vp, vp])
+        L.orc_fluxes_rung.restype = None
+        L.orc_fluxes_rung.argtypes = ([P(Config), i64] + [vp] * 16 + [i64, vp, vp,
+                                      P(FluxStats), vp])
         L.orc_riemann_guess.restype = d
         L.orc_riemann_guess.argtypes = [d] * 7
         L.orc_riemann_star.restype = i32
@@ -294,6 +297,26 @@ def fluxes(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dt, pairs=None,
                      _p(dM), _p(AA), _p(dS))
     out = (dQ, st.as_dict(), faces) + ((dQabs,) if want_abs else ()) + ((dM,) if want_dM else ())
     return out + ((dS,) if A is not None else ())
+
+
+def fluxes_rung(cfg, x, y, z, L, h, omega, B6, prims, grad, alpha, dtp, toff, pairs):
+    """The face arithmetic of an individual-timestep sub-step (§2.3.4): the
+    face (i, j) exchanges over dt_ij = min(dtp_i, dtp_j) and predicts each
+    side over toff + dt_ij / 2.  Returns (dQ[n,6], stats, faces[npairs,9]) as
+    fluxes(..., want_faces=True)."""
+    x, y, z, L, h, omega, B6 = map(_f64, (x, y, z, L, h, omega, B6))
+    grad, alpha, dtp, toff = map(_f64, (grad, alpha, dtp, toff))
+    rho, vx, vy, vz, p = map(_f64, prims)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int64)
+    n = x.size
+    dQ = np.zeros((n, 6))
+    st = FluxStats()
+    faces = np.zeros((pairs.shape[0], 9))
+    lib().orc_fluxes_rung(C.byref(cfg), n, _p(x), _p(y), _p(z), _p(L), _p(h), _p(omega),
+                          _p(B6), _p(rho), _p(vx), _p(vy), _p(vz), _p(p), _p(grad), _p(alpha),
+                          _p(dtp), _p(toff), pairs.shape[0], _p(pairs), _p(dQ), C.byref(st),
+                          _p(faces))
+    return dQ, st.as_dict(), faces
 
 
 OP_KEYS = ("add", "mul", "div", "sqrt", "pow", "cmp", "fabs", "faces", "newton_iters")

@@ -25,8 +25,9 @@
  *   - Smoothing length: safeguarded Newton on Eq. 18 with bisection fallback.
  *   - N_cond > crit  =>  N_NGB,i *= grow, density redone for i (§2.3.5).
  *   - Conditioned Barth-Jespersen limiter and pairwise limiter: the forms of
- *     Hopkins (2015) eqs. B3 and B4 that §2.3.6 cites (parity unpinned:
- *     the paper does not print them).
+ *     Hopkins (2015) eqs. B3 and B4 that §2.3.6 cites (a reading: the paper
+ *     does not print them; the tests pin these forms by closed forms and
+ *     invariants).
  *   - Half-step predictor in the particle (Lagrangian) frame.
  *   - Riemann: exact (Toro 2009) with Toro's adaptive initial guess, or HLLC.
  */
@@ -1185,6 +1186,21 @@ void orc_fluxes(const orc_config *c, int64_t n, const double *x, const double *y
 {
     orc_fluxes_impl(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, dt, NULL,
                     NULL, npairs, pairs, pair_guess, dQ, st, face_out, dQabs, dM, A, dS);
+}
+
+/* The face arithmetic of a rung sub-step on its own, for the tests: dtp[i]
+ * the particle's step and toff[i] the time since its state was taken (the
+ * impl's individual-timestep form below; dQ, stats and face states as in
+ * orc_fluxes). */
+void orc_fluxes_rung(const orc_config *c, int64_t n, const double *x, const double *y,
+                     const double *z, const double *L, const double *h, const double *omega,
+                     const double *B6, const double *rho, const double *vx, const double *vy,
+                     const double *vz, const double *p, const double *grad, const double *alpha,
+                     const double *dtp, const double *toff, int64_t npairs,
+                     const int64_t *pairs, double *dQ, orc_flux_stats *st, double *face_out)
+{
+    orc_fluxes_impl(c, n, x, y, z, L, h, omega, B6, rho, vx, vy, vz, p, grad, alpha, 0.0, dtp,
+                    toff, npairs, pairs, NULL, dQ, st, face_out, NULL, NULL, NULL, NULL);
 }
 
 /* orc_fluxes with individual timesteps (dtp non-NULL): the face (i, j)

@@ -745,6 +745,46 @@ def test_predictor_compresses_with_the_velocity_divergence(orc):
     assert np.abs(F[:, 1]).max() < 1e-13 * vscale and np.abs(F[:, 4]).max() < 1e-13 * vscale
 
 
+def test_rung_predictor_advances_each_side_over_its_own_time(orc):
+    """Individual timesteps (§2.3.4): a face exchanges over dt_ij =
+    min(dt_i, dt_j) and each side is predicted from the state its particle
+    last took, over the time since then plus dt_ij / 2.  With uniform density
+    and pressure and a linear velocity v = K x, Euler's equations give each
+    side's state after a time t as rho (1 - t tr K) and p (1 - t gamma tr K)
+    (first order, as the predictor), whatever the other side's time."""
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1) - 0.5
+    K = np.array([[0.3, 0.1, -0.05], [0.02, -0.1, 0.04], [0.0, 0.07, 0.2]])
+    v = x @ K.T
+    N = x.shape[0]
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, np.full(N, 2.5), v, np.full(N, 3.0))
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    grad, alpha, _ = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    pairs = orc.flux_pairs(w["x"], w["y"], w["z"], w["L"], h)
+    rng = np.random.default_rng(11)
+    dt0 = 0.02
+    dtp = dt0 * 2.0 ** -rng.integers(0, 3, N)          # rungs 0, 1, 2
+    toff = dtp * rng.integers(0, 4, N) / 4.0           # time since the state was taken
+    _, st, F = orc.fluxes_rung(cfg, w["x"], w["y"], w["z"], w["L"], h, om, B6, prims, grad,
+                               alpha, dtp, toff, pairs)
+    inner = np.all(np.abs(x) < 0.5 - h.max() - 1e-3, axis=1)
+    sel = inner[pairs[:, 0]] & inner[pairs[:, 1]]
+    assert sel.sum() > 1000
+    i, j = pairs[sel, 0], pairs[sel, 1]
+    F = F[sel]
+    dtij = np.minimum(dtp[i], dtp[j])
+    tl, tr = toff[i] + 0.5 * dtij, toff[j] + 0.5 * dtij
+    assert np.unique(np.round(tl / dt0, 6)).size >= 4   # several distinct side times
+    trK = np.trace(K)
+    assert np.abs(F[:, 0] - 2.5 * (1.0 - tl * trK)).max() < 1e-13 * 2.5
+    assert np.abs(F[:, 3] - 2.5 * (1.0 - tr * trK)).max() < 1e-13 * 2.5
+    assert np.abs(F[:, 2] - 3.0 * (1.0 - tl * cfg.gamma * trK)).max() < 1e-13 * 3.0
+    assert np.abs(F[:, 5] - 3.0 * (1.0 - tr * cfg.gamma * trK)).max() < 1e-13 * 3.0
+
+
 # --------------------------------------------------------------------------
 # Sedov-Taylor blast (§3.1): shock radius of the self-similar solution
 # --------------------------------------------------------------------------
