@@ -473,6 +473,37 @@ def test_hllc_consistency(orc):
     assert F[0] == pytest.approx(1.0 * 0.2, rel=1e-14)
 
 
+def _phys_flux(rho, u, p, w, n, g):
+    E = p / (g - 1) + 0.5 * rho * (u * u + w @ w)
+    return np.concatenate([[rho * u], rho * u * (u * n + w) + p * n, [u * (E + p)]])
+
+
+def test_hllc_upwinds_supersonic_flow_and_is_mirror_symmetric(orc):
+    """Toro (2009) ch. 10, the solver §2.3.3 allows besides the exact one:
+    when every wave moves right (left) the flux at x/t = 0 is the left
+    (right) state's physical flux; and the problem mirrored through the
+    face (sides swapped, normal velocities negated) has the mirrored flux:
+    mass, energy and tangential momentum flux negated, the normal momentum
+    flux, p* unchanged, S* negated."""
+    g = 1.4
+    n = np.array([0.6, 0.8, 0.0])
+    wl, wr = np.array([0.8, -0.6, 0.5]) * 0.3, np.array([-0.4, 0.3, 0.2]) * 0.2
+    rl, pl, rr, pr = 1.0, 1.0, 0.6, 0.7
+    for ul, ur, side in ((5.0, 6.0, -1), (-6.0, -5.5, 1)):
+        F, ps, ss = orc.hllc(rl, ul, pl, wl, rr, ur, pr, wr, n, g)
+        ref = _phys_flux(rl, ul, pl, wl, n, g) if side < 0 else _phys_flux(rr, ur, pr, wr, n, g)
+        assert np.allclose(F, ref, rtol=1e-13, atol=1e-13)
+    for (ul, ur) in ((0.3, -0.2), (-0.5, 1.1), (2.0, 1.0), (0.0, 0.0)):
+        F, ps, ss = orc.hllc(rl, ul, pl, wl, rr, ur, pr, wr, n, g)
+        G, ps2, ss2 = orc.hllc(rr, -ur, pr, wr, rl, -ul, pl, wl, n, g)
+        assert ps2 == pytest.approx(ps, rel=1e-13) and ss2 == pytest.approx(-ss, rel=1e-13, abs=1e-14)
+        scale = np.abs(F).max()
+        assert abs(G[0] + F[0]) < 1e-13 * scale and abs(G[4] + F[4]) < 1e-13 * scale
+        Fm, Gm = F[1:4], G[1:4]
+        assert abs(Gm @ n - Fm @ n) < 1e-13 * scale
+        assert np.abs((Gm - (Gm @ n) * n) + (Fm - (Fm @ n) * n)).max() < 1e-13 * scale
+
+
 def test_pair_limiter_bounds(orc):
     rng = np.random.default_rng(3)
     for _ in range(2000):
