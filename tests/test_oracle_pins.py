@@ -272,6 +272,32 @@ def test_limiter_bounds(orc):
             assert ext.min() >= 2.0 * (fmin - prims[f][i]) - 1e-12
 
 
+@pytest.mark.parametrize("k", [0.3, -0.3, 0.0])
+def test_signal_velocity_closed_form(orc, k):
+    """The signal velocity of the CFL condition (Eqs. 31-32): at rest or in
+    a uniform expansion every pair carries 2c; a uniform compression
+    v = -k x adds the approach speed k r_ij, largest for the farthest
+    neighbour within h (found by brute force)."""
+    n = 12
+    w = W.lattice_wave(n, jitter=0.0)
+    cfg = orc.config()
+    x = np.stack([w["x"], w["y"], w["z"]], 1) - 0.5
+    N = x.shape[0]
+    v = -k * x
+    h, om, m, P, E, U = _state_with_primitives(orc, cfg, w, np.full(N, 1.0), v, np.full(N, 1.0))
+    prims = orc.primitives(cfg, m, P[:, 0], P[:, 1], P[:, 2], E, U, om)
+    B6, E6, nc = orc.matrices(cfg, w["x"], w["y"], w["z"], w["L"], h, om)
+    _, _, vsig = orc.gradients(cfg, w["x"], w["y"], w["z"], w["L"], h, om, prims, B6, nc)
+    c = math.sqrt(cfg.gamma)
+    inner = np.flatnonzero(np.all(np.abs(x) < 0.5 - h.max() - 1e-3, axis=1))
+    assert inner.size > 50
+    for i in inner[::7]:
+        r = np.sqrt(np.sum((x - x[i]) ** 2, 1))
+        rmax = r[(r < h[i]) & (np.arange(N) != i)].max()
+        expect = 2 * c + max(k, 0.0) * rmax
+        assert vsig[i] == pytest.approx(expect, rel=1e-12)
+
+
 @pytest.mark.parametrize("frac,beta_min,beta_max,ncrit",
                          [(0.9, 1.0, 2.0, 100.0), (-0.8, 1.0, 2.0, 100.0), (0.7, 1.0, 1.0, 100.0),
                           (0.2, 1.0, 2.0, 100.0), (0.9, 0.3, 2.0, 0.5), (0.9, 0.8, 2.0, 0.5)])
