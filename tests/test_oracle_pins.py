@@ -677,6 +677,30 @@ def test_uniform_state_is_stationary(orc):
 
 
 @pytest.mark.parametrize("scheme", ["mfv", "mfm"])
+def test_uniform_flow_is_carried_unchanged(orc, scheme):
+    """A uniform state moving with v0 (Galilean invariance of §2.3.4's
+    update): nothing is exchanged, every particle drifts by v0 dt (modulo
+    the periodic box) and keeps its mass, momentum and energy."""
+    w = dict(W.lattice_wave(8, jitter=0.0))
+    N = w["x"].size
+    v0 = np.array([0.7, -0.4, 0.25])
+    w["m"] = np.full(N, 1.0 / N)
+    w["px"], w["py"], w["pz"] = (w["m"] * v0[a] for a in range(3))
+    w["U"] = w["m"] * 1.0 / (w["gamma"] - 1)
+    w["E"] = w["U"] + 0.5 * w["m"] * (v0 @ v0)
+    cfg = orc.config(scheme=scheme)
+    dt = 1e-3
+    s, out, info = orc.step(cfg, w, dt)
+    assert np.abs(out["dQ"][:, :5]).max() < 1e-15
+    for a, k in enumerate("xyz"):
+        moved = (w[k] + v0[a] * dt) % 1.0
+        dx = (s[k] - moved + 0.5) % 1.0 - 0.5
+        assert np.abs(dx).max() < 1e-15
+    for k in ("m", "px", "py", "pz", "E"):
+        assert np.allclose(s[k], w[k], rtol=1e-13, atol=0.0)
+
+
+@pytest.mark.parametrize("scheme", ["mfv", "mfm"])
 def test_sod_tube_follows_exact_solution(orc, scheme):
     """Multi-step 3D Sod tube (§3.1.2 setup family; gamma = 5/3, rho_R = 1/8):
     the density near the x = 2 interface approaches the exact Riemann
