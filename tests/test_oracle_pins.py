@@ -67,6 +67,29 @@ def test_neighbours_match_kdtree_and_brute_force(orc, L):
         assert i in got  # self included
 
 
+@pytest.mark.parametrize("L", [(1.0, 1.0, 1.0), (1.0, 0.5, 2.0)])
+def test_flux_pairs_match_brute_force(orc, L):
+    """The faces of §2.3.3: every unordered pair {i, j} with r_ij < max(h_i, h_j)
+    (periodic minimum image) exactly once, against an O(N^2) enumeration;
+    with unequal h most pairs are seen from one side only."""
+    rng = np.random.default_rng(13)
+    n = 400
+    L = np.array(L)
+    pos = rng.random((n, 3)) * L
+    h = rng.uniform(0.05, 0.25, n) * L.min()
+    pairs = orc.flux_pairs(pos[:, 0], pos[:, 1], pos[:, 2], L, h)
+    got = {(min(a, b), max(a, b)) for a, b in pairs.tolist()}
+    assert len(got) == pairs.shape[0]             # each pair once
+    d = pos[None, :, :] - pos[:, None, :]
+    d -= np.round(d / L) * L
+    r = np.sqrt(np.sum(d * d, 2))
+    i, j = np.nonzero(np.triu(r < np.maximum(h[:, None], h[None, :]), 1))
+    ref = set(zip(i.tolist(), j.tolist()))
+    assert got == ref
+    one_sided = np.sum((r[i, j] < np.maximum(h[i], h[j])) & (r[i, j] >= np.minimum(h[i], h[j])))
+    assert one_sided > 0.2 * len(ref)
+
+
 # --------------------------------------------------------------------------
 # density and smoothing length (§2.3.2, §2.3.5 Eq. 18)
 # --------------------------------------------------------------------------
