@@ -1,8 +1,8 @@
 """The bench's reference arm (the FP64 oracle on the host cores) runs
 without a GPU: its JSON line carries the contract's keys, and the oracle
 sampler's pair count and rate are consistent; the per-face work the
-roofline uses equals a fresh count by the oracle's counting build.  CPU
-only."""
+roofline uses equals a fresh count by the oracle's counting build, and its
+DRAM traffic per face the committed flux-kernel captures.  CPU only."""
 import json
 import os
 import subprocess
@@ -53,3 +53,21 @@ def test_face_work_constants_match_a_fresh_count():
     # the counts measure real work: a Newton iteration evaluates both sides'
     # pressure functions (two powers at least when a side rarefies)
     assert 30 < t["sod"]["flop_per_iter"] < 80 and t["wave"]["flop_per_iter"] == 0.0
+
+
+def test_traffic_constants_match_the_committed_captures():
+    """The roofline's DRAM traffic per face is the one the committed ncu
+    summaries of the flux kernel state (read + write over the faces of the
+    captured launch), workload by workload."""
+    import re
+    sys.path.insert(0, ROOT)
+    import bench
+    files = {"sod": "k_fluxes_sod3d_n60.md", "lognormal": "k_fluxes_lognormal_2097152.md"}
+    assert set(files) == set(bench.FLUX_TRAFFIC_BYTES_PER_FACE)
+    for kind, name in files.items():
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        rd = float(re.search(r"dram__bytes_read\.sum`\) \| ([0-9.]+) Mbyte", text).group(1))
+        wr = float(re.search(r"dram__bytes_write\.sum`\) \| ([0-9.]+) Mbyte", text).group(1))
+        faces = int(re.search(r"MB / ([0-9,]+) = ", text).group(1).replace(",", ""))
+        per_face = (rd + wr) * 1e6 / faces
+        assert abs(per_face - bench.FLUX_TRAFFIC_BYTES_PER_FACE[kind]) < 0.006, (kind, per_face)
